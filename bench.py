@@ -1,0 +1,297 @@
+"""Benchmark: fwd+bwd render Mpix/s and tracking iterations/s of the differentiable
+3D-Gaussian rasterizer on the 640 x 480, 200k-Gaussian room (plain FP32 attributes).
+
+One step = one full tracking iteration of the hot path on one frame: projection and
+tile binning, per-tile depth sort, front-to-back compositing of colour / depth /
+silhouette with the fused combined loss, reverse compositing, chain rule to the pose,
+FP64 pose reduction and the decoupled Adam update (all CUDA kernels of this library,
+launched from the library's CUDA graph).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Rank 0 prints one JSON line.  With N > 1 (torchrun) every rank tracks its own frame:
+replicas only, weak scaling.  ``--impl reference`` times the FP64 CPU oracle on the
+same workload (bounded samples per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd render Mpix/s & tracking iters/s (640×480, 200k Gauss) vs plain"
+WORKLOAD = "tracking 640x480, 200k room Gaussians, fp32 attributes"
+N_GAUSS = 200_000
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(seed: int = 0):
+    """Synthetic stand-in for a TUM RGB-D tracking frame (the dataset is not available):
+    the room scene, the ground-truth camera, a start pose 2 deg / 5 cm away, an RGB-D
+    frame ray-cast from the ground truth and a depth prior (x (1 + N(0, 0.02)), 5% holes)."""
+    from paper_2408_05635_gb300 import scenes
+    g = scenes.room_scene(N_GAUSS, seed=seed)
+    cam = scenes.TUM_CAM
+    gt = scenes.tracking_gt_pose()
+    rng = np.random.default_rng(seed + 1)
+    start = scenes.perturb_pose(gt, rng, 2.0, 0.05)
+    rgb, depth = scenes.raycast_room(gt, cam, seed=seed)
+    prior = scenes.prior_from_depth(depth, rng, 0.02, 0.05)
+    return g, cam, gt, start, rgb, depth, prior
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(g, cam, start, rgb, depth, prior, budget_s: float):
+    """The FP64 oracle's tracking iteration (render, loss, backward, Adam step) on the
+    host cores, repeated on the same frame until `budget_s` seconds have elapsed."""
+    import oracle
+    p = oracle.Params()
+    sc = oracle.Scene(*g.arrays())
+    oc = oracle.camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    pose, state = np.asarray(start, np.float64).copy(), np.zeros(16)
+    iters, t0 = 0, time.perf_counter()
+    while True:
+        r = oracle.render(sc, oc, pose, p)
+        L = oracle.loss(oc, p, r["rgb"], r["depth"], r["sil"], rgb, depth, prior)
+        b = oracle.backward(sc, oc, pose, p, L["d_rgb"], L["d_depth"], L["d_sil"])
+        pose, state = oracle.adam_step(pose, state, b["pose6"], p)
+        iters += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    its = iters / el
+    return {"value": its * cam.width * cam.height / 1e6, "unit": "Mpix/s", "iters_per_s": its,
+            "cores": oracle.num_threads(p), "kind": "oracle",
+            "sample": f"{iters} full tracking iterations of the 640x480 / 200k workload in {el:.1f} s"}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    g, cam, gt, start, rgb, depth, prior = workload()
+    import oracle
+    p = oracle.Params()
+    sc = oracle.Scene(*g.arrays())
+    oc = oracle.camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    H, W = cam.height, cam.width
+    # each step: one oracle tracking iteration on a 64-row band of the frame (bounded sample)
+    band = 64
+    times = []
+    pose, state = np.asarray(start, np.float64).copy(), np.zeros(16)
+    for it in range(a.warmup + a.steps):
+        y0 = (it * band) % H
+        sub = oracle.camera(cam.fx, cam.fy, cam.cx, cam.cy - y0, W, band)
+        sl = slice(y0, y0 + band)
+        t0 = time.perf_counter()
+        r = oracle.render(sc, sub, pose, p)
+        L = oracle.loss(sub, p, r["rgb"], r["depth"], r["sil"], rgb[:, sl], depth[sl], prior[sl])
+        b = oracle.backward(sc, sub, pose, p, L["d_rgb"], L["d_depth"], L["d_sil"])
+        pose, state = oracle.adam_step(pose, state, b["pose6"], p)
+        dt = time.perf_counter() - t0
+        if it >= a.warmup:
+            times.append(dt)
+    total = sum(times)
+    mpix = a.steps * W * band / total / 1e6
+    sample = f"each step: one full oracle tracking iteration on a {W}x{band} band of the 640x480 / 200k frame"
+    line = {"impl": "reference", "metric": METRIC, "value": mpix, "unit": "Mpix/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": oracle.num_threads(p), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": mpix, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if a.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    import torch
+    import torch.distributed as dist
+    from paper_2408_05635_gb300 import gs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    g, cam, gt_pose, start, rgb, depth, prior = workload(seed=rank)
+    R = gs.Rasterizer(gs.Config(), device=dev)
+    gt = gs.GaussianTensors.from_numpy(g, device=dev)
+    poses = torch.tensor(np.asarray(start)[None], dtype=torch.float64, device=dev)
+    prob = R.plan(gt, [cam], poses, margin=1.5)
+    ws, nb = R.workspace(prob)
+    t_rgb = torch.tensor(rgb.reshape(-1), device=dev)
+    t_depth = torch.tensor(depth.reshape(-1), device=dev)
+    t_prior = torch.tensor(prior.reshape(-1), device=dev)
+    targets = gs.gs_targets(t_rgb.data_ptr(), t_depth.data_ptr(), t_prior.data_ptr())
+    adam = torch.zeros(1, 16, dtype=torch.float64, device=dev)
+    loss = torch.zeros(1, 1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        gs.gs_track_step(R.ctx, prob, gt.c(), targets, poses, adam, loss, 1, ws, nb, stream)
+
+    for _ in range(a.warmup):
+        step()
+    R.sync(stream)
+    counts = R.sync(stream)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(a.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    st, c = gs.gs_sync_status(R.ctx, stream)
+    if st:
+        raise SystemExit(f"device reported {gs._STATUS[st]} during the timed steps")
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    pix = cam.width * cam.height
+    iters_per_s = world * a.steps / (ms_max / 1e3)
+    mpix = iters_per_s * pix / 1e6
+
+    # end to end through the public call with host buffers: pinned frame in, pose and loss out
+    h_rgb = torch.tensor(rgb.reshape(-1)).pin_memory()
+    h_depth = torch.tensor(depth.reshape(-1)).pin_memory()
+    h_prior = torch.tensor(prior.reshape(-1)).pin_memory()
+    h_out = torch.empty(8, dtype=torch.float64).pin_memory()
+    e2e_s, e2e_e = [], []
+    for k in range(a.warmup + a.steps):
+        flush.fill_(float(k))
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        t_rgb.copy_(h_rgb, non_blocking=True)
+        t_depth.copy_(h_depth, non_blocking=True)
+        t_prior.copy_(h_prior, non_blocking=True)
+        step()
+        h_out[:7].copy_(poses[0], non_blocking=True)
+        h_out[7:].copy_(loss[0], non_blocking=True)
+        s1.record(stream)
+        if k >= a.warmup:
+            e2e_s.append(s0)
+            e2e_e.append(s1)
+    torch.cuda.synchronize(dev)
+    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e2e_s, e2e_e))
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_mpix = world * a.steps * pix / (float(te.item()) / 1e3) / 1e6
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": mpix, "unit": "Mpix/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (room scene; ray-cast RGB-D frame)",
+            "config": {"workload": WORKLOAD, "width": cam.width, "height": cam.height, "gaussians": N_GAUSS,
+                       "pairs": int(counts.n_pairs), "records": int(counts.n_records),
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "tracking_iters_per_s": iters_per_s,
+            "e2e": {"value": e2e_mpix, "unit": "Mpix/s",
+                    "h2d_bytes_per_step": int(h_rgb.numel() * 4 + h_depth.numel() * 4 + h_prior.numel() * 4),
+                    "d2h_bytes_per_step": 64},
+            "gpu_launches": a.steps * 7,
+            "clocks": clk.summary(),
+        }
+        if world == 1 and not a.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(g, cam, start, rgb, depth, prior, a.cpu_sample_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * gs.h -- C ABI of the GB300 (sm_103a) differentiable 3D-Gaussian rasterizer used by
+ * the tracking and mapping steps of "Visual SLAM with 3D Gaussian Primitives and Depth
+ * Priors Enabling Novel View Synthesis" (arXiv 2408.05635).
+ *
+ * Conventions shared by every entry point
+ *   - Plain C types only.  "device" pointers are CUDA global memory of the current
+ *     device; "host" pointers are ordinary CPU memory read during the call.
+ *   - The caller owns every buffer (inputs, outputs, workspace).  The library owns only
+ *     the opaque context, which holds settings, the bound workspace layout and cached
+ *     CUDA graphs.  The library never allocates device memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue work
+ *     and return without synchronising, except gs_sync_status.
+ *   - Errors are returned as gs_status; gs_last_error(ctx) gives a one-line message.
+ *     Nothing is thrown and nothing aborts.  Conditions only the device can see
+ *     (capacity overflow, an expired bounded wait) are latched in the workspace from
+ *     the start of the last gs_project / gs_track_step (which clear them) and
+ *     reported by gs_sync_status.
+ *   - Images are planar FP32: colour is 3 x H x W, depth and silhouette H x W, pixel
+ *     (u, v) at index v * W + u and sampled at its centre (u, v).  With several views
+ *     the per-view planes are concatenated in view order: view k starts at pixel
+ *     offset P_k = sum_{j<k} W_j H_j (colour at 3 P_k).
+ *   - A pose is 7 doubles [qw, qx, qy, qz, tx, ty, tz]: the world->camera rotation
+ *     R_{c,w} (unit quaternion, renormalised on read) and translation t_{c,w}, so a
+ *     world point X maps to R X + t (Sec. II-A).  Camera axes: x right, y down, z forward.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1, /* a pointer, size or setting is out of range */
+    GS_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in gs_last_error) */
+    GS_ERR_OOM = 3,         /* host memory for the context could not be allocated */
+    GS_ERR_WORKSPACE = 4,   /* workspace missing, too small or misaligned (256 B) */
+    GS_ERR_CAPACITY = 5,    /* device saw more pairs or records than the capacities */
+    GS_ERR_TIMEOUT = 6,     /* a bounded device-side wait expired */
+    GS_ERR_UNSUPPORTED = 7, /* valid request this build does not implement */
+    GS_ERR_STATE = 8        /* call order violated (e.g. gs_forward before gs_project) */
+} gs_status;
+
+/* Storage type of the per-Gaussian attributes other than the means. */
+typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype;
+
+typedef struct gs_ctx gs_ctx;
+
+/* The map: n anisotropic Gaussians (Eq. 1 with the covariance Sigma = R s s^T R^T).
+ * All arrays device, row-major, n rows.  means: float32 n x 3 (world frame, metres);
+ * quats n x 4 (w, x, y, z), any non-zero norm; log_scales n x 3 (scale = exp);
+ * opacity_logits n (opacity o = sigmoid); rgb n x 3.  The last four use dtype_attr. */
+typedef struct {
+    const float *means;
+    const void *quats;
+    const void *log_scales;
+    const void *opacity_logits;
+    const void *rgb;
+    int32_t dtype_attr; /* gs_dtype */
+    int32_t reserved;
+    int64_t n;
+} gs_gaussians;
+
+/* Gradients w.r.t. the raw parameters, FP32 device arrays with the shapes above.
+ * Every call ADDS into them (sum over views); zero them first.  Any may be NULL. */
+typedef struct {
+    float *means;
+    float *quats;
+    float *log_scales;
+    float *opacity_logits;
+    float *rgb;
+} gs_gaussians_grad;
+
+/* Pinhole intrinsics of pi_m (Sec. II-A) and the image size. */
+typedef struct {
+    double fx, fy, cx, cy;
+    int32_t width, height;
+} gs_camera;
+
+/* One RGB-D observation per view (planar FP32, device).  depth 0 = no measurement;
+ * depth_prior may be NULL (no prior term) and 0 marks a hole. */
+typedef struct {
+    const float *rgb;
+    const float *depth;
+    const float *depth_prior;
+} gs_targets;
+
+/* Renderer, loss and pose-optimiser settings.  The paper states none of these values;
+ * gs_default_config fills the readings documented beside each field. */
+typedef struct {
+    int32_t tile_w, tile_h; /* screen tile, 16 x 16 (the only shape this build has)   */
+    float alpha_min;        /* a Gaussian with alpha < alpha_min is skipped (1/255)    */
+    float alpha_max;        /* alpha = min(alpha_max, o G) (0.99)                      */
+    float t_min;            /* stop before the Gaussian that takes T below t_min (1e-4)*/
+    float dilation;         /* eps added to the diagonal of Sigma' in px^2 (0)         */
+    float z_near;           /* Gaussians with camera depth <= z_near are dropped (0.2) */
+    float sil_thresh;       /* loss mask: S > sil_thresh and depth > 0 (0.99)          */
+    float w_rgb, w_depth, w_vis, w_prior; /* loss weights (0.5, 1, 0.1, 0.5)           */
+    double lr_rot, lr_trans;              /* Adam step sizes, rad and m (2e-3, 2e-3)   */
+    double beta1, beta2, eps;             /* Adam moments (0.9, 0.999, 1e-8)           */
+} gs_config;
+
+/* Sizes that fix the workspace layout. */
+typedef struct {
+    int64_t n_gaussians;       /* upper bound on gs_gaussians.n of the calls that use it */
+    int32_t n_views;           /* V >= 1 views rendered together                         */
+    int32_t reserved;
+    const gs_camera *cameras;  /* host array of n_views cameras                          */
+    int64_t pair_capacity;     /* max (Gaussian, tile) pairs summed over views (< 2^32)  */
+    int64_t record_capacity;   /* max visible (Gaussian, view) pairs; 0 = n_gaussians*V  */
+} gs_problem;
+
+/* Counters read back by gs_sync_status. */
+typedef struct {
+    int64_t n_records; /* visible (Gaussian, view) pairs of the last projection        */
+    int64_t n_pairs;   /* (Gaussian, tile) pairs of the last projection                */
+    uint32_t err_flags;/* bit 0 record overflow, bit 1 pair overflow, bit 2 timeout    */
+    uint32_t reserved;
+} gs_counts;
+
+/* ------------------------------------------------------------------ context */
+
+/* Fill cfg with the default readings listed in gs_config. */
+void gs_default_config(gs_config *cfg);
+
+/* Create a context with a copy of cfg (NULL = defaults).  *out receives the handle.
+ * Errors: GS_ERR_INVALID_ARG (bad setting or NULL out), GS_ERR_OOM, GS_ERR_CUDA. */
+gs_status gs_create(gs_ctx **out, const gs_config *cfg);
+
+/* Destroy a context (NULL is allowed).  Waits for nothing: the caller must make sure no
+ * work enqueued through it is still running if it also frees the workspace. */
+gs_status gs_destroy(gs_ctx *ctx);
+
+/* Message of the last error on this context ("" if none); valid until the next call. */
+const char *gs_last_error(const gs_ctx *ctx);
+
+/* Name of a status code. */
+const char *gs_status_string(gs_status s);
+
+/* Bytes of device workspace the calls below need for `prob`.  Errors: INVALID_ARG
+ * (NULL argument, n_views < 1, a camera with a non-positive size or focal length,
+ * n_gaussians * n_views >= 2^32, pair_capacity outside [1, 2^32)). */
+gs_status gs_workspace_size(const gs_ctx *ctx, const gs_problem *prob, size_t *bytes);
+
+/* ------------------------------------------------------------------ the hot path */
+
+/* Projection and tile binning (forward half of Sec. II-C / Sec. III-B rendering).
+ * For every view k and Gaussian i: camera-frame mean R_k x_i + t_k; drop it when its
+ * depth is <= z_near; Sigma = Rg diag(s^2) Rg^T; Sigma' = J W Sigma W^T J^T (+ dilation);
+ * mu' = pi_m; o = sigmoid(logit); the opacity-aware support o exp(-d^2/2) >= alpha_min;
+ * then one (tile, depth) entry for every 16 x 16 tile the support ellipse meets.
+ * poses: device, n_views x 7 doubles, read on the device when the kernels run.
+ * ws: device workspace of at least gs_workspace_size bytes, 256-byte aligned; it
+ * holds the projected state that gs_forward / gs_backward consume.  The Gaussian
+ * arrays, poses and workspace must stay valid and unchanged until the matching
+ * gs_backward has run.  Errors: INVALID_ARG, WORKSPACE, CUDA. */
+gs_status gs_project(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const double *poses, void *ws,
+                     size_t ws_bytes, void *stream);
+
+/* Depth sort per tile and front-to-back compositing of colour (Eq. 2), depth (Eq. 3,
+ * d_i = camera-frame depth of the mean) and silhouette (Eq. 4) of the views projected
+ * by the last gs_project.  rgb / depth / sil: device outputs (planar, concatenated
+ * views), each may be NULL.  With targets != NULL the combined loss of Sec. III-B
+ *   L = w_rgb sum_M |C - C*|_1 + w_depth sum_M |D - D*| + w_vis sum_{D*>0} (1 - S)
+ *     + w_prior sum_{M, prior>0} |D - prior|,   M = {S > sil_thresh, D* > 0}
+ * is evaluated in the same kernel: loss (device, n_views doubles, may be NULL)
+ * receives it per view and its gradient w.r.t. the rendered maps is kept in the
+ * workspace for gs_backward.  Errors: STATE (no projection bound), CUDA. */
+gs_status gs_forward(gs_ctx *ctx, const gs_targets *targets, float *rgb, float *depth, float *sil, double *loss,
+                     void *stream);
+
+/* Reverse compositing and chain rule (the differentiable rendering of Sec. III-B and
+ * Sec. III-C).  Upstream gradients: either all three of d_rgb / d_depth / d_sil
+ * (device, planar like gs_forward's outputs) or all three NULL to use the gradient of
+ * the loss evaluated by the last gs_forward.  grads (NULL = none) receive, ADDED, the
+ * gradients w.r.t. every Gaussian parameter summed over views.  pose_grad (device,
+ * n_views x 6 doubles, may be NULL) is OVERWRITTEN with (d theta, d t) per view, reduced
+ * in FP64: theta turns the camera about its own centre (camera-frame points
+ * x_c <- Exp(theta) x_c) and t shifts them (x_c <- x_c + t).
+ * Errors: INVALID_ARG (partly NULL upstream), STATE, CUDA. */
+gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, const float *d_sil,
+                      gs_gaussians_grad *grads, double *pose_grad, void *stream);
+
+/* `iters` tracking iterations (Sec. III-B): each renders every view at its current
+ * pose, evaluates the combined loss against `targets`, back-propagates to the pose
+ * only and applies the decoupled rotation / translation Adam step in FP64 on the
+ * device: separate moments for theta and t; the camera turns about its own centre,
+ * R <- Exp(-step_theta) R (quaternion renormalised) and t <- Exp(-step_theta) t, then
+ * moves, t <- t - step_t.  poses (device, n_views x 7) is updated in place;
+ * adam_state (device, n_views x 16 doubles: m_rot 3, v_rot 3, m_t 3, v_t 3, step
+ * count, 3 unused; zero it to start) carries the moments; loss_hist (device,
+ * iters x n_views doubles, may be NULL) receives the loss before each update.  The
+ * iterations are replayed from a CUDA graph that the context builds once per
+ * argument set; no host synchronisation, no allocation.
+ * Errors: INVALID_ARG (iters < 1 or NULL), WORKSPACE, CUDA. */
+gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const gs_targets *targets,
+                        double *poses, double *adam_state, double *loss_hist, int32_t iters, void *ws,
+                        size_t ws_bytes, void *stream);
+
+/* Synchronise `stream`, read the device counters of the bound workspace into counts
+ * (may be NULL) and clear the latched flags.  Returns CAPACITY or TIMEOUT when the
+ * device latched one since the last call (results of that call are invalid), STATE
+ * when no workspace is bound, CUDA on a runtime error. */
+gs_status gs_sync_status(gs_ctx *ctx, void *stream, gs_counts *counts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

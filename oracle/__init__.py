@@ -50,7 +50,7 @@ class _Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_double) for name in (
         "alpha_min", "alpha_max", "t_min", "dilation", "z_near", "sil_thresh",
         "w_rgb", "w_depth", "w_vis", "w_prior", "beta1", "beta2", "eps", "lr_rot", "lr_trans",
-        "amb_alpha", "amb_t", "amb_sil", "amb_depth", "amb_resid")] + [
+        "amb_alpha", "amb_t", "amb_sil", "amb_resid")] + [
         ("brute_force", ctypes.c_int32), ("n_threads", ctypes.c_int32)]
 
 
@@ -87,7 +87,6 @@ class Params:
     amb_alpha: float = 2e-4
     amb_t: float = 2e-4
     amb_sil: float = 1e-5
-    amb_depth: float = 2e-6
     amb_resid: float = 2e-5
     brute_force: bool = False
     n_threads: int = 0
@@ -237,7 +236,8 @@ def backward(scene: Scene, cam: Camera, pose, params: Params, d_rgb, d_depth, d_
 
     Returns grads (n x 14: means 3, quats 4, log_scales 3, logit 1, rgb 3), screen
     (n x 10: d mu' 2, d conic 3, d opacity, d rgb 3, d depth) and pose6 = (d theta, d t)
-    for the left perturbation R <- Exp(theta) R."""
+    for the camera turning about its centre (x_c <- Exp(theta) x_c) and shifting
+    (x_c <- x_c + t)."""
     lib = _load()
     H, W = cam.height, cam.width
     d_rgb, d_depth, d_sil = _f64(d_rgb, (3, H, W)), _f64(d_depth, (H, W)), _f64(d_sil, (H, W))

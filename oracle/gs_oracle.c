@@ -19,9 +19,12 @@
  *   3. The combined tracking loss of Sec. III-B (photometric + depth + visibility)
  *      plus the depth-prior regulariser (Sec. I contributions, Sec. V).
  *   4. Hand-derived gradients of that loss w.r.t. every Gaussian parameter and the
- *      camera pose (left perturbation R <- Exp(dtheta) R, translation t).
+ *      camera pose, as two decoupled blocks: a rotation of the camera about its own
+ *      centre (camera-frame points x_c <- Exp(theta) x_c) and a translation
+ *      (x_c <- x_c + t).
  *   5. The decoupled rotation / translation update (Sec. III-B): one Adam state per
- *      block, rotation applied on the left as Exp(-step) R.
+ *      block; R <- Exp(-step) R and t <- Exp(-step) t (the camera centre stays), then
+ *      t <- t - step_t.
  *
  * Readings where the paper is silent (all passed in og_params, none hard-wired):
  *   alpha = min(alpha_max, f_i(p)); a Gaussian with alpha < alpha_min is skipped; the
@@ -36,11 +39,14 @@
  * has alpha < alpha_min there, so skipping it changes nothing).  A test checks the two
  * agree bit for bit.
  *
+ * Depth order: the order of Eqs. 2-4 and the near-plane test are decided on an
+ * exactly specified FP32 depth key (depth_key below), the precision of the GPU kernels,
+ * so both implementations sort identically; all arithmetic stays FP64.
+ *
  * Ambiguity mask: where FP32 and FP64 may legitimately take a different discrete
- * decision (alpha near alpha_min or alpha_max, transmittance near t_min, two
- * contributing depths almost equal, a mean near the near plane, silhouette near the
- * loss threshold, an L1 residual near zero) the pixel is flagged so that parity tests
- * compare only unambiguous pixels.
+ * decision (alpha near alpha_min or alpha_max, transmittance near t_min, silhouette
+ * near the loss threshold, an L1 residual near zero) the pixel is flagged so that
+ * parity tests compare only unambiguous pixels.
  */
 #include <math.h>
 #include <stdint.h>
@@ -63,7 +69,7 @@ typedef struct {
     double alpha_min, alpha_max, t_min, dilation, z_near, sil_thresh;
     double w_rgb, w_depth, w_vis, w_prior;
     double beta1, beta2, eps, lr_rot, lr_trans;
-    double amb_alpha, amb_t, amb_sil, amb_depth, amb_resid;
+    double amb_alpha, amb_t, amb_sil, amb_resid;
     int32_t brute_force, n_threads;
 } og_params;
 
@@ -78,7 +84,7 @@ typedef struct {
 
 typedef struct {
     int cand;          /* survives the near plane and has det(Sigma') > 0 */
-    int ghost;         /* just in front of the near plane: only flags ambiguity */
+    float zkey;        /* FP32 depth key that orders the Gaussians (see depth_key) */
     int onimage;       /* opacity-aware bounding box meets the image */
     double xc[3];      /* camera-frame mean */
     double mu[2];      /* pixel-space mean */
@@ -146,6 +152,38 @@ static void pose_unpack(const double pose[7], double R[9], double t[3], double q
     t[2] = pose[6];
 }
 
+/* The front-to-back order of Eqs. 2-4 is a discrete decision taken by floating point,
+ * so it is taken in the precision of the GPU kernels, on an exactly specified FP32 key:
+ * the pose rotation is formed in FP64 from the quaternion scaled by 1/sqrt(|q|^2) (each
+ * operation rounded, no contraction), rounded to FP32, and the camera depth of mean m is
+ * fmaf(R20, m0, fmaf(R21, m1, fmaf(R22, m2, t2))) in FP32.  The near-plane test uses the
+ * same key.  Everything else (mu', Sigma', the depth d_i of Eq. 3) stays FP64. */
+static void pose_rot_f32(const double pose[7], float Rf[9], float tf[3]) {
+    double w = pose[0], x = pose[1], y = pose[2], z = pose[3];
+    const double inv = 1.0 / sqrt(((w * w + x * x) + y * y) + z * z);
+    w *= inv;
+    x *= inv;
+    y *= inv;
+    z *= inv;
+    Rf[0] = (float)(1.0 - 2.0 * (y * y + z * z));
+    Rf[1] = (float)(2.0 * (x * y - w * z));
+    Rf[2] = (float)(2.0 * (x * z + w * y));
+    Rf[3] = (float)(2.0 * (x * y + w * z));
+    Rf[4] = (float)(1.0 - 2.0 * (x * x + z * z));
+    Rf[5] = (float)(2.0 * (y * z - w * x));
+    Rf[6] = (float)(2.0 * (x * z - w * y));
+    Rf[7] = (float)(2.0 * (y * z + w * x));
+    Rf[8] = (float)(1.0 - 2.0 * (x * x + y * y));
+    tf[0] = (float)pose[4];
+    tf[1] = (float)pose[5];
+    tf[2] = (float)pose[6];
+}
+
+static float depth_key(const float Rf[9], const float tf[3], const double m[3]) {
+    const float m0 = (float)m[0], m1 = (float)m[1], m2 = (float)m[2];
+    return fmaf(Rf[6], m0, fmaf(Rf[7], m1, fmaf(Rf[8], m2, tf[2])));
+}
+
 /* ------------------------------------------------------------------ step 1: projection */
 
 /* Everything the backward needs again for one Gaussian, recomputed on demand. */
@@ -187,15 +225,14 @@ static void geom_one(const og_scene *sc, int64_t i, const og_camera *cam, const 
 }
 
 static void project_one(const og_scene *sc, int64_t i, const og_camera *cam, const double R[9], const double t[3],
-                        const og_params *p, og_proj *pr) {
+                        const float Rf[9], const float tf[3], const og_params *p, og_proj *pr) {
     og_geom g;
     memset(pr, 0, sizeof(*pr));
     geom_one(sc, i, cam, R, t, &g);
     for (int k = 0; k < 3; ++k) pr->xc[k] = g.xc[k];
     const double z = g.xc[2];
-    const int in_front = z > p->z_near;
-    pr->ghost = !in_front && z > p->z_near * (1.0 - p->amb_depth);
-    if (!(in_front || pr->ghost) || !(g.qnorm > 0)) return;
+    pr->zkey = depth_key(Rf, tf, sc->means + 3 * i);
+    if (!(pr->zkey > (float)p->z_near) || !(g.qnorm > 0)) return;
     /* Sigma' = J Sigma_c J^T + dilation I */
     double JS[6];
     for (int r = 0; r < 2; ++r)
@@ -213,10 +250,7 @@ static void project_one(const og_scene *sc, int64_t i, const og_camera *cam, con
     S00 += p->dilation;
     S11 += p->dilation;
     const double det = S00 * S11 - S01 * S01;
-    if (!(det > 0)) {
-        pr->ghost = 0;
-        return;
-    }
+    if (!(det > 0)) return;
     pr->cov2[0] = S00;
     pr->cov2[1] = S01;
     pr->cov2[2] = S11;
@@ -227,7 +261,7 @@ static void project_one(const og_scene *sc, int64_t i, const og_camera *cam, con
     pr->mu[0] = cam->fx * g.xc[0] / z + cam->cx;
     pr->mu[1] = cam->fy * g.xc[1] / z + cam->cy;
     pr->o = 1.0 / (1.0 + exp(-sc->logits[i]));
-    pr->cand = in_front;
+    pr->cand = 1;
     /* opacity-aware support: o exp(-d2/2) >= alpha_min  <=>  d2 <= 2 ln(o / alpha_min) */
     if (p->alpha_min > 0) {
         if (pr->o < p->alpha_min) {
@@ -259,7 +293,7 @@ static void project_one(const og_scene *sc, int64_t i, const og_camera *cam, con
 /* ------------------------------------------------------------------ ordering */
 
 typedef struct {
-    double z;
+    float z;
     int64_t id;
 } og_key;
 
@@ -270,15 +304,15 @@ static int key_cmp(const void *a, const void *b) {
     return (x->id > y->id) - (x->id < y->id);
 }
 
-/* Candidates (and near-plane ghosts) in ascending (depth, index) order. */
+/* Candidates in ascending (depth key, index) order. */
 static int64_t sorted_candidates(const og_proj *P, int64_t n, int use_bbox, int64_t **out) {
     og_key *keys = (og_key *)malloc(sizeof(og_key) * (size_t)(n > 0 ? n : 1));
     if (!keys) return -1;
     int64_t m = 0;
     for (int64_t i = 0; i < n; ++i) {
-        if (!(P[i].cand || P[i].ghost)) continue;
+        if (!P[i].cand) continue;
         if (use_bbox && !P[i].onimage) continue;
-        keys[m].z = P[i].xc[2];
+        keys[m].z = P[i].zkey;
         keys[m].id = i;
         ++m;
     }
@@ -336,8 +370,6 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
     double T = 1.0, C0 = 0, C1 = 0, C2 = 0, D = 0, S = 0;
     int64_t nc = 0;
     int a = 0;
-    int have_prev = 0;
-    double z_prev = 0;
     for (int64_t k = 0; k < nlist; ++k) {
         const int64_t gi = list[k];
         const og_proj *pr = &P[gi];
@@ -348,15 +380,10 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
         const double araw = pr->o * G;
         if (fabs(araw - p->alpha_min) <= p->amb_alpha * p->alpha_min) a = 1;
         if (araw < p->alpha_min) continue;
-        if (pr->ghost) { /* a Gaussian at the near plane: FP32 may keep it */
-            a = 1;
-            continue;
-        }
         const int clamped = araw >= p->alpha_max;
         const double alpha = clamped ? p->alpha_max : araw;
         if (fabs(araw - p->alpha_max) <= p->amb_alpha * p->alpha_max) a = 1;
         const double z = pr->xc[2];
-        if (have_prev && fabs(z - z_prev) <= p->amb_depth * z) a = 1;
         const double Tn = T * (1.0 - alpha);
         if (fabs(Tn - p->t_min) <= p->amb_t * p->t_min) a = 1;
         if (Tn < p->t_min) break;
@@ -376,8 +403,6 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
         }
         ++nc;
         T = Tn;
-        z_prev = z;
-        have_prev = 1;
     }
     out5[0] = C0;
     out5[1] = C1;
@@ -411,10 +436,12 @@ static int frame_setup(const og_scene *sc, const og_camera *cam, const double po
     memset(f, 0, sizeof(*f));
     if (!sc || !cam || !pose || !p || sc->n < 0 || cam->width <= 0 || cam->height <= 0) return OG_ERR_ARG;
     double R[9], t[3], qn[4];
+    float Rf[9], tf[3];
     pose_unpack(pose, R, t, qn);
+    pose_rot_f32(pose, Rf, tf);
     f->P = (og_proj *)malloc(sizeof(og_proj) * (size_t)(sc->n > 0 ? sc->n : 1));
     if (!f->P) return OG_ERR_OOM;
-    for (int64_t i = 0; i < sc->n; ++i) project_one(sc, i, cam, R, t, p, &f->P[i]);
+    for (int64_t i = 0; i < sc->n; ++i) project_one(sc, i, cam, R, t, Rf, tf, p, &f->P[i]);
     f->use_bbox = !p->brute_force;
     f->m = sorted_candidates(f->P, sc->n, f->use_bbox, &f->order);
     if (f->m < 0) {
@@ -456,10 +483,12 @@ static void set_threads(const og_params *p) {
 int og_project(const og_scene *sc, const og_camera *cam, const double pose[7], const og_params *p, double *out16) {
     if (!sc || !cam || !pose || !p || !out16) return OG_ERR_ARG;
     double R[9], t[3], qn[4];
+    float Rf[9], tf[3];
     pose_unpack(pose, R, t, qn);
+    pose_rot_f32(pose, Rf, tf);
     for (int64_t i = 0; i < sc->n; ++i) {
         og_proj pr;
-        project_one(sc, i, cam, R, t, p, &pr);
+        project_one(sc, i, cam, R, t, Rf, tf, p, &pr);
         double *o = out16 + 16 * i;
         o[0] = (pr.cand && pr.onimage) ? 1.0 : 0.0;
         o[1] = pr.mu[0];
@@ -641,7 +670,7 @@ static void backward_pixel(int px, int py, const og_contrib *cb, int64_t nc, con
 
 /* Chain one Gaussian's screen-space gradient to its parameters and to the pose.
  * grads14 = (means 3, quats 4, log_scales 3, logit 1, rgb 3).  pose6 += (d theta, d t)
- * for the left perturbation R <- Exp(theta) R and the translation t. */
+ * for x_c <- Exp(theta) x_c (rotation about the camera centre) and x_c <- x_c + t. */
 static void chain_one(const og_scene *sc, int64_t i, const og_camera *cam, const double R[9], const double t[3],
                       const og_params *p, const double *a, double *g14, double pose6[6]) {
     og_geom g;
@@ -744,11 +773,11 @@ static void chain_one(const og_scene *sc, int64_t i, const og_camera *cam, const
         pose6[3] += dxc[0];
         pose6[4] += dxc[1];
         pose6[5] += dxc[2];
-        /* rotation, mean part: d x_c = theta x (W m) */
-        const double wm[3] = {g.xc[0] - t[0], g.xc[1] - t[1], g.xc[2] - t[2]};
-        pose6[0] += wm[1] * dxc[2] - wm[2] * dxc[1];
-        pose6[1] += wm[2] * dxc[0] - wm[0] * dxc[2];
-        pose6[2] += wm[0] * dxc[1] - wm[1] * dxc[0];
+        /* rotation about the camera centre, mean part: x_c -> Exp(theta) x_c, d x_c = theta x x_c */
+        const double *xc = g.xc;
+        pose6[0] += xc[1] * dxc[2] - xc[2] * dxc[1];
+        pose6[1] += xc[2] * dxc[0] - xc[0] * dxc[2];
+        pose6[2] += xc[0] * dxc[1] - xc[1] * dxc[0];
         /* rotation, covariance part: Sigma_c -> Sigma_c + [th]x Sigma_c - Sigma_c [th]x gives
          * dL = tr((Sigma_c Gc - Gc Sigma_c)[th]x) = -2 m . th with [m]x = Sigma_c Gc - Gc Sigma_c */
         double SG[9], GS[9];
@@ -764,7 +793,8 @@ static void chain_one(const og_scene *sc, int64_t i, const og_camera *cam, const
 
 /* Gradients of sum_p (d_rgb . C + d_depth D + d_sil S) w.r.t. every parameter and the
  * pose, for given upstream maps (planar, like og_render's outputs).  grads14 is n x 14,
- * grads10 is n x 10 (screen-space layout above), pose6 = (d theta, d t); any may be NULL. */
+ * grads10 is n x 10 (screen-space layout above), pose6 = (d theta, d t) for the two
+ * decoupled blocks of chain_one; any may be NULL. */
 int og_backward(const og_scene *sc, const og_camera *cam, const double pose[7], const og_params *p,
                 const double *d_rgb, const double *d_depth, const double *d_sil, double *grads14, double *grads10,
                 double *pose6) {
@@ -858,8 +888,8 @@ static void quat_mul(const double a[4], const double b[4], double c[4]) {
 
 /* Decoupled rotation / translation step.  state (16 doubles) = m_rot 3, v_rot 3, m_t 3,
  * v_t 3, step count, 3 unused.  Each block runs its own bias-corrected Adam; the rotation
- * step is applied on the left (R <- Exp(-d) R, quaternion renormalised) and the
- * translation step as t <- t - d_t. */
+ * step turns the camera about its centre (R <- Exp(-d) R with the quaternion
+ * renormalised, t <- Exp(-d) t) and the translation step moves it (t <- t - d_t). */
 int og_adam_step(double pose[7], double state[16], const double g6[6], const og_params *p) {
     if (!pose || !state || !g6 || !p) return OG_ERR_ARG;
     state[12] += 1.0;
@@ -889,7 +919,11 @@ int og_adam_step(double pose[7], double state[16], const double g6[6], const og_
     quat_mul(dq, q, qn);
     const double nq = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
     for (int j = 0; j < 4; ++j) pose[j] = qn[j] / nq;
-    for (int j = 0; j < 3; ++j) pose[4 + j] -= step[3 + j];
+    /* the camera turns about its own centre: t follows the rotation, then moves */
+    double Rd[9], tr[3];
+    quat_to_rot(dq, Rd);
+    for (int j = 0; j < 3; ++j) tr[j] = Rd[3 * j] * pose[4] + Rd[3 * j + 1] * pose[5] + Rd[3 * j + 2] * pose[6];
+    for (int j = 0; j < 3; ++j) pose[4 + j] = tr[j] - step[3 + j];
     return OG_OK;
 }
 

@@ -1,0 +1,569 @@
+// gs_abi.cu -- the C ABI declared in include/gs.h: context, workspace layout, launch
+// sequencing and the CUDA-graph tracking loop.  No device memory is allocated here:
+// every device buffer, the workspace included, belongs to the caller.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gs_internal.cuh"
+
+using namespace gsk;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t err, hdr, loss, done_view, tile_cnt, zero_end;
+    size_t views, tile_start, cursor, chunk_start, vis_mask, rec, rec_grad, keys, sorted, t_final, n_last,
+        upstream, pose_part, total;
+};
+
+struct Problem {
+    Dims d{};
+    std::vector<ViewInfo> views;
+    Layout lay{};
+};
+
+struct GraphKey {
+    const void *ws = nullptr;
+    size_t ws_bytes = 0;
+    const void *ptrs[12] = {};
+    int64_t n = 0;
+    int dtype = 0;
+    int iters = 0;
+    std::vector<ViewInfo> views;
+    uint32_t rec_cap = 0, pair_cap = 0;
+    bool operator==(const GraphKey &o) const {
+        if (ws != o.ws || ws_bytes != o.ws_bytes || n != o.n || dtype != o.dtype || iters != o.iters ||
+            rec_cap != o.rec_cap || pair_cap != o.pair_cap || views.size() != o.views.size())
+            return false;
+        for (int k = 0; k < 12; ++k)
+            if (ptrs[k] != o.ptrs[k]) return false;
+        return views.empty() || std::memcmp(views.data(), o.views.data(), views.size() * sizeof(ViewInfo)) == 0;
+    }
+};
+
+}  // namespace
+
+struct gs_ctx {
+    gs_config cfg{};
+    Settings s{};
+    std::string err;
+    // state bound by the last gs_project
+    bool bound = false;
+    Problem prob;
+    WsPtrs ws{};
+    void *ws_base = nullptr;
+    GaussPtrs g{};
+    int dtype = 0;
+    const double *poses = nullptr;
+    bool have_loss = false;
+    // tracking graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    GraphKey graph_key;
+};
+
+namespace {
+
+gs_status fail(gs_ctx *ctx, gs_status st, const char *msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+gs_status cuda_fail(gs_ctx *ctx, cudaError_t e, const char *where) {
+    if (ctx) ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+    return GS_ERR_CUDA;
+}
+
+Settings settings_of(const gs_config &c) {
+    Settings s;
+    s.alpha_min = c.alpha_min;
+    s.alpha_max = c.alpha_max;
+    s.t_min = c.t_min;
+    s.dilation = c.dilation;
+    s.z_near = c.z_near;
+    s.sil_thresh = c.sil_thresh;
+    s.w_rgb = c.w_rgb;
+    s.w_depth = c.w_depth;
+    s.w_vis = c.w_vis;
+    s.w_prior = c.w_prior;
+    s.lr_rot = c.lr_rot;
+    s.lr_trans = c.lr_trans;
+    s.beta1 = c.beta1;
+    s.beta2 = c.beta2;
+    s.eps = c.eps;
+    return s;
+}
+
+gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
+    if (!p || !p->cameras) return fail(ctx, GS_ERR_INVALID_ARG, "problem or cameras is NULL");
+    if (p->n_views < 1) return fail(ctx, GS_ERR_INVALID_ARG, "n_views must be >= 1");
+    if (p->n_gaussians < 0) return fail(ctx, GS_ERR_INVALID_ARG, "n_gaussians must be >= 0");
+    const uint64_t nv = (uint64_t)p->n_gaussians * (uint64_t)p->n_views;
+    if (nv >= (1ull << 32)) return fail(ctx, GS_ERR_INVALID_ARG, "n_gaussians * n_views must be < 2^32");
+    if (p->pair_capacity < 1 || p->pair_capacity >= (int64_t)(1ll << 32))
+        return fail(ctx, GS_ERR_INVALID_ARG, "pair_capacity must be in [1, 2^32)");
+    if (p->record_capacity < 0 || (uint64_t)p->record_capacity > nv)
+        return fail(ctx, GS_ERR_INVALID_ARG, "record_capacity must be in [0, n_gaussians * n_views]");
+    Dims d{};
+    d.n = p->n_gaussians;
+    d.V = p->n_views;
+    d.nblk = (int32_t)((p->n_gaussians + kBlock - 1) / kBlock);
+    if (d.nblk == 0) d.nblk = 1;
+    d.rec_cap = (uint32_t)(p->record_capacity ? p->record_capacity : (int64_t)nv);
+    d.pair_cap = (uint32_t)p->pair_capacity;
+    out.views.resize(p->n_views);
+    uint64_t T = 0, P = 0;
+    for (int v = 0; v < p->n_views; ++v) {
+        const gs_camera &c = p->cameras[v];
+        if (c.width < 1 || c.height < 1 || !(c.fx > 0) || !(c.fy > 0))
+            return fail(ctx, GS_ERR_INVALID_ARG, "camera with non-positive size or focal length");
+        ViewInfo vi{};
+        vi.fx = (float)c.fx;
+        vi.fy = (float)c.fy;
+        vi.cx = (float)c.cx;
+        vi.cy = (float)c.cy;
+        vi.width = c.width;
+        vi.height = c.height;
+        vi.tiles_x = (c.width + kTile - 1) / kTile;
+        vi.tiles_y = (c.height + kTile - 1) / kTile;
+        vi.tile_base = (uint32_t)T;
+        vi.pix_base = (uint32_t)P;
+        T += (uint64_t)vi.tiles_x * vi.tiles_y;
+        P += (uint64_t)c.width * c.height;
+        if (T >= (1ull << 31) || 5 * P >= (1ull << 32))
+            return fail(ctx, GS_ERR_INVALID_ARG, "too many pixels or tiles in one call");
+        out.views[v] = vi;
+    }
+    d.T = (uint32_t)T;
+    d.P = (uint32_t)P;
+    out.d = d;
+    Layout &L = out.lay;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    L.err = take(sizeof(uint32_t));
+    // zeroed before every projection: [hdr, zero_end)
+    L.hdr = take(sizeof(DevHeader));
+    L.loss = take(sizeof(double) * d.V);
+    L.done_view = take(sizeof(uint32_t) * d.V);
+    L.tile_cnt = take(sizeof(uint32_t) * (d.T + 1));
+    L.zero_end = o;
+    L.views = take(sizeof(ViewInfo) * d.V);
+    L.tile_start = take(sizeof(uint32_t) * (d.T + 1));
+    L.cursor = take(sizeof(uint32_t) * (d.T + 1));
+    L.chunk_start = take(sizeof(uint32_t) * (size_t)d.V * d.nblk);
+    L.vis_mask = take(sizeof(uint32_t) * (size_t)d.V * d.nblk * kMaskWords);
+    L.rec = take(sizeof(Rec) * (size_t)d.rec_cap);
+    L.rec_grad = take(sizeof(RecGrad) * (size_t)d.rec_cap);
+    L.keys = take(sizeof(unsigned long long) * (size_t)d.pair_cap);
+    L.sorted = take(sizeof(uint32_t) * (size_t)d.pair_cap);
+    L.t_final = take(sizeof(float) * (size_t)d.P);
+    L.n_last = take(sizeof(uint32_t) * (size_t)d.P);
+    L.upstream = take(sizeof(float) * 5 * (size_t)d.P);
+    L.pose_part = take(sizeof(double) * 6 * (size_t)d.V * d.nblk);
+    L.total = o;
+    return GS_OK;
+}
+
+WsPtrs ws_ptrs(void *base, const Layout &L) {
+    char *b = static_cast<char *>(base);
+    WsPtrs w;
+    w.err = reinterpret_cast<uint32_t *>(b + L.err);
+    w.hdr = reinterpret_cast<DevHeader *>(b + L.hdr);
+    w.loss = reinterpret_cast<double *>(b + L.loss);
+    w.done_view = reinterpret_cast<uint32_t *>(b + L.done_view);
+    w.tile_cnt = reinterpret_cast<uint32_t *>(b + L.tile_cnt);
+    w.views = reinterpret_cast<ViewInfo *>(b + L.views);
+    w.tile_start = reinterpret_cast<uint32_t *>(b + L.tile_start);
+    w.cursor = reinterpret_cast<uint32_t *>(b + L.cursor);
+    w.chunk_start = reinterpret_cast<uint32_t *>(b + L.chunk_start);
+    w.vis_mask = reinterpret_cast<uint32_t *>(b + L.vis_mask);
+    w.rec = reinterpret_cast<Rec *>(b + L.rec);
+    w.rec_grad = reinterpret_cast<RecGrad *>(b + L.rec_grad);
+    w.keys = reinterpret_cast<unsigned long long *>(b + L.keys);
+    w.sorted = reinterpret_cast<uint32_t *>(b + L.sorted);
+    w.t_final = reinterpret_cast<float *>(b + L.t_final);
+    w.n_last = reinterpret_cast<uint32_t *>(b + L.n_last);
+    w.upstream = reinterpret_cast<float *>(b + L.upstream);
+    w.pose_part = reinterpret_cast<double *>(b + L.pose_part);
+    return w;
+}
+
+gs_status check_gaussians(gs_ctx *ctx, const gs_gaussians *g, const Problem &pr) {
+    if (!g) return fail(ctx, GS_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n != pr.d.n) return fail(ctx, GS_ERR_INVALID_ARG, "gaussians.n differs from problem.n_gaussians");
+    if (g->dtype_attr != GS_F32 && g->dtype_attr != GS_BF16 && g->dtype_attr != GS_F16)
+        return fail(ctx, GS_ERR_INVALID_ARG, "unknown dtype_attr");
+    if (g->n > 0 && (!g->means || !g->quats || !g->log_scales || !g->opacity_logits || !g->rgb))
+        return fail(ctx, GS_ERR_INVALID_ARG, "a Gaussian attribute pointer is NULL");
+    return GS_OK;
+}
+
+// Write the view table into the workspace (kernel arguments carry it, so the upload is
+// stream-ordered and safe to capture; it is redone on every call because the library
+// cannot tell whether the caller reused the workspace memory for something else).
+cudaError_t upload_views(const Problem &pr, const WsPtrs &w, cudaStream_t st) {
+    return launch_upload_views(pr.views.data(), (int)pr.views.size(), w.views, st);
+}
+
+// One projection pass: clear the counters, project, emit keys.
+// clear_err also resets the latched error flags (the first word of the workspace).
+cudaError_t enqueue_project(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, void *ws, const GaussPtrs &g, int dtype,
+                            const double *poses, bool clear_err, cudaStream_t st) {
+    const size_t from = clear_err ? pr.lay.err : pr.lay.hdr;
+    cudaError_t e = cudaMemsetAsync(static_cast<char *>(ws) + from, 0, pr.lay.zero_end - from, st);
+    if (e != cudaSuccess) return e;
+    ProjectLaunch P;
+    P.ws = w;
+    P.d = pr.d;
+    P.s = ctx->s;
+    P.g = g;
+    P.dtype = dtype;
+    P.poses = poses;
+    if ((e = launch_project(P, st)) != cudaSuccess) return e;
+    return launch_emit(w, pr.d, st);
+}
+
+cudaError_t enqueue_forward(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, const gs_targets *t, float *rgb,
+                            float *depth, float *sil, cudaStream_t st) {
+    cudaError_t e = launch_tile_sort(w, pr.d, st);
+    if (e != cudaSuccess) return e;
+    ForwardLaunch F;
+    F.ws = w;
+    F.d = pr.d;
+    F.s = ctx->s;
+    F.rgb = rgb;
+    F.depth = depth;
+    F.sil = sil;
+    F.t_rgb = t ? t->rgb : nullptr;
+    F.t_depth = t ? t->depth : nullptr;
+    F.t_prior = t ? t->depth_prior : nullptr;
+    return launch_forward(F, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+void gs_default_config(gs_config *c) {
+    if (!c) return;
+    c->tile_w = kTile;
+    c->tile_h = kTile;
+    c->alpha_min = 1.0f / 255.0f;
+    c->alpha_max = 0.99f;
+    c->t_min = 1e-4f;
+    c->dilation = 0.0f;
+    c->z_near = 0.2f;
+    c->sil_thresh = 0.99f;
+    c->w_rgb = 0.5f;
+    c->w_depth = 1.0f;
+    c->w_vis = 0.1f;
+    c->w_prior = 0.5f;
+    c->lr_rot = 2e-3;
+    c->lr_trans = 2e-3;
+    c->beta1 = 0.9;
+    c->beta2 = 0.999;
+    c->eps = 1e-8;
+}
+
+const char *gs_status_string(gs_status s) {
+    switch (s) {
+        case GS_OK: return "GS_OK";
+        case GS_ERR_INVALID_ARG: return "GS_ERR_INVALID_ARG";
+        case GS_ERR_CUDA: return "GS_ERR_CUDA";
+        case GS_ERR_OOM: return "GS_ERR_OOM";
+        case GS_ERR_WORKSPACE: return "GS_ERR_WORKSPACE";
+        case GS_ERR_CAPACITY: return "GS_ERR_CAPACITY";
+        case GS_ERR_TIMEOUT: return "GS_ERR_TIMEOUT";
+        case GS_ERR_UNSUPPORTED: return "GS_ERR_UNSUPPORTED";
+        case GS_ERR_STATE: return "GS_ERR_STATE";
+    }
+    return "GS_ERR_UNKNOWN";
+}
+
+gs_status gs_create(gs_ctx **out, const gs_config *cfg) {
+    if (!out) return GS_ERR_INVALID_ARG;
+    *out = nullptr;
+    gs_config c;
+    gs_default_config(&c);
+    if (cfg) c = *cfg;
+    if (c.tile_w != kTile || c.tile_h != kTile) return GS_ERR_UNSUPPORTED;
+    if (!(c.alpha_min >= 0.f) || !(c.alpha_max > c.alpha_min) || !(c.alpha_max <= 1.f) || !(c.t_min >= 0.f) ||
+        !(c.t_min < 1.f) || !(c.dilation >= 0.f) || !(c.z_near > 0.f) || !(c.lr_rot >= 0) || !(c.lr_trans >= 0) ||
+        !(c.beta1 >= 0 && c.beta1 < 1) || !(c.beta2 >= 0 && c.beta2 < 1) || !(c.eps > 0))
+        return GS_ERR_INVALID_ARG;
+    gs_ctx *ctx = new (std::nothrow) gs_ctx();
+    if (!ctx) return GS_ERR_OOM;
+    ctx->cfg = c;
+    ctx->s = settings_of(c);
+    *out = ctx;
+    return GS_OK;
+}
+
+gs_status gs_destroy(gs_ctx *ctx) {
+    if (!ctx) return GS_OK;
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    delete ctx;
+    return GS_OK;
+}
+
+const char *gs_last_error(const gs_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+gs_status gs_workspace_size(const gs_ctx *ctx, const gs_problem *prob, size_t *bytes) {
+    gs_ctx *c = const_cast<gs_ctx *>(ctx);
+    if (!ctx || !bytes) return fail(c, GS_ERR_INVALID_ARG, "NULL context or output");
+    Problem pr;
+    gs_status st = build_problem(c, prob, pr);
+    if (st != GS_OK) return st;
+    *bytes = pr.lay.total;
+    return GS_OK;
+}
+
+gs_status gs_project(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const double *poses, void *ws,
+                     size_t ws_bytes, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    Problem pr;
+    gs_status st = build_problem(ctx, prob, pr);
+    if (st != GS_OK) return st;
+    if ((st = check_gaussians(ctx, g, pr)) != GS_OK) return st;
+    if (!poses) return fail(ctx, GS_ERR_INVALID_ARG, "poses is NULL");
+    if (!ws || ws_bytes < pr.lay.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+        return fail(ctx, GS_ERR_WORKSPACE, "workspace NULL, smaller than gs_workspace_size or not 256-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const WsPtrs w = ws_ptrs(ws, pr.lay);
+    cudaError_t e = upload_views(pr, w, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "view upload");
+    GaussPtrs gp{g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb};
+    e = enqueue_project(ctx, pr, w, ws, gp, g->dtype_attr, poses, true, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "projection");
+    ctx->bound = true;
+    ctx->prob = std::move(pr);
+    ctx->ws = w;
+    ctx->ws_base = ws;
+    ctx->g = gp;
+    ctx->dtype = g->dtype_attr;
+    ctx->poses = poses;
+    ctx->have_loss = false;
+    return GS_OK;
+}
+
+gs_status gs_forward(gs_ctx *ctx, const gs_targets *targets, float *rgb, float *depth, float *sil, double *loss,
+                     void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->bound) return fail(ctx, GS_ERR_STATE, "gs_forward before gs_project");
+    if (targets && (!targets->rgb || !targets->depth))
+        return fail(ctx, GS_ERR_INVALID_ARG, "targets need rgb and depth");
+    if (loss && !targets) return fail(ctx, GS_ERR_INVALID_ARG, "loss requested without targets");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = enqueue_forward(ctx, ctx->prob, ctx->ws, targets, rgb, depth, sil, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "forward");
+    if (loss) {
+        e = cudaMemcpyAsync(loss, ctx->ws.loss, sizeof(double) * ctx->prob.d.V, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "loss copy");
+    }
+    ctx->have_loss = targets != nullptr;
+    return GS_OK;
+}
+
+gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, const float *d_sil,
+                      gs_gaussians_grad *grads, double *pose_grad, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->bound) return fail(ctx, GS_ERR_STATE, "gs_backward before gs_project");
+    const int given = (d_rgb != nullptr) + (d_depth != nullptr) + (d_sil != nullptr);
+    if (given != 0 && given != 3) return fail(ctx, GS_ERR_INVALID_ARG, "give all three upstream maps or none");
+    if (given == 0 && !ctx->have_loss)
+        return fail(ctx, GS_ERR_STATE, "no upstream maps and no fused loss from gs_forward");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Problem &pr = ctx->prob;
+    BackwardLaunch B;
+    B.ws = ctx->ws;
+    B.d = pr.d;
+    B.s = ctx->s;
+    const uint32_t P = pr.d.P;
+    B.up_rgb = given ? d_rgb : ctx->ws.upstream;
+    B.up_depth = given ? d_depth : ctx->ws.upstream + 3u * P;
+    B.up_sil = given ? d_sil : ctx->ws.upstream + 4u * P;
+    gs_gaussians_grad none{};
+    const gs_gaussians_grad &G = grads ? *grads : none;
+    const bool params = G.means || G.quats || G.log_scales || G.opacity_logits || G.rgb;
+    B.pose_only = !(G.opacity_logits || G.rgb);
+    cudaError_t e = launch_backward(B, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "backward");
+    if (!params && !pose_grad) return GS_OK;
+    BprojLaunch J;
+    J.ws = ctx->ws;
+    J.d = pr.d;
+    J.s = ctx->s;
+    J.g = ctx->g;
+    J.dtype = ctx->dtype;
+    J.poses_in = ctx->poses;
+    J.poses_out = nullptr;
+    J.adam = nullptr;
+    J.pose_grad = pose_grad;
+    J.loss_out = nullptr;
+    J.grads = G;
+    e = launch_bproject(J, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "backward projection");
+    return GS_OK;
+}
+
+gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const gs_targets *targets,
+                        double *poses, double *adam_state, double *loss_hist, int32_t iters, void *ws,
+                        size_t ws_bytes, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (iters < 1) return fail(ctx, GS_ERR_INVALID_ARG, "iters must be >= 1");
+    if (!targets || !targets->rgb || !targets->depth) return fail(ctx, GS_ERR_INVALID_ARG, "targets need rgb and depth");
+    if (!poses || !adam_state) return fail(ctx, GS_ERR_INVALID_ARG, "poses and adam_state are required");
+    Problem pr;
+    gs_status st = build_problem(ctx, prob, pr);
+    if (st != GS_OK) return st;
+    if ((st = check_gaussians(ctx, g, pr)) != GS_OK) return st;
+    if (!ws || ws_bytes < pr.lay.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+        return fail(ctx, GS_ERR_WORKSPACE, "workspace NULL, smaller than gs_workspace_size or not 256-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const WsPtrs w = ws_ptrs(ws, pr.lay);
+    cudaError_t e = upload_views(pr, w, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "view upload");
+    GaussPtrs gp{g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb};
+
+    auto enqueue_all = [&](cudaStream_t q) -> cudaError_t {
+        for (int it = 0; it < iters; ++it) {
+            cudaError_t r = enqueue_project(ctx, pr, w, ws, gp, g->dtype_attr, poses, false, q);
+            if (r != cudaSuccess) return r;
+            if ((r = enqueue_forward(ctx, pr, w, targets, nullptr, nullptr, nullptr, q)) != cudaSuccess) return r;
+            BackwardLaunch B;
+            B.ws = w;
+            B.d = pr.d;
+            B.s = ctx->s;
+            B.up_rgb = w.upstream;
+            B.up_depth = w.upstream + 3u * pr.d.P;
+            B.up_sil = w.upstream + 4u * pr.d.P;
+            B.pose_only = true;
+            if ((r = launch_backward(B, q)) != cudaSuccess) return r;
+            BprojLaunch J;
+            J.ws = w;
+            J.d = pr.d;
+            J.s = ctx->s;
+            J.g = gp;
+            J.dtype = g->dtype_attr;
+            J.poses_in = poses;
+            J.poses_out = poses;
+            J.adam = adam_state;
+            J.pose_grad = nullptr;
+            J.loss_out = loss_hist ? loss_hist + (size_t)it * pr.d.V : nullptr;
+            J.grads = gs_gaussians_grad{};
+            if ((r = launch_bproject(J, q)) != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    };
+
+    // flags latch over all iterations of this call
+    e = cudaMemsetAsync(w.err, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "flag clear");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream query");
+    if (cap != cudaStreamCaptureStatusNone) {
+        // the caller is capturing: record the kernels into its graph directly
+        e = enqueue_all(s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "tracking enqueue");
+    } else {
+        GraphKey key;
+        key.ws = ws;
+        key.ws_bytes = ws_bytes;
+        const void *ptrs[12] = {g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb, targets->rgb,
+                                targets->depth, targets->depth_prior, poses, adam_state, loss_hist, nullptr};
+        for (int k = 0; k < 12; ++k) key.ptrs[k] = ptrs[k];
+        key.n = g->n;
+        key.dtype = g->dtype_attr;
+        key.iters = iters;
+        key.views = pr.views;
+        key.rec_cap = pr.d.rec_cap;
+        key.pair_cap = pr.d.pair_cap;
+        if (!ctx->graph_exec || !(ctx->graph_key == key)) {
+            if (ctx->graph_exec) {
+                cudaGraphExecDestroy(ctx->graph_exec);
+                ctx->graph_exec = nullptr;
+            }
+            if (!ctx->cap_stream) {
+                e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "capture stream");
+            }
+            e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "begin capture");
+            cudaError_t e_enq = enqueue_all(ctx->cap_stream);
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            if (e_enq != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return cuda_fail(ctx, e_enq, "tracking capture");
+            }
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+            e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                ctx->graph_exec = nullptr;
+                return cuda_fail(ctx, e, "graph instantiate");
+            }
+            ctx->graph_key = key;
+        }
+        e = cudaGraphLaunch(ctx->graph_exec, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    }
+    ctx->bound = true;
+    ctx->prob = std::move(pr);
+    ctx->ws = w;
+    ctx->ws_base = ws;
+    ctx->g = gp;
+    ctx->dtype = g->dtype_attr;
+    ctx->poses = poses;
+    ctx->have_loss = true;
+    return GS_OK;
+}
+
+gs_status gs_sync_status(gs_ctx *ctx, void *stream, gs_counts *counts) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->bound) return fail(ctx, GS_ERR_STATE, "no workspace bound");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    DevHeader h{};
+    uint32_t err = 0;
+    if ((e = cudaMemcpy(&h, ctx->ws.hdr, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(ctx, e, "header read");
+    if ((e = cudaMemcpy(&err, ctx->ws.err, sizeof(err), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(ctx, e, "flag read");
+    if (err && (e = cudaMemset(ctx->ws.err, 0, sizeof(err))) != cudaSuccess) return cuda_fail(ctx, e, "flag clear");
+    if (counts) {
+        counts->n_records = h.n_rec;
+        counts->n_pairs = (int64_t)h.n_pairs;
+        counts->err_flags = err;
+        counts->reserved = 0;
+    }
+    if (err & kErrTimeout) return fail(ctx, GS_ERR_TIMEOUT, "a bounded device wait expired");
+    if (err & (kErrRecords | kErrPairs)) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "capacity exceeded: %u records (capacity %u), %llu pairs (capacity %u)",
+                      h.n_rec, ctx->prob.d.rec_cap, (unsigned long long)h.n_pairs, ctx->prob.d.pair_cap);
+        return fail(ctx, GS_ERR_CAPACITY, msg);
+    }
+    return GS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,313 @@
+// gs_internal.cuh -- device data layout and helpers shared by the rasterizer kernels.
+//
+// Pipeline of one rendering pass (every step is a kernel of this library):
+//   k_project   Gaussian x view: projection, opacity-aware support, tiles touched,
+//               compaction into visible records, per-tile counts; the last block scans
+//               the tile counts into tile offsets.
+//   k_emit      visible record: one 64-bit key (depth bits << 32 | record) per tile met.
+//   k_tile_sort tile: sort its keys by (depth, Gaussian index) and write record ids.
+//   k_forward   tile: Eqs. 2-4 front to back; optional fused combined loss.
+//   k_backward  tile: reverse compositing; per-record screen-space gradients.
+//   k_bproject  Gaussian x view: chain rule to parameters and pose; FP64 pose
+//               reduction and (tracking) the decoupled Adam step.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gsk {
+
+constexpr int kTile = 16;                 // tile edge in pixels
+constexpr int kTilePix = kTile * kTile;   // pixels (= threads) per tile block
+constexpr int kBlock = 256;               // threads per Gaussian-parallel block
+constexpr int kMaskWords = kBlock / 32;   // visibility bitmask words per block
+constexpr int kSortSmemCap = 4096;        // tiles up to this many keys sort in shared memory
+constexpr int kBatch = 256;               // Gaussians staged per compositing batch
+
+enum ErrFlag : uint32_t { kErrRecords = 1u, kErrPairs = 2u, kErrTimeout = 4u };
+
+// One view: intrinsics, image and tile-grid geometry, offsets in the concatenated arrays.
+struct ViewInfo {
+    float fx, fy, cx, cy;
+    int32_t width, height, tiles_x, tiles_y;
+    uint32_t tile_base;  // first global tile index of the view
+    uint32_t pix_base;   // first pixel of the view in the concatenated planes
+    uint32_t pad0, pad1;
+};
+static_assert(sizeof(ViewInfo) == 48, "ViewInfo layout");
+
+// Small counters at the start of the workspace (cleared before every projection).
+struct DevHeader {
+    uint32_t n_rec;     // records handed out by k_project (may exceed the capacity)
+    uint32_t k1_done;   // k_project blocks finished (last-block scan)
+    unsigned long long n_pairs;  // total (Gaussian, tile) pairs of the projection
+    unsigned long long pad[6];
+};
+static_assert(sizeof(DevHeader) == 64, "DevHeader layout");
+
+// A visible (Gaussian, view) pair, as the compositors read it (48 bytes).
+//   a = (mu'_x, mu'_y, depth, opacity)
+//   b = (conic a, conic b, conic c, dmax2)   conic = inverse of Sigma' = [[a, b], [b, c]]
+//   c = (r, g, b, bits of view * n + gaussian)
+struct __align__(16) Rec {
+    float4 a, b, c;
+};
+
+// Per-record screen-space gradient accumulators (48 bytes).
+//   g0 = (d mu'_x, d mu'_y, d depth, d opacity), g1 = (d conic a, b, c, 0), g2 = (d r, g, b, 0)
+struct __align__(16) RecGrad {
+    float4 g0, g1, g2;
+};
+
+// Device pointers into one workspace (computed on the host from the problem sizes).
+struct WsPtrs {
+    uint32_t *err;         // ErrFlag bits, latched until gs_sync_status clears them
+    DevHeader *hdr;
+    double *loss;          // V, combined loss per view
+    uint32_t *done_view;   // V, k_bproject blocks finished per view
+    uint32_t *tile_cnt;    // T, per-tile pair counts (zero between projections)
+    ViewInfo *views;       // V
+    uint32_t *tile_start;  // T + 1, exclusive scan of the counts
+    uint32_t *cursor;      // T, emission cursors
+    uint32_t *chunk_start; // V * nblk, first record of each k_project block
+    uint32_t *vis_mask;    // V * nblk * kMaskWords
+    Rec *rec;              // record_capacity
+    RecGrad *rec_grad;     // record_capacity
+    unsigned long long *keys;  // pair_capacity
+    uint32_t *sorted;      // pair_capacity, record ids in (tile, depth, gaussian) order
+    float *t_final;        // P, transmittance after the last contributor
+    uint32_t *n_last;      // P, tile-list index + 1 of the last contributor
+    float *upstream;       // 5 x P: dL/dC (planar like the images), dL/dD, dL/dS of the fused loss
+    double *pose_part;     // V * nblk * 6, per-block pose-gradient partial sums
+};
+
+struct Dims {
+    int64_t n;             // Gaussians
+    int32_t V;             // views
+    int32_t nblk;          // ceil(n / kBlock)
+    uint32_t T;            // tiles over all views
+    uint32_t P;            // pixels over all views
+    uint32_t rec_cap;
+    uint32_t pair_cap;
+};
+
+struct Settings {
+    float alpha_min, alpha_max, t_min, dilation, z_near, sil_thresh;
+    float w_rgb, w_depth, w_vis, w_prior;
+    double lr_rot, lr_trans, beta1, beta2, eps;
+};
+
+struct GaussPtrs {
+    const float *means;
+    const void *quats, *log_scales, *logits, *rgb;
+};
+
+// ------------------------------------------------------------------ attribute loads
+
+template <int DT> __device__ __forceinline__ float ld_attr(const void *p, int64_t i);
+template <> __device__ __forceinline__ float ld_attr<GS_F32>(const void *p, int64_t i) {
+    return __ldg(static_cast<const float *>(p) + i);
+}
+template <> __device__ __forceinline__ float ld_attr<GS_BF16>(const void *p, int64_t i) {
+    return __bfloat162float(static_cast<const __nv_bfloat16 *>(p)[i]);
+}
+template <> __device__ __forceinline__ float ld_attr<GS_F16>(const void *p, int64_t i) {
+    return __half2float(static_cast<const __half *>(p)[i]);
+}
+
+// ------------------------------------------------------------------ geometry helpers
+
+// Rotation matrix (row-major) of the unit quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float R[9]) {
+    R[0] = 1.f - 2.f * (y * y + z * z);
+    R[1] = 2.f * (x * y - w * z);
+    R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);
+    R[4] = 1.f - 2.f * (x * x + z * z);
+    R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);
+    R[7] = 2.f * (y * z + w * x);
+    R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Pose (7 doubles) -> FP32 rotation (9) and translation (3).  The rotation is formed in
+// FP64 with every operation explicitly rounded (no contraction) and then rounded to
+// FP32, so the camera-frame depth below is an exactly specified FP32 number: the depth
+// order of Eqs. 2-4 and the near-plane test are decided on it.
+__device__ __forceinline__ void load_pose(const double *pose, float Rt[12]) {
+    double w = pose[0], x = pose[1], y = pose[2], z = pose[3];
+    const double ss = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(w, w), __dmul_rn(x, x)), __dmul_rn(y, y)),
+                                __dmul_rn(z, z));
+    const double inv = __ddiv_rn(1.0, __dsqrt_rn(ss));
+    w = __dmul_rn(w, inv);
+    x = __dmul_rn(x, inv);
+    y = __dmul_rn(y, inv);
+    z = __dmul_rn(z, inv);
+    Rt[0] = __double2float_rn(__dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, y), __dmul_rn(z, z)))));
+    Rt[1] = __double2float_rn(__dmul_rn(2.0, __dsub_rn(__dmul_rn(x, y), __dmul_rn(w, z))));
+    Rt[2] = __double2float_rn(__dmul_rn(2.0, __dadd_rn(__dmul_rn(x, z), __dmul_rn(w, y))));
+    Rt[3] = __double2float_rn(__dmul_rn(2.0, __dadd_rn(__dmul_rn(x, y), __dmul_rn(w, z))));
+    Rt[4] = __double2float_rn(__dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(z, z)))));
+    Rt[5] = __double2float_rn(__dmul_rn(2.0, __dsub_rn(__dmul_rn(y, z), __dmul_rn(w, x))));
+    Rt[6] = __double2float_rn(__dmul_rn(2.0, __dsub_rn(__dmul_rn(x, z), __dmul_rn(w, y))));
+    Rt[7] = __double2float_rn(__dmul_rn(2.0, __dadd_rn(__dmul_rn(y, z), __dmul_rn(w, x))));
+    Rt[8] = __double2float_rn(__dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)))));
+    Rt[9] = __double2float_rn(pose[4]);
+    Rt[10] = __double2float_rn(pose[5]);
+    Rt[11] = __double2float_rn(pose[6]);
+}
+
+// Camera-frame coordinate r of mean m: fma(R_r0, m0, fma(R_r1, m1, fma(R_r2, m2, t_r))).
+__device__ __forceinline__ float cam_coord(const float Rt[12], int r, float m0, float m1, float m2) {
+    return __fmaf_rn(Rt[3 * r], m0, __fmaf_rn(Rt[3 * r + 1], m1, __fmaf_rn(Rt[3 * r + 2], m2, Rt[9 + r])));
+}
+
+// Opacity-aware tile rectangle [tx0, tx1] x [ty0, ty1] of a support ellipse whose
+// axis-aligned half-extents are hx, hy pixels (one pixel of margin).  Empty if tx0 > tx1.
+__device__ __forceinline__ void tile_rect(const ViewInfo &vi, float mx, float my, float hx, float hy, int &tx0,
+                                          int &tx1, int &ty0, int &ty1) {
+    const float lim = 1.0e7f;
+    const float x0 = fminf(fmaxf(floorf(mx - hx) - 1.f, -1.f), lim);
+    const float x1 = fminf(fmaxf(ceilf(mx + hx) + 1.f, -1.f), lim);
+    const float y0 = fminf(fmaxf(floorf(my - hy) - 1.f, -1.f), lim);
+    const float y1 = fminf(fmaxf(ceilf(my + hy) + 1.f, -1.f), lim);
+    const int px0 = max((int)x0, 0), px1 = min((int)x1, vi.width - 1);
+    const int py0 = max((int)y0, 0), py1 = min((int)y1, vi.height - 1);
+    if (px0 > px1 || py0 > py1 || x1 < 0.f || y1 < 0.f) {
+        tx0 = 1; tx1 = 0; ty0 = 1; ty1 = 0;
+        return;
+    }
+    tx0 = px0 / kTile; tx1 = px1 / kTile;
+    ty0 = py0 / kTile; ty1 = py1 / kTile;
+}
+
+// Does the support ellipse q(d) = a dx^2 + 2 b dx dy + c dy^2 <= dmax2 meet the
+// rectangle of pixel centres [x0, x1] x [y0, y1]?  The minimum of the convex form over
+// the rectangle is 0 when the centre is inside, otherwise it lies on an edge, where
+// it is a 1-D quadratic minimised in closed form.  Every operation is an explicitly
+// rounded intrinsic so k_project and k_emit take the identical decision.
+__device__ __forceinline__ float qform(float a, float b, float c, float dx, float dy) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(a, __fmul_rn(dx, dx)), __fmul_rn(2.f, __fmul_rn(b, __fmul_rn(dx, dy)))),
+                     __fmul_rn(c, __fmul_rn(dy, dy)));
+}
+
+__device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float a, float b, float c, float dmax2,
+                                                   float x0, float x1, float y0, float y1) {
+    if (!(dmax2 < INFINITY)) return true;
+    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
+    const float lx = __fsub_rn(x0, mx), hx = __fsub_rn(x1, mx);
+    const float ly = __fsub_rn(y0, my), hy = __fsub_rn(y1, my);
+    float best = INFINITY;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float dx = e ? hx : lx;  // vertical edge: dy free
+        const float dy = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, dx), c), ly), hy);
+        best = fminf(best, qform(a, b, c, dx, dy));
+        const float ey = e ? hy : ly;  // horizontal edge: dx free
+        const float ex = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, ey), a), lx), hx);
+        best = fminf(best, qform(a, b, c, ex, ey));
+    }
+    return best <= __fadd_rn(__fmul_rn(dmax2, 1.001f), 1e-3f);
+}
+
+// Pixel-centre rectangle of tile (tx, ty), clipped to the image.
+__device__ __forceinline__ void tile_bounds(const ViewInfo &vi, int tx, int ty, float &x0, float &x1, float &y0,
+                                            float &y1) {
+    x0 = (float)(tx * kTile);
+    y0 = (float)(ty * kTile);
+    x1 = (float)min(tx * kTile + kTile - 1, vi.width - 1);
+    y1 = (float)min(ty * kTile + kTile - 1, vi.height - 1);
+}
+
+// alpha of a staged record at pixel centre (px, py): alpha = min(alpha_max, o exp(power)),
+// power = -1/2 (a dx^2 + c dy^2) - b dx dy.  Shared by the forward and the backward so
+// both take bit-identical decisions (explicitly rounded operations, no contraction).
+struct AlphaEval {
+    float dx, dy, G, araw, alpha;
+};
+
+__device__ __forceinline__ AlphaEval eval_alpha(float px, float py, float4 A, float4 B, float alpha_max) {
+    AlphaEval r;
+    r.dx = __fsub_rn(px, A.x);
+    r.dy = __fsub_rn(py, A.y);
+    const float q = __fadd_rn(__fmul_rn(B.x, __fmul_rn(r.dx, r.dx)), __fmul_rn(B.z, __fmul_rn(r.dy, r.dy)));
+    const float power = __fsub_rn(__fmul_rn(-0.5f, q), __fmul_rn(B.y, __fmul_rn(r.dx, r.dy)));
+    r.G = __expf(power);
+    r.araw = __fmul_rn(A.w, r.G);
+    r.alpha = fminf(alpha_max, r.araw);
+    return r;
+}
+
+// Global tile -> view (binary search over the views' first tiles).
+__device__ __forceinline__ int view_of_tile(const ViewInfo *views, int V, uint32_t tile) {
+    int lo = 0, hi = V - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Entries of a tile's list: [start, start + count) of the key / sorted arrays.  Clamped
+// to what k_emit actually wrote and to the pair capacity, so an overflow (latched in the
+// error flags) can never make a kernel read past its buffers.
+__device__ __forceinline__ uint32_t tile_entries(const WsPtrs &ws, const Dims &d, uint32_t tile, uint32_t &start) {
+    start = ws.tile_start[tile];
+    const uint32_t end = min(min(ws.cursor[tile], ws.tile_start[tile + 1]), d.pair_cap);
+    return end > start ? end - start : 0u;
+}
+
+// ------------------------------------------------------------------ host-side launchers
+
+struct ProjectLaunch {
+    WsPtrs ws;
+    Dims d;
+    Settings s;
+    GaussPtrs g;
+    int dtype;
+    const double *poses;
+};
+
+cudaError_t launch_upload_views(const ViewInfo *host_views, int V, ViewInfo *dev, cudaStream_t st);
+cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st);
+cudaError_t launch_emit(const WsPtrs &ws, const Dims &d, cudaStream_t st);
+cudaError_t launch_tile_sort(const WsPtrs &ws, const Dims &d, cudaStream_t st);
+
+struct ForwardLaunch {
+    WsPtrs ws;
+    Dims d;
+    Settings s;
+    float *rgb, *depth, *sil;  // outputs (nullable)
+    const float *t_rgb, *t_depth, *t_prior;  // targets (t_rgb == nullptr -> no loss)
+};
+cudaError_t launch_forward(const ForwardLaunch &L, cudaStream_t st);
+
+struct BackwardLaunch {
+    WsPtrs ws;
+    Dims d;
+    Settings s;
+    const float *up_rgb, *up_depth, *up_sil;  // upstream planes (P each, rgb 3P)
+    bool pose_only;                            // skip opacity / colour gradients
+};
+cudaError_t launch_backward(const BackwardLaunch &L, cudaStream_t st);
+
+struct BprojLaunch {
+    WsPtrs ws;
+    Dims d;
+    Settings s;
+    GaussPtrs g;
+    int dtype;
+    const double *poses_in;   // poses the projection used
+    double *poses_out;        // updated poses (tracking) or nullptr
+    double *adam;             // n_views x 16 (tracking) or nullptr
+    double *pose_grad;        // n_views x 6 or nullptr
+    double *loss_out;         // n_views, copy of the loss (tracking) or nullptr
+    gs_gaussians_grad grads;  // parameter gradients (each nullable)
+};
+cudaError_t launch_bproject(const BprojLaunch &L, cudaStream_t st);
+
+}  // namespace gsk

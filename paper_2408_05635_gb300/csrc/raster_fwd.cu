@@ -1,0 +1,163 @@
+// raster_fwd.cu -- front-to-back compositing of colour, depth and silhouette.
+//
+// One block per 16 x 16 tile, one thread per pixel.  For pixel p and the tile's
+// Gaussians in (depth, index) order:
+//   C(p) = sum_i c_i a_i T_i   (Eq. 2)
+//   D(p) = sum_i d_i a_i T_i   (Eq. 3, d_i = camera-frame depth of the mean)
+//   S(p) = sum_i a_i T_i       (Eq. 4)
+// with a_i = min(alpha_max, o_i exp(power_i)) the 2-D footprint of Eq. 1 and
+// T_i = prod_{j<i} (1 - a_j).  Gaussians with a_i < alpha_min are skipped; the walk
+// stops before the Gaussian that would take T below t_min, and the block stops as soon
+// as all its pixels have stopped.  Batches of kBatch records are gathered into shared
+// memory by the whole block and then read by every pixel as broadcasts.
+//
+// With targets, the combined loss of Sec. III-B (plus the depth-prior term) is
+// evaluated in the epilogue: its per-pixel gradient goes to the workspace for the
+// backward and its value is reduced per block in FP64 and added to the view's total.
+#include "gs_internal.cuh"
+
+namespace gsk {
+
+__device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
+
+template <bool LOSS>
+__global__ void __launch_bounds__(kTilePix) k_forward(ForwardLaunch L) {
+    __shared__ float4 sA[kBatch], sB[kBatch], sC[kBatch];
+    __shared__ int s_view;
+    __shared__ double s_loss[kTilePix / 32];
+    const uint32_t tile = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_view = view_of_tile(L.ws.views, L.d.V, tile);
+    __syncthreads();
+    const int view = s_view;
+    const ViewInfo vi = L.ws.views[view];
+    const uint32_t local = tile - vi.tile_base;
+    const int tx = (int)(local % (uint32_t)vi.tiles_x), ty = (int)(local / (uint32_t)vi.tiles_x);
+    const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid / kTile);
+    const bool inside = px < vi.width && py < vi.height;
+    const float fpx = (float)px, fpy = (float)py;
+    const Settings &S = L.s;
+
+    uint32_t start;
+    const uint32_t n = tile_entries(L.ws, L.d, tile, start);
+    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, D = 0.f, Sil = 0.f;
+    uint32_t last = 0;
+    bool done = !inside;
+    for (uint32_t b0 = 0; b0 < n; b0 += kBatch) {
+        if (__syncthreads_count(!done) == 0) break;
+        const uint32_t idx = b0 + tid;
+        if (idx < n) {
+            const uint32_t r = L.ws.sorted[start + idx];
+            if (r < L.d.rec_cap) {
+                const Rec rr = L.ws.rec[r];
+                sA[tid] = rr.a;
+                sB[tid] = rr.b;
+                sC[tid] = rr.c;
+            } else {
+                sA[tid] = make_float4(0.f, 0.f, 1.f, 0.f);  // zero opacity: never contributes
+                sB[tid] = make_float4(1.f, 0.f, 1.f, 0.f);
+                sC[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)min((uint32_t)kBatch, n - b0);
+        if (!done) {
+            for (int j = 0; j < cnt; ++j) {
+                const float4 A = sA[j], B = sB[j];
+                const AlphaEval ev = eval_alpha(fpx, fpy, A, B, S.alpha_max);
+                if (ev.alpha < S.alpha_min) continue;
+                const float Tn = T * (1.f - ev.alpha);
+                if (Tn < S.t_min) {
+                    done = true;
+                    break;
+                }
+                const float w = ev.alpha * T;
+                const float4 Cc = sC[j];
+                cr += Cc.x * w;
+                cg += Cc.y * w;
+                cb += Cc.z * w;
+                D += A.z * w;
+                Sil += w;
+                T = Tn;
+                last = b0 + (uint32_t)j + 1u;
+            }
+        }
+    }
+
+    const uint32_t HW = (uint32_t)vi.width * (uint32_t)vi.height;
+    const uint32_t p = (uint32_t)py * (uint32_t)vi.width + (uint32_t)px;
+    const uint32_t gp = vi.pix_base + p;  // pixel in the concatenated planes
+    if (inside) {
+        if (L.rgb) {
+            float *o = L.rgb + 3u * vi.pix_base;
+            o[p] = cr;
+            o[HW + p] = cg;
+            o[2u * HW + p] = cb;
+        }
+        if (L.depth) L.depth[gp] = D;
+        if (L.sil) L.sil[gp] = Sil;
+        L.ws.t_final[gp] = T;
+        L.ws.n_last[gp] = last;
+    }
+    if constexpr (LOSS) {
+        float l = 0.f;
+        if (inside) {
+            const float *trgb = L.t_rgb + 3u * vi.pix_base;
+            const float Dt = L.t_depth[gp];
+            const bool valid = Dt > 0.f;
+            const bool M = valid && Sil > S.sil_thresh;
+            float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, gS = 0.f;
+            if (M) {
+                const float r0 = cr - trgb[p], r1 = cg - trgb[HW + p], r2 = cb - trgb[2u * HW + p];
+                l += S.w_rgb * (fabsf(r0) + fabsf(r1) + fabsf(r2));
+                g0 = S.w_rgb * sgnf(r0);
+                g1 = S.w_rgb * sgnf(r1);
+                g2 = S.w_rgb * sgnf(r2);
+                const float rd = D - Dt;
+                l += S.w_depth * fabsf(rd);
+                gD = S.w_depth * sgnf(rd);
+                if (L.t_prior) {
+                    const float pr = L.t_prior[gp];
+                    if (pr > 0.f) {
+                        const float rp = D - pr;
+                        l += S.w_prior * fabsf(rp);
+                        gD += S.w_prior * sgnf(rp);
+                    }
+                }
+            }
+            if (valid) {
+                l += S.w_vis * (1.f - Sil);
+                gS = -S.w_vis;
+            }
+            // same planar layout as the images: colour 3 x H x W per view, then D, then S
+            const uint32_t P = L.d.P;
+            float *ug = L.ws.upstream + 3u * vi.pix_base;
+            ug[p] = g0;
+            ug[HW + p] = g1;
+            ug[2u * HW + p] = g2;
+            L.ws.upstream[3u * P + gp] = gD;
+            L.ws.upstream[4u * P + gp] = gS;
+        }
+        double dl = (double)l;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, off);
+        if ((tid & 31) == 0) s_loss[tid >> 5] = dl;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < kTilePix / 32; ++w) s += s_loss[w];
+            if (s != 0.0) atomicAdd(L.ws.loss + view, s);
+        }
+    }
+}
+
+cudaError_t launch_forward(const ForwardLaunch &L, cudaStream_t st) {
+    if (L.d.T == 0) return cudaSuccess;
+    if (L.t_rgb)
+        k_forward<true><<<L.d.T, kTilePix, 0, st>>>(L);
+    else
+        k_forward<false><<<L.d.T, kTilePix, 0, st>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace gsk

@@ -1,0 +1,380 @@
+"""ctypes binding of the C ABI in include/gs.h (argument marshalling only).
+
+Every entry point keeps its C name (``gs_project``, ``gs_forward``, ``gs_backward``,
+``gs_track_step`` ...) and takes torch CUDA tensors where the C function takes device
+pointers.  All compute runs in the CUDA library ``_build/libgsgb.so``; there is no CPU
+or PyTorch fallback: loading fails with an error if the library is missing or no CUDA
+device is present.
+
+``Rasterizer`` adds the bookkeeping a Python caller needs: it owns the context, sizes
+and allocates the workspace (a torch uint8 tensor) and can measure the pair and record
+counts of a scene with one sizing pass.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+from typing import Sequence
+
+import torch
+
+from . import build as _build
+
+c_void_p, c_int32, c_int64, c_uint32, c_double, c_float, c_size_t = (
+    ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, ctypes.c_float,
+    ctypes.c_size_t)
+
+GS_F32, GS_BF16, GS_F16 = 0, 1, 2
+_STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_OOM", 4: "GS_ERR_WORKSPACE",
+           5: "GS_ERR_CAPACITY", 6: "GS_ERR_TIMEOUT", 7: "GS_ERR_UNSUPPORTED", 8: "GS_ERR_STATE"}
+GS_ERR_CAPACITY = 5
+ERR_RECORDS, ERR_PAIRS, ERR_TIMEOUT = 1, 2, 4
+
+
+class gs_gaussians(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("quats", c_void_p), ("log_scales", c_void_p),
+                ("opacity_logits", c_void_p), ("rgb", c_void_p), ("dtype_attr", c_int32),
+                ("reserved", c_int32), ("n", c_int64)]
+
+
+class gs_gaussians_grad(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("quats", c_void_p), ("log_scales", c_void_p),
+                ("opacity_logits", c_void_p), ("rgb", c_void_p)]
+
+
+class gs_camera(ctypes.Structure):
+    _fields_ = [("fx", c_double), ("fy", c_double), ("cx", c_double), ("cy", c_double),
+                ("width", c_int32), ("height", c_int32)]
+
+
+class gs_targets(ctypes.Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("depth_prior", c_void_p)]
+
+
+class gs_config(ctypes.Structure):
+    _fields_ = [("tile_w", c_int32), ("tile_h", c_int32)] + [
+        (n, c_float) for n in ("alpha_min", "alpha_max", "t_min", "dilation", "z_near", "sil_thresh",
+                               "w_rgb", "w_depth", "w_vis", "w_prior")] + [
+        (n, c_double) for n in ("lr_rot", "lr_trans", "beta1", "beta2", "eps")]
+
+
+class gs_problem(ctypes.Structure):
+    _fields_ = [("n_gaussians", c_int64), ("n_views", c_int32), ("reserved", c_int32),
+                ("cameras", ctypes.POINTER(gs_camera)), ("pair_capacity", c_int64),
+                ("record_capacity", c_int64)]
+
+
+class gs_counts(ctypes.Structure):
+    _fields_ = [("n_records", c_int64), ("n_pairs", c_int64), ("err_flags", c_uint32), ("reserved", c_uint32)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libgsgb.so (building it first if it is missing or stale).  Raises if no CUDA
+    device is available: the rasterizer has no host fallback."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2408_05635_gb300 needs a CUDA GPU (sm_103a); none is available")
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path}")
+        lib = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        sigs = {
+            "gs_default_config": (None, [P(gs_config)]),
+            "gs_create": (c_int32, [P(c_void_p), P(gs_config)]),
+            "gs_destroy": (c_int32, [c_void_p]),
+            "gs_last_error": (ctypes.c_char_p, [c_void_p]),
+            "gs_status_string": (ctypes.c_char_p, [c_int32]),
+            "gs_workspace_size": (c_int32, [c_void_p, P(gs_problem), P(c_size_t)]),
+            "gs_project": (c_int32, [c_void_p, P(gs_problem), P(gs_gaussians), c_void_p, c_void_p, c_size_t,
+                                     c_void_p]),
+            "gs_forward": (c_int32, [c_void_p, P(gs_targets), c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+            "gs_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, P(gs_gaussians_grad), c_void_p,
+                                      c_void_p]),
+            "gs_track_step": (c_int32, [c_void_p, P(gs_problem), P(gs_gaussians), P(gs_targets), c_void_p,
+                                        c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
+            "gs_sync_status": (c_int32, [c_void_p, c_void_p, P(gs_counts)]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ----------------------------------------------------------------------------- raw C names
+
+def gs_default_config() -> gs_config:
+    c = gs_config()
+    load().gs_default_config(ctypes.byref(c))
+    return c
+
+
+def gs_create(cfg: gs_config | None = None) -> int:
+    h = c_void_p()
+    st = load().gs_create(ctypes.byref(h), ctypes.byref(cfg) if cfg is not None else None)
+    if st:
+        raise GsError(st, "gs_create")
+    return h.value
+
+
+def gs_destroy(ctx: int) -> None:
+    load().gs_destroy(ctx)
+
+
+def gs_last_error(ctx: int) -> str:
+    return (load().gs_last_error(ctx) or b"").decode()
+
+
+def _check(ctx, st, what):
+    if st:
+        raise GsError(st, f"{what}: {gs_last_error(ctx)}")
+
+
+def gs_workspace_size(ctx: int, prob: gs_problem) -> int:
+    n = c_size_t(0)
+    _check(ctx, load().gs_workspace_size(ctx, ctypes.byref(prob), ctypes.byref(n)), "gs_workspace_size")
+    return n.value
+
+
+def gs_project(ctx, prob: gs_problem, g: gs_gaussians, poses: torch.Tensor, ws: torch.Tensor, ws_bytes: int,
+               stream=None) -> None:
+    _check(ctx, load().gs_project(ctx, ctypes.byref(prob), ctypes.byref(g), _ptr(poses), _ptr(ws), ws_bytes,
+                                  _stream(stream)), "gs_project")
+
+
+def gs_forward(ctx, targets: gs_targets | None, rgb=None, depth=None, sil=None, loss=None, stream=None) -> None:
+    _check(ctx, load().gs_forward(ctx, ctypes.byref(targets) if targets is not None else None, _ptr(rgb),
+                                  _ptr(depth), _ptr(sil), _ptr(loss), _stream(stream)), "gs_forward")
+
+
+def gs_backward(ctx, d_rgb=None, d_depth=None, d_sil=None, grads: gs_gaussians_grad | None = None,
+                pose_grad=None, stream=None) -> None:
+    _check(ctx, load().gs_backward(ctx, _ptr(d_rgb), _ptr(d_depth), _ptr(d_sil),
+                                   ctypes.byref(grads) if grads is not None else None, _ptr(pose_grad),
+                                   _stream(stream)), "gs_backward")
+
+
+def gs_track_step(ctx, prob: gs_problem, g: gs_gaussians, targets: gs_targets, poses, adam_state, loss_hist,
+                  iters: int, ws, ws_bytes: int, stream=None) -> None:
+    _check(ctx, load().gs_track_step(ctx, ctypes.byref(prob), ctypes.byref(g), ctypes.byref(targets), _ptr(poses),
+                                     _ptr(adam_state), _ptr(loss_hist), int(iters), _ptr(ws), ws_bytes,
+                                     _stream(stream)), "gs_track_step")
+
+
+def gs_sync_status(ctx, stream=None) -> tuple[int, gs_counts]:
+    """Returns (status, counts); status GS_ERR_CAPACITY / GS_ERR_TIMEOUT are not raised."""
+    c = gs_counts()
+    st = load().gs_sync_status(ctx, _stream(stream), ctypes.byref(c))
+    if st not in (0, GS_ERR_CAPACITY, 6):
+        raise GsError(st, f"gs_sync_status: {gs_last_error(ctx)}")
+    return st, c
+
+
+# ----------------------------------------------------------------------------- convenience
+
+@dataclasses.dataclass
+class Config:
+    """Python mirror of gs_config (defaults = gs_default_config)."""
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    t_min: float = 1e-4
+    dilation: float = 0.0
+    z_near: float = 0.2
+    sil_thresh: float = 0.99
+    w_rgb: float = 0.5
+    w_depth: float = 1.0
+    w_vis: float = 0.1
+    w_prior: float = 0.5
+    lr_rot: float = 2e-3
+    lr_trans: float = 2e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+
+    def c(self) -> gs_config:
+        g = gs_config()
+        g.tile_w = g.tile_h = 16
+        for f in dataclasses.fields(self):
+            setattr(g, f.name, getattr(self, f.name))
+        return g
+
+
+_DT = {torch.float32: GS_F32, torch.bfloat16: GS_BF16, torch.float16: GS_F16}
+
+
+@dataclasses.dataclass
+class GaussianTensors:
+    """Device tensors of a Gaussian map: means float32 n x 3; quats n x 4; log_scales
+    n x 3; logits n; rgb n x 3 (the last four share one dtype: float32, bfloat16 or
+    float16)."""
+    means: torch.Tensor
+    quats: torch.Tensor
+    log_scales: torch.Tensor
+    logits: torch.Tensor
+    rgb: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return self.means.shape[0]
+
+    def c(self) -> gs_gaussians:
+        if self.means.dtype != torch.float32:
+            raise ValueError("means must be float32")
+        dt = self.quats.dtype
+        for t in (self.log_scales, self.logits, self.rgb):
+            if t.dtype != dt:
+                raise ValueError("quats, log_scales, logits and rgb must share one dtype")
+        if dt not in _DT:
+            raise ValueError(f"unsupported attribute dtype {dt}")
+        return gs_gaussians(_ptr(self.means), _ptr(self.quats), _ptr(self.log_scales), _ptr(self.logits),
+                            _ptr(self.rgb), _DT[dt], 0, self.n)
+
+    @staticmethod
+    def from_numpy(g, device="cuda", attr_dtype=torch.float32) -> "GaussianTensors":
+        def t(a, dt):
+            return torch.as_tensor(a, dtype=torch.float32).to(device=device, dtype=dt).contiguous()
+        return GaussianTensors(t(g.means, torch.float32), t(g.quats, attr_dtype), t(g.log_scales, attr_dtype),
+                               t(g.logits, attr_dtype), t(g.rgb, attr_dtype))
+
+
+def cameras_c(cams: Sequence) -> ctypes.Array:
+    arr = (gs_camera * len(cams))()
+    for k, c in enumerate(cams):
+        arr[k] = gs_camera(float(c.fx), float(c.fy), float(c.cx), float(c.cy), int(c.width), int(c.height))
+    return arr
+
+
+class Rasterizer:
+    """Owns a context and a workspace; marshals torch tensors into the C calls."""
+
+    def __init__(self, config: Config | None = None, device: str | torch.device = "cuda"):
+        load()
+        self.config = config or Config()
+        self.device = torch.device(device)
+        self.ctx = gs_create(self.config.c())
+        self._ws = None
+        self._ws_view = None
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            gs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- workspace ---------------------------------------------------------------------
+    def problem(self, n: int, cams: Sequence, pair_capacity: int, record_capacity: int = 0) -> gs_problem:
+        arr = cameras_c(cams)
+        p = gs_problem(int(n), len(cams), 0, ctypes.cast(arr, ctypes.POINTER(gs_camera)), int(pair_capacity),
+                       int(record_capacity))
+        p._cams = arr  # keep the host array alive with the struct
+        return p
+
+    def workspace(self, prob: gs_problem) -> tuple[torch.Tensor, int]:
+        need = gs_workspace_size(self.ctx, prob)
+        if self._ws is None or self._ws.numel() < need + 256:
+            self._ws = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
+        off = (-self._ws.data_ptr()) % 256
+        view = self._ws[off:off + need]
+        return view, need
+
+    def measure(self, g: GaussianTensors, cams: Sequence, poses: torch.Tensor) -> tuple[int, int]:
+        """Project once with minimal capacities and return (pairs, records) of the scene."""
+        prob = self.problem(g.n, cams, pair_capacity=1, record_capacity=1)
+        ws, nb = self.workspace(prob)
+        gs_project(self.ctx, prob, g.c(), poses, ws, nb)
+        _, counts = gs_sync_status(self.ctx)
+        return int(counts.n_pairs), int(counts.n_records)
+
+    def plan(self, g: GaussianTensors, cams: Sequence, poses: torch.Tensor, margin: float = 1.25,
+             min_pairs: int = 1024) -> gs_problem:
+        pairs, recs = self.measure(g, cams, poses)
+        full = g.n * len(cams)
+        return self.problem(g.n, cams, max(min_pairs, int(pairs * margin) + 1024),
+                            min(full, max(1, int(recs * margin) + 1024)))
+
+    # -- one rendering pass ------------------------------------------------------------
+    def render(self, prob: gs_problem, g: GaussianTensors, poses: torch.Tensor, targets=None, stream=None,
+               images: bool = True) -> dict:
+        """gs_project + gs_forward.  targets = (rgb, depth, prior-or-None) tensors enable
+        the fused loss.  Returns the images (and loss) as tensors."""
+        ws, nb = self.workspace(prob)
+        gs_project(self.ctx, prob, g.c(), poses, ws, nb, stream)
+        P = sum(int(c.width) * int(c.height) for c in prob._cams)
+        out = {}
+        if images:
+            out["rgb"] = torch.empty(3 * P, device=self.device)
+            out["depth"] = torch.empty(P, device=self.device)
+            out["sil"] = torch.empty(P, device=self.device)
+        tg = None
+        if targets is not None:
+            trgb, tdep, tprior = targets
+            tg = gs_targets(_ptr(trgb), _ptr(tdep), _ptr(tprior))
+            out["loss"] = torch.empty(prob.n_views, dtype=torch.float64, device=self.device)
+        gs_forward(self.ctx, tg, out.get("rgb"), out.get("depth"), out.get("sil"), out.get("loss"), stream)
+        self._keep = [g, poses, targets]
+        return out
+
+    def backward(self, g: GaussianTensors, upstream=None, params: bool = True, pose: bool = True,
+                 stream=None, n_views: int = 1) -> dict:
+        out = {}
+        grads = None
+        if params:
+            out["grads"] = {k: torch.zeros(getattr(g, k).shape, dtype=torch.float32, device=self.device)
+                            for k in ("means", "quats", "log_scales", "logits", "rgb")}
+            G = out["grads"]
+            grads = gs_gaussians_grad(_ptr(G["means"]), _ptr(G["quats"]), _ptr(G["log_scales"]), _ptr(G["logits"]),
+                                      _ptr(G["rgb"]))
+        if pose:
+            out["pose_grad"] = torch.zeros(n_views, 6, dtype=torch.float64, device=self.device)
+        up = upstream if upstream is not None else (None, None, None)
+        gs_backward(self.ctx, up[0], up[1], up[2], grads, out.get("pose_grad"), stream)
+        return out
+
+    def sync(self, stream=None) -> gs_counts:
+        st, c = gs_sync_status(self.ctx, stream)
+        if st:
+            raise GsError(st, gs_last_error(self.ctx))
+        return c

@@ -268,10 +268,11 @@ def test_backward_matches_finite_differences(seed):
     for k in range(6):
         vals = []
         for sgn in (1, -1):
-            if k < 3:
+            if k < 3:  # rotation about the camera centre: x_c -> Exp(e) x_c
                 e = np.zeros(3)
                 e[k] = sgn * h
-                P = scenes.pose_from_rt(Rotation.from_rotvec(e).as_matrix() @ R, t)
+                Re = Rotation.from_rotvec(e).as_matrix()
+                P = scenes.pose_from_rt(Re @ R, Re @ t)
             else:
                 tt = t.copy()
                 tt[k - 3] += sgn * h
@@ -296,9 +297,11 @@ def test_backward_screen_space_fd():
 
 
 def test_pose_gradient_equals_map_gradient_sums():
-    """Moving the camera is moving the map: dL/dt = R sum_i dL/dmu_i, and rotating the
-    camera by R delta equals rotating every mean and every covariance by delta about the
-    world origin (Sec. II-A x_c = R x + t), with the default thresholds on."""
+    """Moving the camera is moving the map: dL/dt = R sum_i dL/dmu_i.  Rotating every
+    mean and covariance by delta about the world origin equals turning the camera by
+    phi = R delta about its centre plus the translation change -phi x t, so
+    R^T (dL/dtheta - t x dL/dt) is the map-rotation derivative (Sec. II-A x_c = R x + t),
+    with the default thresholds on."""
     g, cam = scenes.cube_scene()
     sc, oc = oracle_scene(g), oracle_cam(cam)
     rng = np.random.default_rng(11)
@@ -316,7 +319,8 @@ def test_pose_gradient_equals_map_gradient_sums():
         qw, qv = sc.quats[:, 0], sc.quats[:, 1:]
         dq = 0.5 * np.concatenate([(-(qv @ e))[:, None], qw[:, None] * e[None, :] + np.cross(e, qv)], axis=1)
         lhs[k] = np.sum(dx * gm) + np.sum(dq * gq)
-    np.testing.assert_allclose(lhs, R.T @ b["pose6"][:3], rtol=1e-8, atol=1e-9 * np.abs(b["pose6"]).max())
+    rhs = R.T @ (b["pose6"][:3] - np.cross(t, b["pose6"][3:]))
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-8, atol=1e-9 * np.abs(b["pose6"]).max())
 
 
 # ----------------------------------------------------------------------------- loss
@@ -380,23 +384,36 @@ def test_adam_first_steps_are_lr_sized():
     assert ang == pytest.approx(1e-3, rel=1e-6)
     assert new[3] < 0 and abs(new[1]) < 1e-15 and abs(new[2]) < 1e-15
     new2, state = oracle.adam_step(new, state, g, p)
-    np.testing.assert_allclose(new2[4:] - new[4:], -5e-3 * np.sign(g[3:]), rtol=1e-6)
-    R1, _ = scenes.pose_rt(new)
-    R2, _ = scenes.pose_rt(new2)
+    R1, t1 = scenes.pose_rt(new)
+    R2, t2 = scenes.pose_rt(new2)
     rel = Rotation.from_matrix(R2 @ R1.T).as_rotvec()
     np.testing.assert_allclose(rel, [0, 0, -1e-3], atol=1e-12)
+    # the camera centre moves by the translation step expressed in the new camera frame
+    c1, c2 = -R1.T @ t1, -R2.T @ t2
+    np.testing.assert_allclose(R2 @ (c2 - c1), 5e-3 * np.sign(g[3:]), rtol=1e-6)
     assert state[12] == 2
 
 
 def test_adam_blocks_are_decoupled():
-    """The rotation step does not depend on the translation gradient and vice versa."""
+    """The rotation block turns the camera about its own centre (a pure rotation step
+    leaves the centre where it was); the translation block moves the centre without
+    turning the camera; neither block's step depends on the other block's gradient."""
     p = oracle.Params()
-    pose = scenes.perturb_pose(scenes.identity_pose(), np.random.default_rng(0), 3.0, 0.1)
+    pose = scenes.perturb_pose(scenes.identity_pose(), np.random.default_rng(0), 3.0, 0.4)
+    R0, t0 = scenes.pose_rt(pose)
+    rot_only, _ = oracle.adam_step(pose, np.zeros(16), np.array([1.0, -2, 3, 0, 0, 0]), p)
+    R1, t1 = scenes.pose_rt(rot_only)
+    np.testing.assert_allclose(-R1.T @ t1, -R0.T @ t0, atol=1e-14)
+    assert np.linalg.norm(Rotation.from_matrix(R1 @ R0.T).as_rotvec()) > 1e-3
+    trans_only, _ = oracle.adam_step(pose, np.zeros(16), np.array([0.0, 0, 0, 4, 5, -6]), p)
+    np.testing.assert_allclose(trans_only[:4], pose[:4], atol=0)
     a, _ = oracle.adam_step(pose, np.zeros(16), np.array([1.0, -2, 3, 4, 5, 6]), p)
     b, _ = oracle.adam_step(pose, np.zeros(16), np.array([1.0, -2, 3, -40, 0.5, 60]), p)
     c, _ = oracle.adam_step(pose, np.zeros(16), np.array([-9.0, 2, 0.3, 4, 5, 6]), p)
     np.testing.assert_allclose(a[:4], b[:4], atol=0)
-    np.testing.assert_allclose(a[4:], c[4:], atol=0)
+    for P in (a, c):  # same translation gradients: the centre moves the same distance
+        R, t = scenes.pose_rt(P)
+        assert np.linalg.norm(-R.T @ t + R0.T @ t0) == pytest.approx(np.sqrt(3) * p.lr_trans, rel=1e-6)
 
 
 def test_adam_converges_on_quadratic():
