@@ -1,7 +1,8 @@
 """Benchmark: fwd+bwd render Mpix/s and tracking iterations/s of the differentiable
 3D-Gaussian rasterizer on the 640 x 480, 200k-Gaussian room (plain FP32 attributes).
 
-One step = one full tracking iteration of the hot path on one frame: projection and
+One step = one full tracking iteration of the hot path on one frame (every 40 steps the
+pose restarts from the frame's start pose, as tracking a new frame would): projection and
 tile binning, per-tile depth sort, front-to-back compositing of colour / depth /
 silhouette with the fused combined loss, reverse compositing, chain rule to the pose,
 FP64 pose reduction and the decoupled Adam update (all CUDA kernels of this library,
@@ -32,13 +33,21 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+bwd render Mpix/s & tracking iters/s (640×480, 200k Gauss) vs plain"
 WORKLOAD = "tracking 640x480, 200k room Gaussians, fp32 attributes"
 N_GAUSS = 200_000
+# FP32 operations (an FMA counts 2, an ex2 or reciprocal 1) of one differentiated
+# (pixel, Gaussian) pair in the pose-gradient backward and of one contributing pair in
+# the forward: the per-unit algorithmic work of the two compositing kernels.
+FLOP_BWD_PAIR = 58
+FLOP_FWD_PAIR = 23
+N_SM, FP32_LANES = 152, 128  # GB300: FP32 FMA lanes per SM
+ITERS_PER_FRAME = 40  # tracking iterations per frame (the 640 x 480 tracking workload); the
+                      # pose and Adam state restart from the frame's start pose every 40 steps
 
 
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
@@ -79,6 +88,9 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:  # first sample before timing starts
+                time.sleep(0.02)
         except OSError:
             self.proc = None
         return self
@@ -214,21 +226,33 @@ def main():
     def step():
         gs.gs_track_step(R.ctx, prob, gt.c(), targets, poses, adam, loss, 1, ws, nb, stream)
 
+    gs.gs_set_profiling(R.ctx, True)  # CUDA-event markers between the library's kernels
     for _ in range(a.warmup):
         step()
-    R.sync(stream)
+    poses.copy_(torch.tensor(np.asarray(start)[None], dtype=torch.float64, device=dev))
+    adam.zero_()
     counts = R.sync(stream)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    kern_ms, contrib = {}, {"fwd_evals": 0, "fwd_contrib": 0, "bwd_evals": 0, "bwd_contrib": 0}
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    start_pose = poses.clone()
     with ClockSampler(local) as clk:
         for k in range(a.steps):
+            if k % ITERS_PER_FRAME == 0:  # a new frame: tracking restarts from the start pose
+                poses.copy_(start_pose)
+                adam.zero_()
             flush.fill_(float(k))
             starts[k].record(stream)
             step()
             ends[k].record(stream)
+            for name, ms in gs.gs_kernel_times(R.ctx):  # waits for this step's markers
+                kern_ms[name] = kern_ms.get(name, 0.0) + ms
+            st_k, c_k = gs.gs_sync_status(R.ctx, stream)
+            for key in contrib:
+                contrib[key] += getattr(c_k, key)
         torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
@@ -251,6 +275,9 @@ def main():
     h_out = torch.empty(8, dtype=torch.float64).pin_memory()
     e2e_s, e2e_e = [], []
     for k in range(a.warmup + a.steps):
+        if k % ITERS_PER_FRAME == 0:
+            poses.copy_(start_pose)
+            adam.zero_()
         flush.fill_(float(k))
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
@@ -271,6 +298,21 @@ def main():
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_mpix = world * a.steps * pix / (float(te.item()) / 1e3) / 1e6
 
+    # roofline of the dominant kernel, from its CUDA-event time inside the timed steps
+    avg = {k: v / a.steps for k, v in kern_ms.items()}
+    dominant = max(avg, key=avg.get)
+    clocks = clk.summary()
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak_tflops = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    per_pair = {"k_backward": (FLOP_BWD_PAIR, contrib["bwd_contrib"]), "k_forward": (FLOP_FWD_PAIR, contrib["fwd_contrib"])}
+    roofline = None
+    if dominant in per_pair:
+        f, units = per_pair[dominant]
+        achieved = f * units / a.steps / (avg[dominant] / 1e3) / 1e12
+        roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                    "work": f"{f} FP32 FLOP per differentiated (pixel, Gaussian) pair x {units // a.steps} pairs",
+                    "peak_from": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz (median SM clock, timed region)"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": mpix, "unit": "Mpix/s", "n_gpus": world, "steps": a.steps,
@@ -278,13 +320,17 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (room scene; ray-cast RGB-D frame)",
             "config": {"workload": WORKLOAD, "width": cam.width, "height": cam.height, "gaussians": N_GAUSS,
                        "pairs": int(counts.n_pairs), "records": int(counts.n_records),
+                       "max_tile_pairs": int(counts.max_tile),
                        "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "tracking_iters_per_s": iters_per_s,
             "e2e": {"value": e2e_mpix, "unit": "Mpix/s",
                     "h2d_bytes_per_step": int(h_rgb.numel() * 4 + h_depth.numel() * 4 + h_prior.numel() * 4),
                     "d2h_bytes_per_step": 64},
             "gpu_launches": a.steps * 7,
-            "clocks": clk.summary(),
+            "clocks": clocks,
+            "roofline": roofline,
+            "kernels_us": {k: round(1e3 * v, 2) for k, v in sorted(avg.items(), key=lambda kv: -kv[1])},
+            "pairs_per_step": {k: v // a.steps for k, v in contrib.items()},
         }
         if world == 1 and not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, cam, start, rgb, depth, prior, a.cpu_sample_seconds)

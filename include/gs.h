@@ -121,6 +121,12 @@ typedef struct {
     int64_t n_pairs;   /* (Gaussian, tile) pairs of the last projection                */
     uint32_t err_flags;/* bit 0 record overflow, bit 1 pair overflow, bit 2 timeout    */
     uint32_t reserved;
+    int64_t fwd_evals;   /* (pixel, Gaussian) footprints evaluated by the last forward    */
+    int64_t fwd_contrib; /* ... of which contributed to Eqs. 2-4                          */
+    int64_t bwd_evals;   /* footprints evaluated by the last backward                     */
+    int64_t bwd_contrib; /* ... of which were differentiated                              */
+    uint32_t max_tile;   /* longest per-tile list of the last projection                  */
+    uint32_t reserved2;
 } gs_counts;
 
 /* ------------------------------------------------------------------ context */
@@ -182,7 +188,9 @@ gs_status gs_forward(gs_ctx *ctx, const gs_targets *targets, float *rgb, float *
  * n_views x 6 doubles, may be NULL) is OVERWRITTEN with (d theta, d t) per view, reduced
  * in FP64: theta turns the camera about its own centre (camera-frame points
  * x_c <- Exp(theta) x_c) and t shifts them (x_c <- x_c + t).
- * Errors: INVALID_ARG (partly NULL upstream), STATE, CUDA. */
+ * One gs_backward per gs_project (the projection clears the per-Gaussian accumulators).
+ * Errors: INVALID_ARG (partly NULL upstream), STATE (no projection, or its gradients
+ * were already taken), CUDA. */
 gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, const float *d_sil,
                       gs_gaussians_grad *grads, double *pose_grad, void *stream);
 
@@ -207,6 +215,25 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
  * device latched one since the last call (results of that call are invalid), STATE
  * when no workspace is bound, CUDA on a runtime error. */
 gs_status gs_sync_status(gs_ctx *ctx, void *stream, gs_counts *counts);
+
+/* ------------------------------------------------------------------ instrumentation */
+
+/* Per-kernel device time of the last enqueued work, for profiling. */
+typedef struct {
+    char name[24]; /* kernel (k_project, k_emit, k_tile_sort, k_forward, k_backward, k_bproject) */
+    float ms;      /* CUDA-event time from the end of the previous kernel to the end of this one */
+} gs_kernel_time;
+
+/* Enable (1) or disable (0) CUDA-event markers between the library's kernels on the
+ * stream they are launched on (also inside the tracking graph, as event nodes).  Off by
+ * default; events are created once per context.  Errors: CUDA. */
+gs_status gs_set_profiling(gs_ctx *ctx, int32_t enable);
+
+/* Synchronise on the last marker and return the per-kernel times of the work enqueued
+ * by the last gs_project / gs_forward / gs_backward sequence or gs_track_step call (all
+ * iterations).  out (host, cap entries) receives min(cap, available) entries; *count the
+ * number available.  Errors: STATE (profiling off or nothing recorded), CUDA. */
+gs_status gs_kernel_times(gs_ctx *ctx, gs_kernel_time *out, int32_t cap, int32_t *count);
 
 #ifdef __cplusplus
 }

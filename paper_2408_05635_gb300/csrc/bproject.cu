@@ -13,10 +13,10 @@
 // own centre (x_c <- Exp(theta) x_c, i.e. W <- Exp(theta) W and t <- Exp(theta) t) and the
 // translation shifts it (x_c <- x_c + t).  d t = dx_c and
 // d theta = x_c x dx_c + axial(dM M^T) with axial(P) = (P21 - P12, P02 - P20, P10 - P01).
-// The per-Gaussian 6-vectors are summed per block in FP64, written as partials, and the
-// last block of every view reduces them in a fixed order; in tracking mode the same
-// block applies the decoupled Adam step in FP64 (separate moments for theta and t;
-// R <- Exp(-step_theta) R, t <- Exp(-step_theta) t - step_t).
+// The per-record 6-vectors are summed over the warp in FP32 (at most 32 terms) and then
+// accumulated per view in FP64; the last block to finish reads the FP64 sums and, in
+// tracking mode, applies the decoupled Adam step in FP64 (separate moments for theta
+// and t; R <- Exp(-step_theta) R, t <- Exp(-step_theta) t - step_t).
 #include "gs_internal.cuh"
 
 namespace gsk {
@@ -74,212 +74,212 @@ __device__ void adam_update(double *pose, double *st, const double g[6], const S
     pose[6] = r20 * t0 + r21 * t1 + r22 * t2 - step[5];
 }
 
+// Butterfly reduce-scatter of 8 values over the warp (9 shuffles); afterwards lanes with
+// (lane & 3) == 0 hold the full warp sum of value `idx`.
+__device__ __forceinline__ float warp_reduce8(float (&v)[8], int lane, int &idx) {
+    idx = 0;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        const int mask = 16 >> s, w = 4 >> s;
+        const bool up = (lane & mask) != 0;
+#pragma unroll
+        for (int k = 0; k < w; ++k) {
+            const float send = up ? v[k] : v[k + w];
+            const float keep = up ? v[k + w] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+        }
+        if (up) idx += w;
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+
+// One thread per visible record (compact, so no idle lanes for culled Gaussians).
 template <int DT, bool PARAMS>
 __global__ void __launch_bounds__(kBlock) k_bproject(BprojLaunch L) {
-    const int v = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    __shared__ float sRt[12];
-    __shared__ ViewInfo sv;
-    __shared__ uint32_t s_words[kMaskWords];
-    __shared__ double s_red[kMaskWords][6];
+    const int tid = threadIdx.x, lane = tid & 31;
     __shared__ int s_last;
-    const size_t cell = (size_t)v * L.d.nblk + b;
-    if (tid == 0) {
-        load_pose(L.poses_in + 7 * v, sRt);
-        sv = L.ws.views[v];
-    }
-    if (tid < kMaskWords) s_words[tid] = L.ws.vis_mask[cell * kMaskWords + tid];
-    __syncthreads();
-    const uint32_t word = s_words[warp];
-    const bool vis = (word >> lane) & 1u;
-    uint32_t rank = __popc(word & ((1u << lane) - 1u));
-    for (int w = 0; w < warp; ++w) rank += __popc(s_words[w]);
-    const uint32_t rec = L.ws.chunk_start[cell] + rank;
-    const int64_t i = (int64_t)b * kBlock + tid;
-    float p6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (vis && rec < L.d.rec_cap && i < L.d.n) {
-        const ViewInfo vi = sv;
-        const RecGrad gg = L.ws.rec_grad[rec];
-        const float4 Bq = L.ws.rec[rec].b;  // conic the compositors used
-        const float mx = __ldg(L.g.means + 3 * i), my = __ldg(L.g.means + 3 * i + 1), mz = __ldg(L.g.means + 3 * i + 2);
-        const float x = cam_coord(sRt, 0, mx, my, mz);
-        const float y = cam_coord(sRt, 1, mx, my, mz);
-        const float z = cam_coord(sRt, 2, mx, my, mz);
-        const float q0 = ld_attr<DT>(L.g.quats, 4 * i), q1 = ld_attr<DT>(L.g.quats, 4 * i + 1);
-        const float q2 = ld_attr<DT>(L.g.quats, 4 * i + 2), q3 = ld_attr<DT>(L.g.quats, 4 * i + 3);
-        const float qn2 = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
-        const float qinv = rsqrtf(qn2);
-        const float w = q0 * qinv, qx = q1 * qinv, qy = q2 * qinv, qz = q3 * qinv;
-        float Rg[9];
-        quat_to_rot(w, qx, qy, qz, Rg);
-        float s[3];
-        s[0] = expf(ld_attr<DT>(L.g.log_scales, 3 * i));
-        s[1] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 1));
-        s[2] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 2));
-        float Bm[9], M[9];  // B = Rg diag(s), M = W B
+    const uint32_t nrec = min(L.ws.hdr->n_rec, L.d.rec_cap);
+    const bool want_pose = L.pose_grad || L.poses_out;
+    for (uint32_t base = blockIdx.x * kBlock; base < nrec; base += gridDim.x * kBlock) {
+        const uint32_t rec = base + tid;
+        float p6[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int view = -1;
+        if (rec < nrec) {
+            const Rec rr = L.ws.rec[rec];
+            const RecGrad gg = L.ws.rec_grad[rec];
+            const uint32_t gv = __float_as_uint(rr.c.w);
+            const int64_t i = (int64_t)((uint64_t)gv % (uint64_t)L.d.n);
+            view = (int)((uint64_t)gv / (uint64_t)L.d.n);
+            const ViewInfo vi = L.ws.views[view];
+            float sRt[12];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+            for (int k = 0; k < 12; ++k) sRt[k] = __ldg(L.ws.view_rt + 12 * view + k);
+            const float4 Bq = rr.b;  // conic the compositors used
+            const float mx = __ldg(L.g.means + 3 * i), my = __ldg(L.g.means + 3 * i + 1), mz = __ldg(L.g.means + 3 * i + 2);
+            const float x = cam_coord(sRt, 0, mx, my, mz);
+            const float y = cam_coord(sRt, 1, mx, my, mz);
+            const float z = cam_coord(sRt, 2, mx, my, mz);
+            const float q0 = ld_attr<DT>(L.g.quats, 4 * i), q1 = ld_attr<DT>(L.g.quats, 4 * i + 1);
+            const float q2 = ld_attr<DT>(L.g.quats, 4 * i + 2), q3 = ld_attr<DT>(L.g.quats, 4 * i + 3);
+            const float qn2 = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
+            const float qinv = rsqrtf(qn2);
+            const float w = q0 * qinv, qx = q1 * qinv, qy = q2 * qinv, qz = q3 * qinv;
+            float Rg[9];
+            quat_to_rot(w, qx, qy, qz, Rg);
+            float s[3];
+            s[0] = expf(ld_attr<DT>(L.g.log_scales, 3 * i));
+            s[1] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 1));
+            s[2] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 2));
+            float Bm[9], M[9];  // B = Rg diag(s), M = W B
 #pragma unroll
-            for (int c = 0; c < 3; ++c) Bm[3 * r + c] = Rg[3 * r + c] * s[c];
+            for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) Bm[3 * r + c] = Rg[3 * r + c] * s[c];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                M[3 * r + c] = sRt[3 * r] * Bm[c] + sRt[3 * r + 1] * Bm[3 + c] + sRt[3 * r + 2] * Bm[6 + c];
-        const float iz = 1.f / z, iz2 = iz * iz;
-        const float J00 = vi.fx * iz, J02 = -vi.fx * x * iz2;
-        const float J11 = vi.fy * iz, J12 = -vi.fy * y * iz2;
-        float N0[3], N1[3];
+            for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            N0[c] = J00 * M[c] + J02 * M[6 + c];
-            N1[c] = J11 * M[3 + c] + J12 * M[6 + c];
-        }
-        // G = -Q Gq Q with Gq = [[da, db/2], [db/2, dc]] and Q = [[a, b], [b, c]]
-        const float qa = Bq.x, qb = Bq.y, qc = Bq.z;
-        const float ga = gg.g1.x, gb = 0.5f * gg.g1.y, gc = gg.g1.z;
-        const float t00 = qa * ga + qb * gb, t01 = qa * gb + qb * gc;
-        const float t10 = qb * ga + qc * gb, t11 = qb * gb + qc * gc;
-        const float G00 = -(t00 * qa + t01 * qb), G01 = -(t00 * qb + t01 * qc), G11 = -(t10 * qb + t11 * qc);
-        float dN0[3], dN1[3];
+                for (int c = 0; c < 3; ++c)
+                    M[3 * r + c] = sRt[3 * r] * Bm[c] + sRt[3 * r + 1] * Bm[3 + c] + sRt[3 * r + 2] * Bm[6 + c];
+            const float iz = 1.f / z, iz2 = iz * iz;
+            const float J00 = vi.fx * iz, J02 = -vi.fx * x * iz2;
+            const float J11 = vi.fy * iz, J12 = -vi.fy * y * iz2;
+            float N0[3], N1[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            dN0[c] = 2.f * (G00 * N0[c] + G01 * N1[c]);
-            dN1[c] = 2.f * (G01 * N0[c] + G11 * N1[c]);
-        }
-        // dJ = dN M^T (only J00, J02, J11, J12 are variables); dM = J^T dN
-        const float dJ00 = dN0[0] * M[0] + dN0[1] * M[1] + dN0[2] * M[2];
-        const float dJ02 = dN0[0] * M[6] + dN0[1] * M[7] + dN0[2] * M[8];
-        const float dJ11 = dN1[0] * M[3] + dN1[1] * M[4] + dN1[2] * M[5];
-        const float dJ12 = dN1[0] * M[6] + dN1[1] * M[7] + dN1[2] * M[8];
-        float dM[9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            dM[c] = J00 * dN0[c];
-            dM[3 + c] = J11 * dN1[c];
-            dM[6 + c] = J02 * dN0[c] + J12 * dN1[c];
-        }
-        const float dmu_x = gg.g0.x, dmu_y = gg.g0.y, dd = gg.g0.z;
-        const float fx = vi.fx, fy = vi.fy;
-        const float dxc0 = dmu_x * J00 - dJ02 * fx * iz2;
-        const float dxc1 = dmu_y * J11 - dJ12 * fy * iz2;
-        const float dxc2 = dmu_x * J02 + dmu_y * J12 + dd - dJ00 * fx * iz2 + dJ02 * 2.f * fx * x * iz2 * iz -
-                           dJ11 * fy * iz2 + dJ12 * 2.f * fy * y * iz2 * iz;
-        // pose: translation and rotation (mean and covariance parts)
-        p6[3] = dxc0;
-        p6[4] = dxc1;
-        p6[5] = dxc2;
-        float P[9];  // dM M^T
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) P[3 * r + c] = dM[3 * r] * M[3 * c] + dM[3 * r + 1] * M[3 * c + 1] + dM[3 * r + 2] * M[3 * c + 2];
-        p6[0] = y * dxc2 - z * dxc1 + (P[7] - P[5]);
-        p6[1] = z * dxc0 - x * dxc2 + (P[2] - P[6]);
-        p6[2] = x * dxc1 - y * dxc0 + (P[3] - P[1]);
-        if constexpr (PARAMS) {
-            const gs_gaussians_grad &G = L.grads;
-            if (G.means) {
-                atomicAdd(G.means + 3 * i, sRt[0] * dxc0 + sRt[3] * dxc1 + sRt[6] * dxc2);
-                atomicAdd(G.means + 3 * i + 1, sRt[1] * dxc0 + sRt[4] * dxc1 + sRt[7] * dxc2);
-                atomicAdd(G.means + 3 * i + 2, sRt[2] * dxc0 + sRt[5] * dxc1 + sRt[8] * dxc2);
+            for (int c = 0; c < 3; ++c) {
+                N0[c] = J00 * M[c] + J02 * M[6 + c];
+                N1[c] = J11 * M[3 + c] + J12 * M[6 + c];
             }
-            if (G.quats || G.log_scales) {
-                float dB[9];  // W^T dM
+            // G = -Q Gq Q with Gq = [[da, db/2], [db/2, dc]] and Q = [[a, b], [b, c]]
+            const float qa = Bq.x, qb = Bq.y, qc = Bq.z;
+            const float ga = gg.g1.x, gb = 0.5f * gg.g1.y, gc = gg.g1.z;
+            const float t00 = qa * ga + qb * gb, t01 = qa * gb + qb * gc;
+            const float t10 = qb * ga + qc * gb, t11 = qb * gb + qc * gc;
+            const float G00 = -(t00 * qa + t01 * qb), G01 = -(t00 * qb + t01 * qc), G11 = -(t10 * qb + t11 * qc);
+            float dN0[3], dN1[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dN0[c] = 2.f * (G00 * N0[c] + G01 * N1[c]);
+                dN1[c] = 2.f * (G01 * N0[c] + G11 * N1[c]);
+            }
+            // dJ = dN M^T (only J00, J02, J11, J12 are variables); dM = J^T dN
+            const float dJ00 = dN0[0] * M[0] + dN0[1] * M[1] + dN0[2] * M[2];
+            const float dJ02 = dN0[0] * M[6] + dN0[1] * M[7] + dN0[2] * M[8];
+            const float dJ11 = dN1[0] * M[3] + dN1[1] * M[4] + dN1[2] * M[5];
+            const float dJ12 = dN1[0] * M[6] + dN1[1] * M[7] + dN1[2] * M[8];
+            float dM[9];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dM[c] = J00 * dN0[c];
+                dM[3 + c] = J11 * dN1[c];
+                dM[6 + c] = J02 * dN0[c] + J12 * dN1[c];
+            }
+            const float dmu_x = gg.g0.x, dmu_y = gg.g0.y, dd = gg.g0.z;
+            const float fx = vi.fx, fy = vi.fy;
+            const float dxc0 = dmu_x * J00 - dJ02 * fx * iz2;
+            const float dxc1 = dmu_y * J11 - dJ12 * fy * iz2;
+            const float dxc2 = dmu_x * J02 + dmu_y * J12 + dd - dJ00 * fx * iz2 + dJ02 * 2.f * fx * x * iz2 * iz -
+                               dJ11 * fy * iz2 + dJ12 * 2.f * fy * y * iz2 * iz;
+            if (want_pose) {
+                // translation, and rotation about the camera centre (mean and covariance parts)
+                float P[9];  // dM M^T
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
-                        dB[3 * r + c] = sRt[r] * dM[c] + sRt[3 + r] * dM[3 + c] + sRt[6 + r] * dM[6 + c];
-                if (G.log_scales) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float ds = dB[c] * Rg[c] + dB[3 + c] * Rg[3 + c] + dB[6 + c] * Rg[6 + c];
-                        atomicAdd(G.log_scales + 3 * i + c, ds * s[c]);
-                    }
+                        P[3 * r + c] = dM[3 * r] * M[3 * c] + dM[3 * r + 1] * M[3 * c + 1] + dM[3 * r + 2] * M[3 * c + 2];
+                p6[0] = y * dxc2 - z * dxc1 + (P[7] - P[5]);
+                p6[1] = z * dxc0 - x * dxc2 + (P[2] - P[6]);
+                p6[2] = x * dxc1 - y * dxc0 + (P[3] - P[1]);
+                p6[3] = dxc0;
+                p6[4] = dxc1;
+                p6[5] = dxc2;
+            }
+            if constexpr (PARAMS) {
+                const gs_gaussians_grad &G = L.grads;
+                if (G.means) {
+                    atomicAdd(G.means + 3 * i, sRt[0] * dxc0 + sRt[3] * dxc1 + sRt[6] * dxc2);
+                    atomicAdd(G.means + 3 * i + 1, sRt[1] * dxc0 + sRt[4] * dxc1 + sRt[7] * dxc2);
+                    atomicAdd(G.means + 3 * i + 2, sRt[2] * dxc0 + sRt[5] * dxc1 + sRt[8] * dxc2);
                 }
-                if (G.quats) {
-                    float dRg[9];
+                if (G.quats || G.log_scales) {
+                    float dB[9];  // W^T dM
 #pragma unroll
                     for (int r = 0; r < 3; ++r)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) dRg[3 * r + c] = dB[3 * r + c] * s[c];
-                    float dqn[4];
-                    rot_grad_to_quat(w, qx, qy, qz, dRg, dqn);
-                    const float pr = dqn[0] * w + dqn[1] * qx + dqn[2] * qy + dqn[3] * qz;
-                    atomicAdd(G.quats + 4 * i, (dqn[0] - w * pr) * qinv);
-                    atomicAdd(G.quats + 4 * i + 1, (dqn[1] - qx * pr) * qinv);
-                    atomicAdd(G.quats + 4 * i + 2, (dqn[2] - qy * pr) * qinv);
-                    atomicAdd(G.quats + 4 * i + 3, (dqn[3] - qz * pr) * qinv);
+                        for (int c = 0; c < 3; ++c)
+                            dB[3 * r + c] = sRt[r] * dM[c] + sRt[3 + r] * dM[3 + c] + sRt[6 + r] * dM[6 + c];
+                    if (G.log_scales) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float ds = dB[c] * Rg[c] + dB[3 + c] * Rg[3 + c] + dB[6 + c] * Rg[6 + c];
+                            atomicAdd(G.log_scales + 3 * i + c, ds * s[c]);
+                        }
+                    }
+                    if (G.quats) {
+                        float dRg[9];
+#pragma unroll
+                        for (int r = 0; r < 3; ++r)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) dRg[3 * r + c] = dB[3 * r + c] * s[c];
+                        float dqn[4];
+                        rot_grad_to_quat(w, qx, qy, qz, dRg, dqn);
+                        const float pr = dqn[0] * w + dqn[1] * qx + dqn[2] * qy + dqn[3] * qz;
+                        atomicAdd(G.quats + 4 * i, (dqn[0] - w * pr) * qinv);
+                        atomicAdd(G.quats + 4 * i + 1, (dqn[1] - qx * pr) * qinv);
+                        atomicAdd(G.quats + 4 * i + 2, (dqn[2] - qy * pr) * qinv);
+                        atomicAdd(G.quats + 4 * i + 3, (dqn[3] - qz * pr) * qinv);
+                    }
+                }
+                if (G.opacity_logits) {
+                    const float o = rr.a.w;
+                    atomicAdd(G.opacity_logits + i, gg.g0.w * o * (1.f - o));
+                }
+                if (G.rgb) {
+                    atomicAdd(G.rgb + 3 * i, gg.g2.x);
+                    atomicAdd(G.rgb + 3 * i + 1, gg.g2.y);
+                    atomicAdd(G.rgb + 3 * i + 2, gg.g2.z);
                 }
             }
-            if (G.opacity_logits) {
-                const float o = L.ws.rec[rec].a.w;
-                atomicAdd(G.opacity_logits + i, gg.g0.w * o * (1.f - o));
-            }
-            if (G.rgb) {
-                atomicAdd(G.rgb + 3 * i, gg.g2.x);
-                atomicAdd(G.rgb + 3 * i + 1, gg.g2.y);
-                atomicAdd(G.rgb + 3 * i + 2, gg.g2.z);
+        }
+        if (want_pose) {
+            // warp sum in FP32 (at most 32 terms), then FP64 accumulation per view
+            const int v0 = __shfl_sync(0xffffffffu, view, 0);
+            if (__all_sync(0xffffffffu, view == v0 || view < 0) && v0 >= 0) {
+                int slot;
+                const float sum = warp_reduce8(p6, lane, slot);
+                if ((lane & 3) == 0 && slot < 6 && sum != 0.f) atomicAdd(L.ws.pose_acc + 6 * v0 + slot, (double)sum);
+            } else if (view >= 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) atomicAdd(L.ws.pose_acc + 6 * view + k, (double)p6[k]);
             }
         }
     }
-    if (!L.pose_grad && !L.poses_out) return;  // uniform across the grid
-    // FP64 block reduction of the pose 6-vectors
-    double d6[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        d6[k] = (double)p6[k];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) d6[k] += __shfl_xor_sync(0xffffffffu, d6[k], off);
-    }
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) s_red[warp][k] = d6[k];
-    __syncthreads();
-    if (tid < 6) {
-        double acc = 0.0;
-        for (int w = 0; w < kMaskWords; ++w) acc += s_red[w][tid];
-        L.ws.pose_part[cell * 6 + tid] = acc;
-    }
+    if (!want_pose) return;  // uniform across the grid
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(L.ws.done_view + v, 1u) == (uint32_t)L.d.nblk - 1u;
+    if (tid == 0) s_last = atomicAdd(&L.ws.hdr->bp_done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // last block of this view: fixed-order reduction of the partials
-    double part[6] = {0, 0, 0, 0, 0, 0};
-    for (int bb = tid; bb < L.d.nblk; bb += kBlock) {
-        const double *src = L.ws.pose_part + ((size_t)v * L.d.nblk + bb) * 6;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) part[k] += __ldcg(src + k);
-    }
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) part[k] += __shfl_xor_sync(0xffffffffu, part[k], off);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) s_red[warp][k] = part[k];
-    __syncthreads();
-    if (tid == 0) {
+    // last block: per-view pose gradient, loss copy and (tracking) the decoupled Adam step
+    for (int v = tid; v < L.d.V; v += kBlock) {
         double g[6];
-        for (int k = 0; k < 6; ++k) {
-            g[k] = 0.0;
-            for (int w = 0; w < kMaskWords; ++w) g[k] += s_red[w][k];
-        }
+        for (int k = 0; k < 6; ++k) g[k] = __ldcg(L.ws.pose_acc + 6 * v + k);
         if (L.pose_grad)
             for (int k = 0; k < 6; ++k) L.pose_grad[6 * v + k] = g[k];
         if (L.loss_out) L.loss_out[v] = __ldcg(L.ws.loss + v);
         if (L.poses_out) adam_update(L.poses_out + 7 * v, L.adam + 16 * v, g, L.s);
-        L.ws.done_view[v] = 0;
     }
 }
 
 cudaError_t launch_bproject(const BprojLaunch &L, cudaStream_t st) {
-    dim3 grid(L.d.nblk, L.d.V);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t want = (L.d.rec_cap + kBlock - 1) / kBlock;
+    const uint32_t grid = max(1u, min(want, (uint32_t)(sms > 0 ? sms * 4 : 512)));
     const bool params = L.grads.means || L.grads.quats || L.grads.log_scales || L.grads.opacity_logits || L.grads.rgb;
 #define GS_BPROJ(DT)                                                   \
     if (params)                                                        \

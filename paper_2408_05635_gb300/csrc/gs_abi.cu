@@ -1,6 +1,8 @@
 // gs_abi.cu -- the C ABI declared in include/gs.h: context, workspace layout, launch
 // sequencing and the CUDA-graph tracking loop.  No device memory is allocated here:
 // every device buffer, the workspace included, belongs to the caller.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -18,9 +20,8 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t err, hdr, loss, done_view, tile_cnt, zero_end;
-    size_t views, tile_start, cursor, chunk_start, vis_mask, rec, rec_grad, keys, sorted, t_final, n_last,
-        upstream, pose_part, total;
+    size_t err, hdr, loss, pose_acc, tile_cnt, zero_end;
+    size_t views, view_rt, tile_start, cursor, rec, rec_grad, keys, sorted, t_final, n_last, upstream, total;
 };
 
 struct Problem {
@@ -38,9 +39,11 @@ struct GraphKey {
     int iters = 0;
     std::vector<ViewInfo> views;
     uint32_t rec_cap = 0, pair_cap = 0;
+    bool profiling = false;
     bool operator==(const GraphKey &o) const {
         if (ws != o.ws || ws_bytes != o.ws_bytes || n != o.n || dtype != o.dtype || iters != o.iters ||
-            rec_cap != o.rec_cap || pair_cap != o.pair_cap || views.size() != o.views.size())
+            rec_cap != o.rec_cap || pair_cap != o.pair_cap || profiling != o.profiling ||
+            views.size() != o.views.size())
             return false;
         for (int k = 0; k < 12; ++k)
             if (ptrs[k] != o.ptrs[k]) return false;
@@ -63,10 +66,17 @@ struct gs_ctx {
     int dtype = 0;
     const double *poses = nullptr;
     bool have_loss = false;
+    bool grads_used = false;  // the record accumulators were consumed by a gs_backward
     // tracking graph
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     GraphKey graph_key;
+    // profiling markers: events[k] ends kernel names[k - 1] (events[0] is the start)
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+    std::vector<const char *> names;
+    size_t n_marks = 0;
+    std::vector<const char *> graph_names;  // markers baked into the tracking graph
 };
 
 namespace {
@@ -81,6 +91,25 @@ gs_status cuda_fail(gs_ctx *ctx, cudaError_t e, const char *where) {
     return GS_ERR_CUDA;
 }
 
+// Append a profiling marker: the end of kernel `name`, or (name NULL) the start of a
+// run of kernels.
+cudaError_t mark(gs_ctx *ctx, cudaStream_t st, const char *name) {
+    if (!ctx->profiling) return cudaSuccess;
+    if (ctx->n_marks == ctx->events.size()) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        ctx->events.push_back(ev);
+        ctx->names.push_back(nullptr);
+    }
+    const size_t k = ctx->n_marks++;
+    ctx->names[k] = name;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    return cap != cudaStreamCaptureStatusNone ? cudaEventRecordWithFlags(ctx->events[k], st, cudaEventRecordExternal)
+                                              : cudaEventRecord(ctx->events[k], st);
+}
+
 Settings settings_of(const gs_config &c) {
     Settings s;
     s.alpha_min = c.alpha_min;
@@ -89,6 +118,7 @@ Settings settings_of(const gs_config &c) {
     s.dilation = c.dilation;
     s.z_near = c.z_near;
     s.sil_thresh = c.sil_thresh;
+    s.log2_alpha_min = c.alpha_min > 0.f ? (float)std::log2((double)c.alpha_min) : -INFINITY;
     s.w_rgb = c.w_rgb;
     s.w_depth = c.w_depth;
     s.w_vis = c.w_vis;
@@ -137,12 +167,13 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
         vi.pix_base = (uint32_t)P;
         T += (uint64_t)vi.tiles_x * vi.tiles_y;
         P += (uint64_t)c.width * c.height;
-        if (T >= (1ull << 31) || 5 * P >= (1ull << 32))
+        if (T >= (1ull << 27) || 5 * P >= (1ull << 32))
             return fail(ctx, GS_ERR_INVALID_ARG, "too many pixels or tiles in one call");
         out.views[v] = vi;
     }
     d.T = (uint32_t)T;
     d.P = (uint32_t)P;
+    d.S = 1;
     out.d = d;
     Layout &L = out.lay;
     size_t o = 0;
@@ -155,14 +186,13 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     // zeroed before every projection: [hdr, zero_end)
     L.hdr = take(sizeof(DevHeader));
     L.loss = take(sizeof(double) * d.V);
-    L.done_view = take(sizeof(uint32_t) * d.V);
-    L.tile_cnt = take(sizeof(uint32_t) * (d.T + 1));
+    L.pose_acc = take(sizeof(double) * 6 * d.V);
+    L.tile_cnt = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
     L.zero_end = o;
     L.views = take(sizeof(ViewInfo) * d.V);
-    L.tile_start = take(sizeof(uint32_t) * (d.T + 1));
-    L.cursor = take(sizeof(uint32_t) * (d.T + 1));
-    L.chunk_start = take(sizeof(uint32_t) * (size_t)d.V * d.nblk);
-    L.vis_mask = take(sizeof(uint32_t) * (size_t)d.V * d.nblk * kMaskWords);
+    L.view_rt = take(sizeof(float) * 12 * d.V);
+    L.tile_start = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
+    L.cursor = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
     L.rec = take(sizeof(Rec) * (size_t)d.rec_cap);
     L.rec_grad = take(sizeof(RecGrad) * (size_t)d.rec_cap);
     L.keys = take(sizeof(unsigned long long) * (size_t)d.pair_cap);
@@ -170,7 +200,6 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     L.t_final = take(sizeof(float) * (size_t)d.P);
     L.n_last = take(sizeof(uint32_t) * (size_t)d.P);
     L.upstream = take(sizeof(float) * 5 * (size_t)d.P);
-    L.pose_part = take(sizeof(double) * 6 * (size_t)d.V * d.nblk);
     L.total = o;
     return GS_OK;
 }
@@ -181,13 +210,12 @@ WsPtrs ws_ptrs(void *base, const Layout &L) {
     w.err = reinterpret_cast<uint32_t *>(b + L.err);
     w.hdr = reinterpret_cast<DevHeader *>(b + L.hdr);
     w.loss = reinterpret_cast<double *>(b + L.loss);
-    w.done_view = reinterpret_cast<uint32_t *>(b + L.done_view);
+    w.pose_acc = reinterpret_cast<double *>(b + L.pose_acc);
     w.tile_cnt = reinterpret_cast<uint32_t *>(b + L.tile_cnt);
     w.views = reinterpret_cast<ViewInfo *>(b + L.views);
+    w.view_rt = reinterpret_cast<float *>(b + L.view_rt);
     w.tile_start = reinterpret_cast<uint32_t *>(b + L.tile_start);
     w.cursor = reinterpret_cast<uint32_t *>(b + L.cursor);
-    w.chunk_start = reinterpret_cast<uint32_t *>(b + L.chunk_start);
-    w.vis_mask = reinterpret_cast<uint32_t *>(b + L.vis_mask);
     w.rec = reinterpret_cast<Rec *>(b + L.rec);
     w.rec_grad = reinterpret_cast<RecGrad *>(b + L.rec_grad);
     w.keys = reinterpret_cast<unsigned long long *>(b + L.keys);
@@ -195,7 +223,6 @@ WsPtrs ws_ptrs(void *base, const Layout &L) {
     w.t_final = reinterpret_cast<float *>(b + L.t_final);
     w.n_last = reinterpret_cast<uint32_t *>(b + L.n_last);
     w.upstream = reinterpret_cast<float *>(b + L.upstream);
-    w.pose_part = reinterpret_cast<double *>(b + L.pose_part);
     return w;
 }
 
@@ -223,6 +250,7 @@ cudaError_t enqueue_project(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, voi
     const size_t from = clear_err ? pr.lay.err : pr.lay.hdr;
     cudaError_t e = cudaMemsetAsync(static_cast<char *>(ws) + from, 0, pr.lay.zero_end - from, st);
     if (e != cudaSuccess) return e;
+    if ((e = mark(ctx, st, nullptr)) != cudaSuccess) return e;
     ProjectLaunch P;
     P.ws = w;
     P.d = pr.d;
@@ -231,13 +259,16 @@ cudaError_t enqueue_project(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, voi
     P.dtype = dtype;
     P.poses = poses;
     if ((e = launch_project(P, st)) != cudaSuccess) return e;
-    return launch_emit(w, pr.d, st);
+    if ((e = mark(ctx, st, "k_project")) != cudaSuccess) return e;
+    if ((e = launch_emit(w, pr.d, st)) != cudaSuccess) return e;
+    return mark(ctx, st, "k_emit");
 }
 
 cudaError_t enqueue_forward(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, const gs_targets *t, float *rgb,
                             float *depth, float *sil, cudaStream_t st) {
     cudaError_t e = launch_tile_sort(w, pr.d, st);
     if (e != cudaSuccess) return e;
+    if ((e = mark(ctx, st, "k_tile_sort")) != cudaSuccess) return e;
     ForwardLaunch F;
     F.ws = w;
     F.d = pr.d;
@@ -248,7 +279,8 @@ cudaError_t enqueue_forward(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, con
     F.t_rgb = t ? t->rgb : nullptr;
     F.t_depth = t ? t->depth : nullptr;
     F.t_prior = t ? t->depth_prior : nullptr;
-    return launch_forward(F, st);
+    if ((e = launch_forward(F, st)) != cudaSuccess) return e;
+    return mark(ctx, st, "k_forward");
 }
 
 }  // namespace
@@ -314,6 +346,7 @@ gs_status gs_destroy(gs_ctx *ctx) {
     if (!ctx) return GS_OK;
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (cudaEvent_t ev : ctx->events) cudaEventDestroy(ev);
     delete ctx;
     return GS_OK;
 }
@@ -346,6 +379,7 @@ gs_status gs_project(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
     cudaError_t e = upload_views(pr, w, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "view upload");
     GaussPtrs gp{g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb};
+    ctx->n_marks = 0;
     e = enqueue_project(ctx, pr, w, ws, gp, g->dtype_attr, poses, true, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "projection");
     ctx->bound = true;
@@ -356,6 +390,7 @@ gs_status gs_project(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
     ctx->dtype = g->dtype_attr;
     ctx->poses = poses;
     ctx->have_loss = false;
+    ctx->grads_used = false;
     return GS_OK;
 }
 
@@ -387,6 +422,7 @@ gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, con
     if (given != 0 && given != 3) return fail(ctx, GS_ERR_INVALID_ARG, "give all three upstream maps or none");
     if (given == 0 && !ctx->have_loss)
         return fail(ctx, GS_ERR_STATE, "no upstream maps and no fused loss from gs_forward");
+    if (ctx->grads_used) return fail(ctx, GS_ERR_STATE, "one gs_backward per gs_project");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Problem &pr = ctx->prob;
     BackwardLaunch B;
@@ -402,8 +438,12 @@ gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, con
     const bool params = G.means || G.quats || G.log_scales || G.opacity_logits || G.rgb;
     B.pose_only = !(G.opacity_logits || G.rgb);
     cudaError_t e = launch_backward(B, s);
+    if (e == cudaSuccess) e = mark(ctx, s, "k_backward");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "backward");
-    if (!params && !pose_grad) return GS_OK;
+    if (!params && !pose_grad) {
+        ctx->grads_used = true;
+        return GS_OK;
+    }
     BprojLaunch J;
     J.ws = ctx->ws;
     J.d = pr.d;
@@ -417,7 +457,9 @@ gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, con
     J.loss_out = nullptr;
     J.grads = G;
     e = launch_bproject(J, s);
+    if (e == cudaSuccess) e = mark(ctx, s, "k_bproject");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "backward projection");
+    ctx->grads_used = true;
     return GS_OK;
 }
 
@@ -455,6 +497,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
             B.up_sil = w.upstream + 4u * pr.d.P;
             B.pose_only = true;
             if ((r = launch_backward(B, q)) != cudaSuccess) return r;
+            if ((r = mark(ctx, q, "k_backward")) != cudaSuccess) return r;
             BprojLaunch J;
             J.ws = w;
             J.d = pr.d;
@@ -468,6 +511,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
             J.loss_out = loss_hist ? loss_hist + (size_t)it * pr.d.V : nullptr;
             J.grads = gs_gaussians_grad{};
             if ((r = launch_bproject(J, q)) != cudaSuccess) return r;
+            if ((r = mark(ctx, q, "k_bproject")) != cudaSuccess) return r;
         }
         return cudaSuccess;
     };
@@ -478,6 +522,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream query");
+    ctx->n_marks = 0;
     if (cap != cudaStreamCaptureStatusNone) {
         // the caller is capturing: record the kernels into its graph directly
         e = enqueue_all(s);
@@ -495,6 +540,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
         key.views = pr.views;
         key.rec_cap = pr.d.rec_cap;
         key.pair_cap = pr.d.pair_cap;
+        key.profiling = ctx->profiling;
         if (!ctx->graph_exec || !(ctx->graph_key == key)) {
             if (ctx->graph_exec) {
                 cudaGraphExecDestroy(ctx->graph_exec);
@@ -521,7 +567,10 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
                 return cuda_fail(ctx, e, "graph instantiate");
             }
             ctx->graph_key = key;
+            ctx->graph_names.assign(ctx->names.begin(), ctx->names.begin() + ctx->n_marks);
         }
+        ctx->n_marks = ctx->graph_names.size();
+        std::copy(ctx->graph_names.begin(), ctx->graph_names.end(), ctx->names.begin());
         e = cudaGraphLaunch(ctx->graph_exec, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
     }
@@ -533,6 +582,37 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
     ctx->dtype = g->dtype_attr;
     ctx->poses = poses;
     ctx->have_loss = true;
+    ctx->grads_used = true;
+    return GS_OK;
+}
+
+gs_status gs_set_profiling(gs_ctx *ctx, int32_t enable) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    ctx->profiling = enable != 0;
+    ctx->n_marks = 0;
+    return GS_OK;
+}
+
+gs_status gs_kernel_times(gs_ctx *ctx, gs_kernel_time *out, int32_t cap, int32_t *count) {
+    if (!ctx || !count || cap < 0 || (cap > 0 && !out)) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->profiling || ctx->n_marks < 2) return fail(ctx, GS_ERR_STATE, "profiling off or nothing recorded");
+    cudaError_t e = cudaEventSynchronize(ctx->events[ctx->n_marks - 1]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event synchronize");
+    int32_t k = 0;
+    for (size_t m = 1; m < ctx->n_marks; ++m) {
+        if (!ctx->names[m]) continue;
+        if (k < cap) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ctx->events[m - 1], ctx->events[m]);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "event elapsed time");
+            std::snprintf(out[k].name, sizeof out[k].name, "%s", ctx->names[m]);
+            out[k].ms = ms;
+        }
+        ++k;
+    }
+    *count = k;
     return GS_OK;
 }
 
@@ -555,6 +635,11 @@ gs_status gs_sync_status(gs_ctx *ctx, void *stream, gs_counts *counts) {
         counts->n_pairs = (int64_t)h.n_pairs;
         counts->err_flags = err;
         counts->reserved = 0;
+        counts->fwd_evals = (int64_t)h.fwd_evals;
+        counts->fwd_contrib = (int64_t)h.fwd_contrib;
+        counts->bwd_evals = (int64_t)h.bwd_evals;
+        counts->bwd_contrib = (int64_t)h.bwd_contrib;
+        counts->max_tile = h.max_tile;
     }
     if (err & kErrTimeout) return fail(ctx, GS_ERR_TIMEOUT, "a bounded device wait expired");
     if (err & (kErrRecords | kErrPairs)) {

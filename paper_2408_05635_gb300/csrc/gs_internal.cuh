@@ -24,7 +24,7 @@ namespace gsk {
 constexpr int kTile = 16;                 // tile edge in pixels
 constexpr int kTilePix = kTile * kTile;   // pixels (= threads) per tile block
 constexpr int kBlock = 256;               // threads per Gaussian-parallel block
-constexpr int kMaskWords = kBlock / 32;   // visibility bitmask words per block
+constexpr int kWarps = kBlock / 32;       // warps per Gaussian-parallel block
 constexpr int kSortSmemCap = 4096;        // tiles up to this many keys sort in shared memory
 constexpr int kBatch = 256;               // Gaussians staged per compositing batch
 
@@ -45,7 +45,14 @@ struct DevHeader {
     uint32_t n_rec;     // records handed out by k_project (may exceed the capacity)
     uint32_t k1_done;   // k_project blocks finished (last-block scan)
     unsigned long long n_pairs;  // total (Gaussian, tile) pairs of the projection
-    unsigned long long pad[6];
+    uint32_t bp_done;   // k_bproject blocks finished (last-block pose update)
+    uint32_t pad0;
+    unsigned long long fwd_evals;    // (pixel, Gaussian) footprints evaluated by k_forward
+    unsigned long long fwd_contrib;  // ... of which contributed (alpha >= alpha_min, before the stop)
+    unsigned long long bwd_evals;    // footprints evaluated by k_backward
+    unsigned long long bwd_contrib;  // ... of which were differentiated
+    uint32_t max_tile;               // longest tile list of the projection
+    uint32_t pad1;
 };
 static_assert(sizeof(DevHeader) == 64, "DevHeader layout");
 
@@ -68,13 +75,12 @@ struct WsPtrs {
     uint32_t *err;         // ErrFlag bits, latched until gs_sync_status clears them
     DevHeader *hdr;
     double *loss;          // V, combined loss per view
-    uint32_t *done_view;   // V, k_bproject blocks finished per view
-    uint32_t *tile_cnt;    // T, per-tile pair counts (zero between projections)
+    double *pose_acc;      // V x 6, FP64 pose-gradient sums of the backward projection
+    uint32_t *tile_cnt;    // T x S, per-(tile, sub-bucket) pair counts (zero between projections)
     ViewInfo *views;       // V
-    uint32_t *tile_start;  // T + 1, exclusive scan of the counts
-    uint32_t *cursor;      // T, emission cursors
-    uint32_t *chunk_start; // V * nblk, first record of each k_project block
-    uint32_t *vis_mask;    // V * nblk * kMaskWords
+    float *view_rt;        // V x 12, FP32 rotation and translation of each pose (k_project)
+    uint32_t *tile_start;  // T x S + 1, exclusive scan of the counts
+    uint32_t *cursor;      // T x S, emission cursors
     Rec *rec;              // record_capacity
     RecGrad *rec_grad;     // record_capacity
     unsigned long long *keys;  // pair_capacity
@@ -82,7 +88,6 @@ struct WsPtrs {
     float *t_final;        // P, transmittance after the last contributor
     uint32_t *n_last;      // P, tile-list index + 1 of the last contributor
     float *upstream;       // 5 x P: dL/dC (planar like the images), dL/dD, dL/dS of the fused loss
-    double *pose_part;     // V * nblk * 6, per-block pose-gradient partial sums
 };
 
 struct Dims {
@@ -90,6 +95,10 @@ struct Dims {
     int32_t V;             // views
     int32_t nblk;          // ceil(n / kBlock)
     uint32_t T;            // tiles over all views
+    uint32_t S;            // sub-buckets per tile (power of two): a tile's pairs are counted and
+                           // placed through S counters picked by Gaussian index, so no single
+                           // counter takes every pair of a crowded tile; the S sub-ranges are
+                           // contiguous, so the tile's list is still one range
     uint32_t P;            // pixels over all views
     uint32_t rec_cap;
     uint32_t pair_cap;
@@ -97,6 +106,7 @@ struct Dims {
 
 struct Settings {
     float alpha_min, alpha_max, t_min, dilation, z_near, sil_thresh;
+    float log2_alpha_min;  // skip threshold on the footprint exponent (-inf when alpha_min = 0)
     float w_rgb, w_depth, w_vis, w_prior;
     double lr_rot, lr_trans, beta1, beta2, eps;
 };
@@ -105,6 +115,29 @@ struct GaussPtrs {
     const float *means;
     const void *quats, *log_scales, *logits, *rgb;
 };
+
+// Block-wide sum of two per-thread counters, added once per block to the header.
+__device__ __forceinline__ void count_pairs(uint32_t evals, uint32_t contrib, unsigned long long *e_out,
+                                            unsigned long long *c_out) {
+    __shared__ unsigned long long s_e, s_c;
+    if (threadIdx.x == 0) s_e = s_c = 0ull;
+    __syncthreads();
+    const uint32_t we = __reduce_add_sync(0xffffffffu, evals), wc = __reduce_add_sync(0xffffffffu, contrib);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_e, (unsigned long long)we);
+        atomicAdd(&s_c, (unsigned long long)wc);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(e_out, s_e);
+        atomicAdd(c_out, s_c);
+    }
+}
+
+// Fire-and-forget global add (no value returned, so the thread does not wait for it).
+__device__ __forceinline__ void red_add(uint32_t *p, uint32_t v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // ------------------------------------------------------------------ attribute loads
 
@@ -188,27 +221,30 @@ __device__ __forceinline__ void tile_rect(const ViewInfo &vi, float mx, float my
 // Does the support ellipse q(d) = a dx^2 + 2 b dx dy + c dy^2 <= dmax2 meet the
 // rectangle of pixel centres [x0, x1] x [y0, y1]?  The minimum of the convex form over
 // the rectangle is 0 when the centre is inside, otherwise it lies on an edge, where
-// it is a 1-D quadratic minimised in closed form.  Every operation is an explicitly
-// rounded intrinsic so k_project and k_emit take the identical decision.
+// it is a 1-D quadratic minimised in closed form (ia = 1/a, ic = 1/c).  The minimiser
+// only has to be close: the threshold carries a relative margin of 1e-3, far above the
+// FP32 error, so no tile with a pixel at alpha >= alpha_min is dropped.  Every operation
+// is an explicitly rounded intrinsic so k_project and k_emit take identical decisions.
 __device__ __forceinline__ float qform(float a, float b, float c, float dx, float dy) {
     return __fadd_rn(__fadd_rn(__fmul_rn(a, __fmul_rn(dx, dx)), __fmul_rn(2.f, __fmul_rn(b, __fmul_rn(dx, dy)))),
                      __fmul_rn(c, __fmul_rn(dy, dy)));
 }
 
-__device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float a, float b, float c, float dmax2,
-                                                   float x0, float x1, float y0, float y1) {
+__device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float a, float b, float c, float ia, float ic,
+                                                   float dmax2, float x0, float x1, float y0, float y1) {
     if (!(dmax2 < INFINITY)) return true;
     if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
     const float lx = __fsub_rn(x0, mx), hx = __fsub_rn(x1, mx);
     const float ly = __fsub_rn(y0, my), hy = __fsub_rn(y1, my);
+    const float nb = -b;
     float best = INFINITY;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const float dx = e ? hx : lx;  // vertical edge: dy free
-        const float dy = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, dx), c), ly), hy);
+        const float dx = e ? hx : lx;  // vertical edge: dy free, minimum at dy = -b dx / c
+        const float dy = fminf(fmaxf(__fmul_rn(__fmul_rn(nb, dx), ic), ly), hy);
         best = fminf(best, qform(a, b, c, dx, dy));
-        const float ey = e ? hy : ly;  // horizontal edge: dx free
-        const float ex = fminf(fmaxf(__fdiv_rn(-__fmul_rn(b, ey), a), lx), hx);
+        const float ey = e ? hy : ly;  // horizontal edge: dx free, minimum at dx = -b dy / a
+        const float ex = fminf(fmaxf(__fmul_rn(__fmul_rn(nb, ey), ia), lx), hx);
         best = fminf(best, qform(a, b, c, ex, ey));
     }
     return best <= __fadd_rn(__fmul_rn(dmax2, 1.001f), 1e-3f);
@@ -223,23 +259,74 @@ __device__ __forceinline__ void tile_bounds(const ViewInfo &vi, int tx, int ty, 
     y1 = (float)min(ty * kTile + kTile - 1, vi.height - 1);
 }
 
-// alpha of a staged record at pixel centre (px, py): alpha = min(alpha_max, o exp(power)),
-// power = -1/2 (a dx^2 + c dy^2) - b dx dy.  Shared by the forward and the backward so
-// both take bit-identical decisions (explicitly rounded operations, no contraction).
-struct AlphaEval {
-    float dx, dy, G, araw, alpha;
+// ------------------------------------------------------------------ per-tile footprint
+//
+// For a tile with origin (x0, y0) and tile-local pixel centre (u, v) = (px - x0, py - y0),
+// the footprint of Eq. 1, alpha_raw = o exp(power) with
+//   power = -1/2 [a dx^2 + 2 b dx dy + c dy^2],  (dx, dy) = (u - cu, v - cv),
+//   (cu, cv) = mu' - (x0, y0),
+// is evaluated as alpha_raw = 2^poly with
+//   poly = dx (kuu dx + kuv dy) + kvv dy^2 + lo,
+//   kuu = -L a / 2, kuv = -L b, kvv = -L c / 2, lo = log2 o,   L = log2(e),
+// so log2(e) and the opacity are folded into the staged coefficients; per pixel the
+// footprint costs two subtractions, five multiply-adds and one ex2.  (Expanding the
+// quadratic in u, v would save two operations but cancels catastrophically for sharp
+// Gaussians centred far from the tile origin.)  A Gaussian is skipped where
+// poly < log2(alpha_min).  Staging and evaluation use explicitly rounded operations and
+// are shared by the forward and the backward, so both take bit-identical decisions.
+constexpr float kLog2e = 1.4426950408889634f;
+
+struct Footprint {
+    float4 p0;  // (lo, cu, cv, kuu)
+    float2 p1;  // (kuv, kvv)
 };
 
-__device__ __forceinline__ AlphaEval eval_alpha(float px, float py, float4 A, float4 B, float alpha_max) {
-    AlphaEval r;
-    r.dx = __fsub_rn(px, A.x);
-    r.dy = __fsub_rn(py, A.y);
-    const float q = __fadd_rn(__fmul_rn(B.x, __fmul_rn(r.dx, r.dx)), __fmul_rn(B.z, __fmul_rn(r.dy, r.dy)));
-    const float power = __fsub_rn(__fmul_rn(-0.5f, q), __fmul_rn(B.y, __fmul_rn(r.dx, r.dy)));
-    r.G = __expf(power);
-    r.araw = __fmul_rn(A.w, r.G);
-    r.alpha = fminf(alpha_max, r.araw);
-    return r;
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ Footprint stage_footprint(const float4 A, const float4 B, float x0, float y0) {
+    Footprint f;
+    f.p0 = make_float4(lg2_approx(A.w), __fsub_rn(A.x, x0), __fsub_rn(A.y, y0), __fmul_rn(-0.5f * kLog2e, B.x));
+    f.p1 = make_float2(__fmul_rn(-kLog2e, B.y), __fmul_rn(-0.5f * kLog2e, B.z));
+    return f;
+}
+
+// Conservative support box of a staged Gaussian in tile-local pixel coordinates
+// (umin, umax, vmin, vmax): the ellipse poly >= log2(alpha_min) has half-extents
+// sqrt(dmax2 Sigma'_xx), sqrt(dmax2 Sigma'_yy), widened by a relative 1e-3 and 0.01 px so
+// FP32 rounding can never drop a pixel with alpha >= alpha_min.
+__device__ __forceinline__ float4 stage_box(const float4 B, float cu, float cv) {
+    const float detc = B.x * B.z - B.y * B.y;
+    if (!(detc > 0.f) || !(B.w < INFINITY)) return make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
+    const float hx = sqrtf(B.w * B.z / detc) * 1.001f + 0.01f;
+    const float hy = sqrtf(B.w * B.x / detc) * 1.001f + 0.01f;
+    return make_float4(cu - hx, cu + hx, cv - hy, cv + hy);
+}
+
+// Pixel layout of a 16 x 16 tile block: warp w owns the 8 x 4 patch at
+// ((w & 1) * 8, (w >> 1) * 4); lane l its pixel (l & 7, l >> 3) inside the patch.
+constexpr int kPatchW = 8, kPatchH = 4;
+
+struct PolyEval {
+    float dx, dy, poly;
+};
+
+__device__ __forceinline__ PolyEval eval_poly(float u, float v, float4 p0, float2 p1) {
+    PolyEval e;
+    e.dx = __fsub_rn(u, p0.y);
+    e.dy = __fsub_rn(v, p0.z);
+    const float t = __fmaf_rn(p0.w, e.dx, __fmul_rn(p1.x, e.dy));
+    e.poly = __fmaf_rn(e.dx, t, __fmaf_rn(__fmul_rn(p1.y, e.dy), e.dy, p0.x));
+    return e;
 }
 
 // Global tile -> view (binary search over the views' first tiles).
@@ -252,12 +339,13 @@ __device__ __forceinline__ int view_of_tile(const ViewInfo *views, int V, uint32
     return lo;
 }
 
-// Entries of a tile's list: [start, start + count) of the key / sorted arrays.  Clamped
-// to what k_emit actually wrote and to the pair capacity, so an overflow (latched in the
-// error flags) can never make a kernel read past its buffers.
+// Entries of a tile's list: [start, start + count) of the key / sorted arrays, clamped to
+// the pair capacity so an overflow (latched in the error flags) can never make a kernel
+// read past its buffers.  k_project and k_emit enumerate the same (record, tile) pairs,
+// so every slot of the range is written; record ids are bounds-checked where used.
 __device__ __forceinline__ uint32_t tile_entries(const WsPtrs &ws, const Dims &d, uint32_t tile, uint32_t &start) {
-    start = ws.tile_start[tile];
-    const uint32_t end = min(min(ws.cursor[tile], ws.tile_start[tile + 1]), d.pair_cap);
+    start = min(ws.tile_start[tile * d.S], d.pair_cap);
+    const uint32_t end = min(ws.tile_start[(tile + 1) * d.S], d.pair_cap);
     return end > start ? end - start : 0u;
 }
 

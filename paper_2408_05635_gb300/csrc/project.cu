@@ -10,23 +10,58 @@
 
 namespace gsk {
 
-// Tiles met by a record's support ellipse.  The pixel box is derived from the stored
-// conic (Sigma'_xx = c / det, Sigma'_yy = a / det of the conic) with explicitly rounded
-// operations, so k_project (counting) and k_emit (writing) enumerate the same tiles.
-template <class F>
-__device__ __forceinline__ void for_each_tile(const ViewInfo &vi, float4 A, float4 B, F &&f) {
+// Tile rectangle of a record's support ellipse.  The pixel box is derived from the
+// stored conic (Sigma'_xx = c / det, Sigma'_yy = a / det of the conic) with explicitly
+// rounded operations, so k_project (counting) and k_emit (writing) enumerate the same
+// tiles.  Returns false when the box misses the image.
+__device__ __forceinline__ bool record_rect(const ViewInfo &vi, float4 A, float4 B, int &tx0, int &tx1, int &ty0,
+                                            int &ty1) {
     const float detc = __fsub_rn(__fmul_rn(B.x, B.z), __fmul_rn(B.y, B.y));
-    if (!(detc > 0.f)) return;
+    if (!(detc > 0.f)) return false;
     const float hx = __fsqrt_rn(__fmul_rn(B.w, __fdiv_rn(B.z, detc)));
     const float hy = __fsqrt_rn(__fmul_rn(B.w, __fdiv_rn(B.x, detc)));
-    int tx0, tx1, ty0, ty1;
     tile_rect(vi, A.x, A.y, hx, hy, tx0, tx1, ty0, ty1);
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            float x0, x1, y0, y1;
-            tile_bounds(vi, tx, ty, x0, x1, y0, y1);
-            if (ellipse_meets_rect(A.x, A.y, B.x, B.y, B.z, B.w, x0, x1, y0, y1)) f(tx, ty);
+    return tx0 <= tx1 && ty0 <= ty1;
+}
+
+__device__ __forceinline__ bool tile_hit(const ViewInfo &vi, float4 A, float4 B, float ia, float ic, int tx, int ty) {
+    float x0, x1, y0, y1;
+    tile_bounds(vi, tx, ty, x0, x1, y0, y1);
+    return ellipse_meets_rect(A.x, A.y, B.x, B.y, B.z, ia, ic, B.w, x0, x1, y0, y1);
+}
+
+// The whole warp walks the tiles of one record at a time: the record's lane broadcasts
+// it and the 32 lanes split its tile rectangle, so one large Gaussian does not keep the
+// other 31 lanes waiting.  body(src lane, tile, record's A, record's tag) runs for every
+// tile the support meets.
+template <class Body>
+__device__ __forceinline__ void warp_tiles(uint32_t bits, const ViewInfo &vi_own, float4 A_own, float4 B_own,
+                                           int lane, const ViewInfo *views_or_null, int view_own, uint32_t tag_own,
+                                           Body &&body) {
+    while (bits) {
+        const int src = __ffs(bits) - 1;
+        bits &= bits - 1;
+        float4 A, B;
+        A.x = __shfl_sync(0xffffffffu, A_own.x, src);
+        A.y = __shfl_sync(0xffffffffu, A_own.y, src);
+        A.z = __shfl_sync(0xffffffffu, A_own.z, src);
+        A.w = __shfl_sync(0xffffffffu, A_own.w, src);
+        B.x = __shfl_sync(0xffffffffu, B_own.x, src);
+        B.y = __shfl_sync(0xffffffffu, B_own.y, src);
+        B.z = __shfl_sync(0xffffffffu, B_own.z, src);
+        B.w = __shfl_sync(0xffffffffu, B_own.w, src);
+        const int view = __shfl_sync(0xffffffffu, view_own, src);
+        const uint32_t tag = __shfl_sync(0xffffffffu, tag_own, src);
+        const ViewInfo vi = views_or_null ? views_or_null[view] : vi_own;
+        int tx0, tx1, ty0, ty1;
+        if (!record_rect(vi, A, B, tx0, tx1, ty0, ty1)) continue;
+        const float ia = __frcp_rn(B.x), ic = __frcp_rn(B.z);
+        const int rw = tx1 - tx0 + 1, count = rw * (ty1 - ty0 + 1);
+        for (int t = lane; t < count; t += 32) {
+            const int ty = ty0 + t / rw, tx = tx0 + t % rw;
+            if (tile_hit(vi, A, B, ia, ic, tx, ty)) body(src, vi.tile_base + (uint32_t)(ty * vi.tiles_x + tx), A, tag);
         }
+    }
 }
 
 struct ViewChunk {
@@ -48,39 +83,73 @@ cudaError_t launch_upload_views(const ViewInfo *host_views, int V, ViewInfo *dev
     return cudaGetLastError();
 }
 
-// Exclusive scan of the per-tile counts by one block (run by the last k_project block).
+// Exclusive scan of the per-(tile, sub-bucket) counts by one block (the last k_project
+// block): chunks of 4 x kBlock counters, vector loads, warp scans and a running carry.
 __device__ void scan_tiles(const WsPtrs &ws, const Dims &d) {
-    __shared__ unsigned long long part[kBlock];
-    const uint32_t T = d.T;
-    const uint32_t per = (T + kBlock - 1) / kBlock;
-    const uint32_t lo = min(T, threadIdx.x * per), hi = min(T, lo + per);
-    unsigned long long s = 0;
-    for (uint32_t t = lo; t < hi; ++t) s += __ldcg(ws.tile_cnt + t);
-    part[threadIdx.x] = s;
+    __shared__ uint32_t warp_sum[kWarps];
+    __shared__ unsigned long long s_carry;
+    const uint32_t TS = d.T * d.S;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    uint32_t max_tile = 0;
     __syncthreads();
-    // Hillis-Steele inclusive scan of the partial sums
-    for (int off = 1; off < kBlock; off <<= 1) {
-        unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
+    for (uint32_t base = 0; base < TS; base += 4 * kBlock) {
+        const uint32_t i0 = base + 4 * threadIdx.x;
+        uint32_t c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = i0 + k < TS ? __ldcg(ws.tile_cnt + i0 + k) : 0u;
+        const uint32_t mine = c[0] + c[1] + c[2] + c[3];
+        uint32_t incl = mine;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
         __syncthreads();
-        part[threadIdx.x] += v;
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            if (w < warp) before += warp_sum[w];
+            total += warp_sum[w];
+        }
+        unsigned long long run = s_carry + before + (incl - mine);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (i0 + k < TS) {
+                const uint32_t o = (uint32_t)min(run, (unsigned long long)0xffffffffu);
+                ws.tile_start[i0 + k] = o;
+                ws.cursor[i0 + k] = o;
+                ws.tile_cnt[i0 + k] = 0;
+                run += c[k];
+            }
+        // longest tile list: a tile's S sub-buckets are consecutive (S divides 4)
+        if (d.S <= 4) {
+            for (int k = 0; k < 4; k += d.S) {
+                uint32_t t = 0;
+                for (uint32_t q = 0; q < d.S; ++q) t += c[k + q];
+                max_tile = max(max_tile, t);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += total;
         __syncthreads();
     }
-    unsigned long long run = part[threadIdx.x] - s;
-    for (uint32_t t = lo; t < hi; ++t) {
-        const uint32_t c = __ldcg(ws.tile_cnt + t);
-        const uint32_t o = (uint32_t)min(run, (unsigned long long)0xffffffffu);
-        ws.tile_start[t] = o;
-        ws.cursor[t] = o;
-        ws.tile_cnt[t] = 0;
-        run += c;
+    if (d.S > 4) {  // tiles span several threads' chunks: measure from the finished offsets
+        const uint32_t total = (uint32_t)min(s_carry, (unsigned long long)0xffffffffu);
+        for (uint32_t t = threadIdx.x; t < d.T; t += kBlock) {
+            const uint32_t end = t + 1 < d.T ? ws.tile_start[(t + 1) * d.S] : total;
+            max_tile = max(max_tile, end - ws.tile_start[t * d.S]);
+        }
     }
-    if (threadIdx.x == kBlock - 1) {
-        const unsigned long long total = part[kBlock - 1];
-        ws.tile_start[T] = (uint32_t)min(total, (unsigned long long)0xffffffffu);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long total = s_carry;
+        ws.tile_start[TS] = (uint32_t)min(total, (unsigned long long)0xffffffffu);
         ws.hdr->n_pairs = total;
         if (total > d.pair_cap) atomicOr(ws.err, (uint32_t)kErrPairs);
         ws.hdr->k1_done = 0;
     }
+    atomicMax(&ws.hdr->max_tile, max_tile);
 }
 
 template <int DT>
@@ -89,7 +158,7 @@ __global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
     const int lane = tid & 31, warp = tid >> 5;
     __shared__ float sRt[12];
     __shared__ ViewInfo sv;
-    __shared__ uint32_t warp_off[kMaskWords + 1];
+    __shared__ uint32_t warp_off[kWarps];
     __shared__ uint32_t s_chunk;
     __shared__ int s_last;
     if (tid == 0) {
@@ -97,6 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
         sv = L.ws.views[v];
     }
     __syncthreads();
+    if (b == 0 && tid < 12) L.ws.view_rt[12 * v + tid] = sRt[tid];
     const ViewInfo vi = sv;
     const int64_t i = (int64_t)b * kBlock + tid;
     const Settings &S = L.s;
@@ -154,36 +224,24 @@ __global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
                     C = make_float4(ld_attr<DT>(L.g.rgb, 3 * i), ld_attr<DT>(L.g.rgb, 3 * i + 1),
                                     ld_attr<DT>(L.g.rgb, 3 * i + 2),
                                     __uint_as_float((uint32_t)((int64_t)v * L.d.n + i)));
-                    const uint32_t base = vi.tile_base;
-                    const int tx_n = vi.tiles_x;
-                    uint32_t *cnt = L.ws.tile_cnt;
-                    int touched = 0;
-                    for_each_tile(vi, A, B, [&](int tx, int ty) {
-                        atomicAdd(cnt + base + (uint32_t)(ty * tx_n + tx), 1u);
-                        ++touched;
-                    });
-                    vis = touched > 0;
+                    int tx0, tx1, ty0, ty1;
+                    vis = record_rect(vi, A, B, tx0, tx1, ty0, ty1);
                 }
             }
         }
     }
     // compaction: visible pairs of this block get consecutive records in Gaussian order
     const uint32_t ballot = __ballot_sync(0xffffffffu, vis);
-    const size_t cell = (size_t)v * L.d.nblk + b;
-    if (lane == 0) {
-        warp_off[warp] = __popc(ballot);
-        L.ws.vis_mask[cell * kMaskWords + warp] = ballot;
-    }
+    if (lane == 0) warp_off[warp] = __popc(ballot);
     __syncthreads();
     if (tid == 0) {
         uint32_t run = 0;
-        for (int w = 0; w < kMaskWords; ++w) {
+        for (int w = 0; w < kWarps; ++w) {
             const uint32_t c = warp_off[w];
             warp_off[w] = run;
             run += c;
         }
         s_chunk = run ? atomicAdd(&L.ws.hdr->n_rec, run) : 0u;
-        L.ws.chunk_start[cell] = s_chunk;
     }
     __syncthreads();
     if (vis) {
@@ -199,6 +257,12 @@ __global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
             atomicOr(L.ws.err, (uint32_t)kErrRecords);
         }
     }
+    // per-(tile, sub-bucket) pair counts, the warp sharing each visible Gaussian's tiles
+    uint32_t *cnt = L.ws.tile_cnt;
+    const uint32_t nsub = L.d.S;
+    warp_tiles(ballot, vi, A, B, lane, nullptr, v, (uint32_t)i & (nsub - 1), [&](int, uint32_t tile, float4, uint32_t sub) {
+        red_add(cnt + tile * nsub + sub, 1u);
+    });
     // the last block to finish turns the per-tile counts into offsets
     __threadfence();
     __syncthreads();
@@ -221,21 +285,35 @@ cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// One key per (record, tile met): depth bits (positive floats sort as unsigned ints)
-// in the high word, the record in the low word, stored at the tile's next free slot.
+// One key per (record, tile met): depth bits (positive floats sort as unsigned ints) in
+// the high word, the record in the low word, stored at the next free slot of the tile's
+// sub-bucket.  Each warp takes 32 consecutive records and walks their tiles together
+// (warp_tiles): a Gaussian close to the camera that spans thousands of tiles is split
+// over 32 lanes instead of holding one thread while the rest of the grid finishes.
 __global__ void __launch_bounds__(kBlock) k_emit(WsPtrs ws, Dims d) {
     const uint32_t n = min(ws.hdr->n_rec, d.rec_cap);
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
-        const float4 A = ws.rec[r].a, B = ws.rec[r].b;
-        const uint32_t gv = __float_as_uint(ws.rec[r].c.w);
-        const int v = (int)((uint64_t)gv / (uint64_t)d.n);
-        const ViewInfo vi = ws.views[v];
-        const unsigned long long key = ((unsigned long long)__float_as_uint(A.z) << 32) | r;
-        for_each_tile(vi, A, B, [&](int tx, int ty) {
-            const uint32_t tile = vi.tile_base + (uint32_t)(ty * vi.tiles_x + tx);
-            const uint32_t slot = atomicAdd(ws.cursor + tile, 1u);
-            if (slot < ws.tile_start[tile + 1] && slot < d.pair_cap)
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (blockDim.x / 32);
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) / 32 * 32; base < n; base += warps * 32) {
+        const uint32_t r = base + lane;
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
+        int view = 0;
+        uint32_t sub = 0;
+        if (r < n) {
+            const Rec rec = ws.rec[r];
+            A = rec.a;
+            B = rec.b;
+            const uint64_t gv = __float_as_uint(rec.c.w);
+            view = (int)(gv / (uint64_t)d.n);
+            sub = (uint32_t)(gv % (uint64_t)d.n) & (d.S - 1);
+        }
+        const uint32_t bits = __ballot_sync(0xffffffffu, r < n);
+        const ViewInfo none{};
+        warp_tiles(bits, none, A, B, lane, ws.views, view, sub, [&](int src, uint32_t tile, float4 As, uint32_t sb) {
+            const unsigned long long key = ((unsigned long long)__float_as_uint(As.z) << 32) | (base + (uint32_t)src);
+            const uint32_t bucket = tile * d.S + sb;
+            const uint32_t slot = atomicAdd(ws.cursor + bucket, 1u);
+            if (slot < ws.tile_start[bucket + 1] && slot < d.pair_cap)
                 ws.keys[slot] = key;
             else
                 atomicOr(ws.err, (uint32_t)kErrPairs);
@@ -247,8 +325,8 @@ cudaError_t launch_emit(const WsPtrs &ws, const Dims &d, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint32_t want = (d.rec_cap + kBlock - 1) / kBlock;
-    const uint32_t grid = max(1u, min(want, (uint32_t)(sms > 0 ? sms * 8 : 1024)));
+    const uint64_t want = ((uint64_t)d.rec_cap + kBlock - 1) / kBlock;
+    const uint32_t grid = (uint32_t)max((uint64_t)1, min(want, (uint64_t)(sms > 0 ? sms * 8 : 1024)));
     k_emit<<<grid, kBlock, 0, st>>>(ws, d);
     return cudaGetLastError();
 }

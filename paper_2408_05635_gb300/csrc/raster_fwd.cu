@@ -9,7 +9,8 @@
 // T_i = prod_{j<i} (1 - a_j).  Gaussians with a_i < alpha_min are skipped; the walk
 // stops before the Gaussian that would take T below t_min, and the block stops as soon
 // as all its pixels have stopped.  Batches of kBatch records are gathered into shared
-// memory by the whole block and then read by every pixel as broadcasts.
+// memory by the whole block; each warp (an 8 x 4 patch of the tile) then lists the batch
+// Gaussians whose conservative support box meets its patch and walks only those.
 //
 // With targets, the combined loss of Sec. III-B (plus the depth-prior term) is
 // evaluated in the epilogue: its per-pixel gradient goes to the workspace for the
@@ -22,26 +23,34 @@ __device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x <
 
 template <bool LOSS>
 __global__ void __launch_bounds__(kTilePix) k_forward(ForwardLaunch L) {
-    __shared__ float4 sA[kBatch], sB[kBatch], sC[kBatch];
+    __shared__ float4 sP0[kBatch], sC[kBatch], sBox[kBatch];
+    __shared__ float2 sP1[kBatch];
+    __shared__ uint8_t sList[kTilePix / 32][kBatch];
     __shared__ int s_view;
     __shared__ double s_loss[kTilePix / 32];
     const uint32_t tile = blockIdx.x;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_view = view_of_tile(L.ws.views, L.d.V, tile);
     __syncthreads();
     const int view = s_view;
     const ViewInfo vi = L.ws.views[view];
     const uint32_t local = tile - vi.tile_base;
     const int tx = (int)(local % (uint32_t)vi.tiles_x), ty = (int)(local / (uint32_t)vi.tiles_x);
-    const int px = tx * kTile + (tid & (kTile - 1)), py = ty * kTile + (tid / kTile);
+    const int pu0 = (warp & 1) * kPatchW, pv0 = (warp >> 1) * kPatchH;
+    const int lu = pu0 + (lane & (kPatchW - 1)), lv = pv0 + lane / kPatchW;
+    const int px = tx * kTile + lu, py = ty * kTile + lv;
     const bool inside = px < vi.width && py < vi.height;
-    const float fpx = (float)px, fpy = (float)py;
+    const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
+    const float fu = (float)lu, fv = (float)lv;
+    const float pu_lo = (float)pu0, pu_hi = (float)(pu0 + kPatchW - 1);
+    const float pv_lo = (float)pv0, pv_hi = (float)(pv0 + kPatchH - 1);
     const Settings &S = L.s;
+    const float thr = S.log2_alpha_min;
 
     uint32_t start;
     const uint32_t n = tile_entries(L.ws, L.d, tile, start);
-    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, D = 0.f, Sil = 0.f;
-    uint32_t last = 0;
+    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, D = 0.f;
+    uint32_t last = 0, n_eval = 0, n_contrib = 0;
     bool done = !inside;
     for (uint32_t b0 = 0; b0 < n; b0 += kBatch) {
         if (__syncthreads_count(!done) == 0) break;
@@ -50,39 +59,61 @@ __global__ void __launch_bounds__(kTilePix) k_forward(ForwardLaunch L) {
             const uint32_t r = L.ws.sorted[start + idx];
             if (r < L.d.rec_cap) {
                 const Rec rr = L.ws.rec[r];
-                sA[tid] = rr.a;
-                sB[tid] = rr.b;
-                sC[tid] = rr.c;
+                const Footprint f = stage_footprint(rr.a, rr.b, x0, y0);
+                sP0[tid] = f.p0;
+                sP1[tid] = f.p1;
+                sC[tid] = make_float4(rr.c.x, rr.c.y, rr.c.z, rr.a.z);
+                sBox[tid] = stage_box(rr.b, f.p0.y, f.p0.z);
             } else {
-                sA[tid] = make_float4(0.f, 0.f, 1.f, 0.f);  // zero opacity: never contributes
-                sB[tid] = make_float4(1.f, 0.f, 1.f, 0.f);
-                sC[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sBox[tid] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);  // empty: never listed
             }
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)kBatch, n - b0);
-        if (!done) {
-            for (int j = 0; j < cnt; ++j) {
-                const float4 A = sA[j], B = sB[j];
-                const AlphaEval ev = eval_alpha(fpx, fpy, A, B, S.alpha_max);
-                if (ev.alpha < S.alpha_min) continue;
-                const float Tn = T * (1.f - ev.alpha);
-                if (Tn < S.t_min) {
-                    done = true;
-                    break;
+        if (__any_sync(0xffffffffu, !done)) {
+            // this warp's list: the batch Gaussians whose support box meets its 8 x 4 patch
+            int nl = 0;
+            for (int k = 0; k < cnt; k += 32) {
+                const int j = k + lane;
+                bool hit = false;
+                if (j < cnt) {
+                    const float4 bx = sBox[j];
+                    hit = bx.y >= pu_lo && bx.x <= pu_hi && bx.w >= pv_lo && bx.z <= pv_hi;
                 }
-                const float w = ev.alpha * T;
-                const float4 Cc = sC[j];
-                cr += Cc.x * w;
-                cg += Cc.y * w;
-                cb += Cc.z * w;
-                D += A.z * w;
-                Sil += w;
-                T = Tn;
-                last = b0 + (uint32_t)j + 1u;
+                const uint32_t m = __ballot_sync(0xffffffffu, hit);
+                if (hit) sList[warp][nl + __popc(m & ((1u << lane) - 1u))] = (uint8_t)j;
+                nl += __popc(m);
+            }
+            __syncwarp();
+            if (!done) {
+                for (int e = 0; e < nl; ++e) {
+                    const int j = sList[warp][e];
+                    const float poly = eval_poly(fu, fv, sP0[j], sP1[j]).poly;
+                    ++n_eval;
+                    if (poly < thr) continue;
+                    const float alpha = fminf(S.alpha_max, ex2_approx(poly));
+                    const float Tn = T * (1.f - alpha);
+                    if (Tn < S.t_min) {
+                        done = true;
+                        break;
+                    }
+                    const float w = alpha * T;
+                    const float4 Cc = sC[j];
+                    cr += Cc.x * w;
+                    cg += Cc.y * w;
+                    cb += Cc.z * w;
+                    D += Cc.w * w;
+                    T = Tn;
+                    last = b0 + (uint32_t)j + 1u;
+                    ++n_contrib;
+                }
             }
         }
     }
+    // Eq. 4 summed equals 1 - prod(1 - a_i) = 1 - T exactly; the identity is used instead
+    // of a fifth accumulator
+    const float Sil = 1.f - T;
+    count_pairs(n_eval, n_contrib, &L.ws.hdr->fwd_evals, &L.ws.hdr->fwd_contrib);
 
     const uint32_t HW = (uint32_t)vi.width * (uint32_t)vi.height;
     const uint32_t p = (uint32_t)py * (uint32_t)vi.width + (uint32_t)px;
@@ -138,10 +169,10 @@ __global__ void __launch_bounds__(kTilePix) k_forward(ForwardLaunch L) {
             L.ws.upstream[3u * P + gp] = gD;
             L.ws.upstream[4u * P + gp] = gS;
         }
-        double dl = (double)l;
+        // per-pixel terms summed over the warp in FP32 (32 terms), over warps and tiles in FP64
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, off);
-        if ((tid & 31) == 0) s_loss[tid >> 5] = dl;
+        for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+        if ((tid & 31) == 0) s_loss[tid >> 5] = (double)l;
         __syncthreads();
         if (tid == 0) {
             double s = 0.0;

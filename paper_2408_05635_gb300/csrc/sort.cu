@@ -5,8 +5,9 @@
 // oracle uses).  k_emit leaves each tile's 64-bit keys (depth bits << 32 | record) in
 // arrival order inside the tile's own slice of the key array, so the sort is segmented
 // by construction: one block per tile sorts only its slice.  Slices of up to
-// kSortSmemCap keys are sorted in shared memory, longer ones in place in global memory,
-// both with the same bitonic network (padding is virtual: a missing partner is +inf).
+// kRankSortMax keys are sorted by ranking (no barriers), up to kSortSmemCap keys by a
+// bitonic network in shared memory, longer ones by the same network in place in global
+// memory (padding is virtual: a missing partner is +inf).
 #include "gs_internal.cuh"
 
 namespace gsk {
@@ -67,21 +68,45 @@ __device__ void fix_ties(unsigned long long *k, int n, const Rec *rec) {
     __syncthreads();
 }
 
+// Short lists (the common case): each thread ranks its keys by counting the smaller
+// ones (keys are unique: the low word is the record) and scatters them; no barrier
+// between steps, O(n^2 / threads) compares.
+constexpr int kRankSortMax = 512;
+
 __global__ void __launch_bounds__(kTilePix) k_tile_sort(WsPtrs ws, Dims d) {
-    __shared__ unsigned long long sk[kSortSmemCap];
+    __shared__ __align__(16) unsigned long long sk[kSortSmemCap];
+    __shared__ unsigned long long so[kRankSortMax];
     const uint32_t tile = blockIdx.x;
     uint32_t start;
     const int n = (int)tile_entries(ws, d, tile, start);
     if (n == 0) return;
     unsigned long long *k;
-    if (n <= kSortSmemCap) {
+    if (n <= kRankSortMax) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = ws.keys[start + i];
+        if (threadIdx.x == 0 && (n & 1)) sk[n] = ~0ull;  // pad to pairs: compares as largest
+        __syncthreads();
+        const ulonglong2 *sk2 = reinterpret_cast<const ulonglong2 *>(sk);
+        const int n2 = (n + 1) >> 1;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const unsigned long long key = sk[i];
+            int rank = 0;
+            for (int j = 0; j < n2; ++j) {
+                const ulonglong2 p = sk2[j];
+                rank += (p.x < key) + (p.y < key);
+            }
+            so[rank] = key;
+        }
+        __syncthreads();
+        k = so;
+    } else if (n <= kSortSmemCap) {
         for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = ws.keys[start + i];
         __syncthreads();
+        bitonic_sort(sk, n);
         k = sk;
     } else {
         k = ws.keys + start;
+        bitonic_sort(k, n);
     }
-    bitonic_sort(k, n);
     fix_ties(k, n, ws.rec);
     for (int i = threadIdx.x; i < n; i += blockDim.x) ws.sorted[start + i] = (uint32_t)k[i];
 }

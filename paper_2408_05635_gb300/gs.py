@@ -66,8 +66,14 @@ class gs_problem(ctypes.Structure):
                 ("record_capacity", c_int64)]
 
 
+class gs_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("ms", ctypes.c_float)]
+
+
 class gs_counts(ctypes.Structure):
-    _fields_ = [("n_records", c_int64), ("n_pairs", c_int64), ("err_flags", c_uint32), ("reserved", c_uint32)]
+    _fields_ = [("n_records", c_int64), ("n_pairs", c_int64), ("err_flags", c_uint32), ("reserved", c_uint32),
+                ("fwd_evals", c_int64), ("fwd_contrib", c_int64), ("bwd_evals", c_int64), ("bwd_contrib", c_int64),
+                ("max_tile", c_uint32), ("reserved2", c_uint32)]
 
 
 _lib = None
@@ -107,6 +113,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "gs_track_step": (c_int32, [c_void_p, P(gs_problem), P(gs_gaussians), P(gs_targets), c_void_p,
                                         c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
             "gs_sync_status": (c_int32, [c_void_p, c_void_p, P(gs_counts)]),
+            "gs_set_profiling": (c_int32, [c_void_p, c_int32]),
+            "gs_kernel_times": (c_int32, [c_void_p, P(gs_kernel_time), c_int32, P(c_int32)]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -205,6 +213,18 @@ def gs_sync_status(ctx, stream=None) -> tuple[int, gs_counts]:
     if st not in (0, GS_ERR_CAPACITY, 6):
         raise GsError(st, f"gs_sync_status: {gs_last_error(ctx)}")
     return st, c
+
+
+def gs_set_profiling(ctx, enable: bool) -> None:
+    _check(ctx, load().gs_set_profiling(ctx, int(bool(enable))), "gs_set_profiling")
+
+
+def gs_kernel_times(ctx, cap: int = 4096) -> list[tuple[str, float]]:
+    """(kernel name, ms) of every library kernel of the last enqueued sequence."""
+    arr = (gs_kernel_time * cap)()
+    cnt = c_int32(0)
+    _check(ctx, load().gs_kernel_times(ctx, arr, cap, ctypes.byref(cnt)), "gs_kernel_times")
+    return [(arr[k].name.decode(), float(arr[k].ms)) for k in range(min(cap, cnt.value))]
 
 
 # ----------------------------------------------------------------------------- convenience
