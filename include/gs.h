@@ -112,14 +112,15 @@ typedef struct {
     int32_t reserved;
     const gs_camera *cameras;  /* host array of n_views cameras                          */
     int64_t pair_capacity;     /* max (Gaussian, tile) pairs summed over views (< 2^32)  */
-    int64_t record_capacity;   /* max visible (Gaussian, view) pairs; 0 = n_gaussians*V  */
+    int64_t record_capacity;   /* reserved, must be 0 (every (Gaussian, view) pair has a
+                                  record slot in the workspace)                          */
 } gs_problem;
 
 /* Counters read back by gs_sync_status. */
 typedef struct {
     int64_t n_records; /* visible (Gaussian, view) pairs of the last projection        */
     int64_t n_pairs;   /* (Gaussian, tile) pairs of the last projection                */
-    uint32_t err_flags;/* bit 0 record overflow, bit 1 pair overflow, bit 2 timeout    */
+    uint32_t err_flags;/* bit 1 pair overflow, bit 2 timeout (bit 0 unused)            */
     uint32_t reserved;
     int64_t fwd_evals;   /* (pixel, Gaussian) footprints evaluated by the last forward    */
     int64_t fwd_contrib; /* ... of which contributed to Eqs. 2-4                          */
@@ -148,9 +149,11 @@ const char *gs_last_error(const gs_ctx *ctx);
 /* Name of a status code. */
 const char *gs_status_string(gs_status s);
 
-/* Bytes of device workspace the calls below need for `prob`.  Errors: INVALID_ARG
+/* Bytes of device workspace the calls below need for `prob` (about 96 B per
+ * (Gaussian, view) pair, 12 B per pair capacity, 28 B per pixel).  Errors: INVALID_ARG
  * (NULL argument, n_views < 1, a camera with a non-positive size or focal length,
- * n_gaussians * n_views >= 2^32, pair_capacity outside [1, 2^32)). */
+ * n_gaussians * n_views too large for 32-bit record indices, pair_capacity outside
+ * [1, 2^32), record_capacity not 0). */
 gs_status gs_workspace_size(const gs_ctx *ctx, const gs_problem *prob, size_t *bytes);
 
 /* ------------------------------------------------------------------ the hot path */
@@ -201,7 +204,7 @@ gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, con
  * R <- Exp(-step_theta) R (quaternion renormalised) and t <- Exp(-step_theta) t, then
  * moves, t <- t - step_t.  poses (device, n_views x 7) is updated in place;
  * adam_state (device, n_views x 16 doubles: m_rot 3, v_rot 3, m_t 3, v_t 3, step
- * count, 3 unused; zero it to start) carries the moments; loss_hist (device,
+ * count, beta1^k, beta2^k, 1 unused; zero it to start) carries the moments; loss_hist (device,
  * iters x n_views doubles, may be NULL) receives the loss before each update.  The
  * iterations are replayed from a CUDA graph that the context builds once per
  * argument set; no host synchronisation, no allocation.
@@ -220,7 +223,8 @@ gs_status gs_sync_status(gs_ctx *ctx, void *stream, gs_counts *counts);
 
 /* Per-kernel device time of the last enqueued work, for profiling. */
 typedef struct {
-    char name[24]; /* kernel (k_project, k_emit, k_tile_sort, k_forward, k_backward, k_bproject) */
+    char name[24]; /* kernel (k_project, k_scan_tiles, k_emit, k_tile_sort, k_forward, k_backward,
+                      k_bproject, k_finalize) */
     float ms;      /* CUDA-event time from the end of the previous kernel to the end of this one */
 } gs_kernel_time;
 

@@ -13,10 +13,10 @@
 // own centre (x_c <- Exp(theta) x_c, i.e. W <- Exp(theta) W and t <- Exp(theta) t) and the
 // translation shifts it (x_c <- x_c + t).  d t = dx_c and
 // d theta = x_c x dx_c + axial(dM M^T) with axial(P) = (P21 - P12, P02 - P20, P10 - P01).
-// The per-record 6-vectors are summed over the warp in FP32 (at most 32 terms) and then
-// accumulated per view in FP64; the last block to finish reads the FP64 sums and, in
-// tracking mode, applies the decoupled Adam step in FP64 (separate moments for theta
-// and t; R <- Exp(-step_theta) R, t <- Exp(-step_theta) t - step_t).
+// The per-record 6-vectors are summed over the warp in FP32 (at most 32 terms) and over
+// the cell's warps in FP64; k_finalize sums the view's cells in a fixed order (FP64)
+// and, in tracking mode, applies the decoupled Adam step in FP64 (separate moments for
+// theta and t; R <- Exp(-step_theta) R, t <- Exp(-step_theta) t - step_t).
 #include "gs_internal.cuh"
 
 namespace gsk {
@@ -32,34 +32,54 @@ __device__ __forceinline__ void rot_grad_to_quat(float w, float x, float y, floa
                    y * dR[7]);
 }
 
-__device__ void adam_update(double *pose, double *st, const double g[6], const Settings &S) {
-    st[12] += 1.0;
-    const double k = st[12];
-    const double bc1 = 1.0 - pow(S.beta1, k), bc2 = 1.0 - pow(S.beta2, k);
-    double step[6];
-    for (int j = 0; j < 6; ++j) {
-        double &m = st[j < 3 ? j : 6 + (j - 3)];
-        double &v = st[j < 3 ? 3 + j : 9 + (j - 3)];
-        m = S.beta1 * m + (1.0 - S.beta1) * g[j];
-        v = S.beta2 * v + (1.0 - S.beta2) * g[j] * g[j];
-        const double lr = j < 3 ? S.lr_rot : S.lr_trans;
-        step[j] = lr * (m / bc1) / (sqrt(v / bc2) + S.eps);
+// cos(h) and sin(h) / h for |h| <= 0.1 by their Taylor series through h^8 (the first
+// omitted terms, h^10 / 10! and h^10 / 11!, are below 3e-17): the half-angle of a pose
+// step is ~1e-3 rad, where FP64 transcendentals are long dependent chains on this GPU.
+__device__ __forceinline__ void cos_sinc_small(double h2, double &c, double &sc) {
+    c = 1.0 + h2 * (-1.0 / 2 + h2 * (1.0 / 24 + h2 * (-1.0 / 720 + h2 * (1.0 / 40320))));
+    sc = 1.0 + h2 * (-1.0 / 6 + h2 * (1.0 / 120 + h2 * (-1.0 / 5040 + h2 * (1.0 / 362880))));
+}
+
+// Decoupled Adam step of one view, FP64, by six threads of the block (one per pose
+// coordinate; tid 0 also applies the step).  state: m_rot 3, v_rot 3, m_t 3, v_t 3, step
+// count, beta1^k, beta2^k (running products, 0 before the first step), 1 unused.
+__device__ void adam_update(double *pose, double *st, const double *g, const Settings &S, double *s_step, int tid) {
+    const double k = st[12] + 1.0;
+    const double p1 = st[12] > 0.0 ? st[13] * S.beta1 : S.beta1;
+    const double p2 = st[12] > 0.0 ? st[14] * S.beta2 : S.beta2;
+    if (tid < 6) {
+        const int im = tid < 3 ? tid : 6 + (tid - 3), iv = im + 3;
+        const double m = S.beta1 * st[im] + (1.0 - S.beta1) * g[tid];
+        const double v = S.beta2 * st[iv] + (1.0 - S.beta2) * g[tid] * g[tid];
+        st[im] = m;
+        st[iv] = v;
+        const double lr = tid < 3 ? S.lr_rot : S.lr_trans;
+        s_step[tid] = lr * (m / (1.0 - p1)) / (sqrt(v / (1.0 - p2)) + S.eps);
     }
-    const double th = sqrt(step[0] * step[0] + step[1] * step[1] + step[2] * step[2]);
-    double a0 = 1.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;  // quaternion of Exp(-step_rot)
-    if (th > 0.0) {
-        const double s = sin(0.5 * th) / th;
-        a0 = cos(0.5 * th);
-        a1 = -step[0] * s;
-        a2 = -step[1] * s;
-        a3 = -step[2] * s;
+    __syncthreads();
+    if (tid != 0) return;
+    st[12] = k;
+    st[13] = p1;
+    st[14] = p2;
+    const double sx = s_step[0], sy = s_step[1], sz = s_step[2];
+    const double th2 = sx * sx + sy * sy + sz * sz;
+    const double h2 = 0.25 * th2;  // (theta / 2)^2
+    double c, sinc;
+    if (h2 <= 0.01) {
+        cos_sinc_small(h2, c, sinc);
+    } else {
+        const double h = sqrt(h2);
+        c = cos(h);
+        sinc = sin(h) / h;
     }
+    // quaternion of Exp(-step): (cos(theta/2), -step sin(theta/2) / theta), sin(h)/theta = sinc(h)/2
+    const double a0 = c, a1 = -0.5 * sinc * sx, a2 = -0.5 * sinc * sy, a3 = -0.5 * sinc * sz;
     const double b0 = pose[0], b1 = pose[1], b2 = pose[2], b3 = pose[3];
-    double q0 = a0 * b0 - a1 * b1 - a2 * b2 - a3 * b3;
-    double q1 = a0 * b1 + a1 * b0 + a2 * b3 - a3 * b2;
-    double q2 = a0 * b2 - a1 * b3 + a2 * b0 + a3 * b1;
-    double q3 = a0 * b3 + a1 * b2 - a2 * b1 + a3 * b0;
-    const double inv = 1.0 / sqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    const double q0 = a0 * b0 - a1 * b1 - a2 * b2 - a3 * b3;
+    const double q1 = a0 * b1 + a1 * b0 + a2 * b3 - a3 * b2;
+    const double q2 = a0 * b2 - a1 * b3 + a2 * b0 + a3 * b1;
+    const double q3 = a0 * b3 + a1 * b2 - a2 * b1 + a3 * b0;
+    const double inv = rsqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
     pose[0] = q0 * inv;
     pose[1] = q1 * inv;
     pose[2] = q2 * inv;
@@ -69,9 +89,9 @@ __device__ void adam_update(double *pose, double *st, const double g[6], const S
     const double r10 = 2.0 * (a1 * a2 + a0 * a3), r11 = 1.0 - 2.0 * (a1 * a1 + a3 * a3), r12 = 2.0 * (a2 * a3 - a0 * a1);
     const double r20 = 2.0 * (a1 * a3 - a0 * a2), r21 = 2.0 * (a2 * a3 + a0 * a1), r22 = 1.0 - 2.0 * (a1 * a1 + a2 * a2);
     const double t0 = pose[4], t1 = pose[5], t2 = pose[6];
-    pose[4] = r00 * t0 + r01 * t1 + r02 * t2 - step[3];
-    pose[5] = r10 * t0 + r11 * t1 + r12 * t2 - step[4];
-    pose[6] = r20 * t0 + r21 * t1 + r22 * t2 - step[5];
+    pose[4] = r00 * t0 + r01 * t1 + r02 * t2 - s_step[3];
+    pose[5] = r10 * t0 + r11 * t1 + r12 * t2 - s_step[4];
+    pose[6] = r20 * t0 + r21 * t1 + r22 * t2 - s_step[5];
 }
 
 // Butterfly reduce-scatter of 8 values over the warp (9 shuffles); afterwards lanes with
@@ -95,191 +115,209 @@ __device__ __forceinline__ float warp_reduce8(float (&v)[8], int lane, int &idx)
     return v[0];
 }
 
-// One thread per visible record (compact, so no idle lanes for culled Gaussians).
+// One block per cell, one thread per record of the cell.
 template <int DT, bool PARAMS>
 __global__ void __launch_bounds__(kBlock) k_bproject(BprojLaunch L) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    __shared__ int s_last;
-    const uint32_t nrec = min(L.ws.hdr->n_rec, L.d.rec_cap);
-    const bool want_pose = L.pose_grad || L.poses_out;
-    for (uint32_t base = blockIdx.x * kBlock; base < nrec; base += gridDim.x * kBlock) {
-        const uint32_t rec = base + tid;
-        float p6[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        int view = -1;
-        if (rec < nrec) {
-            const Rec rr = L.ws.rec[rec];
-            const RecGrad gg = L.ws.rec_grad[rec];
-            const uint32_t gv = __float_as_uint(rr.c.w);
-            const int64_t i = (int64_t)((uint64_t)gv % (uint64_t)L.d.n);
-            view = (int)((uint64_t)gv / (uint64_t)L.d.n);
-            const ViewInfo vi = L.ws.views[view];
-            float sRt[12];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ float s_red[kWarps][8];
+    const uint32_t cell = blockIdx.x;
+    const uint32_t cnt = L.ws.cell_cnt[cell];
+    const int view = (int)(cell / (uint32_t)L.d.nblk);
+    float p6[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if ((uint32_t)tid < cnt) {
+        const uint32_t rec = cell * kCell + (uint32_t)tid;
+        const Rec rr = L.ws.rec[rec];
+        const RecGrad gg = L.ws.rec_grad[rec];
+        const uint32_t gv = __float_as_uint(rr.c.w);
+        const int64_t i = (int64_t)((uint64_t)gv % (uint64_t)L.d.n);
+        const ViewInfo vi = L.ws.views[view];
+        float sRt[12];
 #pragma unroll
-            for (int k = 0; k < 12; ++k) sRt[k] = __ldg(L.ws.view_rt + 12 * view + k);
-            const float4 Bq = rr.b;  // conic the compositors used
-            const float mx = __ldg(L.g.means + 3 * i), my = __ldg(L.g.means + 3 * i + 1), mz = __ldg(L.g.means + 3 * i + 2);
-            const float x = cam_coord(sRt, 0, mx, my, mz);
-            const float y = cam_coord(sRt, 1, mx, my, mz);
-            const float z = cam_coord(sRt, 2, mx, my, mz);
-            const float q0 = ld_attr<DT>(L.g.quats, 4 * i), q1 = ld_attr<DT>(L.g.quats, 4 * i + 1);
-            const float q2 = ld_attr<DT>(L.g.quats, 4 * i + 2), q3 = ld_attr<DT>(L.g.quats, 4 * i + 3);
-            const float qn2 = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
-            const float qinv = rsqrtf(qn2);
-            const float w = q0 * qinv, qx = q1 * qinv, qy = q2 * qinv, qz = q3 * qinv;
-            float Rg[9];
-            quat_to_rot(w, qx, qy, qz, Rg);
-            float s[3];
-            s[0] = expf(ld_attr<DT>(L.g.log_scales, 3 * i));
-            s[1] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 1));
-            s[2] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 2));
-            float Bm[9], M[9];  // B = Rg diag(s), M = W B
+        for (int k = 0; k < 12; ++k) sRt[k] = __ldg(L.ws.view_rt + 12 * view + k);
+        const float4 Bq = rr.b;  // conic the compositors used
+        const float mx = __ldg(L.g.means + 3 * i), my = __ldg(L.g.means + 3 * i + 1), mz = __ldg(L.g.means + 3 * i + 2);
+        const float x = cam_coord(sRt, 0, mx, my, mz);
+        const float y = cam_coord(sRt, 1, mx, my, mz);
+        const float z = cam_coord(sRt, 2, mx, my, mz);
+        const float q0 = ld_attr<DT>(L.g.quats, 4 * i), q1 = ld_attr<DT>(L.g.quats, 4 * i + 1);
+        const float q2 = ld_attr<DT>(L.g.quats, 4 * i + 2), q3 = ld_attr<DT>(L.g.quats, 4 * i + 3);
+        const float qn2 = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
+        const float qinv = rsqrtf(qn2);
+        const float w = q0 * qinv, qx = q1 * qinv, qy = q2 * qinv, qz = q3 * qinv;
+        float Rg[9];
+        quat_to_rot(w, qx, qy, qz, Rg);
+        float s[3];
+        s[0] = expf(ld_attr<DT>(L.g.log_scales, 3 * i));
+        s[1] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 1));
+        s[2] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 2));
+        float Bm[9], M[9];  // B = Rg diag(s), M = W B
 #pragma unroll
-            for (int r = 0; r < 3; ++r)
+        for (int r = 0; r < 3; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) Bm[3 * r + c] = Rg[3 * r + c] * s[c];
+            for (int c = 0; c < 3; ++c) Bm[3 * r + c] = Rg[3 * r + c] * s[c];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                M[3 * r + c] = sRt[3 * r] * Bm[c] + sRt[3 * r + 1] * Bm[3 + c] + sRt[3 * r + 2] * Bm[6 + c];
+        const float iz = 1.f / z, iz2 = iz * iz;
+        const float J00 = vi.fx * iz, J02 = -vi.fx * x * iz2;
+        const float J11 = vi.fy * iz, J12 = -vi.fy * y * iz2;
+        float N0[3], N1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            N0[c] = J00 * M[c] + J02 * M[6 + c];
+            N1[c] = J11 * M[3 + c] + J12 * M[6 + c];
+        }
+        // G = -Q Gq Q with Gq = [[da, db/2], [db/2, dc]] and Q = [[a, b], [b, c]]
+        const float qa = Bq.x, qb = Bq.y, qc = Bq.z;
+        const float ga = gg.g1.x, gb = 0.5f * gg.g1.y, gc = gg.g1.z;
+        const float t00 = qa * ga + qb * gb, t01 = qa * gb + qb * gc;
+        const float t10 = qb * ga + qc * gb, t11 = qb * gb + qc * gc;
+        const float G00 = -(t00 * qa + t01 * qb), G01 = -(t00 * qb + t01 * qc), G11 = -(t10 * qb + t11 * qc);
+        float dN0[3], dN1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            dN0[c] = 2.f * (G00 * N0[c] + G01 * N1[c]);
+            dN1[c] = 2.f * (G01 * N0[c] + G11 * N1[c]);
+        }
+        // dJ = dN M^T (only J00, J02, J11, J12 are variables); dM = J^T dN
+        const float dJ00 = dN0[0] * M[0] + dN0[1] * M[1] + dN0[2] * M[2];
+        const float dJ02 = dN0[0] * M[6] + dN0[1] * M[7] + dN0[2] * M[8];
+        const float dJ11 = dN1[0] * M[3] + dN1[1] * M[4] + dN1[2] * M[5];
+        const float dJ12 = dN1[0] * M[6] + dN1[1] * M[7] + dN1[2] * M[8];
+        float dM[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            dM[c] = J00 * dN0[c];
+            dM[3 + c] = J11 * dN1[c];
+            dM[6 + c] = J02 * dN0[c] + J12 * dN1[c];
+        }
+        const float dmu_x = gg.g0.x, dmu_y = gg.g0.y, dd = gg.g0.z;
+        const float fx = vi.fx, fy = vi.fy;
+        const float dxc0 = dmu_x * J00 - dJ02 * fx * iz2;
+        const float dxc1 = dmu_y * J11 - dJ12 * fy * iz2;
+        const float dxc2 = dmu_x * J02 + dmu_y * J12 + dd - dJ00 * fx * iz2 + dJ02 * 2.f * fx * x * iz2 * iz -
+                           dJ11 * fy * iz2 + dJ12 * 2.f * fy * y * iz2 * iz;
+        if (L.want_pose) {
+            // translation, and rotation about the camera centre (mean and covariance parts)
+            float P[9];  // dM M^T
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
-                    M[3 * r + c] = sRt[3 * r] * Bm[c] + sRt[3 * r + 1] * Bm[3 + c] + sRt[3 * r + 2] * Bm[6 + c];
-            const float iz = 1.f / z, iz2 = iz * iz;
-            const float J00 = vi.fx * iz, J02 = -vi.fx * x * iz2;
-            const float J11 = vi.fy * iz, J12 = -vi.fy * y * iz2;
-            float N0[3], N1[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                N0[c] = J00 * M[c] + J02 * M[6 + c];
-                N1[c] = J11 * M[3 + c] + J12 * M[6 + c];
+                    P[3 * r + c] = dM[3 * r] * M[3 * c] + dM[3 * r + 1] * M[3 * c + 1] + dM[3 * r + 2] * M[3 * c + 2];
+            p6[0] = y * dxc2 - z * dxc1 + (P[7] - P[5]);
+            p6[1] = z * dxc0 - x * dxc2 + (P[2] - P[6]);
+            p6[2] = x * dxc1 - y * dxc0 + (P[3] - P[1]);
+            p6[3] = dxc0;
+            p6[4] = dxc1;
+            p6[5] = dxc2;
+        }
+        if constexpr (PARAMS) {
+            const gs_gaussians_grad &G = L.grads;
+            if (G.means) {
+                atomicAdd(G.means + 3 * i, sRt[0] * dxc0 + sRt[3] * dxc1 + sRt[6] * dxc2);
+                atomicAdd(G.means + 3 * i + 1, sRt[1] * dxc0 + sRt[4] * dxc1 + sRt[7] * dxc2);
+                atomicAdd(G.means + 3 * i + 2, sRt[2] * dxc0 + sRt[5] * dxc1 + sRt[8] * dxc2);
             }
-            // G = -Q Gq Q with Gq = [[da, db/2], [db/2, dc]] and Q = [[a, b], [b, c]]
-            const float qa = Bq.x, qb = Bq.y, qc = Bq.z;
-            const float ga = gg.g1.x, gb = 0.5f * gg.g1.y, gc = gg.g1.z;
-            const float t00 = qa * ga + qb * gb, t01 = qa * gb + qb * gc;
-            const float t10 = qb * ga + qc * gb, t11 = qb * gb + qc * gc;
-            const float G00 = -(t00 * qa + t01 * qb), G01 = -(t00 * qb + t01 * qc), G11 = -(t10 * qb + t11 * qc);
-            float dN0[3], dN1[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                dN0[c] = 2.f * (G00 * N0[c] + G01 * N1[c]);
-                dN1[c] = 2.f * (G01 * N0[c] + G11 * N1[c]);
-            }
-            // dJ = dN M^T (only J00, J02, J11, J12 are variables); dM = J^T dN
-            const float dJ00 = dN0[0] * M[0] + dN0[1] * M[1] + dN0[2] * M[2];
-            const float dJ02 = dN0[0] * M[6] + dN0[1] * M[7] + dN0[2] * M[8];
-            const float dJ11 = dN1[0] * M[3] + dN1[1] * M[4] + dN1[2] * M[5];
-            const float dJ12 = dN1[0] * M[6] + dN1[1] * M[7] + dN1[2] * M[8];
-            float dM[9];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                dM[c] = J00 * dN0[c];
-                dM[3 + c] = J11 * dN1[c];
-                dM[6 + c] = J02 * dN0[c] + J12 * dN1[c];
-            }
-            const float dmu_x = gg.g0.x, dmu_y = gg.g0.y, dd = gg.g0.z;
-            const float fx = vi.fx, fy = vi.fy;
-            const float dxc0 = dmu_x * J00 - dJ02 * fx * iz2;
-            const float dxc1 = dmu_y * J11 - dJ12 * fy * iz2;
-            const float dxc2 = dmu_x * J02 + dmu_y * J12 + dd - dJ00 * fx * iz2 + dJ02 * 2.f * fx * x * iz2 * iz -
-                               dJ11 * fy * iz2 + dJ12 * 2.f * fy * y * iz2 * iz;
-            if (want_pose) {
-                // translation, and rotation about the camera centre (mean and covariance parts)
-                float P[9];  // dM M^T
+            if (G.quats || G.log_scales) {
+                float dB[9];  // W^T dM
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
-                        P[3 * r + c] = dM[3 * r] * M[3 * c] + dM[3 * r + 1] * M[3 * c + 1] + dM[3 * r + 2] * M[3 * c + 2];
-                p6[0] = y * dxc2 - z * dxc1 + (P[7] - P[5]);
-                p6[1] = z * dxc0 - x * dxc2 + (P[2] - P[6]);
-                p6[2] = x * dxc1 - y * dxc0 + (P[3] - P[1]);
-                p6[3] = dxc0;
-                p6[4] = dxc1;
-                p6[5] = dxc2;
-            }
-            if constexpr (PARAMS) {
-                const gs_gaussians_grad &G = L.grads;
-                if (G.means) {
-                    atomicAdd(G.means + 3 * i, sRt[0] * dxc0 + sRt[3] * dxc1 + sRt[6] * dxc2);
-                    atomicAdd(G.means + 3 * i + 1, sRt[1] * dxc0 + sRt[4] * dxc1 + sRt[7] * dxc2);
-                    atomicAdd(G.means + 3 * i + 2, sRt[2] * dxc0 + sRt[5] * dxc1 + sRt[8] * dxc2);
+                        dB[3 * r + c] = sRt[r] * dM[c] + sRt[3 + r] * dM[3 + c] + sRt[6 + r] * dM[6 + c];
+                if (G.log_scales) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float ds = dB[c] * Rg[c] + dB[3 + c] * Rg[3 + c] + dB[6 + c] * Rg[6 + c];
+                        atomicAdd(G.log_scales + 3 * i + c, ds * s[c]);
+                    }
                 }
-                if (G.quats || G.log_scales) {
-                    float dB[9];  // W^T dM
+                if (G.quats) {
+                    float dRg[9];
 #pragma unroll
                     for (int r = 0; r < 3; ++r)
 #pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            dB[3 * r + c] = sRt[r] * dM[c] + sRt[3 + r] * dM[3 + c] + sRt[6 + r] * dM[6 + c];
-                    if (G.log_scales) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const float ds = dB[c] * Rg[c] + dB[3 + c] * Rg[3 + c] + dB[6 + c] * Rg[6 + c];
-                            atomicAdd(G.log_scales + 3 * i + c, ds * s[c]);
-                        }
-                    }
-                    if (G.quats) {
-                        float dRg[9];
-#pragma unroll
-                        for (int r = 0; r < 3; ++r)
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) dRg[3 * r + c] = dB[3 * r + c] * s[c];
-                        float dqn[4];
-                        rot_grad_to_quat(w, qx, qy, qz, dRg, dqn);
-                        const float pr = dqn[0] * w + dqn[1] * qx + dqn[2] * qy + dqn[3] * qz;
-                        atomicAdd(G.quats + 4 * i, (dqn[0] - w * pr) * qinv);
-                        atomicAdd(G.quats + 4 * i + 1, (dqn[1] - qx * pr) * qinv);
-                        atomicAdd(G.quats + 4 * i + 2, (dqn[2] - qy * pr) * qinv);
-                        atomicAdd(G.quats + 4 * i + 3, (dqn[3] - qz * pr) * qinv);
-                    }
-                }
-                if (G.opacity_logits) {
-                    const float o = rr.a.w;
-                    atomicAdd(G.opacity_logits + i, gg.g0.w * o * (1.f - o));
-                }
-                if (G.rgb) {
-                    atomicAdd(G.rgb + 3 * i, gg.g2.x);
-                    atomicAdd(G.rgb + 3 * i + 1, gg.g2.y);
-                    atomicAdd(G.rgb + 3 * i + 2, gg.g2.z);
+                        for (int c = 0; c < 3; ++c) dRg[3 * r + c] = dB[3 * r + c] * s[c];
+                    float dqn[4];
+                    rot_grad_to_quat(w, qx, qy, qz, dRg, dqn);
+                    const float pr = dqn[0] * w + dqn[1] * qx + dqn[2] * qy + dqn[3] * qz;
+                    atomicAdd(G.quats + 4 * i, (dqn[0] - w * pr) * qinv);
+                    atomicAdd(G.quats + 4 * i + 1, (dqn[1] - qx * pr) * qinv);
+                    atomicAdd(G.quats + 4 * i + 2, (dqn[2] - qy * pr) * qinv);
+                    atomicAdd(G.quats + 4 * i + 3, (dqn[3] - qz * pr) * qinv);
                 }
             }
-        }
-        if (want_pose) {
-            // warp sum in FP32 (at most 32 terms), then FP64 accumulation per view
-            const int v0 = __shfl_sync(0xffffffffu, view, 0);
-            if (__all_sync(0xffffffffu, view == v0 || view < 0) && v0 >= 0) {
-                int slot;
-                const float sum = warp_reduce8(p6, lane, slot);
-                if ((lane & 3) == 0 && slot < 6 && sum != 0.f) atomicAdd(L.ws.pose_acc + 6 * v0 + slot, (double)sum);
-            } else if (view >= 0) {
-#pragma unroll
-                for (int k = 0; k < 6; ++k) atomicAdd(L.ws.pose_acc + 6 * view + k, (double)p6[k]);
+            if (G.opacity_logits) {
+                const float o = rr.a.w;
+                atomicAdd(G.opacity_logits + i, gg.g0.w * o * (1.f - o));
+            }
+            if (G.rgb) {
+                atomicAdd(G.rgb + 3 * i, gg.g2.x);
+                atomicAdd(G.rgb + 3 * i + 1, gg.g2.y);
+                atomicAdd(G.rgb + 3 * i + 2, gg.g2.z);
             }
         }
     }
-    if (!want_pose) return;  // uniform across the grid
-    __threadfence();
+    if (!L.want_pose) return;  // uniform across the grid
+    // cell sum: FP32 over the warp (at most 32 terms), then FP64 over the warps
+    int slot;
+    const float sum = warp_reduce8(p6, lane, slot);
+    if ((lane & 3) == 0 && slot < 6) s_red[warp][slot] = sum;
     __syncthreads();
-    if (tid == 0) s_last = atomicAdd(&L.ws.hdr->bp_done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // last block: per-view pose gradient, loss copy and (tracking) the decoupled Adam step
-    for (int v = tid; v < L.d.V; v += kBlock) {
-        double g[6];
-        for (int k = 0; k < 6; ++k) g[k] = __ldcg(L.ws.pose_acc + 6 * v + k);
-        if (L.pose_grad)
-            for (int k = 0; k < 6; ++k) L.pose_grad[6 * v + k] = g[k];
-        if (L.loss_out) L.loss_out[v] = __ldcg(L.ws.loss + v);
-        if (L.poses_out) adam_update(L.poses_out + 7 * v, L.adam + 16 * v, g, L.s);
+    if (tid < 6) {
+        double acc = 0.0;
+        for (int w = 0; w < kWarps; ++w) acc += (double)s_red[w][tid];
+        L.ws.pose_part[(size_t)cell * 6 + tid] = acc;
     }
 }
 
+// One block per view: fixed-order sums of the view's tile losses and cell pose partials,
+// then (tracking) the decoupled Adam step.
+__global__ void __launch_bounds__(kBlock) k_finalize(FinalizeLaunch L) {
+    const int v = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ double s_part[kWarps][7];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (L.loss_out) {
+        const ViewInfo vi = L.ws.views[v];
+        const uint32_t nt = (uint32_t)vi.tiles_x * (uint32_t)vi.tiles_y;
+        for (uint32_t t = tid; t < nt; t += kBlock) acc[6] += L.ws.tile_loss[vi.tile_base + t];
+    }
+    if (L.pose) {
+        const size_t c0 = (size_t)v * L.d.nblk;
+        for (int c = tid; c < L.d.nblk; c += kBlock)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[k] += L.ws.pose_part[(c0 + c) * 6 + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s_part[warp][k] = acc[k];
+    __syncthreads();
+    __shared__ double s_g[7], s_step[6];
+    if (tid < 7) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += s_part[w][tid];
+        s_g[tid] = t;
+        if (tid == 6 && L.loss_out) L.loss_out[v] = t;
+        if (tid < 6 && L.pose && L.pose_grad) L.pose_grad[6 * v + tid] = t;
+    }
+    __syncthreads();
+    if (L.pose && L.poses) adam_update(L.poses + 7 * v, L.adam + 16 * v, s_g, L.s, s_step, tid);
+}
+
+cudaError_t launch_finalize(const FinalizeLaunch &L, cudaStream_t st) {
+    k_finalize<<<L.d.V, kBlock, 0, st>>>(L);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bproject(const BprojLaunch &L, cudaStream_t st) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint32_t want = (L.d.rec_cap + kBlock - 1) / kBlock;
-    const uint32_t grid = max(1u, min(want, (uint32_t)(sms > 0 ? sms * 4 : 512)));
+    const uint32_t grid = (uint32_t)L.d.V * (uint32_t)L.d.nblk;
     const bool params = L.grads.means || L.grads.quats || L.grads.log_scales || L.grads.opacity_logits || L.grads.rgb;
 #define GS_BPROJ(DT)                                                   \
     if (params)                                                        \

@@ -20,8 +20,9 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t err, hdr, loss, pose_acc, tile_cnt, zero_end;
-    size_t views, view_rt, tile_start, cursor, rec, rec_grad, keys, sorted, t_final, n_last, upstream, total;
+    size_t err, hdr, tile_cnt, zero_end;
+    size_t views, view_rt, cell_cnt, tile_start, cursor, rec, rec_grad, keys, sorted, t_final, n_last, upstream,
+        tile_loss, pose_part, total;
 };
 
 struct Problem {
@@ -38,11 +39,11 @@ struct GraphKey {
     int dtype = 0;
     int iters = 0;
     std::vector<ViewInfo> views;
-    uint32_t rec_cap = 0, pair_cap = 0;
+    uint32_t pair_cap = 0;
     bool profiling = false;
     bool operator==(const GraphKey &o) const {
         if (ws != o.ws || ws_bytes != o.ws_bytes || n != o.n || dtype != o.dtype || iters != o.iters ||
-            rec_cap != o.rec_cap || pair_cap != o.pair_cap || profiling != o.profiling ||
+            pair_cap != o.pair_cap || profiling != o.profiling ||
             views.size() != o.views.size())
             return false;
         for (int k = 0; k < 12; ++k)
@@ -139,14 +140,14 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     if (nv >= (1ull << 32)) return fail(ctx, GS_ERR_INVALID_ARG, "n_gaussians * n_views must be < 2^32");
     if (p->pair_capacity < 1 || p->pair_capacity >= (int64_t)(1ll << 32))
         return fail(ctx, GS_ERR_INVALID_ARG, "pair_capacity must be in [1, 2^32)");
-    if (p->record_capacity < 0 || (uint64_t)p->record_capacity > nv)
-        return fail(ctx, GS_ERR_INVALID_ARG, "record_capacity must be in [0, n_gaussians * n_views]");
+    if (p->record_capacity != 0) return fail(ctx, GS_ERR_INVALID_ARG, "record_capacity is reserved and must be 0");
     Dims d{};
     d.n = p->n_gaussians;
     d.V = p->n_views;
     d.nblk = (int32_t)((p->n_gaussians + kBlock - 1) / kBlock);
     if (d.nblk == 0) d.nblk = 1;
-    d.rec_cap = (uint32_t)(p->record_capacity ? p->record_capacity : (int64_t)nv);
+    if ((uint64_t)d.nblk * kCell * (uint64_t)p->n_views >= (1ull << 32))
+        return fail(ctx, GS_ERR_INVALID_ARG, "n_gaussians * n_views too large for 32-bit record slots");
     d.pair_cap = (uint32_t)p->pair_capacity;
     out.views.resize(p->n_views);
     uint64_t T = 0, P = 0;
@@ -173,7 +174,8 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     }
     d.T = (uint32_t)T;
     d.P = (uint32_t)P;
-    d.S = 1;
+    d.S = 4;
+    while (d.S > 1 && (uint64_t)d.T * d.S > (1ull << 22)) d.S >>= 1;
     out.d = d;
     Layout &L = out.lay;
     size_t o = 0;
@@ -185,21 +187,23 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     L.err = take(sizeof(uint32_t));
     // zeroed before every projection: [hdr, zero_end)
     L.hdr = take(sizeof(DevHeader));
-    L.loss = take(sizeof(double) * d.V);
-    L.pose_acc = take(sizeof(double) * 6 * d.V);
     L.tile_cnt = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
     L.zero_end = o;
+    const size_t cells = (size_t)d.V * d.nblk;
     L.views = take(sizeof(ViewInfo) * d.V);
     L.view_rt = take(sizeof(float) * 12 * d.V);
+    L.cell_cnt = take(sizeof(uint32_t) * cells);
     L.tile_start = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
     L.cursor = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
-    L.rec = take(sizeof(Rec) * (size_t)d.rec_cap);
-    L.rec_grad = take(sizeof(RecGrad) * (size_t)d.rec_cap);
+    L.rec = take(sizeof(Rec) * cells * kCell);
+    L.rec_grad = take(sizeof(RecGrad) * cells * kCell);
     L.keys = take(sizeof(unsigned long long) * (size_t)d.pair_cap);
     L.sorted = take(sizeof(uint32_t) * (size_t)d.pair_cap);
     L.t_final = take(sizeof(float) * (size_t)d.P);
     L.n_last = take(sizeof(uint32_t) * (size_t)d.P);
     L.upstream = take(sizeof(float) * 5 * (size_t)d.P);
+    L.tile_loss = take(sizeof(double) * (size_t)d.T);
+    L.pose_part = take(sizeof(double) * 6 * cells);
     L.total = o;
     return GS_OK;
 }
@@ -209,11 +213,10 @@ WsPtrs ws_ptrs(void *base, const Layout &L) {
     WsPtrs w;
     w.err = reinterpret_cast<uint32_t *>(b + L.err);
     w.hdr = reinterpret_cast<DevHeader *>(b + L.hdr);
-    w.loss = reinterpret_cast<double *>(b + L.loss);
-    w.pose_acc = reinterpret_cast<double *>(b + L.pose_acc);
     w.tile_cnt = reinterpret_cast<uint32_t *>(b + L.tile_cnt);
     w.views = reinterpret_cast<ViewInfo *>(b + L.views);
     w.view_rt = reinterpret_cast<float *>(b + L.view_rt);
+    w.cell_cnt = reinterpret_cast<uint32_t *>(b + L.cell_cnt);
     w.tile_start = reinterpret_cast<uint32_t *>(b + L.tile_start);
     w.cursor = reinterpret_cast<uint32_t *>(b + L.cursor);
     w.rec = reinterpret_cast<Rec *>(b + L.rec);
@@ -223,6 +226,8 @@ WsPtrs ws_ptrs(void *base, const Layout &L) {
     w.t_final = reinterpret_cast<float *>(b + L.t_final);
     w.n_last = reinterpret_cast<uint32_t *>(b + L.n_last);
     w.upstream = reinterpret_cast<float *>(b + L.upstream);
+    w.tile_loss = reinterpret_cast<double *>(b + L.tile_loss);
+    w.pose_part = reinterpret_cast<double *>(b + L.pose_part);
     return w;
 }
 
@@ -260,6 +265,8 @@ cudaError_t enqueue_project(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, voi
     P.poses = poses;
     if ((e = launch_project(P, st)) != cudaSuccess) return e;
     if ((e = mark(ctx, st, "k_project")) != cudaSuccess) return e;
+    if ((e = launch_scan_tiles(w, pr.d, st)) != cudaSuccess) return e;
+    if ((e = mark(ctx, st, "k_scan_tiles")) != cudaSuccess) return e;
     if ((e = launch_emit(w, pr.d, st)) != cudaSuccess) return e;
     return mark(ctx, st, "k_emit");
 }
@@ -406,8 +413,14 @@ gs_status gs_forward(gs_ctx *ctx, const gs_targets *targets, float *rgb, float *
     cudaError_t e = enqueue_forward(ctx, ctx->prob, ctx->ws, targets, rgb, depth, sil, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "forward");
     if (loss) {
-        e = cudaMemcpyAsync(loss, ctx->ws.loss, sizeof(double) * ctx->prob.d.V, cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "loss copy");
+        FinalizeLaunch F{};
+        F.ws = ctx->ws;
+        F.d = ctx->prob.d;
+        F.s = ctx->s;
+        F.loss_out = loss;
+        e = launch_finalize(F, s);
+        if (e == cudaSuccess) e = mark(ctx, s, "k_finalize");
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "loss reduction");
     }
     ctx->have_loss = targets != nullptr;
     return GS_OK;
@@ -450,15 +463,22 @@ gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, con
     J.s = ctx->s;
     J.g = ctx->g;
     J.dtype = ctx->dtype;
-    J.poses_in = ctx->poses;
-    J.poses_out = nullptr;
-    J.adam = nullptr;
-    J.pose_grad = pose_grad;
-    J.loss_out = nullptr;
+    J.want_pose = pose_grad != nullptr;
     J.grads = G;
     e = launch_bproject(J, s);
     if (e == cudaSuccess) e = mark(ctx, s, "k_bproject");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "backward projection");
+    if (pose_grad) {
+        FinalizeLaunch F{};
+        F.ws = ctx->ws;
+        F.d = pr.d;
+        F.s = ctx->s;
+        F.pose_grad = pose_grad;
+        F.pose = true;
+        e = launch_finalize(F, s);
+        if (e == cudaSuccess) e = mark(ctx, s, "k_finalize");
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "pose reduction");
+    }
     ctx->grads_used = true;
     return GS_OK;
 }
@@ -504,14 +524,20 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
             J.s = ctx->s;
             J.g = gp;
             J.dtype = g->dtype_attr;
-            J.poses_in = poses;
-            J.poses_out = poses;
-            J.adam = adam_state;
-            J.pose_grad = nullptr;
-            J.loss_out = loss_hist ? loss_hist + (size_t)it * pr.d.V : nullptr;
+            J.want_pose = true;
             J.grads = gs_gaussians_grad{};
             if ((r = launch_bproject(J, q)) != cudaSuccess) return r;
             if ((r = mark(ctx, q, "k_bproject")) != cudaSuccess) return r;
+            FinalizeLaunch F{};
+            F.ws = w;
+            F.d = pr.d;
+            F.s = ctx->s;
+            F.loss_out = loss_hist ? loss_hist + (size_t)it * pr.d.V : nullptr;
+            F.pose = true;
+            F.poses = poses;
+            F.adam = adam_state;
+            if ((r = launch_finalize(F, q)) != cudaSuccess) return r;
+            if ((r = mark(ctx, q, "k_finalize")) != cudaSuccess) return r;
         }
         return cudaSuccess;
     };
@@ -538,7 +564,6 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
         key.dtype = g->dtype_attr;
         key.iters = iters;
         key.views = pr.views;
-        key.rec_cap = pr.d.rec_cap;
         key.pair_cap = pr.d.pair_cap;
         key.profiling = ctx->profiling;
         if (!ctx->graph_exec || !(ctx->graph_key == key)) {
@@ -631,7 +656,7 @@ gs_status gs_sync_status(gs_ctx *ctx, void *stream, gs_counts *counts) {
         return cuda_fail(ctx, e, "flag read");
     if (err && (e = cudaMemset(ctx->ws.err, 0, sizeof(err))) != cudaSuccess) return cuda_fail(ctx, e, "flag clear");
     if (counts) {
-        counts->n_records = h.n_rec;
+        counts->n_records = (int64_t)h.n_rec;
         counts->n_pairs = (int64_t)h.n_pairs;
         counts->err_flags = err;
         counts->reserved = 0;
@@ -644,8 +669,8 @@ gs_status gs_sync_status(gs_ctx *ctx, void *stream, gs_counts *counts) {
     if (err & kErrTimeout) return fail(ctx, GS_ERR_TIMEOUT, "a bounded device wait expired");
     if (err & (kErrRecords | kErrPairs)) {
         char msg[160];
-        std::snprintf(msg, sizeof msg, "capacity exceeded: %u records (capacity %u), %llu pairs (capacity %u)",
-                      h.n_rec, ctx->prob.d.rec_cap, (unsigned long long)h.n_pairs, ctx->prob.d.pair_cap);
+        std::snprintf(msg, sizeof msg, "capacity exceeded: %llu pairs (capacity %u)", (unsigned long long)h.n_pairs,
+                      ctx->prob.d.pair_cap);
         return fail(ctx, GS_ERR_CAPACITY, msg);
     }
     return GS_OK;

@@ -26,6 +26,7 @@ constexpr int kTilePix = kTile * kTile;   // pixels (= threads) per tile block
 constexpr int kBlock = 256;               // threads per Gaussian-parallel block
 constexpr int kWarps = kBlock / 32;       // warps per Gaussian-parallel block
 constexpr int kSortSmemCap = 4096;        // tiles up to this many keys sort in shared memory
+constexpr int kCell = kBlock;             // Gaussians (and record slots) per cell
 constexpr int kBatch = 256;               // Gaussians staged per compositing batch
 
 enum ErrFlag : uint32_t { kErrRecords = 1u, kErrPairs = 2u, kErrTimeout = 4u };
@@ -42,17 +43,15 @@ static_assert(sizeof(ViewInfo) == 48, "ViewInfo layout");
 
 // Small counters at the start of the workspace (cleared before every projection).
 struct DevHeader {
-    uint32_t n_rec;     // records handed out by k_project (may exceed the capacity)
-    uint32_t k1_done;   // k_project blocks finished (last-block scan)
-    unsigned long long n_pairs;  // total (Gaussian, tile) pairs of the projection
-    uint32_t bp_done;   // k_bproject blocks finished (last-block pose update)
-    uint32_t pad0;
+    unsigned long long n_pairs;      // total (Gaussian, tile) pairs of the projection
+    unsigned long long n_rec;        // visible (Gaussian, view) records of the projection
     unsigned long long fwd_evals;    // (pixel, Gaussian) footprints evaluated by k_forward
     unsigned long long fwd_contrib;  // ... of which contributed (alpha >= alpha_min, before the stop)
     unsigned long long bwd_evals;    // footprints evaluated by k_backward
     unsigned long long bwd_contrib;  // ... of which were differentiated
     uint32_t max_tile;               // longest tile list of the projection
-    uint32_t pad1;
+    uint32_t pad0;
+    unsigned long long pad1;
 };
 static_assert(sizeof(DevHeader) == 64, "DevHeader layout");
 
@@ -60,6 +59,10 @@ static_assert(sizeof(DevHeader) == 64, "DevHeader layout");
 //   a = (mu'_x, mu'_y, depth, opacity)
 //   b = (conic a, conic b, conic c, dmax2)   conic = inverse of Sigma' = [[a, b], [b, c]]
 //   c = (r, g, b, bits of view * n + gaussian)
+// Records live in cells: cell (v, k) holds the visible Gaussians of view v among
+// Gaussians [256 k, 256 k + 256), packed at the front of its 256 slots in Gaussian
+// order, so record index order is (view, Gaussian) order and no allocation counter is
+// needed.
 struct __align__(16) Rec {
     float4 a, b, c;
 };
@@ -74,33 +77,33 @@ struct __align__(16) RecGrad {
 struct WsPtrs {
     uint32_t *err;         // ErrFlag bits, latched until gs_sync_status clears them
     DevHeader *hdr;
-    double *loss;          // V, combined loss per view
-    double *pose_acc;      // V x 6, FP64 pose-gradient sums of the backward projection
     uint32_t *tile_cnt;    // T x S, per-(tile, sub-bucket) pair counts (zero between projections)
     ViewInfo *views;       // V
     float *view_rt;        // V x 12, FP32 rotation and translation of each pose (k_project)
+    uint32_t *cell_cnt;    // V x nblk, visible records per cell
     uint32_t *tile_start;  // T x S + 1, exclusive scan of the counts
     uint32_t *cursor;      // T x S, emission cursors
-    Rec *rec;              // record_capacity
-    RecGrad *rec_grad;     // record_capacity
+    Rec *rec;              // V x nblk x 256 record slots
+    RecGrad *rec_grad;     // same slots
     unsigned long long *keys;  // pair_capacity
     uint32_t *sorted;      // pair_capacity, record ids in (tile, depth, gaussian) order
     float *t_final;        // P, transmittance after the last contributor
     uint32_t *n_last;      // P, tile-list index + 1 of the last contributor
     float *upstream;       // 5 x P: dL/dC (planar like the images), dL/dD, dL/dS of the fused loss
+    double *tile_loss;     // T, combined loss of each tile's pixels (fused loss)
+    double *pose_part;     // V x nblk x 6, pose-gradient sum of each cell's records
 };
 
 struct Dims {
     int64_t n;             // Gaussians
     int32_t V;             // views
-    int32_t nblk;          // ceil(n / kBlock)
+    int32_t nblk;          // ceil(n / kBlock): cells per view
     uint32_t T;            // tiles over all views
     uint32_t S;            // sub-buckets per tile (power of two): a tile's pairs are counted and
                            // placed through S counters picked by Gaussian index, so no single
                            // counter takes every pair of a crowded tile; the S sub-ranges are
                            // contiguous, so the tile's list is still one range
     uint32_t P;            // pixels over all views
-    uint32_t rec_cap;
     uint32_t pair_cap;
 };
 
@@ -129,8 +132,8 @@ __device__ __forceinline__ void count_pairs(uint32_t evals, uint32_t contrib, un
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        atomicAdd(e_out, s_e);
-        atomicAdd(c_out, s_c);
+        asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(e_out), "l"(s_e) : "memory");
+        asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(c_out), "l"(s_c) : "memory");
     }
 }
 
@@ -342,11 +345,16 @@ __device__ __forceinline__ int view_of_tile(const ViewInfo *views, int V, uint32
 // Entries of a tile's list: [start, start + count) of the key / sorted arrays, clamped to
 // the pair capacity so an overflow (latched in the error flags) can never make a kernel
 // read past its buffers.  k_project and k_emit enumerate the same (record, tile) pairs,
-// so every slot of the range is written; record ids are bounds-checked where used.
+// so every slot of the range is written; record ids are bounds-checked where used
+// (rec_slots(d) = V x nblk x 256).
 __device__ __forceinline__ uint32_t tile_entries(const WsPtrs &ws, const Dims &d, uint32_t tile, uint32_t &start) {
     start = min(ws.tile_start[tile * d.S], d.pair_cap);
     const uint32_t end = min(ws.tile_start[(tile + 1) * d.S], d.pair_cap);
     return end > start ? end - start : 0u;
+}
+
+__device__ __host__ __forceinline__ uint32_t rec_slots(const Dims &d) {
+    return (uint32_t)d.V * (uint32_t)d.nblk * (uint32_t)kCell;
 }
 
 // ------------------------------------------------------------------ host-side launchers
@@ -362,6 +370,7 @@ struct ProjectLaunch {
 
 cudaError_t launch_upload_views(const ViewInfo *host_views, int V, ViewInfo *dev, cudaStream_t st);
 cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st);
+cudaError_t launch_scan_tiles(const WsPtrs &ws, const Dims &d, cudaStream_t st);
 cudaError_t launch_emit(const WsPtrs &ws, const Dims &d, cudaStream_t st);
 cudaError_t launch_tile_sort(const WsPtrs &ws, const Dims &d, cudaStream_t st);
 
@@ -389,13 +398,23 @@ struct BprojLaunch {
     Settings s;
     GaussPtrs g;
     int dtype;
-    const double *poses_in;   // poses the projection used
-    double *poses_out;        // updated poses (tracking) or nullptr
-    double *adam;             // n_views x 16 (tracking) or nullptr
-    double *pose_grad;        // n_views x 6 or nullptr
-    double *loss_out;         // n_views, copy of the loss (tracking) or nullptr
+    bool want_pose;           // write the per-cell pose partials
     gs_gaussians_grad grads;  // parameter gradients (each nullable)
 };
 cudaError_t launch_bproject(const BprojLaunch &L, cudaStream_t st);
+
+// Per-view reductions in a fixed order: loss from the tile partials, pose gradient from
+// the cell partials, and (tracking) the decoupled Adam step.
+struct FinalizeLaunch {
+    WsPtrs ws;
+    Dims d;
+    Settings s;
+    double *loss_out;   // n_views, or nullptr
+    double *pose_grad;  // n_views x 6, or nullptr
+    double *poses;      // updated in place by the Adam step, or nullptr
+    double *adam;       // n_views x 16 (with poses)
+    bool pose;          // reduce the pose partials
+};
+cudaError_t launch_finalize(const FinalizeLaunch &L, cudaStream_t st);
 
 }  // namespace gsk

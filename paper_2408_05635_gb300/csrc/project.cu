@@ -11,15 +11,21 @@
 namespace gsk {
 
 // Tile rectangle of a record's support ellipse.  The pixel box is derived from the
-// stored conic (Sigma'_xx = c / det, Sigma'_yy = a / det of the conic) with explicitly
-// rounded operations, so k_project (counting) and k_emit (writing) enumerate the same
-// tiles.  Returns false when the box misses the image.
+// stored conic (Sigma'_xx = c / det, Sigma'_yy = a / det of the conic); the one-pixel
+// margin of tile_rect absorbs the error of the fast reciprocal and square root.  Both
+// k_project (counting) and k_emit (writing) call exactly this code on the same floats,
+// so they enumerate the same tiles.  Returns false when the box misses the image.
 __device__ __forceinline__ bool record_rect(const ViewInfo &vi, float4 A, float4 B, int &tx0, int &tx1, int &ty0,
                                             int &ty1) {
     const float detc = __fsub_rn(__fmul_rn(B.x, B.z), __fmul_rn(B.y, B.y));
     if (!(detc > 0.f)) return false;
-    const float hx = __fsqrt_rn(__fmul_rn(B.w, __fdiv_rn(B.z, detc)));
-    const float hy = __fsqrt_rn(__fmul_rn(B.w, __fdiv_rn(B.x, detc)));
+    float hx = INFINITY, hy = INFINITY;
+    if (B.w < INFINITY) {
+        const float idet = __fdividef(1.f, detc);
+        const float qx = __fmul_rn(B.w, __fmul_rn(B.z, idet)), qy = __fmul_rn(B.w, __fmul_rn(B.x, idet));
+        hx = qx > 0.f ? __fmul_rn(qx, rsqrtf(qx)) : 0.f;
+        hy = qy > 0.f ? __fmul_rn(qy, rsqrtf(qy)) : 0.f;
+    }
     tile_rect(vi, A.x, A.y, hx, hy, tx0, tx1, ty0, ty1);
     return tx0 <= tx1 && ty0 <= ty1;
 }
@@ -30,36 +36,47 @@ __device__ __forceinline__ bool tile_hit(const ViewInfo &vi, float4 A, float4 B,
     return ellipse_meets_rect(A.x, A.y, B.x, B.y, B.z, ia, ic, B.w, x0, x1, y0, y1);
 }
 
-// The whole warp walks the tiles of one record at a time: the record's lane broadcasts
-// it and the 32 lanes split its tile rectangle, so one large Gaussian does not keep the
-// other 31 lanes waiting.  body(src lane, tile, record's A, record's tag) runs for every
-// tile the support meets.
+// Tiles met by each lane's own record (mine = the lane has one).  A lane whose tile
+// rectangle has at most kSoloTiles candidates tests them alone; larger rectangles (a
+// Gaussian close to the camera can span thousands of tiles) are split over the 32 lanes
+// of the warp, so one of them never holds the rest of the grid.  body(src lane, tile,
+// record's A, record's tag) runs once for every tile the support meets.
+constexpr int kSoloTiles = 24;
+
 template <class Body>
-__device__ __forceinline__ void warp_tiles(uint32_t bits, const ViewInfo &vi_own, float4 A_own, float4 B_own,
-                                           int lane, const ViewInfo *views_or_null, int view_own, uint32_t tag_own,
-                                           Body &&body) {
-    while (bits) {
-        const int src = __ffs(bits) - 1;
-        bits &= bits - 1;
-        float4 A, B;
-        A.x = __shfl_sync(0xffffffffu, A_own.x, src);
-        A.y = __shfl_sync(0xffffffffu, A_own.y, src);
-        A.z = __shfl_sync(0xffffffffu, A_own.z, src);
-        A.w = __shfl_sync(0xffffffffu, A_own.w, src);
-        B.x = __shfl_sync(0xffffffffu, B_own.x, src);
-        B.y = __shfl_sync(0xffffffffu, B_own.y, src);
-        B.z = __shfl_sync(0xffffffffu, B_own.z, src);
-        B.w = __shfl_sync(0xffffffffu, B_own.w, src);
-        const int view = __shfl_sync(0xffffffffu, view_own, src);
-        const uint32_t tag = __shfl_sync(0xffffffffu, tag_own, src);
-        const ViewInfo vi = views_or_null ? views_or_null[view] : vi_own;
-        int tx0, tx1, ty0, ty1;
-        if (!record_rect(vi, A, B, tx0, tx1, ty0, ty1)) continue;
-        const float ia = __frcp_rn(B.x), ic = __frcp_rn(B.z);
-        const int rw = tx1 - tx0 + 1, count = rw * (ty1 - ty0 + 1);
-        for (int t = lane; t < count; t += 32) {
+__device__ __forceinline__ void record_tiles(bool mine, const ViewInfo &vi, float4 A, float4 B, uint32_t tag, int lane,
+                                             Body &&body) {
+    int tx0 = 1, tx1 = 0, ty0 = 1, ty1 = 0;
+    const bool has = mine && record_rect(vi, A, B, tx0, tx1, ty0, ty1);
+    const int rw = tx1 - tx0 + 1;
+    const int count = has ? rw * (ty1 - ty0 + 1) : 0;
+    if (has && count <= kSoloTiles) {
+        const float ia = __fdividef(1.f, B.x), ic = __fdividef(1.f, B.z);
+        for (int t = 0; t < count; ++t) {
             const int ty = ty0 + t / rw, tx = tx0 + t % rw;
-            if (tile_hit(vi, A, B, ia, ic, tx, ty)) body(src, vi.tile_base + (uint32_t)(ty * vi.tiles_x + tx), A, tag);
+            if (tile_hit(vi, A, B, ia, ic, tx, ty)) body(lane, vi.tile_base + (uint32_t)(ty * vi.tiles_x + tx), A, tag);
+        }
+    }
+    uint32_t big = __ballot_sync(0xffffffffu, count > kSoloTiles);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        float4 As, Bs;
+        As.x = __shfl_sync(0xffffffffu, A.x, src);
+        As.y = __shfl_sync(0xffffffffu, A.y, src);
+        As.z = __shfl_sync(0xffffffffu, A.z, src);
+        As.w = __shfl_sync(0xffffffffu, A.w, src);
+        Bs.x = __shfl_sync(0xffffffffu, B.x, src);
+        Bs.y = __shfl_sync(0xffffffffu, B.y, src);
+        Bs.z = __shfl_sync(0xffffffffu, B.z, src);
+        Bs.w = __shfl_sync(0xffffffffu, B.w, src);
+        const uint32_t tg = __shfl_sync(0xffffffffu, tag, src);
+        const int sx0 = __shfl_sync(0xffffffffu, tx0, src), sy0 = __shfl_sync(0xffffffffu, ty0, src);
+        const int srw = __shfl_sync(0xffffffffu, rw, src), scount = __shfl_sync(0xffffffffu, count, src);
+        const float ia = __fdividef(1.f, Bs.x), ic = __fdividef(1.f, Bs.z);
+        for (int t = lane; t < scount; t += 32) {
+            const int ty = sy0 + t / srw, tx = sx0 + t % srw;
+            if (tile_hit(vi, As, Bs, ia, ic, tx, ty)) body(src, vi.tile_base + (uint32_t)(ty * vi.tiles_x + tx), As, tg);
         }
     }
 }
@@ -83,21 +100,27 @@ cudaError_t launch_upload_views(const ViewInfo *host_views, int V, ViewInfo *dev
     return cudaGetLastError();
 }
 
-// Exclusive scan of the per-(tile, sub-bucket) counts by one block (the last k_project
-// block): chunks of 4 x kBlock counters, vector loads, warp scans and a running carry.
-__device__ void scan_tiles(const WsPtrs &ws, const Dims &d) {
-    __shared__ uint32_t warp_sum[kWarps];
-    __shared__ unsigned long long s_carry;
+// Exclusive scan of the per-(tile, sub-bucket) counts into list offsets, by one block of
+// kScanThreads (chunks of 4 counters per thread, warp scans, a running carry); also the
+// total pair count, the longest tile list and the number of visible records.
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(WsPtrs ws, Dims d) {
+    __shared__ uint32_t warp_sum[kScanThreads / 32];
+    __shared__ uint32_t s_max;
+    __shared__ unsigned long long s_recs;
     const uint32_t TS = d.T * d.S;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    uint32_t max_tile = 0;
-    __syncthreads();
-    for (uint32_t base = 0; base < TS; base += 4 * kBlock) {
+    if (threadIdx.x == 0) {
+        s_max = 0;
+        s_recs = 0;
+    }
+    unsigned long long carry = 0;  // identical in every thread
+    for (uint32_t base = 0; base < TS; base += 4 * kScanThreads) {
         const uint32_t i0 = base + 4 * threadIdx.x;
         uint32_t c[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) c[k] = i0 + k < TS ? __ldcg(ws.tile_cnt + i0 + k) : 0u;
+        for (int k = 0; k < 4; ++k) c[k] = i0 + k < TS ? ws.tile_cnt[i0 + k] : 0u;
         const uint32_t mine = c[0] + c[1] + c[2] + c[3];
         uint32_t incl = mine;
 #pragma unroll
@@ -107,49 +130,54 @@ __device__ void scan_tiles(const WsPtrs &ws, const Dims &d) {
         }
         if (lane == 31) warp_sum[warp] = incl;
         __syncthreads();
-        uint32_t before = 0, total = 0;
-        for (int w = 0; w < kWarps; ++w) {
-            if (w < warp) before += warp_sum[w];
-            total += warp_sum[w];
+        uint32_t wi = lane < kScanThreads / 32 ? warp_sum[lane] : 0u;  // inclusive scan of the warp totals
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += v;
         }
-        unsigned long long run = s_carry + before + (incl - mine);
+        const uint32_t prev = __shfl_sync(0xffffffffu, wi, (warp + 31) & 31);
+        const uint32_t before = warp > 0 ? prev : 0u;
+        const uint32_t total = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
+        unsigned long long run = carry + before + (incl - mine);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (i0 + k < TS) {
                 const uint32_t o = (uint32_t)min(run, (unsigned long long)0xffffffffu);
                 ws.tile_start[i0 + k] = o;
                 ws.cursor[i0 + k] = o;
-                ws.tile_cnt[i0 + k] = 0;
                 run += c[k];
             }
-        // longest tile list: a tile's S sub-buckets are consecutive (S divides 4)
-        if (d.S <= 4) {
-            for (int k = 0; k < 4; k += d.S) {
-                uint32_t t = 0;
-                for (uint32_t q = 0; q < d.S; ++q) t += c[k + q];
-                max_tile = max(max_tile, t);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry += total;
+        carry += total;
         __syncthreads();
     }
-    if (d.S > 4) {  // tiles span several threads' chunks: measure from the finished offsets
-        const uint32_t total = (uint32_t)min(s_carry, (unsigned long long)0xffffffffu);
-        for (uint32_t t = threadIdx.x; t < d.T; t += kBlock) {
-            const uint32_t end = t + 1 < d.T ? ws.tile_start[(t + 1) * d.S] : total;
-            max_tile = max(max_tile, end - ws.tile_start[t * d.S]);
-        }
+    const uint32_t all = (uint32_t)min(carry, (unsigned long long)0xffffffffu);
+    if (threadIdx.x == 0) ws.tile_start[TS] = all;
+    __syncthreads();
+    uint32_t max_tile = 0;
+    for (uint32_t t = threadIdx.x; t < d.T; t += kScanThreads)
+        max_tile = max(max_tile, ws.tile_start[(t + 1) * d.S] - ws.tile_start[t * d.S]);
+    unsigned long long recs = 0;
+    for (uint32_t c = threadIdx.x; c < (uint32_t)d.V * (uint32_t)d.nblk; c += kScanThreads) recs += ws.cell_cnt[c];
+    max_tile = __reduce_max_sync(0xffffffffu, max_tile);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) recs += __shfl_xor_sync(0xffffffffu, recs, off);
+    if (lane == 0) {
+        atomicMax(&s_max, max_tile);
+        atomicAdd(&s_recs, recs);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned long long total = s_carry;
-        ws.tile_start[TS] = (uint32_t)min(total, (unsigned long long)0xffffffffu);
-        ws.hdr->n_pairs = total;
-        if (total > d.pair_cap) atomicOr(ws.err, (uint32_t)kErrPairs);
-        ws.hdr->k1_done = 0;
+        ws.hdr->max_tile = s_max;
+        ws.hdr->n_rec = s_recs;
+        ws.hdr->n_pairs = carry;
+        if (carry > d.pair_cap) atomicOr(ws.err, (uint32_t)kErrPairs);
     }
-    atomicMax(&ws.hdr->max_tile, max_tile);
+}
+
+cudaError_t launch_scan_tiles(const WsPtrs &ws, const Dims &d, cudaStream_t st) {
+    k_scan_tiles<<<1, kScanThreads, 0, st>>>(ws, d);
+    return cudaGetLastError();
 }
 
 template <int DT>
@@ -159,8 +187,7 @@ __global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
     __shared__ float sRt[12];
     __shared__ ViewInfo sv;
     __shared__ uint32_t warp_off[kWarps];
-    __shared__ uint32_t s_chunk;
-    __shared__ int s_last;
+    const uint32_t cell = (uint32_t)v * (uint32_t)L.d.nblk + (uint32_t)b;
     if (tid == 0) {
         load_pose(L.poses + 7 * v, sRt);
         sv = L.ws.views[v];
@@ -230,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
             }
         }
     }
-    // compaction: visible pairs of this block get consecutive records in Gaussian order
+    // compaction into this block's cell: visible Gaussians take the first slots, in order
     const uint32_t ballot = __ballot_sync(0xffffffffu, vis);
     if (lane == 0) warp_off[warp] = __popc(ballot);
     __syncthreads();
@@ -241,37 +268,24 @@ __global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
             warp_off[w] = run;
             run += c;
         }
-        s_chunk = run ? atomicAdd(&L.ws.hdr->n_rec, run) : 0u;
+        L.ws.cell_cnt[cell] = run;
     }
     __syncthreads();
     if (vis) {
-        const uint32_t rec = s_chunk + warp_off[warp] + __popc(ballot & ((1u << lane) - 1u));
-        if (rec < L.d.rec_cap) {
-            Rec r;
-            r.a = A; r.b = B; r.c = C;
-            L.ws.rec[rec] = r;
-            RecGrad z;
-            z.g0 = z.g1 = z.g2 = make_float4(0.f, 0.f, 0.f, 0.f);
-            L.ws.rec_grad[rec] = z;
-        } else {
-            atomicOr(L.ws.err, (uint32_t)kErrRecords);
-        }
+        const uint32_t rec = cell * kCell + warp_off[warp] + __popc(ballot & ((1u << lane) - 1u));
+        Rec r;
+        r.a = A; r.b = B; r.c = C;
+        L.ws.rec[rec] = r;
+        RecGrad z;
+        z.g0 = z.g1 = z.g2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        L.ws.rec_grad[rec] = z;
     }
     // per-(tile, sub-bucket) pair counts, the warp sharing each visible Gaussian's tiles
     uint32_t *cnt = L.ws.tile_cnt;
     const uint32_t nsub = L.d.S;
-    warp_tiles(ballot, vi, A, B, lane, nullptr, v, (uint32_t)i & (nsub - 1), [&](int, uint32_t tile, float4, uint32_t sub) {
+    record_tiles(vis, vi, A, B, (uint32_t)i & (nsub - 1), lane, [&](int, uint32_t tile, float4, uint32_t sub) {
         red_add(cnt + tile * nsub + sub, 1u);
     });
-    // the last block to finish turns the per-tile counts into offsets
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = atomicAdd(&L.ws.hdr->k1_done, 1u) == gridDim.x * gridDim.y - 1;
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        scan_tiles(L.ws, L.d);
-    }
 }
 
 cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st) {
@@ -287,47 +301,38 @@ cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st) {
 
 // One key per (record, tile met): depth bits (positive floats sort as unsigned ints) in
 // the high word, the record in the low word, stored at the next free slot of the tile's
-// sub-bucket.  Each warp takes 32 consecutive records and walks their tiles together
-// (warp_tiles): a Gaussian close to the camera that spans thousands of tiles is split
-// over 32 lanes instead of holding one thread while the rest of the grid finishes.
+// sub-bucket.  One block per cell, one thread per record (record_tiles).
 __global__ void __launch_bounds__(kBlock) k_emit(WsPtrs ws, Dims d) {
-    const uint32_t n = min(ws.hdr->n_rec, d.rec_cap);
+    const uint32_t cell = blockIdx.x;
+    const uint32_t cnt = ws.cell_cnt[cell];
+    if ((uint32_t)(threadIdx.x & ~31u) >= cnt) return;  // whole warps without records leave
     const int lane = threadIdx.x & 31;
-    const uint32_t warps = gridDim.x * (blockDim.x / 32);
-    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) / 32 * 32; base < n; base += warps * 32) {
-        const uint32_t r = base + lane;
-        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
-        int view = 0;
-        uint32_t sub = 0;
-        if (r < n) {
-            const Rec rec = ws.rec[r];
-            A = rec.a;
-            B = rec.b;
-            const uint64_t gv = __float_as_uint(rec.c.w);
-            view = (int)(gv / (uint64_t)d.n);
-            sub = (uint32_t)(gv % (uint64_t)d.n) & (d.S - 1);
-        }
-        const uint32_t bits = __ballot_sync(0xffffffffu, r < n);
-        const ViewInfo none{};
-        warp_tiles(bits, none, A, B, lane, ws.views, view, sub, [&](int src, uint32_t tile, float4 As, uint32_t sb) {
-            const unsigned long long key = ((unsigned long long)__float_as_uint(As.z) << 32) | (base + (uint32_t)src);
-            const uint32_t bucket = tile * d.S + sb;
-            const uint32_t slot = atomicAdd(ws.cursor + bucket, 1u);
-            if (slot < ws.tile_start[bucket + 1] && slot < d.pair_cap)
-                ws.keys[slot] = key;
-            else
-                atomicOr(ws.err, (uint32_t)kErrPairs);
-        });
+    const int view = (int)(cell / (uint32_t)d.nblk);
+    const ViewInfo vi = ws.views[view];
+    const uint32_t r = cell * kCell + threadIdx.x;
+    const bool mine = threadIdx.x < cnt;
+    float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
+    uint32_t sub = 0;
+    if (mine) {
+        const Rec rec = ws.rec[r];
+        A = rec.a;
+        B = rec.b;
+        sub = (uint32_t)((uint64_t)__float_as_uint(rec.c.w) % (uint64_t)d.n) & (d.S - 1);
     }
+    const uint32_t rbase = cell * kCell + (threadIdx.x & ~31u);
+    record_tiles(mine, vi, A, B, sub, lane, [&](int src, uint32_t tile, float4 As, uint32_t sb) {
+        const unsigned long long key = ((unsigned long long)__float_as_uint(As.z) << 32) | (rbase + (uint32_t)src);
+        const uint32_t bucket = tile * d.S + sb;
+        const uint32_t slot = atomicAdd(ws.cursor + bucket, 1u);
+        if (slot < ws.tile_start[bucket + 1] && slot < d.pair_cap)
+            ws.keys[slot] = key;
+        else
+            atomicOr(ws.err, (uint32_t)kErrPairs);
+    });
 }
 
 cudaError_t launch_emit(const WsPtrs &ws, const Dims &d, cudaStream_t st) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const uint64_t want = ((uint64_t)d.rec_cap + kBlock - 1) / kBlock;
-    const uint32_t grid = (uint32_t)max((uint64_t)1, min(want, (uint64_t)(sms > 0 ? sms * 8 : 1024)));
-    k_emit<<<grid, kBlock, 0, st>>>(ws, d);
+    k_emit<<<(uint32_t)d.V * (uint32_t)d.nblk, kBlock, 0, st>>>(ws, d);
     return cudaGetLastError();
 }
 

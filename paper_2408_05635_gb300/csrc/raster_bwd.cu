@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kTilePix) k_backward(BackwardLaunch L) {
         const int cnt = (int)min((uint32_t)kBatch, nmax - (uint32_t)b0);
         if (tid < cnt) {
             const uint32_t r = L.ws.sorted[start + (uint32_t)b0 + tid];
-            if (r < L.d.rec_cap) {
+            if (r < rec_slots(L.d)) {
                 const Rec rr = L.ws.rec[r];
                 const Footprint f = stage_footprint(rr.a, rr.b, x0, y0);
                 sP0[tid] = f.p0;
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kTilePix) k_backward(BackwardLaunch L) {
         __syncthreads();
         if (tid < cnt) {
             const uint32_t r = L.ws.sorted[start + (uint32_t)b0 + tid];
-            if (r < L.d.rec_cap) {
+            if (r < rec_slots(L.d)) {
                 const float *a = sAcc + tid * kAccStride;
                 const float4 v0 = make_float4(a[0], a[1], a[2], a[3]);
                 const float4 v1 = make_float4(a[4], a[5], a[6], 0.f);

@@ -14,7 +14,7 @@
 //
 // With targets, the combined loss of Sec. III-B (plus the depth-prior term) is
 // evaluated in the epilogue: its per-pixel gradient goes to the workspace for the
-// backward and its value is reduced per block in FP64 and added to the view's total.
+// backward and its value is reduced per tile in FP64 (summed per view by k_finalize).
 #include "gs_internal.cuh"
 
 namespace gsk {
@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(kTilePix) k_forward(ForwardLaunch L) {
     if (tid == 0) s_view = view_of_tile(L.ws.views, L.d.V, tile);
     __syncthreads();
     const int view = s_view;
+    (void)view;
     const ViewInfo vi = L.ws.views[view];
     const uint32_t local = tile - vi.tile_base;
     const int tx = (int)(local % (uint32_t)vi.tiles_x), ty = (int)(local / (uint32_t)vi.tiles_x);
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(kTilePix) k_forward(ForwardLaunch L) {
         const uint32_t idx = b0 + tid;
         if (idx < n) {
             const uint32_t r = L.ws.sorted[start + idx];
-            if (r < L.d.rec_cap) {
+            if (r < rec_slots(L.d)) {
                 const Rec rr = L.ws.rec[r];
                 const Footprint f = stage_footprint(rr.a, rr.b, x0, y0);
                 sP0[tid] = f.p0;
@@ -174,10 +175,10 @@ __global__ void __launch_bounds__(kTilePix) k_forward(ForwardLaunch L) {
         for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
         if ((tid & 31) == 0) s_loss[tid >> 5] = (double)l;
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0) {  // the tile's share; k_finalize sums the view's tiles in order
             double s = 0.0;
             for (int w = 0; w < kTilePix / 32; ++w) s += s_loss[w];
-            if (s != 0.0) atomicAdd(L.ws.loss + view, s);
+            L.ws.tile_loss[tile] = s;
         }
     }
 }

@@ -2,7 +2,8 @@
 //
 // Eqs. 2-4 composite the Gaussians of a pixel front to back, so every tile needs its
 // entries in ascending camera depth; ties are broken by Gaussian index (the order the
-// oracle uses).  k_emit leaves each tile's 64-bit keys (depth bits << 32 | record) in
+// oracle uses), which the record index already encodes (records are numbered in
+// (view, Gaussian) order).  k_emit leaves each tile's 64-bit keys (depth bits << 32 | record) in
 // arrival order inside the tile's own slice of the key array, so the sort is segmented
 // by construction: one block per tile sorts only its slice.  Slices of up to
 // kRankSortMax keys are sorted by ranking (no barriers), up to kSortSmemCap keys by a
@@ -46,28 +47,6 @@ __device__ void bitonic_sort(unsigned long long *k, int n) {
     }
 }
 
-// Keys with equal depth bits came out ordered by record; reorder each such run by
-// Gaussian index (one thread; runs are rare and short).
-__device__ void fix_ties(unsigned long long *k, int n, const Rec *rec) {
-    int tie = 0;
-    for (int i = threadIdx.x; i + 1 < n; i += blockDim.x)
-        if ((k[i] >> 32) == (k[i + 1] >> 32)) tie = 1;
-    if (!__syncthreads_or(tie)) return;
-    if (threadIdx.x == 0) {
-        for (int i = 1; i < n; ++i) {
-            int j = i;
-            while (j > 0 && (k[j - 1] >> 32) == (k[j] >> 32) &&
-                   __float_as_uint(rec[(uint32_t)k[j - 1]].c.w) > __float_as_uint(rec[(uint32_t)k[j]].c.w)) {
-                const unsigned long long t = k[j - 1];
-                k[j - 1] = k[j];
-                k[j] = t;
-                --j;
-            }
-        }
-    }
-    __syncthreads();
-}
-
 // Short lists (the common case): each thread ranks its keys by counting the smaller
 // ones (keys are unique: the low word is the record) and scatters them; no barrier
 // between steps, O(n^2 / threads) compares.
@@ -107,7 +86,6 @@ __global__ void __launch_bounds__(kTilePix) k_tile_sort(WsPtrs ws, Dims d) {
         k = ws.keys + start;
         bitonic_sort(k, n);
     }
-    fix_ties(k, n, ws.rec);
     for (int i = threadIdx.x; i < n; i += blockDim.x) ws.sorted[start + i] = (uint32_t)k[i];
 }
 

@@ -325,10 +325,9 @@ class Rasterizer:
             pass
 
     # -- workspace ---------------------------------------------------------------------
-    def problem(self, n: int, cams: Sequence, pair_capacity: int, record_capacity: int = 0) -> gs_problem:
+    def problem(self, n: int, cams: Sequence, pair_capacity: int) -> gs_problem:
         arr = cameras_c(cams)
-        p = gs_problem(int(n), len(cams), 0, ctypes.cast(arr, ctypes.POINTER(gs_camera)), int(pair_capacity),
-                       int(record_capacity))
+        p = gs_problem(int(n), len(cams), 0, ctypes.cast(arr, ctypes.POINTER(gs_camera)), int(pair_capacity), 0)
         p._cams = arr  # keep the host array alive with the struct
         return p
 
@@ -342,7 +341,7 @@ class Rasterizer:
 
     def measure(self, g: GaussianTensors, cams: Sequence, poses: torch.Tensor) -> tuple[int, int]:
         """Project once with minimal capacities and return (pairs, records) of the scene."""
-        prob = self.problem(g.n, cams, pair_capacity=1, record_capacity=1)
+        prob = self.problem(g.n, cams, pair_capacity=1)
         ws, nb = self.workspace(prob)
         gs_project(self.ctx, prob, g.c(), poses, ws, nb)
         _, counts = gs_sync_status(self.ctx)
@@ -350,10 +349,8 @@ class Rasterizer:
 
     def plan(self, g: GaussianTensors, cams: Sequence, poses: torch.Tensor, margin: float = 1.25,
              min_pairs: int = 1024) -> gs_problem:
-        pairs, recs = self.measure(g, cams, poses)
-        full = g.n * len(cams)
-        return self.problem(g.n, cams, max(min_pairs, int(pairs * margin) + 1024),
-                            min(full, max(1, int(recs * margin) + 1024)))
+        pairs, _ = self.measure(g, cams, poses)
+        return self.problem(g.n, cams, max(min_pairs, int(pairs * margin) + 1024))
 
     # -- one rendering pass ------------------------------------------------------------
     def render(self, prob: gs_problem, g: GaussianTensors, poses: torch.Tensor, targets=None, stream=None,

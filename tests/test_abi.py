@@ -63,8 +63,10 @@ def test_workspace_size_validation(libpath):
     prob = gs.gs_problem(200000, 2, 0, ctypes.cast(cams, ctypes.POINTER(gs.gs_camera)), 1 << 22, 0)
     n = ctypes.c_size_t(0)
     assert lib.gs_workspace_size(h, ctypes.byref(prob), ctypes.byref(n)) == 0
-    # records 2N x 96 B, pairs 12 B each, pixels 28 B each: a lower bound on the layout
+    # record slots 2N x 96 B, pairs 12 B each, pixels 28 B each: a lower bound on the layout
     assert n.value >= 2 * 200000 * 96 + (1 << 22) * 12 + (640 * 480 + 400) * 28
+    bad = gs.gs_problem(1000, 2, 0, ctypes.cast(cams, ctypes.POINTER(gs.gs_camera)), 1 << 22, 5)
+    assert lib.gs_workspace_size(h, ctypes.byref(bad), ctypes.byref(n)) == 1  # reserved field
     bad = gs.gs_problem(1 << 31, 4, 0, ctypes.cast(cams, ctypes.POINTER(gs.gs_camera)), 1 << 22, 0)
     assert lib.gs_workspace_size(h, ctypes.byref(bad), ctypes.byref(n)) == 1
     bad = gs.gs_problem(1000, 2, 0, ctypes.cast(cams, ctypes.POINTER(gs.gs_camera)), 0, 0)
