@@ -223,7 +223,7 @@ gs_status gs_sync_status(gs_ctx *ctx, void *stream, gs_counts *counts);
 
 /* Per-kernel device time of the last enqueued work, for profiling. */
 typedef struct {
-    char name[24]; /* kernel (k_project, k_scan_tiles, k_emit, k_tile_sort, k_forward, k_backward,
+    char name[24]; /* kernel (k_project, k_scan_tiles, k_emit, k_forward, k_backward,
                       k_bproject, k_finalize) */
     float ms;      /* CUDA-event time from the end of the previous kernel to the end of this one */
 } gs_kernel_time;

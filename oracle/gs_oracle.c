@@ -154,26 +154,27 @@ static void pose_unpack(const double pose[7], double R[9], double t[3], double q
 
 /* The front-to-back order of Eqs. 2-4 is a discrete decision taken by floating point,
  * so it is taken in the precision of the GPU kernels, on an exactly specified FP32 key:
- * the pose rotation is formed in FP64 from the quaternion scaled by 1/sqrt(|q|^2) (each
- * operation rounded, no contraction), rounded to FP32, and the camera depth of mean m is
- * fmaf(R20, m0, fmaf(R21, m1, fmaf(R22, m2, t2))) in FP32.  The near-plane test uses the
- * same key.  Everything else (mu', Sigma', the depth d_i of Eq. 3) stays FP64. */
+ * the pose quaternion and translation are rounded to FP32, |q|^2 is summed left to
+ * right, q is divided by the correctly rounded sqrt(|q|^2), the rotation entries are
+ * formed with every FP32 operation rounded (no contraction), and the camera depth of
+ * mean m is fmaf(R20, m0, fmaf(R21, m1, fmaf(R22, m2, t2))).  The near-plane test uses
+ * the same key.  Everything else (mu', Sigma', the depth d_i of Eq. 3) stays FP64. */
 static void pose_rot_f32(const double pose[7], float Rf[9], float tf[3]) {
-    double w = pose[0], x = pose[1], y = pose[2], z = pose[3];
-    const double inv = 1.0 / sqrt(((w * w + x * x) + y * y) + z * z);
-    w *= inv;
-    x *= inv;
-    y *= inv;
-    z *= inv;
-    Rf[0] = (float)(1.0 - 2.0 * (y * y + z * z));
-    Rf[1] = (float)(2.0 * (x * y - w * z));
-    Rf[2] = (float)(2.0 * (x * z + w * y));
-    Rf[3] = (float)(2.0 * (x * y + w * z));
-    Rf[4] = (float)(1.0 - 2.0 * (x * x + z * z));
-    Rf[5] = (float)(2.0 * (y * z - w * x));
-    Rf[6] = (float)(2.0 * (x * z - w * y));
-    Rf[7] = (float)(2.0 * (y * z + w * x));
-    Rf[8] = (float)(1.0 - 2.0 * (x * x + y * y));
+    float w = (float)pose[0], x = (float)pose[1], y = (float)pose[2], z = (float)pose[3];
+    const float nrm = sqrtf(((w * w + x * x) + y * y) + z * z);
+    w = w / nrm;
+    x = x / nrm;
+    y = y / nrm;
+    z = z / nrm;
+    Rf[0] = 1.0f - 2.0f * (y * y + z * z);
+    Rf[1] = 2.0f * (x * y - w * z);
+    Rf[2] = 2.0f * (x * z + w * y);
+    Rf[3] = 2.0f * (x * y + w * z);
+    Rf[4] = 1.0f - 2.0f * (x * x + z * z);
+    Rf[5] = 2.0f * (y * z - w * x);
+    Rf[6] = 2.0f * (x * z - w * y);
+    Rf[7] = 2.0f * (y * z + w * x);
+    Rf[8] = 1.0f - 2.0f * (x * x + y * y);
     tf[0] = (float)pose[4];
     tf[1] = (float)pose[5];
     tf[2] = (float)pose[6];

@@ -21,8 +21,8 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
     size_t err, hdr, tile_cnt, zero_end;
-    size_t views, view_rt, cell_cnt, tile_start, cursor, rec, rec_grad, keys, sorted, t_final, n_last, upstream,
-        tile_loss, pose_part, total;
+    size_t views, view_rt, cell_cnt, tile_start, cursor, tile_order, rec, rec_grad, keys, sorted, t_final, n_last,
+        upstream, tile_loss, pose_part, total;
 };
 
 struct Problem {
@@ -195,6 +195,7 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     L.cell_cnt = take(sizeof(uint32_t) * cells);
     L.tile_start = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
     L.cursor = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
+    L.tile_order = take(sizeof(uint32_t) * (size_t)d.T);
     L.rec = take(sizeof(Rec) * cells * kCell);
     L.rec_grad = take(sizeof(RecGrad) * cells * kCell);
     L.keys = take(sizeof(unsigned long long) * (size_t)d.pair_cap);
@@ -219,6 +220,7 @@ WsPtrs ws_ptrs(void *base, const Layout &L) {
     w.cell_cnt = reinterpret_cast<uint32_t *>(b + L.cell_cnt);
     w.tile_start = reinterpret_cast<uint32_t *>(b + L.tile_start);
     w.cursor = reinterpret_cast<uint32_t *>(b + L.cursor);
+    w.tile_order = reinterpret_cast<uint32_t *>(b + L.tile_order);
     w.rec = reinterpret_cast<Rec *>(b + L.rec);
     w.rec_grad = reinterpret_cast<RecGrad *>(b + L.rec_grad);
     w.keys = reinterpret_cast<unsigned long long *>(b + L.keys);
@@ -273,9 +275,7 @@ cudaError_t enqueue_project(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, voi
 
 cudaError_t enqueue_forward(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, const gs_targets *t, float *rgb,
                             float *depth, float *sil, cudaStream_t st) {
-    cudaError_t e = launch_tile_sort(w, pr.d, st);
-    if (e != cudaSuccess) return e;
-    if ((e = mark(ctx, st, "k_tile_sort")) != cudaSuccess) return e;
+    cudaError_t e;
     ForwardLaunch F;
     F.ws = w;
     F.d = pr.d;

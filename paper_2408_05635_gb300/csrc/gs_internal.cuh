@@ -1,15 +1,16 @@
 // gs_internal.cuh -- device data layout and helpers shared by the rasterizer kernels.
 //
 // Pipeline of one rendering pass (every step is a kernel of this library):
-//   k_project   Gaussian x view: projection, opacity-aware support, tiles touched,
-//               compaction into visible records, per-tile counts; the last block scans
-//               the tile counts into tile offsets.
+//   k_project   Gaussian x view: projection, opacity-aware support, compaction into
+//               visible records, per-tile pair counts.
+//   k_scan_tiles  tile offsets, tile launch order (longest lists first).
 //   k_emit      visible record: one 64-bit key (depth bits << 32 | record) per tile met.
-//   k_tile_sort tile: sort its keys by (depth, Gaussian index) and write record ids.
-//   k_forward   tile: Eqs. 2-4 front to back; optional fused combined loss.
+//   k_forward   tile: sort its keys by (depth, Gaussian index), then Eqs. 2-4 front to
+//               back; optional fused combined loss.
 //   k_backward  tile: reverse compositing; per-record screen-space gradients.
-//   k_bproject  Gaussian x view: chain rule to parameters and pose; FP64 pose
-//               reduction and (tracking) the decoupled Adam step.
+//   k_bproject  record: chain rule to parameters and pose; per-cell pose partials.
+//   k_finalize  view: FP64 sums of the loss and pose partials; (tracking) the decoupled
+//               Adam step.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -25,7 +26,6 @@ constexpr int kTile = 16;                 // tile edge in pixels
 constexpr int kTilePix = kTile * kTile;   // pixels (= threads) per tile block
 constexpr int kBlock = 256;               // threads per Gaussian-parallel block
 constexpr int kWarps = kBlock / 32;       // warps per Gaussian-parallel block
-constexpr int kSortSmemCap = 4096;        // tiles up to this many keys sort in shared memory
 constexpr int kCell = kBlock;             // Gaussians (and record slots) per cell
 constexpr int kBatch = 256;               // Gaussians staged per compositing batch
 
@@ -83,6 +83,7 @@ struct WsPtrs {
     uint32_t *cell_cnt;    // V x nblk, visible records per cell
     uint32_t *tile_start;  // T x S + 1, exclusive scan of the counts
     uint32_t *cursor;      // T x S, emission cursors
+    uint32_t *tile_order;  // T, tiles by descending list length (launch order of the tile kernels)
     Rec *rec;              // V x nblk x 256 record slots
     RecGrad *rec_grad;     // same slots
     unsigned long long *keys;  // pair_capacity
@@ -170,28 +171,30 @@ __device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, 
     R[8] = 1.f - 2.f * (x * x + y * y);
 }
 
-// Pose (7 doubles) -> FP32 rotation (9) and translation (3).  The rotation is formed in
-// FP64 with every operation explicitly rounded (no contraction) and then rounded to
-// FP32, so the camera-frame depth below is an exactly specified FP32 number: the depth
-// order of Eqs. 2-4 and the near-plane test are decided on it.
+// Pose (7 doubles) -> FP32 rotation (9) and translation (3), an exactly specified FP32
+// computation: every input rounded to FP32, |q|^2 summed left to right, the unit
+// quaternion q / sqrt(|q|^2) with a correctly rounded square root and division, then the
+// rotation entries with every operation rounded (no contraction).  The camera-frame
+// depth below is therefore an exactly specified FP32 number: the depth order of
+// Eqs. 2-4 and the near-plane test are decided on it.
 __device__ __forceinline__ void load_pose(const double *pose, float Rt[12]) {
-    double w = pose[0], x = pose[1], y = pose[2], z = pose[3];
-    const double ss = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(w, w), __dmul_rn(x, x)), __dmul_rn(y, y)),
-                                __dmul_rn(z, z));
-    const double inv = __ddiv_rn(1.0, __dsqrt_rn(ss));
-    w = __dmul_rn(w, inv);
-    x = __dmul_rn(x, inv);
-    y = __dmul_rn(y, inv);
-    z = __dmul_rn(z, inv);
-    Rt[0] = __double2float_rn(__dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, y), __dmul_rn(z, z)))));
-    Rt[1] = __double2float_rn(__dmul_rn(2.0, __dsub_rn(__dmul_rn(x, y), __dmul_rn(w, z))));
-    Rt[2] = __double2float_rn(__dmul_rn(2.0, __dadd_rn(__dmul_rn(x, z), __dmul_rn(w, y))));
-    Rt[3] = __double2float_rn(__dmul_rn(2.0, __dadd_rn(__dmul_rn(x, y), __dmul_rn(w, z))));
-    Rt[4] = __double2float_rn(__dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(z, z)))));
-    Rt[5] = __double2float_rn(__dmul_rn(2.0, __dsub_rn(__dmul_rn(y, z), __dmul_rn(w, x))));
-    Rt[6] = __double2float_rn(__dmul_rn(2.0, __dsub_rn(__dmul_rn(x, z), __dmul_rn(w, y))));
-    Rt[7] = __double2float_rn(__dmul_rn(2.0, __dadd_rn(__dmul_rn(y, z), __dmul_rn(w, x))));
-    Rt[8] = __double2float_rn(__dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)))));
+    float w = __double2float_rn(pose[0]), x = __double2float_rn(pose[1]);
+    float y = __double2float_rn(pose[2]), z = __double2float_rn(pose[3]);
+    const float ss = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(w, w), __fmul_rn(x, x)), __fmul_rn(y, y)), __fmul_rn(z, z));
+    const float nrm = __fsqrt_rn(ss);
+    w = __fdiv_rn(w, nrm);
+    x = __fdiv_rn(x, nrm);
+    y = __fdiv_rn(y, nrm);
+    z = __fdiv_rn(z, nrm);
+    Rt[0] = __fsub_rn(1.f, __fmul_rn(2.f, __fadd_rn(__fmul_rn(y, y), __fmul_rn(z, z))));
+    Rt[1] = __fmul_rn(2.f, __fsub_rn(__fmul_rn(x, y), __fmul_rn(w, z)));
+    Rt[2] = __fmul_rn(2.f, __fadd_rn(__fmul_rn(x, z), __fmul_rn(w, y)));
+    Rt[3] = __fmul_rn(2.f, __fadd_rn(__fmul_rn(x, y), __fmul_rn(w, z)));
+    Rt[4] = __fsub_rn(1.f, __fmul_rn(2.f, __fadd_rn(__fmul_rn(x, x), __fmul_rn(z, z))));
+    Rt[5] = __fmul_rn(2.f, __fsub_rn(__fmul_rn(y, z), __fmul_rn(w, x)));
+    Rt[6] = __fmul_rn(2.f, __fsub_rn(__fmul_rn(x, z), __fmul_rn(w, y)));
+    Rt[7] = __fmul_rn(2.f, __fadd_rn(__fmul_rn(y, z), __fmul_rn(w, x)));
+    Rt[8] = __fsub_rn(1.f, __fmul_rn(2.f, __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y))));
     Rt[9] = __double2float_rn(pose[4]);
     Rt[10] = __double2float_rn(pose[5]);
     Rt[11] = __double2float_rn(pose[6]);
@@ -372,7 +375,6 @@ cudaError_t launch_upload_views(const ViewInfo *host_views, int V, ViewInfo *dev
 cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st);
 cudaError_t launch_scan_tiles(const WsPtrs &ws, const Dims &d, cudaStream_t st);
 cudaError_t launch_emit(const WsPtrs &ws, const Dims &d, cudaStream_t st);
-cudaError_t launch_tile_sort(const WsPtrs &ws, const Dims &d, cudaStream_t st);
 
 struct ForwardLaunch {
     WsPtrs ws;

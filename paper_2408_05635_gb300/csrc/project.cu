@@ -43,14 +43,14 @@ __device__ __forceinline__ bool tile_hit(const ViewInfo &vi, float4 A, float4 B,
 // record's A, record's tag) runs once for every tile the support meets.
 constexpr int kSoloTiles = 24;
 
-template <class Body>
+template <bool SOLO = true, class Body>
 __device__ __forceinline__ void record_tiles(bool mine, const ViewInfo &vi, float4 A, float4 B, uint32_t tag, int lane,
                                              Body &&body) {
     int tx0 = 1, tx1 = 0, ty0 = 1, ty1 = 0;
     const bool has = mine && record_rect(vi, A, B, tx0, tx1, ty0, ty1);
     const int rw = tx1 - tx0 + 1;
     const int count = has ? rw * (ty1 - ty0 + 1) : 0;
-    if (has && count <= kSoloTiles) {
+    if (SOLO && has && count <= kSoloTiles) {
         const float ia = __fdividef(1.f, B.x), ic = __fdividef(1.f, B.z);
         for (int t = 0; t < count; ++t) {
             const int ty = ty0 + t / rw, tx = tx0 + t % rw;
@@ -104,6 +104,7 @@ cudaError_t launch_upload_views(const ViewInfo *host_views, int V, ViewInfo *dev
 // kScanThreads (chunks of 4 counters per thread, warp scans, a running carry); also the
 // total pair count, the longest tile list and the number of visible records.
 constexpr int kScanThreads = 1024;
+constexpr int kOrderBuckets = kScanThreads;  // list lengths >= kOrderBuckets - 1 share the first bucket
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(WsPtrs ws, Dims d) {
     __shared__ uint32_t warp_sum[kScanThreads / 32];
@@ -153,10 +154,43 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(WsPtrs ws, Dims d) 
     }
     const uint32_t all = (uint32_t)min(carry, (unsigned long long)0xffffffffu);
     if (threadIdx.x == 0) ws.tile_start[TS] = all;
+    // launch order of the tile kernels: longest lists first (counting sort on the length,
+    // descending), so the slowest tiles start in the first wave instead of the tail
+    __shared__ uint32_t s_bucket[kOrderBuckets];
+    s_bucket[threadIdx.x] = 0;
     __syncthreads();
     uint32_t max_tile = 0;
-    for (uint32_t t = threadIdx.x; t < d.T; t += kScanThreads)
-        max_tile = max(max_tile, ws.tile_start[(t + 1) * d.S] - ws.tile_start[t * d.S]);
+    for (uint32_t t = threadIdx.x; t < d.T; t += kScanThreads) {
+        const uint32_t len = ws.tile_start[(t + 1) * d.S] - ws.tile_start[t * d.S];
+        max_tile = max(max_tile, len);
+        atomicAdd(&s_bucket[kOrderBuckets - 1 - min(len, (uint32_t)kOrderBuckets - 1)], 1u);
+    }
+    __syncthreads();
+    {  // exclusive scan of the buckets, one bucket per thread
+        const uint32_t c = s_bucket[threadIdx.x];
+        uint32_t incl = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        uint32_t wi = lane < kScanThreads / 32 ? warp_sum[lane] : 0u;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += v;
+        }
+        const uint32_t prev = __shfl_sync(0xffffffffu, wi, (warp + 31) & 31);
+        s_bucket[threadIdx.x] = (warp > 0 ? prev : 0u) + incl - c;
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < d.T; t += kScanThreads) {
+        const uint32_t len = ws.tile_start[(t + 1) * d.S] - ws.tile_start[t * d.S];
+        const uint32_t pos = atomicAdd(&s_bucket[kOrderBuckets - 1 - min(len, (uint32_t)kOrderBuckets - 1)], 1u);
+        ws.tile_order[pos] = t;
+    }
     unsigned long long recs = 0;
     for (uint32_t c = threadIdx.x; c < (uint32_t)d.V * (uint32_t)d.nblk; c += kScanThreads) recs += ws.cell_cnt[c];
     max_tile = __reduce_max_sync(0xffffffffu, max_tile);
@@ -181,7 +215,7 @@ cudaError_t launch_scan_tiles(const WsPtrs &ws, const Dims &d, cudaStream_t st) 
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
+__global__ void __launch_bounds__(kBlock, 5) k_project(ProjectLaunch L) {
     const int v = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     __shared__ float sRt[12];
@@ -212,9 +246,9 @@ __global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
             qw *= qi; qx *= qi; qy *= qi; qz *= qi;
             float Rg[9];
             quat_to_rot(qw, qx, qy, qz, Rg);
-            const float s0 = expf(ld_attr<DT>(L.g.log_scales, 3 * i));
-            const float s1 = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 1));
-            const float s2 = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 2));
+            const float s0 = __expf(ld_attr<DT>(L.g.log_scales, 3 * i));
+            const float s1 = __expf(ld_attr<DT>(L.g.log_scales, 3 * i + 1));
+            const float s2 = __expf(ld_attr<DT>(L.g.log_scales, 3 * i + 2));
             // M = W Rg diag(s): Sigma_c = M M^T
             float M[9];
 #pragma unroll
@@ -223,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
                 M[3 * r + 1] = (sRt[3 * r] * Rg[1] + sRt[3 * r + 1] * Rg[4] + sRt[3 * r + 2] * Rg[7]) * s1;
                 M[3 * r + 2] = (sRt[3 * r] * Rg[2] + sRt[3 * r + 1] * Rg[5] + sRt[3 * r + 2] * Rg[8]) * s2;
             }
-            const float iz = 1.f / z;
+            const float iz = __fdividef(1.f, z);
             const float J00 = vi.fx * iz, J02 = -vi.fx * x * iz * iz;
             const float J11 = vi.fy * iz, J12 = -vi.fy * y * iz * iz;
             // N = J M, Sigma' = N N^T + dilation I
@@ -238,11 +272,11 @@ __global__ void __launch_bounds__(kBlock) k_project(ProjectLaunch L) {
             const float S11 = N1[0] * N1[0] + N1[1] * N1[1] + N1[2] * N1[2] + S.dilation;
             const float det = S00 * S11 - S01 * S01;
             if (det > 0.f) {
-                const float idet = 1.f / det;
-                const float o = 1.f / (1.f + expf(-ld_attr<DT>(L.g.logits, i)));
+                const float idet = __fdividef(1.f, det);
+                const float o = __fdividef(1.f, 1.f + __expf(-ld_attr<DT>(L.g.logits, i)));
                 float dmax2;
                 if (S.alpha_min > 0.f)
-                    dmax2 = o >= S.alpha_min ? 2.f * logf(o / S.alpha_min) : -1.f;
+                    dmax2 = o >= S.alpha_min ? 2.f * __logf(__fdividef(o, S.alpha_min)) : -1.f;
                 else
                     dmax2 = INFINITY;
                 if (dmax2 >= 0.f) {
@@ -320,7 +354,43 @@ __global__ void __launch_bounds__(kBlock) k_emit(WsPtrs ws, Dims d) {
         sub = (uint32_t)((uint64_t)__float_as_uint(rec.c.w) % (uint64_t)d.n) & (d.S - 1);
     }
     const uint32_t rbase = cell * kCell + (threadIdx.x & ~31u);
-    record_tiles(mine, vi, A, B, sub, lane, [&](int src, uint32_t tile, float4 As, uint32_t sb) {
+    // small rectangles: this lane alone, slot atomics issued eight at a time before the
+    // dependent stores, so a record waits for about one atomic round trip per eight tiles
+    int tx0 = 1, tx1 = 0, ty0 = 1, ty1 = 0;
+    const bool has = mine && record_rect(vi, A, B, tx0, tx1, ty0, ty1);
+    const int rw = tx1 - tx0 + 1;
+    const int count = has ? rw * (ty1 - ty0 + 1) : 0;
+    if (has && count <= kSoloTiles) {
+        const float ia = __fdividef(1.f, B.x), ic = __fdividef(1.f, B.z);
+        uint32_t hits = 0;
+        for (int t = 0; t < count; ++t)
+            if (tile_hit(vi, A, B, ia, ic, tx0 + t % rw, ty0 + t / rw)) hits |= 1u << t;
+        const unsigned long long key = ((unsigned long long)__float_as_uint(A.z) << 32) | r;
+        while (hits) {
+            uint32_t bucket[8], slot[8];
+            bool live[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                live[k] = hits != 0;
+                const int t = live[k] ? __ffs(hits) - 1 : 0;
+                hits &= hits - 1;
+                bucket[k] = (vi.tile_base + (uint32_t)((ty0 + t / rw) * vi.tiles_x + tx0 + t % rw)) * d.S + sub;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (live[k]) slot[k] = atomicAdd(ws.cursor + bucket[k], 1u);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (live[k]) {
+                    if (slot[k] < ws.tile_start[bucket[k] + 1] && slot[k] < d.pair_cap)
+                        ws.keys[slot[k]] = key;
+                    else
+                        atomicOr(ws.err, (uint32_t)kErrPairs);
+                }
+        }
+    }
+    // large rectangles: the warp splits them
+    record_tiles<false>(mine, vi, A, B, sub, lane, [&](int src, uint32_t tile, float4 As, uint32_t sb) {
         const unsigned long long key = ((unsigned long long)__float_as_uint(As.z) << 32) | (rbase + (uint32_t)src);
         const uint32_t bucket = tile * d.S + sb;
         const uint32_t slot = atomicAdd(ws.cursor + bucket, 1u);

@@ -53,14 +53,14 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV], int lane, i
 // Value slots follow RecGrad: 0 d mu'_x, 1 d mu'_y, 2 d depth, 3 d opacity,
 // 4..6 d conic (a, b, c), 8..10 d rgb; other slots stay zero.
 template <int NV>
-__global__ void __launch_bounds__(kTilePix) k_backward(BackwardLaunch L) {
+__global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     __shared__ float4 sP0[kBatch], sC[kBatch], sQ[kBatch], sBox[kBatch];
     __shared__ float2 sP1[kBatch];
     __shared__ float sAcc[kBatch * kAccStride];
     __shared__ uint8_t sList[kTilePix / 32][kBatch];
     __shared__ int s_view;
     __shared__ uint32_t s_nmax;
-    const uint32_t tile = blockIdx.x;
+    const uint32_t tile = L.ws.tile_order[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         s_view = view_of_tile(L.ws.views, L.d.V, tile);
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kTilePix) k_backward(BackwardLaunch L) {
                     ++n_contrib;
                     const float araw = ex2_approx(pe.poly);
                     const float a = fminf(S.alpha_max, araw), om = 1.f - a;
-                    T = T * __frcp_rn(om);  // transmittance in front of this Gaussian
+                    T = T * __fdividef(1.f, om);  // transmittance in front of this Gaussian
                     const float4 Cc = sC[j];
                     const float d0 = Cc.x - B0, d1 = Cc.y - B1, d2 = Cc.z - B2, d3 = Cc.w - B3, d4 = 1.f - B4;
                     const float dalpha = T * (g0 * d0 + g1 * d1 + g2 * d2 + gD * d3 + gS * d4);

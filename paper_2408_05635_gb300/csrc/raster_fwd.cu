@@ -1,6 +1,7 @@
 // raster_fwd.cu -- front-to-back compositing of colour, depth and silhouette.
 //
-// One block per 16 x 16 tile, one thread per pixel.  For pixel p and the tile's
+// One block per 16 x 16 tile, one thread per pixel.  The block first sorts its tile's
+// list (tile_sort.cuh).  For pixel p and the tile's
 // Gaussians in (depth, index) order:
 //   C(p) = sum_i c_i a_i T_i   (Eq. 2)
 //   D(p) = sum_i d_i a_i T_i   (Eq. 3, d_i = camera-frame depth of the mean)
@@ -16,19 +17,21 @@
 // evaluated in the epilogue: its per-pixel gradient goes to the workspace for the
 // backward and its value is reduced per tile in FP64 (summed per view by k_finalize).
 #include "gs_internal.cuh"
+#include "tile_sort.cuh"
 
 namespace gsk {
 
 __device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
 template <bool LOSS>
-__global__ void __launch_bounds__(kTilePix) k_forward(ForwardLaunch L) {
+__global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     __shared__ float4 sP0[kBatch], sC[kBatch], sBox[kBatch];
     __shared__ float2 sP1[kBatch];
     __shared__ uint8_t sList[kTilePix / 32][kBatch];
+    __shared__ unsigned long long sKeys[kSortSmemKeys];
     __shared__ int s_view;
     __shared__ double s_loss[kTilePix / 32];
-    const uint32_t tile = blockIdx.x;
+    const uint32_t tile = L.ws.tile_order[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_view = view_of_tile(L.ws.views, L.d.V, tile);
     __syncthreads();
@@ -50,6 +53,7 @@ __global__ void __launch_bounds__(kTilePix) k_forward(ForwardLaunch L) {
 
     uint32_t start;
     const uint32_t n = tile_entries(L.ws, L.d, tile, start);
+    sort_tile(L.ws, start, (int)n, sKeys);  // this tile's list in (depth, Gaussian) order
     float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, D = 0.f;
     uint32_t last = 0, n_eval = 0, n_contrib = 0;
     bool done = !inside;
