@@ -239,6 +239,38 @@ gs_status gs_set_profiling(gs_ctx *ctx, int32_t enable);
  * number available.  Errors: STATE (profiling off or nothing recorded), CUDA. */
 gs_status gs_kernel_times(gs_ctx *ctx, gs_kernel_time *out, int32_t cap, int32_t *count);
 
+/* ------------------------------------------------------------------ no-allocation render */
+
+/* Limits of gs_render_static. */
+#define GS_STATIC_MAX_GAUSSIANS 65536
+#define GS_STATIC_MAX_PIXELS (640 * 480)
+#define GS_STATIC_MAX_PAIRS (1 << 19)
+
+/* Render one view -- projection, tile binning, per-tile depth sort and compositing of
+ * colour, depth and silhouette, with the combined loss when targets are given -- the
+ * same computation as gs_project + gs_forward, but with no workspace and no allocation.
+ * The paper has no counterpart: this is for callers that cannot allocate device memory
+ * where they render (a plugin or real-time loop inside a host application that owns
+ * the memory pool, or code that must not call cudaMalloc / cudaFree because they
+ * synchronise the device).  Its scratch (about 24 MB) is a static device array of the
+ * library, which every GPU that loads the library holds until the process exits.
+ *   cfg: settings (gs_default_config for the defaults); no context is needed.
+ *   g: at most GS_STATIC_MAX_GAUSSIANS Gaussians; cam: at most GS_STATIC_MAX_PIXELS
+ *   pixels; pose: device, 7 doubles; targets: NULL or an RGB-D observation (loss then
+ *   optional); rgb / depth / sil: device outputs, each may be NULL; loss: device, one
+ *   double, may be NULL; err_flags: device, one uint32 receiving the device-detected
+ *   flags of gs_counts (bit 1: more than GS_STATIC_MAX_PAIRS pairs, output invalid),
+ *   may be NULL.
+ * The first call on a device looks up the array's device address (with that device
+ * current); make it before any stream capture.  Every call uses the same array and the
+ * array keeps the last call's contents: calls that overlap on the GPU (different
+ * streams, or several host threads) race and corrupt each other's results.  Nothing is
+ * allocated, host or device.  Errors: INVALID_ARG (NULL argument, a size above the
+ * limits), UNSUPPORTED (tile shape), CUDA. */
+gs_status gs_render_static(const gs_config *cfg, const gs_gaussians *g, const gs_camera *cam, const double *pose,
+                           const gs_targets *targets, float *rgb, float *depth, float *sil, double *loss,
+                           uint32_t *err_flags, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -114,6 +114,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                         c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
             "gs_sync_status": (c_int32, [c_void_p, c_void_p, P(gs_counts)]),
             "gs_set_profiling": (c_int32, [c_void_p, c_int32]),
+            "gs_render_static": (c_int32, [P(gs_config), P(gs_gaussians), P(gs_camera), c_void_p, P(gs_targets),
+                                           c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
             "gs_kernel_times": (c_int32, [c_void_p, P(gs_kernel_time), c_int32, P(c_int32)]),
         }
         for name, (res, args) in sigs.items():
@@ -225,6 +227,17 @@ def gs_kernel_times(ctx, cap: int = 4096) -> list[tuple[str, float]]:
     cnt = c_int32(0)
     _check(ctx, load().gs_kernel_times(ctx, arr, cap, ctypes.byref(cnt)), "gs_kernel_times")
     return [(arr[k].name.decode(), float(arr[k].ms)) for k in range(min(cap, cnt.value))]
+
+
+def gs_render_static(cfg: gs_config, g: gs_gaussians, cam: gs_camera, pose, targets: gs_targets | None = None,
+                     rgb=None, depth=None, sil=None, loss=None, err_flags=None, stream=None) -> None:
+    """Single-view render whose scratch is a static device array of the library: no
+    workspace, no allocation (see include/gs.h for the limits and the sharing rules)."""
+    st = load().gs_render_static(ctypes.byref(cfg), ctypes.byref(g), ctypes.byref(cam), _ptr(pose),
+                                 ctypes.byref(targets) if targets is not None else None, _ptr(rgb), _ptr(depth),
+                                 _ptr(sil), _ptr(loss), _ptr(err_flags), _stream(stream))
+    if st:
+        raise GsError(st, "gs_render_static")
 
 
 # ----------------------------------------------------------------------------- convenience
