@@ -403,6 +403,39 @@ class Rasterizer:
         gs_backward(self.ctx, up[0], up[1], up[2], grads, out.get("pose_grad"), stream)
         return out
 
+    def mapping_grads(self, g: GaussianTensors, cams: Sequence, poses: torch.Tensor, targets: Sequence,
+                      chunk: int = 2, grads: dict | None = None, probs: list | None = None, stream=None) -> dict:
+        """Gradients of the combined loss summed over a keyframe window (Sec. III-C: poses
+        fixed, Gaussians updated).  Views are processed `chunk` at a time through one
+        workspace: each chunk is projected, binned, sorted, composited and differentiated
+        before the next, so the per-tile lists and transmittances of the window are
+        recomputed per chunk and never stored together.  targets: per view (rgb 3HW,
+        depth HW, prior HW or None) device tensors.  Returns {'grads': ..., 'loss': V}."""
+        V = len(cams)
+        if grads is None:
+            grads = {k: torch.zeros(getattr(g, k).shape, dtype=torch.float32, device=self.device)
+                     for k in ("means", "quats", "log_scales", "logits", "rgb")}
+        G = gs_gaussians_grad(_ptr(grads["means"]), _ptr(grads["quats"]), _ptr(grads["log_scales"]),
+                              _ptr(grads["logits"]), _ptr(grads["rgb"]))
+        loss = torch.zeros(V, dtype=torch.float64, device=self.device)
+        gc = g.c()
+        for ci, v0 in enumerate(range(0, V, chunk)):
+            sl = slice(v0, min(V, v0 + chunk))
+            vc = list(cams[sl])
+            prob = probs[ci] if probs is not None else self.plan(g, vc, poses[sl].contiguous())
+            ws, nb = self.workspace(prob)
+            tg = targets[sl]
+            t_rgb = torch.cat([t[0].reshape(-1) for t in tg]).contiguous()
+            t_depth = torch.cat([t[1].reshape(-1) for t in tg]).contiguous()
+            has_prior = all(t[2] is not None for t in tg)
+            t_prior = torch.cat([t[2].reshape(-1) for t in tg]).contiguous() if has_prior else None
+            self._keep = [t_rgb, t_depth, t_prior]
+            gs_project(self.ctx, prob, gc, poses[sl].contiguous(), ws, nb, stream)
+            gs_forward(self.ctx, gs_targets(_ptr(t_rgb), _ptr(t_depth), _ptr(t_prior)), None, None, None,
+                       loss[sl], stream)
+            gs_backward(self.ctx, None, None, None, G, None, stream)
+        return {"grads": grads, "loss": loss}
+
     def sync(self, stream=None) -> gs_counts:
         st, c = gs_sync_status(self.ctx, stream)
         if st:

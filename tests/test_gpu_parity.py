@@ -278,3 +278,42 @@ def test_track_step_converges_on_room():
     c1, r1 = _pose_diff(poses.cpu().numpy()[0], gtp)
     print(f"room tracking: centre {c0:.3f} -> {c1:.3f} m, rotation {np.degrees(r0):.2f} -> {np.degrees(r1):.2f} deg")
     assert c1 < 0.8 * c0 and r1 < 0.5 * r0
+
+
+def test_mapping_window_grads_sum_over_views():
+    """Mapping (Sec. III-C): parameter gradients of the combined loss summed over a
+    window of keyframes, processed a chunk of views at a time (lists recomputed per
+    chunk).  Against the oracle's per-view gradients of the same loss, summed (the fused
+    loss differentiates every pixel, so the < 1 % ambiguous pixels enter both sides and
+    the bound is 1e-2 in the 2-norm); and chunk sizes 1 and 4 agree to float-atomic order."""
+    g = scenes.room_scene(60_000, seed=3)
+    cam = scenes.Cam(150.0, 150.0, 79.5, 44.5, 160, 90)
+    poses_np = scenes.mapping_keyframes(4)
+    gcfg, op = params_pair()
+    sc, oc = oracle.Scene(*g.arrays()), ocam(cam)
+    rng = np.random.default_rng(5)
+    targets, ref_grads, ref_loss = [], np.zeros((g.n, 14)), []
+    for pose in poses_np:
+        t = oracle.render(sc, oc, scenes.perturb_pose(pose, rng, 0.5, 0.01), op)
+        prior = scenes.prior_from_depth(t["depth"], rng, 0.03, 0.08)
+        t_rgb, t_depth = t["rgb"].astype(np.float32), t["depth"].astype(np.float32)
+        r = oracle.render(sc, oc, pose, op)
+        L = oracle.loss(oc, op, r["rgb"], r["depth"], r["sil"], t_rgb, t_depth, prior)
+        ref_grads += oracle.backward(sc, oc, pose, op, L["d_rgb"], L["d_depth"], L["d_sil"])["grads"]
+        ref_loss.append(L["loss"])
+        targets.append(tuple(torch.tensor(a.reshape(-1), device="cuda") for a in (t_rgb, t_depth, prior)))
+    gt = gs.GaussianTensors.from_numpy(g)
+    poses = torch.tensor(np.stack(poses_np), dtype=torch.float64, device="cuda")
+    outs = {}
+    for chunk in (1, 2, 4):
+        R = gs.Rasterizer(gcfg)
+        outs[chunk] = R.mapping_grads(gt, [cam] * 4, poses, targets, chunk=chunk)
+        R.sync()
+    np.testing.assert_allclose(outs[2]["loss"].cpu().numpy(), ref_loss, rtol=2e-3)
+    for name, lo, hi in GRAD_KEYS:
+        got = outs[2]["grads"][name].cpu().numpy().reshape(g.n, -1)
+        ri, r2 = rel_err(got, ref_grads[:, lo:hi])
+        assert r2 < 1e-2, (name, ri, r2)
+        a = outs[1]["grads"][name].cpu().numpy()
+        b = outs[4]["grads"][name].cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-5 * max(1e-30, np.abs(a).max()), name
