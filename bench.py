@@ -70,7 +70,7 @@ def workload(seed: int = 0):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -85,7 +85,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
             t0 = time.time()
@@ -150,6 +150,23 @@ def cpu_baseline(g, cam, start, rgb, depth, prior, budget_s: float):
     return {"value": its * cam.width * cam.height / 1e6, "unit": "Mpix/s", "iters_per_s": its,
             "cores": oracle.num_threads(p), "kind": "oracle",
             "sample": f"{iters} full tracking iterations of the 640x480 / 200k workload in {el:.1f} s"}
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None once the
+    kernel's sources differ from the ones the counters were taken on."""
+    import glob
+    import hashlib
+    root = os.path.dirname(os.path.abspath(__file__))
+    for path in sorted(glob.glob(os.path.join(root, "profiles", "*.md"))):
+        for line in open(path):
+            f = line.split()
+            if len(f) >= 5 and f[0] == "traffic" and f[1] == kernel:
+                h = hashlib.sha256()
+                for src in f[4:]:
+                    h.update(open(os.path.join(root, "paper_2408_05635_gb300", "csrc", src), "rb").read())
+                return int(f[2]) if h.hexdigest()[:16] == f[3] else None
+    return None
 
 
 def run_reference(a, rank, world):
@@ -235,6 +252,7 @@ def main():
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     kern_ms, contrib = {}, {"fwd_evals": 0, "fwd_contrib": 0, "bwd_evals": 0, "bwd_contrib": 0}
+    launches = 0
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -248,8 +266,10 @@ def main():
             starts[k].record(stream)
             step()
             ends[k].record(stream)
-            for name, ms in gs.gs_kernel_times(R.ctx):  # waits for this step's markers
+            kt = gs.gs_kernel_times(R.ctx)  # waits for this step's markers
+            for name, ms in kt:
                 kern_ms[name] = kern_ms.get(name, 0.0) + ms
+            launches += len(kt) + 1  # the marked kernels and the view-table copy
             st_k, c_k = gs.gs_sync_status(R.ctx, stream)
             for key in contrib:
                 contrib[key] += getattr(c_k, key)
@@ -310,7 +330,9 @@ def main():
         f, units = per_pair[dominant]
         achieved = f * units / a.steps / (avg[dominant] / 1e3) / 1e12
         roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": ncu_traffic(dominant),
+                    "traffic_from": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold cache "
+                                    "(profiles/k_backward_k_forward_tracking_640x480_200k.md)",
                     "work": f"{f} FP32 FLOP per differentiated (pixel, Gaussian) pair x {units // a.steps} pairs",
                     "peak_from": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz (median SM clock, timed region)"}
     if rank == 0:
@@ -326,7 +348,7 @@ def main():
             "e2e": {"value": e2e_mpix, "unit": "Mpix/s",
                     "h2d_bytes_per_step": int(h_rgb.numel() * 4 + h_depth.numel() * 4 + h_prior.numel() * 4),
                     "d2h_bytes_per_step": 64},
-            "gpu_launches": a.steps * 7,
+            "gpu_launches": launches,
             "clocks": clocks,
             "roofline": roofline,
             "kernels_us": {k: round(1e3 * v, 2) for k, v in sorted(avg.items(), key=lambda kv: -kv[1])},
