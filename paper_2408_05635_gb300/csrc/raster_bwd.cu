@@ -11,13 +11,19 @@
 // and through a_i = o G, G = exp(power): dL/do = dL/da G, dL/dpower = dL/da a
 // (both zero where a_i is clamped at alpha_max), dpower/dmu' = conic (p - mu'),
 // dpower/d(conic a, b, c) = (-dx^2 / 2, -dx dy, -dy^2 / 2).
+// Only the scalar g . B enters dL/da, so the walk carries that scalar instead of B:
+// g.B <- g.B + a_i (g.v_i - g.B).  The conic is constant per Gaussian, so the pixel sums
+// are taken of the moments dp (dx, dy, dx^2, dx dy, dy^2), dp = dL/dpower, and the conic is
+// applied once per (tile, Gaussian) when the sums are flushed.
 //
 // Each warp owns an 8 x 4 patch of the tile and walks, back to front, only the staged
 // Gaussians whose support box meets the patch and that precede its last contributor.
 // Reduction: every (pixel, Gaussian) term is summed over the warp with a butterfly
-// reduce-scatter (NV values in NV - 1 + log2(32 / NV) shuffles instead of 5 NV), added
-// by the owning lanes into a per-batch shared-memory accumulator, and flushed once per
-// (tile, Gaussian) with vector float4 atomics into the record's global accumulator.
+// reduce-scatter (6 values in 8 shuffles for the pose-only walk, 16 in 16 otherwise),
+// added by the owning lanes into a per-batch shared-memory accumulator, and flushed once
+// per (tile, Gaussian) with vector float4 atomics into the record's global accumulator.
+// Lanes whose pixel the Gaussian does not reach take a = 0, which leaves T and g.B
+// unchanged and zeroes every term, so the walk has no divergent branch.
 #include "gs_internal.cuh"
 
 namespace gsk {
@@ -49,10 +55,28 @@ __device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV], int lane, i
     return v[0];
 }
 
-// NV = 16: all ten screen-space values; NV = 8: the six the pose needs (mu', conic, depth).
-// Value slots follow RecGrad: 0 d mu'_x, 1 d mu'_y, 2 d depth, 3 d opacity,
-// 4..6 d conic (a, b, c), 8..10 d rgb; other slots stay zero.
-template <int NV>
+// Butterfly reduce-scatter of six per-lane values: three exchanges over lane bit 4, two
+// over bit 3 (the third value of each half is summed by both partners), one over bit 2,
+// then a plain sum over bits 1 and 0.  Value 3 * b4 + (b2 ? 2 : b3) ends in the lane;
+// owners are the lanes with bits 1, 0 clear and not both of bits 3, 2 set.
+__device__ __forceinline__ float warp_reduce_scatter6(float v0, float v1, float v2, float v3, float v4,
+                                                      float v5, int lane) {
+    const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0, h2 = (lane & 4) != 0;
+    const float u0 = (h4 ? v3 : v0) + __shfl_xor_sync(0xffffffffu, h4 ? v0 : v3, 16);
+    const float u1 = (h4 ? v4 : v1) + __shfl_xor_sync(0xffffffffu, h4 ? v1 : v4, 16);
+    const float u2 = (h4 ? v5 : v2) + __shfl_xor_sync(0xffffffffu, h4 ? v2 : v5, 16);
+    const float a = (h3 ? u1 : u0) + __shfl_xor_sync(0xffffffffu, h3 ? u0 : u1, 8);
+    const float b = u2 + __shfl_xor_sync(0xffffffffu, u2, 8);
+    float c = (h2 ? b : a) + __shfl_xor_sync(0xffffffffu, h2 ? a : b, 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
+// Shared accumulator slots per staged Gaussian: 0, 1 sum dp dx, dp dy; 2 sum a T g_D;
+// 3 sum dL/da a_raw; 4..6 sum dp dx^2, dp dx dy, dp dy^2; 8..10 sum a T g_C; 7, 11 unused.
+// POSE: only slots 0, 1, 2, 4, 5, 6 (what the pose gradient needs).
+template <bool POSE>
 __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     __shared__ float4 sP0[kBatch], sC[kBatch], sQ[kBatch], sBox[kBatch];
     __shared__ float2 sP1[kBatch];
@@ -80,6 +104,21 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     const float pv_lo = (float)pv0, pv_hi = (float)(pv0 + kPatchH - 1);
     const Settings &S = L.s;
     const float thr = S.log2_alpha_min;
+    // the accumulator slot this lane adds after a reduction, or -1
+    int my_slot = -1;
+    if (POSE) {
+        if ((lane & 3) == 0 && !((lane & 8) && (lane & 4))) {
+            const int k = ((lane & 16) ? 3 : 0) + ((lane & 4) ? 2 : ((lane & 8) ? 1 : 0));
+            my_slot = k < 3 ? k : k + 1;  // values 0..5 -> slots 0, 1, 2, 4, 5, 6
+        }
+    } else {
+        int idx = 0;
+        if (lane & 16) idx += 8;
+        if (lane & 8) idx += 4;
+        if (lane & 4) idx += 2;
+        if (lane & 2) idx += 1;
+        if ((lane & 1) == 0 && idx != 7 && idx != 11 && idx < kAccStride) my_slot = idx;
+    }
 
     uint32_t start;
     const uint32_t n = tile_entries(L.ws, L.d, tile, start);
@@ -106,7 +145,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     if (lane == 0 && wlast) atomicMax(&s_nmax, wlast);
     __syncthreads();
     const uint32_t nmax = s_nmax;
-    float B0 = 0.f, B1 = 0.f, B2 = 0.f, B3 = 0.f, B4 = 0.f;  // colour behind, per channel
+    float GB = 0.f;  // g . (colour, depth, 1) of everything behind, back-to-front
     uint32_t n_eval = 0, n_contrib = 0;
 
     for (int64_t b0 = nmax ? (int64_t)((nmax - 1) / kBatch) * kBatch : -1; b0 >= 0; b0 -= kBatch) {
@@ -146,66 +185,48 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
         for (int e = nl - 1; e >= 0; --e) {
             const int j = sList[warp][e];
             const uint32_t idx = (uint32_t)b0 + (uint32_t)j;
-            float vals[NV];
-#pragma unroll
-            for (int k = 0; k < NV; ++k) vals[k] = 0.f;
-            bool c = false;
-            if (idx < last) {
-                const PolyEval pe = eval_poly(fu, fv, sP0[j], sP1[j]);
-                ++n_eval;
-                if (pe.poly >= thr) {
-                    c = true;
-                    ++n_contrib;
-                    const float araw = ex2_approx(pe.poly);
-                    const float a = fminf(S.alpha_max, araw), om = 1.f - a;
-                    T = T * __fdividef(1.f, om);  // transmittance in front of this Gaussian
-                    const float4 Cc = sC[j];
-                    const float d0 = Cc.x - B0, d1 = Cc.y - B1, d2 = Cc.z - B2, d3 = Cc.w - B3, d4 = 1.f - B4;
-                    const float dalpha = T * (g0 * d0 + g1 * d1 + g2 * d2 + gD * d3 + gS * d4);
-                    B0 += a * d0;
-                    B1 += a * d1;
-                    B2 += a * d2;
-                    B3 += a * d3;
-                    B4 += a * d4;
-                    const float w = a * T;
-                    vals[2] = w * gD;
-                    if (araw < S.alpha_max) {
-                        const float4 Qc = sQ[j];
-                        const float dp = dalpha * a;
-                        const float dx = pe.dx, dy = pe.dy;
-                        vals[0] = dp * (Qc.x * dx + Qc.y * dy);
-                        vals[1] = dp * (Qc.y * dx + Qc.z * dy);
-                        const float hdp = -0.5f * dp;
-                        vals[4] = hdp * dx * dx;
-                        vals[5] = -dp * dx * dy;
-                        vals[6] = hdp * dy * dy;
-                        if constexpr (NV == 16) vals[3] = dalpha * araw / Qc.w;
-                    }
-                    if constexpr (NV == 16) {
-                        vals[8] = w * g0;
-                        vals[9] = w * g1;
-                        vals[10] = w * g2;
-                    }
-                }
-            }
-            if (__any_sync(0xffffffffu, c)) {
+            const bool live = idx < last;
+            const PolyEval pe = eval_poly(fu, fv, sP0[j], sP1[j]);
+            n_eval += live;
+            const bool c = live && pe.poly >= thr;
+            if (!__any_sync(0xffffffffu, c)) continue;
+            n_contrib += c;
+            const float araw = ex2_approx(pe.poly);
+            const float a = c ? fminf(S.alpha_max, araw) : 0.f;
+            if (c) T = T * __fdividef(1.f, 1.f - a);  // transmittance in front of this Gaussian
+            const float4 Cc = sC[j];
+            const float gv = fmaf(g0, Cc.x, fmaf(g1, Cc.y, fmaf(g2, Cc.z, fmaf(gD, Cc.w, gS))));
+            const float diff = gv - GB;
+            const float dalpha = T * diff;
+            GB = fmaf(a, diff, GB);
+            const float w = a * T;
+            const float dp = araw < S.alpha_max ? dalpha * a : 0.f;
+            const float dpx = dp * pe.dx, dpy = dp * pe.dy;
+            if constexpr (POSE) {
+                const float sum = warp_reduce_scatter6(dpx, dpy, w * gD, dpx * pe.dx, dpx * pe.dy, dpy * pe.dy, lane);
+                if (my_slot >= 0 && sum != 0.f) atomicAdd(&sAcc[j * kAccStride + my_slot], sum);
+            } else {
+                float vals[16] = {dpx,     dpy,     w * gD, c && araw < S.alpha_max ? dalpha * araw : 0.f,
+                                  dpx * pe.dx, dpx * pe.dy, dpy * pe.dy, 0.f,
+                                  w * g0,  w * g1,  w * g2, 0.f, 0.f, 0.f, 0.f, 0.f};
                 int slot;
-                const float sum = warp_reduce_scatter<NV>(vals, lane, slot);
-                if ((lane & (32 / NV - 1)) == 0 && slot < kAccStride && slot != 7 && slot != 11 && sum != 0.f)
-                    atomicAdd(&sAcc[j * kAccStride + slot], sum);
+                const float sum = warp_reduce_scatter<16>(vals, lane, slot);
+                if (my_slot >= 0 && sum != 0.f) atomicAdd(&sAcc[j * kAccStride + my_slot], sum);
             }
         }
         __syncthreads();
         if (tid < cnt) {
             const uint32_t r = L.ws.sorted[start + (uint32_t)b0 + tid];
             if (r < rec_slots(L.d)) {
-                const float *a = sAcc + tid * kAccStride;
-                const float4 v0 = make_float4(a[0], a[1], a[2], a[3]);
-                const float4 v1 = make_float4(a[4], a[5], a[6], 0.f);
+                const float *m = sAcc + tid * kAccStride;
+                const float4 Q = sQ[tid];
+                const float4 v0 = make_float4(Q.x * m[0] + Q.y * m[1], Q.y * m[0] + Q.z * m[1], m[2],
+                                              POSE ? 0.f : m[3] / Q.w);
+                const float4 v1 = make_float4(-0.5f * m[4], -m[5], -0.5f * m[6], 0.f);
                 if (v0.x != 0.f || v0.y != 0.f || v0.z != 0.f || v0.w != 0.f) atomicAdd(&L.ws.rec_grad[r].g0, v0);
                 if (v1.x != 0.f || v1.y != 0.f || v1.z != 0.f) atomicAdd(&L.ws.rec_grad[r].g1, v1);
-                if constexpr (NV == 16) {
-                    const float4 v2 = make_float4(a[8], a[9], a[10], 0.f);
+                if constexpr (!POSE) {
+                    const float4 v2 = make_float4(m[8], m[9], m[10], 0.f);
                     if (v2.x != 0.f || v2.y != 0.f || v2.z != 0.f) atomicAdd(&L.ws.rec_grad[r].g2, v2);
                 }
             }
@@ -218,9 +239,9 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
 cudaError_t launch_backward(const BackwardLaunch &L, cudaStream_t st) {
     if (L.d.T == 0) return cudaSuccess;
     if (L.pose_only)
-        k_backward<8><<<L.d.T, kTilePix, 0, st>>>(L);
+        k_backward<true><<<L.d.T, kTilePix, 0, st>>>(L);
     else
-        k_backward<16><<<L.d.T, kTilePix, 0, st>>>(L);
+        k_backward<false><<<L.d.T, kTilePix, 0, st>>>(L);
     return cudaGetLastError();
 }
 
