@@ -14,7 +14,8 @@
 // translation shifts it (x_c <- x_c + t).  d t = dx_c and
 // d theta = x_c x dx_c + axial(dM M^T) with axial(P) = (P21 - P12, P02 - P20, P10 - P01).
 // The per-record 6-vectors are summed over the warp in FP32 (at most 32 terms) and over
-// the cell's warps in FP64; k_finalize sums the view's cells in a fixed order (FP64)
+// the cell's warps in double-float; k_finalize sums the view's cells in a fixed order
+// (double-float)
 // and, in tracking mode, applies the decoupled Adam step in FP64 (separate moments for
 // theta and t; R <- Exp(-step_theta) R, t <- Exp(-step_theta) t - step_t).
 #include "gs_internal.cuh"
@@ -268,51 +269,98 @@ __global__ void __launch_bounds__(kBlock) k_bproject(BprojLaunch L) {
     if ((lane & 3) == 0 && slot < 6) s_red[warp][slot] = sum;
     __syncthreads();
     if (tid < 6) {
-        double acc = 0.0;
-        for (int w = 0; w < kWarps; ++w) acc += (double)s_red[w][tid];
-        L.ws.pose_part[(size_t)cell * 6 + tid] = acc;
+        DF acc{0.f, 0.f};
+        for (int w = 0; w < kWarps; ++w) acc = df_add(acc, DF{s_red[w][tid], 0.f});
+        L.ws.pose_part[(size_t)cell * 6 + tid] = df_pack(acc);
     }
 }
 
-// One block per view: fixed-order sums of the view's tile losses and cell pose partials,
-// then (tracking) the decoupled Adam step.
-__global__ void __launch_bounds__(kBlock) k_finalize(FinalizeLaunch L) {
+// One block per view: fixed-order double-float sums of the view's tile losses and cell
+// pose partials, then (tracking) the decoupled Adam step in FP64.  The kernel is a chain
+// of dependent steps, so every global load is issued as early as possible: the pose and
+// the optimiser state first, then kFinUnroll partials per thread per round.  A cell's six
+// partials are read as three 16-byte pairs; with a thread count divisible by three every
+// thread always holds the same pair of components.  The block's partials are summed per
+// component by one warp (strided columns, then a butterfly).
+constexpr int kFinThreads = 384;
+constexpr int kFinUnroll = 4;
+
+__global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeLaunch L) {
     const int v = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    __shared__ double s_part[kWarps][7];
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    constexpr int kPerComp = kFinThreads / 3;  // pose partial columns per component
+    __shared__ float2 s_pose_acc[6][kPerComp];
+    __shared__ float2 s_loss_acc[kFinThreads];
+    __shared__ double s_g[7], s_step[6], s_pose[7], s_st[16];
+    const bool adam = L.pose && L.poses;
+    if (adam) {
+        if (tid < 7)
+            s_pose[tid] = L.poses[7 * v + tid];
+        else if (tid >= 32 && tid < 48)
+            s_st[tid - 32] = L.adam[16 * v + tid - 32];
+    }
+    DF lacc{0.f, 0.f}, pa{0.f, 0.f}, pb{0.f, 0.f};  // loss; components 2 (tid % 3), 2 (tid % 3) + 1
     if (L.loss_out) {
         const ViewInfo vi = L.ws.views[v];
         const uint32_t nt = (uint32_t)vi.tiles_x * (uint32_t)vi.tiles_y;
-        for (uint32_t t = tid; t < nt; t += kBlock) acc[6] += L.ws.tile_loss[vi.tile_base + t];
+        const float2 *tl = L.ws.tile_loss + vi.tile_base;
+        for (uint32_t b = 0; b < nt; b += kFinThreads * kFinUnroll) {
+            float2 x[kFinUnroll];
+#pragma unroll
+            for (int k = 0; k < kFinUnroll; ++k) {
+                const uint32_t t = b + (uint32_t)(k * kFinThreads + tid);
+                x[k] = t < nt ? tl[t] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < kFinUnroll; ++k) lacc = df_add(lacc, df_load(x[k]));
+        }
     }
     if (L.pose) {
-        const size_t c0 = (size_t)v * L.d.nblk;
-        for (int c = tid; c < L.d.nblk; c += kBlock)
+        const size_t nq = (size_t)L.d.nblk * 3;  // 16-byte pairs of the view
+        const float4 *pp = reinterpret_cast<const float4 *>(L.ws.pose_part + (size_t)v * (size_t)L.d.nblk * 6);
+        for (size_t b = 0; b < nq; b += kFinThreads * kFinUnroll) {
+            float4 x[kFinUnroll];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc[k] += L.ws.pose_part[(c0 + c) * 6 + k];
+            for (int k = 0; k < kFinUnroll; ++k) {
+                const size_t q = b + (size_t)(k * kFinThreads + tid);
+                x[k] = q < nq ? pp[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < kFinUnroll; ++k) {
+                pa = df_add(pa, DF{x[k].x, x[k].y});
+                pb = df_add(pb, DF{x[k].z, x[k].w});
+            }
+        }
     }
-#pragma unroll
-    for (int k = 0; k < 7; ++k)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 7; ++k) s_part[warp][k] = acc[k];
+    s_loss_acc[tid] = df_pack(lacc);
+    s_pose_acc[2 * (tid % 3)][tid / 3] = df_pack(pa);
+    s_pose_acc[2 * (tid % 3) + 1][tid / 3] = df_pack(pb);
     __syncthreads();
-    __shared__ double s_g[7], s_step[6];
-    if (tid < 7) {
-        double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) t += s_part[w][tid];
-        s_g[tid] = t;
-        if (tid == 6 && L.loss_out) L.loss_out[v] = t;
-        if (tid < 6 && L.pose && L.pose_grad) L.pose_grad[6 * v + tid] = t;
+    if (warp < 7) {
+        DF t{0.f, 0.f};
+        if (warp < 6)
+            for (int i = lane; i < kPerComp; i += 32) t = df_add(t, df_load(s_pose_acc[warp][i]));
+        else
+            for (int i = lane; i < kFinThreads; i += 32) t = df_add(t, df_load(s_loss_acc[i]));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t = df_add(t, df_shfl_xor(t, off));
+        if (lane == 0) {
+            const double g = (double)t.hi + (double)t.lo;
+            s_g[warp] = g;
+            if (warp == 6 && L.loss_out) L.loss_out[v] = g;
+            if (warp < 6 && L.pose && L.pose_grad) L.pose_grad[6 * v + warp] = g;
+        }
     }
     __syncthreads();
-    if (L.pose && L.poses) adam_update(L.poses + 7 * v, L.adam + 16 * v, s_g, L.s, s_step, tid);
+    if (!adam) return;
+    adam_update(s_pose, s_st, s_g, L.s, s_step, tid);  // thread 0 alone returns from it with the result
+    if (tid == 0) {
+        for (int k = 0; k < 7; ++k) L.poses[7 * v + k] = s_pose[k];
+        for (int k = 0; k < 16; ++k) L.adam[16 * v + k] = s_st[k];
+    }
 }
 
 cudaError_t launch_finalize(const FinalizeLaunch &L, cudaStream_t st) {
-    k_finalize<<<L.d.V, kBlock, 0, st>>>(L);
+    k_finalize<<<L.d.V, kFinThreads, 0, st>>>(L);
     return cudaGetLastError();
 }
 

@@ -203,8 +203,8 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     L.t_final = take(sizeof(float) * (size_t)d.P);
     L.n_last = take(sizeof(uint32_t) * (size_t)d.P);
     L.upstream = take(sizeof(float) * 5 * (size_t)d.P);
-    L.tile_loss = take(sizeof(double) * (size_t)d.T);
-    L.pose_part = take(sizeof(double) * 6 * cells);
+    L.tile_loss = take(sizeof(float2) * (size_t)d.T);
+    L.pose_part = take(sizeof(float2) * 6 * cells);
     L.total = o;
     return GS_OK;
 }
@@ -228,8 +228,8 @@ WsPtrs ws_ptrs(void *base, const Layout &L) {
     w.t_final = reinterpret_cast<float *>(b + L.t_final);
     w.n_last = reinterpret_cast<uint32_t *>(b + L.n_last);
     w.upstream = reinterpret_cast<float *>(b + L.upstream);
-    w.tile_loss = reinterpret_cast<double *>(b + L.tile_loss);
-    w.pose_part = reinterpret_cast<double *>(b + L.pose_part);
+    w.tile_loss = reinterpret_cast<float2 *>(b + L.tile_loss);
+    w.pose_part = reinterpret_cast<float2 *>(b + L.pose_part);
     return w;
 }
 
@@ -245,18 +245,19 @@ gs_status check_gaussians(gs_ctx *ctx, const gs_gaussians *g, const Problem &pr)
 
 // Write the view table into the workspace (kernel arguments carry it, so the upload is
 // stream-ordered and safe to capture; it is redone on every call because the library
-// cannot tell whether the caller reused the workspace memory for something else).
-cudaError_t upload_views(const Problem &pr, const WsPtrs &w, cudaStream_t st) {
-    return launch_upload_views(pr.views.data(), (int)pr.views.size(), w.views, st);
+// cannot tell whether the caller reused the workspace memory for something else).  The
+// same launch zeroes the latched error flags, the header and the tile counters; later
+// iterations of a call find the counters zeroed by the scan that consumed them and the
+// header by the projection.
+cudaError_t upload_views(const Problem &pr, const WsPtrs &w, void *ws, cudaStream_t st) {
+    return launch_upload_views(pr.views.data(), (int)pr.views.size(), w.views, static_cast<char *>(ws) + pr.lay.err,
+                               pr.lay.zero_end - pr.lay.err, st);
 }
 
-// One projection pass: clear the counters, project, emit keys.
-// clear_err also resets the latched error flags (the first word of the workspace).
-cudaError_t enqueue_project(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, void *ws, const GaussPtrs &g, int dtype,
-                            const double *poses, bool clear_err, cudaStream_t st) {
-    const size_t from = clear_err ? pr.lay.err : pr.lay.hdr;
-    cudaError_t e = cudaMemsetAsync(static_cast<char *>(ws) + from, 0, pr.lay.zero_end - from, st);
-    if (e != cudaSuccess) return e;
+// One projection pass: project, scan the tile counts, emit keys.
+cudaError_t enqueue_project(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, const GaussPtrs &g, int dtype,
+                            const double *poses, cudaStream_t st) {
+    cudaError_t e;
     if ((e = mark(ctx, st, nullptr)) != cudaSuccess) return e;
     ProjectLaunch P;
     P.ws = w;
@@ -383,11 +384,11 @@ gs_status gs_project(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
         return fail(ctx, GS_ERR_WORKSPACE, "workspace NULL, smaller than gs_workspace_size or not 256-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const WsPtrs w = ws_ptrs(ws, pr.lay);
-    cudaError_t e = upload_views(pr, w, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "view upload");
     GaussPtrs gp{g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb};
     ctx->n_marks = 0;
-    e = enqueue_project(ctx, pr, w, ws, gp, g->dtype_attr, poses, true, s);
+    cudaError_t e = upload_views(pr, w, ws, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "view upload");
+    e = enqueue_project(ctx, pr, w, gp, g->dtype_attr, poses, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "projection");
     ctx->bound = true;
     ctx->prob = std::move(pr);
@@ -499,13 +500,14 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
         return fail(ctx, GS_ERR_WORKSPACE, "workspace NULL, smaller than gs_workspace_size or not 256-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const WsPtrs w = ws_ptrs(ws, pr.lay);
-    cudaError_t e = upload_views(pr, w, s);
+    // flags latch over all iterations of this call
+    cudaError_t e = upload_views(pr, w, ws, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "view upload");
     GaussPtrs gp{g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb};
 
     auto enqueue_all = [&](cudaStream_t q) -> cudaError_t {
         for (int it = 0; it < iters; ++it) {
-            cudaError_t r = enqueue_project(ctx, pr, w, ws, gp, g->dtype_attr, poses, false, q);
+            cudaError_t r = enqueue_project(ctx, pr, w, gp, g->dtype_attr, poses, q);
             if (r != cudaSuccess) return r;
             if ((r = enqueue_forward(ctx, pr, w, targets, nullptr, nullptr, nullptr, q)) != cudaSuccess) return r;
             BackwardLaunch B;
@@ -542,9 +544,6 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
         return cudaSuccess;
     };
 
-    // flags latch over all iterations of this call
-    e = cudaMemsetAsync(w.err, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "flag clear");
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream query");

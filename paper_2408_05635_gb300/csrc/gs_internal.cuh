@@ -55,6 +55,28 @@ struct DevHeader {
 };
 static_assert(sizeof(DevHeader) == 64, "DevHeader layout");
 
+// Double-float: the unevaluated sum hi + lo of two FP32 values (about 46 significant bits
+// after additions), added with Knuth's error-free TwoSum of the high parts followed by a
+// Fast2Sum renormalisation (Dekker, 1971).  The fixed-order loss and pose sums use it so
+// they run on the FP32 pipes: FP64 issue on this GPU is a small fraction of FP32.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));
+    const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, t);
+    return DF{hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ DF df_load(const float2 &x) { return DF{x.x, x.y}; }
+__device__ __forceinline__ float2 df_pack(DF a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ DF df_shfl_xor(DF a, int mask) {
+    return DF{__shfl_xor_sync(0xffffffffu, a.hi, mask), __shfl_xor_sync(0xffffffffu, a.lo, mask)};
+}
+
 // A visible (Gaussian, view) pair, as the compositors read it (48 bytes).
 //   a = (mu'_x, mu'_y, depth, opacity)
 //   b = (conic a, conic b, conic c, dmax2)   conic = inverse of Sigma' = [[a, b], [b, c]]
@@ -91,8 +113,8 @@ struct WsPtrs {
     float *t_final;        // P, transmittance after the last contributor
     uint32_t *n_last;      // P, tile-list index + 1 of the last contributor
     float *upstream;       // 5 x P: dL/dC (planar like the images), dL/dD, dL/dS of the fused loss
-    double *tile_loss;     // T, combined loss of each tile's pixels (fused loss)
-    double *pose_part;     // V x nblk x 6, pose-gradient sum of each cell's records
+    float2 *tile_loss;     // T, combined loss of each tile's pixels (fused loss), double-float
+    float2 *pose_part;     // V x nblk x 6, pose-gradient sum of each cell's records, double-float
 };
 
 struct Dims {
@@ -371,7 +393,9 @@ struct ProjectLaunch {
     const double *poses;
 };
 
-cudaError_t launch_upload_views(const ViewInfo *host_views, int V, ViewInfo *dev, cudaStream_t st);
+// Also zeroes zero_bytes (a multiple of 4) at `zero` in the same launch.
+cudaError_t launch_upload_views(const ViewInfo *host_views, int V, ViewInfo *dev, void *zero, size_t zero_bytes,
+                                cudaStream_t st);
 cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st);
 cudaError_t launch_scan_tiles(const WsPtrs &ws, const Dims &d, cudaStream_t st);
 cudaError_t launch_emit(const WsPtrs &ws, const Dims &d, cudaStream_t st);

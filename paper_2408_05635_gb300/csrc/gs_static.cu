@@ -137,13 +137,12 @@ extern "C" gs_status gs_render_static(const gs_config *cfg, const gs_gaussians *
     w.t_final = reinterpret_cast<float *>(take(4 * (size_t)d.P));
     w.n_last = reinterpret_cast<uint32_t *>(take(4 * (size_t)d.P));
     w.upstream = reinterpret_cast<float *>(take(20 * (size_t)d.P));
-    w.tile_loss = reinterpret_cast<double *>(take(8 * (size_t)d.T));
-    w.pose_part = reinterpret_cast<double *>(take(48 * (size_t)d.nblk));
+    w.tile_loss = reinterpret_cast<float2 *>(take(8 * (size_t)d.T));
+    w.pose_part = reinterpret_cast<float2 *>(take(48 * (size_t)d.nblk));
     if (o > kScratchBytes) return GS_ERR_WORKSPACE;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(base, 0, zero_bytes, st) != cudaSuccess) return GS_ERR_CUDA;
-    if (launch_upload_views(&vi, 1, w.views, st) != cudaSuccess) return GS_ERR_CUDA;
+    if (launch_upload_views(&vi, 1, w.views, base, zero_bytes, st) != cudaSuccess) return GS_ERR_CUDA;
     ProjectLaunch P{};
     P.ws = w;
     P.d = d;

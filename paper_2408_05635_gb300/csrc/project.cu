@@ -85,114 +85,174 @@ struct ViewChunk {
     ViewInfo v[32];
 };
 
-__global__ void k_copy_views(ViewInfo *dst, int count, ViewChunk chunk) {
-    const int i = threadIdx.x;
-    if (i < count) dst[i] = chunk.v[i];
+// Copies up to 32 views into the device table (block 0) and zeroes `zero_words` 32-bit
+// words at `zero` (all blocks, grid-stride): the per-call reset of the flag word, the
+// header and the tile counters, folded into the same launch.
+__global__ void k_copy_views(ViewInfo *dst, int count, ViewChunk chunk, uint32_t *zero, size_t zero_words) {
+    if (blockIdx.x == 0 && threadIdx.x < count) dst[threadIdx.x] = chunk.v[threadIdx.x];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < zero_words; i += (size_t)gridDim.x * blockDim.x)
+        zero[i] = 0u;
 }
 
-cudaError_t launch_upload_views(const ViewInfo *host_views, int V, ViewInfo *dev, cudaStream_t st) {
-    for (int base = 0; base < V; base += 32) {
+cudaError_t launch_upload_views(const ViewInfo *host_views, int V, ViewInfo *dev, void *zero, size_t zero_bytes,
+                                cudaStream_t st) {
+    constexpr int kThreads = 256;
+    for (int base = 0; base < V || (base == 0 && zero_bytes); base += 32) {
         ViewChunk c;
-        const int cnt = V - base < 32 ? V - base : 32;
+        const int cnt = V - base < 32 ? (V - base > 0 ? V - base : 0) : 32;
         for (int k = 0; k < cnt; ++k) c.v[k] = host_views[base + k];
-        k_copy_views<<<1, 32, 0, st>>>(dev + base, cnt, c);
+        const size_t words = base == 0 ? zero_bytes / 4 : 0;
+        size_t blocks = (words + 4 * kThreads - 1) / (4 * kThreads);
+        blocks = blocks < 1 ? 1 : (blocks > 1024 ? 1024 : blocks);
+        k_copy_views<<<(unsigned)blocks, kThreads, 0, st>>>(dev + base, cnt, c, static_cast<uint32_t *>(zero), words);
     }
     return cudaGetLastError();
 }
 
 // Exclusive scan of the per-(tile, sub-bucket) counts into list offsets, by one block of
-// kScanThreads (chunks of 4 counters per thread, warp scans, a running carry); also the
-// total pair count, the longest tile list and the number of visible records.
+// kScanThreads.  Each pass loads kScanPer contiguous counters per thread in one round
+// (and zeroes them for the next projection), scans the per-thread totals across the
+// block and writes the offsets.  Since S divides kScanPer, a tile's S counters sit in
+// one thread, which also counts the tile's list length into the buckets of the
+// longest-first launch order; the lengths stay in registers when one pass covers all
+// counters.  Also: the total pair count, the longest list and the number of records.
 constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
 constexpr int kOrderBuckets = kScanThreads;  // list lengths >= kOrderBuckets - 1 share the first bucket
+
+__device__ __forceinline__ uint32_t order_bucket(uint32_t len) {
+    return kOrderBuckets - 1 - min(len, (uint32_t)kOrderBuckets - 1);
+}
+
+// Exclusive block-wide scan of one value per thread; `total` gets the block sum.  Uses
+// warp_sum (kScanThreads / 32 words) and ends with a barrier.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *warp_sum, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    uint32_t wi = lane < kScanThreads / 32 ? warp_sum[lane] : 0u;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, wi, off);
+        if (lane >= off) wi += v;
+    }
+    const uint32_t prev = __shfl_sync(0xffffffffu, wi, (warp + 31) & 31);
+    total = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
+    __syncthreads();
+    return (warp > 0 ? prev : 0u) + incl - x;
+}
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(WsPtrs ws, Dims d) {
     __shared__ uint32_t warp_sum[kScanThreads / 32];
+    __shared__ uint32_t s_bucket[kOrderBuckets];
     __shared__ uint32_t s_max;
     __shared__ unsigned long long s_recs;
-    const uint32_t TS = d.T * d.S;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
+    const uint32_t TS = d.T * d.S, S = d.S, smask = d.S - 1, sshift = __ffs(d.S) - 1;  // S: 1, 2 or 4
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
         s_max = 0;
         s_recs = 0;
     }
-    unsigned long long carry = 0;  // identical in every thread
-    for (uint32_t base = 0; base < TS; base += 4 * kScanThreads) {
-        const uint32_t i0 = base + 4 * threadIdx.x;
-        uint32_t c[4];
+    s_bucket[tid] = 0;
+    // record counts of the first cells, fetched now so their latency overlaps the scan
+    const uint32_t ncell = (uint32_t)d.V * (uint32_t)d.nblk;
+    uint32_t cc[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) c[k] = i0 + k < TS ? ws.tile_cnt[i0 + k] : 0u;
-        const uint32_t mine = c[0] + c[1] + c[2] + c[3];
-        uint32_t incl = mine;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += v;
-        }
-        if (lane == 31) warp_sum[warp] = incl;
-        __syncthreads();
-        uint32_t wi = lane < kScanThreads / 32 ? warp_sum[lane] : 0u;  // inclusive scan of the warp totals
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, wi, off);
-            if (lane >= off) wi += v;
-        }
-        const uint32_t prev = __shfl_sync(0xffffffffu, wi, (warp + 31) & 31);
-        const uint32_t before = warp > 0 ? prev : 0u;
-        const uint32_t total = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
-        unsigned long long run = carry + before + (incl - mine);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (i0 + k < TS) {
-                const uint32_t o = (uint32_t)min(run, (unsigned long long)0xffffffffu);
-                ws.tile_start[i0 + k] = o;
-                ws.cursor[i0 + k] = o;
-                run += c[k];
-            }
-        carry += total;
-        __syncthreads();
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t c = (uint32_t)tid + (uint32_t)k * kScanThreads;
+        cc[k] = c < ncell ? ws.cell_cnt[c] : 0u;
     }
-    const uint32_t all = (uint32_t)min(carry, (unsigned long long)0xffffffffu);
-    if (threadIdx.x == 0) ws.tile_start[TS] = all;
-    // launch order of the tile kernels: longest lists first (counting sort on the length,
-    // descending), so the slowest tiles start in the first wave instead of the tail
-    __shared__ uint32_t s_bucket[kOrderBuckets];
-    s_bucket[threadIdx.x] = 0;
     __syncthreads();
+    const bool one_pass = TS <= (uint32_t)kScanThreads * kScanPer;
+    uint32_t len[kScanPer];  // length of the tile whose first counter is j (j % S == 0)
+    unsigned long long carry = 0;  // identical in every thread
     uint32_t max_tile = 0;
-    for (uint32_t t = threadIdx.x; t < d.T; t += kScanThreads) {
-        const uint32_t len = ws.tile_start[(t + 1) * d.S] - ws.tile_start[t * d.S];
-        max_tile = max(max_tile, len);
-        atomicAdd(&s_bucket[kOrderBuckets - 1 - min(len, (uint32_t)kOrderBuckets - 1)], 1u);
+    for (uint32_t base = 0; base < TS; base += (uint32_t)kScanThreads * kScanPer) {
+        const uint32_t i0 = base + (uint32_t)tid * kScanPer;
+        uint32_t c[kScanPer];
+        if (i0 + kScanPer <= TS) {
+            uint4 *q = reinterpret_cast<uint4 *>(ws.tile_cnt + i0);
+            const uint4 a = q[0], b = q[1];
+            c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+            c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+            q[0] = make_uint4(0u, 0u, 0u, 0u);
+            q[1] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanPer; ++k) {
+                c[k] = i0 + k < TS ? ws.tile_cnt[i0 + k] : 0u;
+                if (i0 + k < TS) ws.tile_cnt[i0 + k] = 0u;
+            }
+        }
+        uint32_t mine = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) mine += c[k];
+        uint32_t total;
+        const uint32_t excl = block_exclusive_scan(mine, warp_sum, total);
+        unsigned long long run = carry + excl;
+        uint32_t o[kScanPer];
+#pragma unroll
+        for (int k = 0; k < kScanPer; ++k) {
+            o[k] = (uint32_t)min(run, (unsigned long long)0xffffffffu);
+            run += c[k];
+        }
+        if (i0 + kScanPer <= TS) {  // whole 32-byte rows: two vector stores per array
+            const uint4 a = make_uint4(o[0], o[1], o[2], o[3]), b = make_uint4(o[4], o[5], o[6], o[7]);
+            reinterpret_cast<uint4 *>(ws.tile_start + i0)[0] = a;
+            reinterpret_cast<uint4 *>(ws.tile_start + i0)[1] = b;
+            reinterpret_cast<uint4 *>(ws.cursor + i0)[0] = a;
+            reinterpret_cast<uint4 *>(ws.cursor + i0)[1] = b;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanPer; ++k)
+                if (i0 + k < TS) {
+                    ws.tile_start[i0 + k] = o[k];
+                    ws.cursor[i0 + k] = o[k];
+                }
+        }
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            len[j] = 0;
+            if ((j & smask) == 0 && i0 + j < TS) {
+                uint32_t l = c[j];
+                if (S > 1) l += c[(j + 1) % kScanPer];
+                if (S > 2) l += c[(j + 2) % kScanPer] + c[(j + 3) % kScanPer];
+                len[j] = l;
+                max_tile = max(max_tile, l);
+                atomicAdd(&s_bucket[order_bucket(l)], 1u);
+            }
+        }
+        carry += total;
     }
+    if (tid == 0) ws.tile_start[TS] = (uint32_t)min(carry, (unsigned long long)0xffffffffu);
     __syncthreads();
     {  // exclusive scan of the buckets, one bucket per thread
-        const uint32_t c = s_bucket[threadIdx.x];
-        uint32_t incl = c;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += v;
-        }
-        if (lane == 31) warp_sum[warp] = incl;
-        __syncthreads();
-        uint32_t wi = lane < kScanThreads / 32 ? warp_sum[lane] : 0u;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, wi, off);
-            if (lane >= off) wi += v;
-        }
-        const uint32_t prev = __shfl_sync(0xffffffffu, wi, (warp + 31) & 31);
-        s_bucket[threadIdx.x] = (warp > 0 ? prev : 0u) + incl - c;
+        uint32_t total;
+        const uint32_t c = s_bucket[tid];
+        const uint32_t excl = block_exclusive_scan(c, warp_sum, total);
+        s_bucket[tid] = excl;
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < d.T; t += kScanThreads) {
-        const uint32_t len = ws.tile_start[(t + 1) * d.S] - ws.tile_start[t * d.S];
-        const uint32_t pos = atomicAdd(&s_bucket[kOrderBuckets - 1 - min(len, (uint32_t)kOrderBuckets - 1)], 1u);
-        ws.tile_order[pos] = t;
+    if (one_pass) {
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            const uint32_t i = (uint32_t)tid * kScanPer + (uint32_t)j;
+            if ((j & smask) == 0 && i < TS) ws.tile_order[atomicAdd(&s_bucket[order_bucket(len[j])], 1u)] = i >> sshift;
+        }
+    } else {
+        for (uint32_t t = tid; t < d.T; t += kScanThreads) {
+            const uint32_t l = ws.tile_start[(t + 1) * S] - ws.tile_start[t * S];
+            ws.tile_order[atomicAdd(&s_bucket[order_bucket(l)], 1u)] = t;
+        }
     }
-    unsigned long long recs = 0;
-    for (uint32_t c = threadIdx.x; c < (uint32_t)d.V * (uint32_t)d.nblk; c += kScanThreads) recs += ws.cell_cnt[c];
+    unsigned long long recs = (unsigned long long)cc[0] + cc[1] + cc[2] + cc[3];
+    for (uint32_t c = (uint32_t)tid + 4u * kScanThreads; c < ncell; c += kScanThreads) recs += ws.cell_cnt[c];
     max_tile = __reduce_max_sync(0xffffffffu, max_tile);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) recs += __shfl_xor_sync(0xffffffffu, recs, off);
@@ -201,7 +261,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(WsPtrs ws, Dims d) 
         atomicAdd(&s_recs, recs);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         ws.hdr->max_tile = s_max;
         ws.hdr->n_rec = s_recs;
         ws.hdr->n_pairs = carry;
@@ -228,6 +288,9 @@ __global__ void __launch_bounds__(kBlock, 5) k_project(ProjectLaunch L) {
     }
     __syncthreads();
     if (b == 0 && tid < 12) L.ws.view_rt[12 * v + tid] = sRt[tid];
+    // per-iteration counters start at zero (nothing else touches the header before the scan)
+    if (b == 0 && v == 0 && tid < (int)(sizeof(DevHeader) / 8))
+        reinterpret_cast<unsigned long long *>(L.ws.hdr)[tid] = 0ull;
     const ViewInfo vi = sv;
     const int64_t i = (int64_t)b * kBlock + tid;
     const Settings &S = L.s;

@@ -73,6 +73,28 @@ __device__ __forceinline__ float warp_reduce_scatter6(float v0, float v1, float 
     return c;
 }
 
+// One back-to-front step of the pose-only walk for this lane's pixel: updates T and g.B
+// and returns the six moment terms (all zero where c is false).
+__device__ __forceinline__ void bwd_step6(bool c, const PolyEval &pe, float4 Cc, float g0, float g1, float g2,
+                                          float gD, float gS, float amax, float &T, float &GB, float (&v)[6]) {
+    const float araw = ex2_approx(pe.poly);
+    const float a = c ? fminf(amax, araw) : 0.f;
+    if (c) T = T * __fdividef(1.f, 1.f - a);  // transmittance in front of this Gaussian
+    const float gv = fmaf(g0, Cc.x, fmaf(g1, Cc.y, fmaf(g2, Cc.z, fmaf(gD, Cc.w, gS))));
+    const float diff = gv - GB;
+    const float dalpha = T * diff;
+    GB = fmaf(a, diff, GB);
+    const float w = a * T;
+    const float dp = araw < amax ? dalpha * a : 0.f;
+    const float dpx = dp * pe.dx, dpy = dp * pe.dy;
+    v[0] = dpx;
+    v[1] = dpy;
+    v[2] = w * gD;
+    v[3] = dpx * pe.dx;
+    v[4] = dpx * pe.dy;
+    v[5] = dpy * pe.dy;
+}
+
 // Shared accumulator slots per staged Gaussian: 0, 1 sum dp dx, dp dy; 2 sum a T g_D;
 // 3 sum dL/da a_raw; 4..6 sum dp dx^2, dp dx dy, dp dy^2; 8..10 sum a T g_C; 7, 11 unused.
 // POSE: only slots 0, 1, 2, 4, 5, 6 (what the pose gradient needs).
@@ -182,7 +204,32 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
             nl += __popc(m);
         }
         __syncwarp();
-        for (int e = nl - 1; e >= 0; --e) {
+        int e = nl - 1;
+        if constexpr (POSE) {
+            // two Gaussians per step: the pixel state is updated in depth order (the back
+            // one first), and the two reductions are independent, so they overlap
+            for (; e >= 1; e -= 2) {
+                const int jA = sList[warp][e], jB = sList[warp][e - 1];
+                const uint32_t iA = (uint32_t)b0 + (uint32_t)jA, iB = (uint32_t)b0 + (uint32_t)jB;
+                const PolyEval pA = eval_poly(fu, fv, sP0[jA], sP1[jA]);
+                const PolyEval pB = eval_poly(fu, fv, sP0[jB], sP1[jB]);
+                const bool lA = iA < last, lB = iB < last;
+                n_eval += lA + lB;
+                const bool cA = lA && pA.poly >= thr, cB = lB && pB.poly >= thr;
+                if (!__any_sync(0xffffffffu, cA || cB)) continue;
+                n_contrib += cA + cB;
+                float vA[6], vB[6];
+                bwd_step6(cA, pA, sC[jA], g0, g1, g2, gD, gS, S.alpha_max, T, GB, vA);
+                bwd_step6(cB, pB, sC[jB], g0, g1, g2, gD, gS, S.alpha_max, T, GB, vB);
+                const float sA = warp_reduce_scatter6(vA[0], vA[1], vA[2], vA[3], vA[4], vA[5], lane);
+                const float sB = warp_reduce_scatter6(vB[0], vB[1], vB[2], vB[3], vB[4], vB[5], lane);
+                if (my_slot >= 0) {
+                    if (sA != 0.f) atomicAdd(&sAcc[jA * kAccStride + my_slot], sA);
+                    if (sB != 0.f) atomicAdd(&sAcc[jB * kAccStride + my_slot], sB);
+                }
+            }
+        }
+        for (; e >= 0; --e) {
             const int j = sList[warp][e];
             const uint32_t idx = (uint32_t)b0 + (uint32_t)j;
             const bool live = idx < last;
@@ -191,21 +238,23 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
             const bool c = live && pe.poly >= thr;
             if (!__any_sync(0xffffffffu, c)) continue;
             n_contrib += c;
-            const float araw = ex2_approx(pe.poly);
-            const float a = c ? fminf(S.alpha_max, araw) : 0.f;
-            if (c) T = T * __fdividef(1.f, 1.f - a);  // transmittance in front of this Gaussian
-            const float4 Cc = sC[j];
-            const float gv = fmaf(g0, Cc.x, fmaf(g1, Cc.y, fmaf(g2, Cc.z, fmaf(gD, Cc.w, gS))));
-            const float diff = gv - GB;
-            const float dalpha = T * diff;
-            GB = fmaf(a, diff, GB);
-            const float w = a * T;
-            const float dp = araw < S.alpha_max ? dalpha * a : 0.f;
-            const float dpx = dp * pe.dx, dpy = dp * pe.dy;
             if constexpr (POSE) {
-                const float sum = warp_reduce_scatter6(dpx, dpy, w * gD, dpx * pe.dx, dpx * pe.dy, dpy * pe.dy, lane);
+                float v[6];
+                bwd_step6(c, pe, sC[j], g0, g1, g2, gD, gS, S.alpha_max, T, GB, v);
+                const float sum = warp_reduce_scatter6(v[0], v[1], v[2], v[3], v[4], v[5], lane);
                 if (my_slot >= 0 && sum != 0.f) atomicAdd(&sAcc[j * kAccStride + my_slot], sum);
             } else {
+                const float araw = ex2_approx(pe.poly);
+                const float a = c ? fminf(S.alpha_max, araw) : 0.f;
+                if (c) T = T * __fdividef(1.f, 1.f - a);  // transmittance in front of this Gaussian
+                const float4 Cc = sC[j];
+                const float gv = fmaf(g0, Cc.x, fmaf(g1, Cc.y, fmaf(g2, Cc.z, fmaf(gD, Cc.w, gS))));
+                const float diff = gv - GB;
+                const float dalpha = T * diff;
+                GB = fmaf(a, diff, GB);
+                const float w = a * T;
+                const float dp = araw < S.alpha_max ? dalpha * a : 0.f;
+                const float dpx = dp * pe.dx, dpy = dp * pe.dy;
                 float vals[16] = {dpx,     dpy,     w * gD, c && araw < S.alpha_max ? dalpha * araw : 0.f,
                                   dpx * pe.dx, dpx * pe.dy, dpy * pe.dy, 0.f,
                                   w * g0,  w * g1,  w * g2, 0.f, 0.f, 0.f, 0.f, 0.f};

@@ -15,7 +15,7 @@
 //
 // With targets, the combined loss of Sec. III-B (plus the depth-prior term) is
 // evaluated in the epilogue: its per-pixel gradient goes to the workspace for the
-// backward and its value is reduced per tile in FP64 (summed per view by k_finalize).
+// backward and its value is reduced per tile in double-float (summed per view by k_finalize).
 #include "gs_internal.cuh"
 #include "tile_sort.cuh"
 
@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     __shared__ uint8_t sList[kTilePix / 32][kBatch];
     __shared__ unsigned long long sKeys[kSortSmemKeys];
     __shared__ int s_view;
-    __shared__ double s_loss[kTilePix / 32];
+    __shared__ float s_loss[kTilePix / 32];
     const uint32_t tile = L.ws.tile_order[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_view = view_of_tile(L.ws.views, L.d.V, tile);
@@ -174,15 +174,16 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
             L.ws.upstream[3u * P + gp] = gD;
             L.ws.upstream[4u * P + gp] = gS;
         }
-        // per-pixel terms summed over the warp in FP32 (32 terms), over warps and tiles in FP64
+        // per-pixel terms summed over the warp in FP32 (32 terms), over the warps in
+        // double-float; k_finalize sums the view's tiles in order
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
-        if ((tid & 31) == 0) s_loss[tid >> 5] = (double)l;
+        if ((tid & 31) == 0) s_loss[tid >> 5] = l;
         __syncthreads();
-        if (tid == 0) {  // the tile's share; k_finalize sums the view's tiles in order
-            double s = 0.0;
-            for (int w = 0; w < kTilePix / 32; ++w) s += s_loss[w];
-            L.ws.tile_loss[tile] = s;
+        if (tid == 0) {
+            DF s{0.f, 0.f};
+            for (int w = 0; w < kTilePix / 32; ++w) s = df_add(s, DF{s_loss[w], 0.f});
+            L.ws.tile_loss[tile] = df_pack(s);
         }
     }
 }
