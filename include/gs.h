@@ -225,13 +225,22 @@ gs_status gs_sync_status(gs_ctx *ctx, void *stream, gs_counts *counts);
 typedef struct {
     char name[24]; /* kernel (k_project, k_scan_tiles, k_emit, k_forward, k_backward,
                       k_bproject, k_finalize) */
-    float ms;      /* CUDA-event time from the end of the previous kernel to the end of this one */
+    float ms;      /* CUDA-event time from the marker before this kernel's launch (which is the
+                      end marker of the previous kernel when that one is also marked) to the
+                      marker after it */
 } gs_kernel_time;
 
 /* Enable (1) or disable (0) CUDA-event markers between the library's kernels on the
  * stream they are launched on (also inside the tracking graph, as event nodes).  Off by
  * default; events are created once per context.  Errors: CUDA. */
 gs_status gs_set_profiling(gs_ctx *ctx, int32_t enable);
+
+/* Select the kernels bracketed by profiling markers: bit k of mask selects, in order,
+ * k_project, k_scan_tiles, k_emit, k_forward, k_backward, k_bproject, k_finalize (0x7F:
+ * all, as gs_set_profiling(ctx, 1); 0: off).  Unselected kernels get no events, so timing
+ * one kernel disturbs the launch chain of the others less.  Errors: INVALID_ARG (a bit
+ * above 6). */
+gs_status gs_set_profiling_mask(gs_ctx *ctx, uint32_t mask);
 
 /* Synchronise on the last marker and return the per-kernel times of the work enqueued
  * by the last gs_project / gs_forward / gs_backward sequence or gs_track_step call (all

@@ -47,7 +47,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-I", INCLUDE, "-I", CSRC,
                      "--expt-relaxed-constexpr"] + (extra_flags or [])
 
     def compile_one(src: str) -> str:

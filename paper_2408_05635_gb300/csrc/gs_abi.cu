@@ -40,10 +40,10 @@ struct GraphKey {
     int iters = 0;
     std::vector<ViewInfo> views;
     uint32_t pair_cap = 0;
-    bool profiling = false;
+    uint32_t prof_mask = 0;
     bool operator==(const GraphKey &o) const {
         if (ws != o.ws || ws_bytes != o.ws_bytes || n != o.n || dtype != o.dtype || iters != o.iters ||
-            pair_cap != o.pair_cap || profiling != o.profiling ||
+            pair_cap != o.pair_cap || prof_mask != o.prof_mask ||
             views.size() != o.views.size())
             return false;
         for (int k = 0; k < 12; ++k)
@@ -72,8 +72,11 @@ struct gs_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     GraphKey graph_key;
-    // profiling markers: events[k] ends kernel names[k - 1] (events[0] is the start)
-    bool profiling = false;
+    // profiling markers: a named event ends that kernel, the event before it starts it;
+    // prof_mask selects kernels (bit k: kKernelNames[k]); adjacent: the last recorded
+    // event directly precedes the next launch, so it can serve as that kernel's start
+    uint32_t prof_mask = 0;
+    bool adjacent = false;
     std::vector<cudaEvent_t> events;
     std::vector<const char *> names;
     size_t n_marks = 0;
@@ -92,10 +95,17 @@ gs_status cuda_fail(gs_ctx *ctx, cudaError_t e, const char *where) {
     return GS_ERR_CUDA;
 }
 
-// Append a profiling marker: the end of kernel `name`, or (name NULL) the start of a
-// run of kernels.
-cudaError_t mark(gs_ctx *ctx, cudaStream_t st, const char *name) {
-    if (!ctx->profiling) return cudaSuccess;
+const char *const kKernelNames[] = {"k_project", "k_scan_tiles", "k_emit", "k_forward",
+                                    "k_backward", "k_bproject", "k_finalize"};
+constexpr uint32_t kAllKernels = (1u << (sizeof(kKernelNames) / sizeof(kKernelNames[0]))) - 1u;
+
+bool selected(const gs_ctx *ctx, const char *name) {
+    for (size_t k = 0; k < sizeof(kKernelNames) / sizeof(kKernelNames[0]); ++k)
+        if (std::strcmp(kKernelNames[k], name) == 0) return (ctx->prof_mask >> k) & 1u;
+    return false;
+}
+
+cudaError_t record_mark(gs_ctx *ctx, cudaStream_t st, const char *name) {
     if (ctx->n_marks == ctx->events.size()) {
         cudaEvent_t ev;
         cudaError_t e = cudaEventCreate(&ev);
@@ -105,10 +115,33 @@ cudaError_t mark(gs_ctx *ctx, cudaStream_t st, const char *name) {
     }
     const size_t k = ctx->n_marks++;
     ctx->names[k] = name;
+    ctx->adjacent = true;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cap);
     return cap != cudaStreamCaptureStatusNone ? cudaEventRecordWithFlags(ctx->events[k], st, cudaEventRecordExternal)
                                               : cudaEventRecord(ctx->events[k], st);
+}
+
+// Profiling marker before the launch of kernel `name` (only when it is selected and the
+// last marker does not already sit right before it).
+cudaError_t mark_begin(gs_ctx *ctx, cudaStream_t st, const char *name) {
+    if (!ctx->prof_mask || ctx->adjacent || !selected(ctx, name)) return cudaSuccess;
+    return record_mark(ctx, st, nullptr);
+}
+
+// Profiling marker after the launch of kernel `name`.
+cudaError_t mark(gs_ctx *ctx, cudaStream_t st, const char *name) {
+    if (!ctx->prof_mask) return cudaSuccess;
+    if (!selected(ctx, name)) {
+        ctx->adjacent = false;
+        return cudaSuccess;
+    }
+    return record_mark(ctx, st, name);
+}
+
+void reset_marks(gs_ctx *ctx) {
+    ctx->n_marks = 0;
+    ctx->adjacent = false;
 }
 
 Settings settings_of(const gs_config &c) {
@@ -258,7 +291,6 @@ cudaError_t upload_views(const Problem &pr, const WsPtrs &w, void *ws, cudaStrea
 cudaError_t enqueue_project(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, const GaussPtrs &g, int dtype,
                             const double *poses, cudaStream_t st) {
     cudaError_t e;
-    if ((e = mark(ctx, st, nullptr)) != cudaSuccess) return e;
     ProjectLaunch P;
     P.ws = w;
     P.d = pr.d;
@@ -266,10 +298,13 @@ cudaError_t enqueue_project(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, con
     P.g = g;
     P.dtype = dtype;
     P.poses = poses;
+    if ((e = mark_begin(ctx, st, "k_project")) != cudaSuccess) return e;
     if ((e = launch_project(P, st)) != cudaSuccess) return e;
     if ((e = mark(ctx, st, "k_project")) != cudaSuccess) return e;
+    if ((e = mark_begin(ctx, st, "k_scan_tiles")) != cudaSuccess) return e;
     if ((e = launch_scan_tiles(w, pr.d, st)) != cudaSuccess) return e;
     if ((e = mark(ctx, st, "k_scan_tiles")) != cudaSuccess) return e;
+    if ((e = mark_begin(ctx, st, "k_emit")) != cudaSuccess) return e;
     if ((e = launch_emit(w, pr.d, st)) != cudaSuccess) return e;
     return mark(ctx, st, "k_emit");
 }
@@ -287,6 +322,7 @@ cudaError_t enqueue_forward(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, con
     F.t_rgb = t ? t->rgb : nullptr;
     F.t_depth = t ? t->depth : nullptr;
     F.t_prior = t ? t->depth_prior : nullptr;
+    if ((e = mark_begin(ctx, st, "k_forward")) != cudaSuccess) return e;
     if ((e = launch_forward(F, st)) != cudaSuccess) return e;
     return mark(ctx, st, "k_forward");
 }
@@ -385,7 +421,7 @@ gs_status gs_project(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const WsPtrs w = ws_ptrs(ws, pr.lay);
     GaussPtrs gp{g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb};
-    ctx->n_marks = 0;
+    reset_marks(ctx);
     cudaError_t e = upload_views(pr, w, ws, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "view upload");
     e = enqueue_project(ctx, pr, w, gp, g->dtype_attr, poses, s);
@@ -419,7 +455,8 @@ gs_status gs_forward(gs_ctx *ctx, const gs_targets *targets, float *rgb, float *
         F.d = ctx->prob.d;
         F.s = ctx->s;
         F.loss_out = loss;
-        e = launch_finalize(F, s);
+        e = mark_begin(ctx, s, "k_finalize");
+        if (e == cudaSuccess) e = launch_finalize(F, s);
         if (e == cudaSuccess) e = mark(ctx, s, "k_finalize");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "loss reduction");
     }
@@ -451,7 +488,8 @@ gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, con
     const gs_gaussians_grad &G = grads ? *grads : none;
     const bool params = G.means || G.quats || G.log_scales || G.opacity_logits || G.rgb;
     B.pose_only = !(G.opacity_logits || G.rgb);
-    cudaError_t e = launch_backward(B, s);
+    cudaError_t e = mark_begin(ctx, s, "k_backward");
+    if (e == cudaSuccess) e = launch_backward(B, s);
     if (e == cudaSuccess) e = mark(ctx, s, "k_backward");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "backward");
     if (!params && !pose_grad) {
@@ -466,7 +504,8 @@ gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, con
     J.dtype = ctx->dtype;
     J.want_pose = pose_grad != nullptr;
     J.grads = G;
-    e = launch_bproject(J, s);
+    e = mark_begin(ctx, s, "k_bproject");
+    if (e == cudaSuccess) e = launch_bproject(J, s);
     if (e == cudaSuccess) e = mark(ctx, s, "k_bproject");
     if (e != cudaSuccess) return cuda_fail(ctx, e, "backward projection");
     if (pose_grad) {
@@ -476,7 +515,8 @@ gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, con
         F.s = ctx->s;
         F.pose_grad = pose_grad;
         F.pose = true;
-        e = launch_finalize(F, s);
+        e = mark_begin(ctx, s, "k_finalize");
+        if (e == cudaSuccess) e = launch_finalize(F, s);
         if (e == cudaSuccess) e = mark(ctx, s, "k_finalize");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "pose reduction");
     }
@@ -518,6 +558,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
             B.up_depth = w.upstream + 3u * pr.d.P;
             B.up_sil = w.upstream + 4u * pr.d.P;
             B.pose_only = true;
+            if ((r = mark_begin(ctx, q, "k_backward")) != cudaSuccess) return r;
             if ((r = launch_backward(B, q)) != cudaSuccess) return r;
             if ((r = mark(ctx, q, "k_backward")) != cudaSuccess) return r;
             BprojLaunch J;
@@ -528,6 +569,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
             J.dtype = g->dtype_attr;
             J.want_pose = true;
             J.grads = gs_gaussians_grad{};
+            if ((r = mark_begin(ctx, q, "k_bproject")) != cudaSuccess) return r;
             if ((r = launch_bproject(J, q)) != cudaSuccess) return r;
             if ((r = mark(ctx, q, "k_bproject")) != cudaSuccess) return r;
             FinalizeLaunch F{};
@@ -538,6 +580,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
             F.pose = true;
             F.poses = poses;
             F.adam = adam_state;
+            if ((r = mark_begin(ctx, q, "k_finalize")) != cudaSuccess) return r;
             if ((r = launch_finalize(F, q)) != cudaSuccess) return r;
             if ((r = mark(ctx, q, "k_finalize")) != cudaSuccess) return r;
         }
@@ -547,7 +590,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream query");
-    ctx->n_marks = 0;
+    reset_marks(ctx);
     if (cap != cudaStreamCaptureStatusNone) {
         // the caller is capturing: record the kernels into its graph directly
         e = enqueue_all(s);
@@ -564,7 +607,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
         key.iters = iters;
         key.views = pr.views;
         key.pair_cap = pr.d.pair_cap;
-        key.profiling = ctx->profiling;
+        key.prof_mask = ctx->prof_mask;
         if (!ctx->graph_exec || !(ctx->graph_key == key)) {
             if (ctx->graph_exec) {
                 cudaGraphExecDestroy(ctx->graph_exec);
@@ -613,15 +656,24 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
 gs_status gs_set_profiling(gs_ctx *ctx, int32_t enable) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     ctx->err.clear();
-    ctx->profiling = enable != 0;
-    ctx->n_marks = 0;
+    ctx->prof_mask = enable ? kAllKernels : 0u;
+    reset_marks(ctx);
+    return GS_OK;
+}
+
+gs_status gs_set_profiling_mask(gs_ctx *ctx, uint32_t mask) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (mask & ~kAllKernels) return fail(ctx, GS_ERR_INVALID_ARG, "profiling mask selects an unknown kernel");
+    ctx->prof_mask = mask;
+    reset_marks(ctx);
     return GS_OK;
 }
 
 gs_status gs_kernel_times(gs_ctx *ctx, gs_kernel_time *out, int32_t cap, int32_t *count) {
     if (!ctx || !count || cap < 0 || (cap > 0 && !out)) return GS_ERR_INVALID_ARG;
     ctx->err.clear();
-    if (!ctx->profiling || ctx->n_marks < 2) return fail(ctx, GS_ERR_STATE, "profiling off or nothing recorded");
+    if (!ctx->prof_mask || ctx->n_marks < 2) return fail(ctx, GS_ERR_STATE, "profiling off or nothing recorded");
     cudaError_t e = cudaEventSynchronize(ctx->events[ctx->n_marks - 1]);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "event synchronize");
     int32_t k = 0;

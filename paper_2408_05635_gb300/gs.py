@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                         c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
             "gs_sync_status": (c_int32, [c_void_p, c_void_p, P(gs_counts)]),
             "gs_set_profiling": (c_int32, [c_void_p, c_int32]),
+            "gs_set_profiling_mask": (c_int32, [c_void_p, ctypes.c_uint32]),
             "gs_render_static": (c_int32, [P(gs_config), P(gs_gaussians), P(gs_camera), c_void_p, P(gs_targets),
                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
             "gs_kernel_times": (c_int32, [c_void_p, P(gs_kernel_time), c_int32, P(c_int32)]),
@@ -219,6 +220,17 @@ def gs_sync_status(ctx, stream=None) -> tuple[int, gs_counts]:
 
 def gs_set_profiling(ctx, enable: bool) -> None:
     _check(ctx, load().gs_set_profiling(ctx, int(bool(enable))), "gs_set_profiling")
+
+
+KERNELS = ("k_project", "k_scan_tiles", "k_emit", "k_forward", "k_backward", "k_bproject", "k_finalize")
+
+
+def gs_set_profiling_mask(ctx, kernels) -> None:
+    """Bracket only the named kernels (names from KERNELS) with profiling markers."""
+    mask = 0
+    for k in kernels:
+        mask |= 1 << KERNELS.index(k)
+    _check(ctx, load().gs_set_profiling_mask(ctx, mask), "gs_set_profiling_mask")
 
 
 def gs_kernel_times(ctx, cap: int = 4096) -> list[tuple[str, float]]:
