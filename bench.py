@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    ap.add_argument("--batched-steps", type=int, default=10,
+                    help="timed steps of the batched BF16 hypothesis leg (0 skips it)")
     return ap.parse_args()
 
 
@@ -67,6 +69,127 @@ def workload(seed: int = 0):
     rgb, depth = scenes.raycast_room(gt, cam, seed=seed)
     prior = scenes.prior_from_depth(depth, rng, 0.02, 0.05)
     return g, cam, gt, start, rgb, depth, prior
+
+
+N_BATCH_GAUSS = 500_000
+BATCH_FRAMES, BATCH_HYP = 32, 16
+
+
+def batched_workload(seed: int = 0):
+    """Pose hypotheses over keyframes of uneven resolution: 32 keyframes (320 x 240, 640 x 480
+    or 1200 x 680), 16 hypotheses each (rotation N(0, 2 deg), translation N(0, 4 cm)), a
+    500k-Gaussian room; each keyframe's RGB-D target is ray-cast from its ground truth, with
+    a depth prior (x (1 + N(0, 0.02)), 5% holes)."""
+    from paper_2408_05635_gb300 import scenes
+    g = scenes.room_scene(N_BATCH_GAUSS, seed=seed)
+    cams, poses, frame_of, gts, frame_cams = scenes.batched_keyframes(BATCH_FRAMES, BATCH_HYP, seed=seed)
+    rng = np.random.default_rng(seed + 2)
+    frames = []
+    for f in range(BATCH_FRAMES):
+        rgb, depth = scenes.raycast_room(gts[f], frame_cams[f], seed=seed)
+        frames.append((rgb, depth, scenes.prior_from_depth(depth, rng, 0.02, 0.05)))
+    return g, cams, poses, frame_of, frames
+
+
+def run_batched(a, dev, stream):
+    """The batched / low-precision form beside the plain one, on the same views: all 512
+    hypotheses tracked in one call with BF16 attributes, against the same keyframes'
+    views tracked one call per view with FP32 attributes (one hypothesis per keyframe)."""
+    import torch
+    from paper_2408_05635_gb300 import gs
+    g, cams, poses0, frame_of, frames = batched_workload()
+    V = len(cams)
+    pix = [c.width * c.height for c in cams]
+    P = sum(pix)
+    # targets of every view, in view order (a keyframe's target repeated for its hypotheses)
+    t_rgb = torch.cat([torch.from_numpy(frames[f][0].reshape(-1)) for f in frame_of]).to(dev)
+    t_depth = torch.cat([torch.from_numpy(frames[f][1].reshape(-1)) for f in frame_of]).to(dev)
+    t_prior = torch.cat([torch.from_numpy(frames[f][2].reshape(-1)) for f in frame_of]).to(dev)
+    start = torch.tensor(np.asarray(poses0), dtype=torch.float64, device=dev)
+
+    def track(R, gt, prob, ws, nb, poses, adam, loss, targets):
+        gs.gs_track_step(R.ctx, prob, gt.c(), targets, poses, adam, loss, 1, ws, nb, stream)
+
+    # batched: one call over all views, BF16 attributes
+    R = gs.Rasterizer(gs.Config(), device=dev)
+    gtb = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=torch.bfloat16)
+    poses = start.clone()
+    prob = R.plan(gtb, cams, poses, margin=1.5)
+    ws, nb = R.workspace(prob)
+    tg = gs.gs_targets(t_rgb.data_ptr(), t_depth.data_ptr(), t_prior.data_ptr())
+    adam = torch.zeros(V, 16, dtype=torch.float64, device=dev)
+    loss = torch.zeros(1, V, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        track(R, gtb, prob, ws, nb, poses, adam, loss, tg)
+    gs.gs_set_profiling(R.ctx, True)
+    track(R, gtb, prob, ws, nb, poses, adam, loss, tg)
+    kernels = {k: round(1e3 * ms, 1) for k, ms in gs.gs_kernel_times(R.ctx)}
+    gs.gs_set_profiling(R.ctx, False)
+    poses.copy_(start)
+    adam.zero_()
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(a.batched_steps):
+        track(R, gtb, prob, ws, nb, poses, adam, loss, tg)
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    st, c = gs.gs_sync_status(R.ctx, stream)
+    if st:
+        raise SystemExit(f"batched leg: device reported {gs._STATUS[st]}")
+    b_ms = ev[0].elapsed_time(ev[1]) / a.batched_steps
+    # the same start poses, pose gradient in BF16 (batched) for the accuracy comparison
+    poses.copy_(start)
+    out = R.render(prob, gtb, poses, targets=(t_rgb, t_depth, t_prior), stream=stream, images=False)
+    g_b = R.backward(gtb, params=False, pose=True, stream=stream, n_views=V)["pose_grad"].clone()
+    ws_bytes = nb
+    R.close()
+    del ws, R
+
+    # plain: one hypothesis per keyframe, one call per view, FP32 attributes
+    gtf = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=torch.float32)
+    Rp = gs.Rasterizer(gs.Config(), device=dev)
+    sub = [int(np.flatnonzero(frame_of == f)[0]) for f in range(BATCH_FRAMES)]
+    off = np.concatenate([[0], np.cumsum(pix)])
+    plain_ms, rel = 0.0, []
+    reps = 10
+    for v in sub:
+        pv = start[v:v + 1].clone()
+        pr = Rp.plan(gtf, [cams[v]], pv, margin=1.5)
+        wsv, nbv = Rp.workspace(pr)
+        tr = (t_rgb[3 * off[v]:3 * off[v + 1]], t_depth[off[v]:off[v + 1]], t_prior[off[v]:off[v + 1]])
+        tgv = gs.gs_targets(tr[0].data_ptr(), tr[1].data_ptr(), tr[2].data_ptr())
+        av = torch.zeros(1, 16, dtype=torch.float64, device=dev)
+        lv = torch.zeros(1, 1, dtype=torch.float64, device=dev)
+        track(Rp, gtf, pr, wsv, nbv, pv, av, lv, tgv)  # captures this view's graph
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for _ in range(reps):
+            track(Rp, gtf, pr, wsv, nbv, pv, av, lv, tgv)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms += ev[0].elapsed_time(ev[1]) / reps
+        pv.copy_(start[v:v + 1])
+        Rp.render(pr, gtf, pv, targets=tr, stream=stream, images=False)
+        g_f = Rp.backward(gtf, params=False, pose=True, stream=stream)["pose_grad"][0]
+        rel.append(float((g_b[v] - g_f).norm() / g_f.norm().clamp_min(1e-30)))
+    Rp.close()
+    sub_pix = sum(pix[v] for v in sub)
+    plain_view_its = len(sub) / (plain_ms / 1e3)
+    batched_view_its = V / (b_ms / 1e3)
+    return {
+        "workload": f"{BATCH_FRAMES} keyframes x {BATCH_HYP} pose hypotheses (uneven 320x240 / 640x480 / "
+                    f"1200x680), {N_BATCH_GAUSS // 1000}k room Gaussians",
+        "views": V, "pixels_per_step": P, "workspace_gb": round(ws_bytes / 1e9, 2),
+        "batched_bf16": {"ms_per_step": b_ms, "view_iters_per_s": batched_view_its, "mpix_per_s": P / b_ms / 1e3,
+                         "launch": "one gs_track_step call (one CUDA graph) for all views", "kernels_us": kernels},
+        "plain_fp32": {"views_timed": len(sub), "ms_per_view_iter": plain_ms / len(sub),
+                       "view_iters_per_s": plain_view_its, "mpix_per_s": sub_pix / plain_ms / 1e3,
+                       "launch": "one gs_track_step call per view"},
+        "speedup_view_iters": batched_view_its / plain_view_its,
+        "pose_grad_rel_diff_bf16_vs_fp32": {"max": max(rel), "median": float(np.median(rel))},
+        "l2": "working set far above L2 (no flush)",
+    }
 
 
 class ClockSampler:
@@ -372,6 +495,8 @@ def main():
                                f"the timed steps mark only {dominant}",
             "pairs_per_step": {k: v // a.steps for k, v in contrib.items()},
         }
+        if world == 1 and a.batched_steps > 0:
+            line["batched"] = run_batched(a, dev, stream)
         if world == 1 and not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, cam, start, rgb, depth, prior, a.cpu_sample_seconds)
         print(json.dumps(line), flush=True)

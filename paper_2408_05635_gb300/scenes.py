@@ -297,18 +297,22 @@ def spline_trajectory(n_frames: int, seed: int = 0, n_ctrl: int = 8) -> list:
 def batched_keyframes(n_frames: int = 32, n_hyp: int = 16, seed: int = 0):
     """Keyframes of uneven resolution (uniform over 320 x 240, 640 x 480, 1200 x 680, focal
     length scaled with width) at seeded positions inside the room, each with `n_hyp` pose
-    hypotheses: rotation vector N(0, 2 deg) and translation N(0, 4 cm) per axis."""
+    hypotheses: rotation vector N(0, 2 deg) and translation N(0, 4 cm) per axis.  Returns the
+    per-view cameras and hypothesis poses, the keyframe of each view, and the keyframes'
+    ground-truth poses and cameras."""
     rng = np.random.default_rng(seed + 15485863)
     cams_choice = [QVGA_CAM, TUM_CAM, WIDE_CAM]
     X, Y, Z = ROOM
-    cams, poses, frame_of = [], [], []
+    cams, poses, frame_of, gts, frame_cams = [], [], [], [], []
     for f in range(n_frames):
         cam = cams_choice[rng.integers(0, 3)]
         pos = np.array([rng.uniform(1.0, X - 1.0), rng.uniform(1.0, Y - 1.0), rng.uniform(1.0, Z - 1.0)])
         yaw = rng.uniform(0.0, 2.0 * np.pi)
         gt = look_at(pos, (np.sin(yaw), rng.uniform(-0.2, 0.2), np.cos(yaw)))
+        gts.append(gt)
+        frame_cams.append(cam)
         for _ in range(n_hyp):
             cams.append(cam)
             poses.append(jitter_pose(gt, rng, 2.0, 0.04))
             frame_of.append(f)
-    return cams, poses, np.array(frame_of)
+    return cams, poses, np.array(frame_of), gts, frame_cams
