@@ -54,6 +54,9 @@
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
+
+/* Unit roundoff of IEEE binary32 (2^-24): the FP32 renderer's relative rounding. */
+#define OG_FP32_ROUNDOFF 5.9604644775390625e-8
 #endif
 
 #define OG_OK 0
@@ -69,7 +72,7 @@ typedef struct {
     double alpha_min, alpha_max, t_min, dilation, z_near, sil_thresh;
     double w_rgb, w_depth, w_vis, w_prior;
     double beta1, beta2, eps, lr_rot, lr_trans;
-    double amb_alpha, amb_t, amb_sil, amb_resid;
+    double amb_alpha, amb_t, amb_sil, amb_resid, amb_terms, amb_value;
     int32_t brute_force, n_threads;
 } og_params;
 
@@ -369,6 +372,7 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
                             const og_scene *sc, const og_params *p, double out5[5], double *t_final,
                             og_contrib *contrib, int64_t *ncontrib, int *amb) {
     double T = 1.0, C0 = 0, C1 = 0, C2 = 0, D = 0, S = 0;
+    double eT = 0.0; /* bound of the relative error of an FP32 renderer's T so far */
     int64_t nc = 0;
     int a = 0;
     for (int64_t k = 0; k < nlist; ++k) {
@@ -379,16 +383,37 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
         const double q = pr->conic[0] * dx * dx + 2.0 * pr->conic[1] * dx * dy + pr->conic[2] * dy * dy;
         const double G = exp(-0.5 * q);
         const double araw = pr->o * G;
-        if (fabs(araw - p->alpha_min) <= p->amb_alpha * p->alpha_min) a = 1;
+        /* Relative margin of the alpha decisions: the fixed amb_alpha, or the error with
+         * which an FP32 renderer can know the exponent of Eq. 1 at this pixel, whichever is
+         * larger.  The screen mean is held to 24 bits (|d exponent / d mu'| = |conic d|
+         * times the rounding of |mu'|) and the quadratic form's terms are rounded once each;
+         * a footprint evaluated thousands of pixels from its mean therefore has an alpha
+         * known only to ~1e-3, where an ordinary one is known to ~1e-5. */
+        const double gx = pr->conic[0] * dx + pr->conic[1] * dy, gy = pr->conic[1] * dx + pr->conic[2] * dy;
+        const double terms = fabs(pr->conic[0] * dx * dx) + 2.0 * fabs(pr->conic[1] * dx * dy) +
+                             fabs(pr->conic[2] * dy * dy);
+        const double mu_mag = fmax(fabs(pr->mu[0]), fabs(pr->mu[1]));
+        const double dexp = 4.0 * OG_FP32_ROUNDOFF * (sqrt(gx * gx + gy * gy) * mu_mag + terms);
+        const double margin = fmax(p->amb_alpha, dexp);
+        if (araw > 0.0 && fabs(log(araw / p->alpha_min)) <= margin) a = 1;
         if (araw < p->alpha_min) continue;
         const int clamped = araw >= p->alpha_max;
         const double alpha = clamped ? p->alpha_max : araw;
-        if (fabs(araw - p->alpha_max) <= p->amb_alpha * p->alpha_max) a = 1;
+        if (araw > 0.0 && fabs(log(araw / p->alpha_max)) <= margin) a = 1;
         const double z = pr->xc[2];
         const double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - p->t_min) <= p->amb_t * p->t_min) a = 1;
+        /* an alpha known to a relative dexp gives 1 - alpha to alpha dexp / (1 - alpha): the
+         * product T = prod (1 - alpha_i) compounds it (a clamped alpha is exact) */
+        if (!clamped) eT += alpha * dexp / (1.0 - alpha);
+        if (fabs(Tn - p->t_min) <= fmax(p->amb_t, 2.0 * eT) * p->t_min) a = 1;
         if (Tn < p->t_min) break;
         const double w = alpha * T;
+        /* A quadratic form whose terms exceed amb_terms while their sum, the exponent, stays
+         * small (a very elongated footprint evaluated far from its mean, typically a
+         * Gaussian a few cm beyond the near plane) is known to FP32 only to ~terms x 2^-24;
+         * the pixel itself is uncertain once the contribution times that error exceeds
+         * amb_value. */
+        if (terms > p->amb_terms && w * dexp * (1.0 + fabs(z)) > p->amb_value) a = 1;
         const double *c = sc->rgb + 3 * gi;
         C0 += c[0] * w;
         C1 += c[1] * w;
