@@ -332,8 +332,19 @@ __device__ __forceinline__ Footprint stage_footprint(const float4 A, const float
 // (umin, umax, vmin, vmax): the ellipse poly >= log2(alpha_min) has half-extents
 // sqrt(dmax2 Sigma'_xx), sqrt(dmax2 Sigma'_yy), widened by a relative 1e-3 and 0.01 px so
 // FP32 rounding can never drop a pixel with alpha >= alpha_min.
+// a b - c d with Kahan's fused correction (analysed by Jeannerod, Louvet and Muller, 2013):
+// the rounding error of c d is recovered exactly by an FMA, so the difference of two
+// nearly equal products keeps ~2 ulp of relative accuracy instead of losing the digits the
+// products share.  Explicit intrinsics: every caller computes bit-identical results.
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    const float w = __fmul_rn(c, d);
+    const float e = __fmaf_rn(-c, d, w);
+    const float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, e);
+}
+
 __device__ __forceinline__ float4 stage_box(const float4 B, float cu, float cv) {
-    const float detc = B.x * B.z - B.y * B.y;
+    const float detc = diff_of_products(B.x, B.z, B.y, B.y);
     if (!(detc > 0.f) || !(B.w < INFINITY)) return make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
     const float hx = sqrtf(B.w * B.z / detc) * 1.001f + 0.01f;
     const float hy = sqrtf(B.w * B.x / detc) * 1.001f + 0.01f;

@@ -17,7 +17,7 @@ namespace gsk {
 // so they enumerate the same tiles.  Returns false when the box misses the image.
 __device__ __forceinline__ bool record_rect(const ViewInfo &vi, float4 A, float4 B, int &tx0, int &tx1, int &ty0,
                                             int &ty1) {
-    const float detc = __fsub_rn(__fmul_rn(B.x, B.z), __fmul_rn(B.y, B.y));
+    const float detc = diff_of_products(B.x, B.z, B.y, B.y);
     if (!(detc > 0.f)) return false;
     float hx = INFINITY, hy = INFINITY;
     if (B.w < INFINITY) {
@@ -333,7 +333,13 @@ __global__ void __launch_bounds__(kBlock, 5) k_project(ProjectLaunch L) {
             const float S00 = N0[0] * N0[0] + N0[1] * N0[1] + N0[2] * N0[2] + S.dilation;
             const float S01 = N0[0] * N1[0] + N0[1] * N1[1] + N0[2] * N1[2];
             const float S11 = N1[0] * N1[0] + N1[1] * N1[1] + N1[2] * N1[2] + S.dilation;
-            const float det = S00 * S11 - S01 * S01;
+            // det(N N^T + e I) = |N0 x N1|^2 + e (S00 + S11) - e^2 (Cauchy-Binet): a sum of
+            // squares, where S00 S11 - S01^2 cancels catastrophically once the footprint is
+            // thin (N0, N1 nearly parallel: a Gaussian seen edge-on or close to the camera)
+            const float cx = diff_of_products(N0[1], N1[2], N0[2], N1[1]);
+            const float cy = diff_of_products(N0[2], N1[0], N0[0], N1[2]);
+            const float cz = diff_of_products(N0[0], N1[1], N0[1], N1[0]);
+            const float det = cx * cx + cy * cy + cz * cz + S.dilation * (S00 + S11 - S.dilation);
             if (det > 0.f) {
                 const float idet = __fdividef(1.f, det);
                 const float o = __fdividef(1.f, 1.f + __expf(-ld_attr<DT>(L.g.logits, i)));
