@@ -11,8 +11,9 @@ checked against the FP64 oracle on what it can compute at that size.
   pose gradient must be exactly zero), and the first graph-launched update.
 
 The batched views include Gaussians within a few cm of the near plane (cameras right
-above the room's boxes): their screen mean and conic are recomputed in FP64 (k_refine),
-and the oracle masks the pixels where their FP32 footprint evaluation stays uncertain.
+above the room's boxes): their thin screen covariances are inverted with a cancellation-
+free determinant (k_project), and the oracle masks the pixels where their FP32 footprint
+evaluation stays uncertain.
 
 Tolerances as in the small parity tests: images 1e-4 max-abs on unambiguous pixels,
 gradients 1e-3 relative (inf and 2-norm) with the ambiguous pixels' upstream zeroed on
