@@ -50,7 +50,7 @@ class _Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_double) for name in (
         "alpha_min", "alpha_max", "t_min", "dilation", "z_near", "sil_thresh",
         "w_rgb", "w_depth", "w_vis", "w_prior", "beta1", "beta2", "eps", "lr_rot", "lr_trans",
-        "amb_alpha", "amb_t", "amb_sil", "amb_resid", "amb_terms", "amb_value")] + [
+        "amb_alpha", "amb_t", "amb_sil", "amb_resid", "amb_effect")] + [
         ("brute_force", ctypes.c_int32), ("n_threads", ctypes.c_int32)]
 
 
@@ -66,9 +66,9 @@ class Params:
     alpha_max / alpha_min / t_min: opacity clamp, skip threshold and early-termination
     transmittance; z_near: near plane (m); dilation: eps added to Sigma' (px^2);
     sil_thresh and the w_* weights define the combined loss; beta1/beta2/eps/lr_* the
-    decoupled Adam; amb_* the margins of the ambiguity mask (amb_terms / amb_value: pixels
-    where a footprint whose quadratic-form terms exceed amb_terms contributes more than
-    amb_value times its FP32 exponent error); brute_force selects the
+    decoupled Adam; amb_* the floors of the ambiguity-mask margins (which otherwise follow
+    the FP32 error of the footprint exponent at each pixel), amb_effect the smallest pixel
+    change an alpha_min decision must be able to make to count; brute_force selects the
     walk over every Gaussian instead of the opacity-aware boxes.
     """
     alpha_min: float = 1.0 / 255.0
@@ -90,8 +90,7 @@ class Params:
     amb_t: float = 2e-4
     amb_sil: float = 1e-5
     amb_resid: float = 2e-5
-    amb_terms: float = 1e3
-    amb_value: float = 2.5e-5
+    amb_effect: float = 2.5e-5
     brute_force: bool = False
     n_threads: int = 0
 

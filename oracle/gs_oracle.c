@@ -54,10 +54,10 @@
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
+#endif
 
 /* Unit roundoff of IEEE binary32 (2^-24): the FP32 renderer's relative rounding. */
 #define OG_FP32_ROUNDOFF 5.9604644775390625e-8
-#endif
 
 #define OG_OK 0
 #define OG_ERR_ARG 1
@@ -72,7 +72,7 @@ typedef struct {
     double alpha_min, alpha_max, t_min, dilation, z_near, sil_thresh;
     double w_rgb, w_depth, w_vis, w_prior;
     double beta1, beta2, eps, lr_rot, lr_trans;
-    double amb_alpha, amb_t, amb_sil, amb_resid, amb_terms, amb_value;
+    double amb_alpha, amb_t, amb_sil, amb_resid, amb_effect;
     int32_t brute_force, n_threads;
 } og_params;
 
@@ -95,6 +95,7 @@ typedef struct {
     double conic[3];   /* Sigma'^-1 entries (a, b, c) */
     double o;          /* opacity */
     double dmax2;      /* largest Mahalanobis^2 with o exp(-d2/2) >= alpha_min */
+    double dmu;        /* bound of an FP32 renderer's screen-mean error from its camera transform */
     int x0, x1, y0, y1;/* inclusive pixel box, clamped to the image */
 } og_proj;
 
@@ -264,6 +265,17 @@ static void project_one(const og_scene *sc, int64_t i, const og_camera *cam, con
     /* pi_m of Sec. II-A */
     pr->mu[0] = cam->fx * g.xc[0] / z + cam->cx;
     pr->mu[1] = cam->fy * g.xc[1] / z + cam->cy;
+    /* An FP32 renderer applies the pose rounded to FP32: its camera-frame mean is off by
+     * ~u (|x| + |t|) (twice that as the bound), nearly the same for neighbouring Gaussians,
+     * which moves their screen means together by (f / z)(1 + |x_c / z| + |y_c / z|) times
+     * that; the roundings of the product itself differ from Gaussian to Gaussian and
+     * average out in the compositing. */
+    {
+        const double *m = sc->means + 3 * i;
+        const double dxc = 2.0 * OG_FP32_ROUNDOFF * (sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) +
+                                                     sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]));
+        pr->dmu = fmax(cam->fx, cam->fy) / z * dxc * (1.0 + fabs(g.xc[0] / z) + fabs(g.xc[1] / z));
+    }
     pr->o = 1.0 / (1.0 + exp(-sc->logits[i]));
     pr->cand = 1;
     /* opacity-aware support: o exp(-d2/2) >= alpha_min  <=>  d2 <= 2 ln(o / alpha_min) */
@@ -385,17 +397,22 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
         const double araw = pr->o * G;
         /* Relative margin of the alpha decisions: the fixed amb_alpha, or the error with
          * which an FP32 renderer can know the exponent of Eq. 1 at this pixel, whichever is
-         * larger.  The screen mean is held to 24 bits (|d exponent / d mu'| = |conic d|
-         * times the rounding of |mu'|) and the quadratic form's terms are rounded once each;
-         * a footprint evaluated thousands of pixels from its mean therefore has an alpha
-         * known only to ~1e-3, where an ordinary one is known to ~1e-5. */
+         * larger.  |d exponent / d mu'| = |conic d| times the screen-mean error (its 24-bit
+         * rounding plus dmu, the FP32 camera transform), and the quadratic form's terms are
+         * rounded once each; a footprint evaluated thousands of pixels from its mean has an
+         * alpha known only to ~1e-3, an ordinary one to ~1e-5. */
         const double gx = pr->conic[0] * dx + pr->conic[1] * dy, gy = pr->conic[1] * dx + pr->conic[2] * dy;
         const double terms = fabs(pr->conic[0] * dx * dx) + 2.0 * fabs(pr->conic[1] * dx * dy) +
                              fabs(pr->conic[2] * dy * dy);
         const double mu_mag = fmax(fabs(pr->mu[0]), fabs(pr->mu[1]));
-        const double dexp = 4.0 * OG_FP32_ROUNDOFF * (sqrt(gx * gx + gy * gy) * mu_mag + terms);
+        const double dexp = 4.0 * OG_FP32_ROUNDOFF * (sqrt(gx * gx + gy * gy) * mu_mag + terms) +
+                            sqrt(gx * gx + gy * gy) * pr->dmu;
         const double margin = fmax(p->amb_alpha, dexp);
-        if (araw > 0.0 && fabs(log(araw / p->alpha_min)) <= margin) a = 1;
+        /* skipping or keeping an alpha ~ alpha_min Gaussian moves the pixel by at most about
+         * 2 alpha_min T max(1, z): only a decision that can matter is ambiguous */
+        if (araw > 0.0 && fabs(log(araw / p->alpha_min)) <= margin &&
+            2.0 * p->alpha_min * T * fmax(1.0, fabs(pr->xc[2])) > p->amb_effect)
+            a = 1;
         if (araw < p->alpha_min) continue;
         const int clamped = araw >= p->alpha_max;
         const double alpha = clamped ? p->alpha_max : araw;
@@ -405,15 +422,9 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
         /* an alpha known to a relative dexp gives 1 - alpha to alpha dexp / (1 - alpha): the
          * product T = prod (1 - alpha_i) compounds it (a clamped alpha is exact) */
         if (!clamped) eT += alpha * dexp / (1.0 - alpha);
-        if (fabs(Tn - p->t_min) <= fmax(p->amb_t, 2.0 * eT) * p->t_min) a = 1;
+        if (fabs(Tn - p->t_min) <= fmax(p->amb_t, eT) * p->t_min) a = 1;
         if (Tn < p->t_min) break;
         const double w = alpha * T;
-        /* A quadratic form whose terms exceed amb_terms while their sum, the exponent, stays
-         * small (a very elongated footprint evaluated far from its mean, typically a
-         * Gaussian a few cm beyond the near plane) is known to FP32 only to ~terms x 2^-24;
-         * the pixel itself is uncertain once the contribution times that error exceeds
-         * amb_value. */
-        if (terms > p->amb_terms && w * dexp * (1.0 + fabs(z)) > p->amb_value) a = 1;
         const double *c = sc->rgb + 3 * gi;
         C0 += c[0] * w;
         C1 += c[1] * w;
