@@ -48,7 +48,7 @@ class Camera(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [(name, ctypes.c_double) for name in (
-        "alpha_min", "alpha_max", "t_min", "dilation", "z_near", "sil_thresh",
+        "alpha_min", "alpha_max", "t_min", "dilation", "z_near", "jac_clip", "sil_thresh",
         "w_rgb", "w_depth", "w_vis", "w_prior", "beta1", "beta2", "eps", "lr_rot", "lr_trans",
         "amb_alpha", "amb_t", "amb_sil", "amb_resid", "amb_effect")] + [
         ("brute_force", ctypes.c_int32), ("n_threads", ctypes.c_int32)]
@@ -65,6 +65,8 @@ class Params:
 
     alpha_max / alpha_min / t_min: opacity clamp, skip threshold and early-termination
     transmittance; z_near: near plane (m); dilation: eps added to Sigma' (px^2);
+    jac_clip: the Jacobian of Sigma' is taken at the mean's image-plane tangent clamped
+    to +-jac_clip half-extents of the view (0 disables the clamp);
     sil_thresh and the w_* weights define the combined loss; beta1/beta2/eps/lr_* the
     decoupled Adam; amb_* the floors of the ambiguity-mask margins (which otherwise follow
     the FP32 error of the footprint exponent at each pixel), amb_effect the smallest pixel
@@ -76,6 +78,7 @@ class Params:
     t_min: float = 1e-4
     dilation: float = 0.0
     z_near: float = 0.2
+    jac_clip: float = 1.3
     sil_thresh: float = 0.99
     w_rgb: float = 0.5
     w_depth: float = 1.0

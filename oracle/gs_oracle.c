@@ -31,7 +31,13 @@
  *   walk stops before the Gaussian whose inclusion would drop the transmittance below
  *   t_min; background is 0 for C, D and S; pixel (u, v) is sampled at integer (u, v);
  *   Gaussians with camera depth <= z_near are dropped; an optional dilation eps*I is
- *   added to Sigma'.
+ *   added to Sigma'; the Jacobian J of Sigma' is taken at the mean's image-plane
+ *   tangent (x_c / z, y_c / z) clamped to +-jac_clip times the half-extent of the view
+ *   (W / 2 fx, H / 2 fy), as the 3DGS rasterizer the paper builds on (SplaTAM's) does:
+ *   the local affine approximation is meaningless for a mean far outside the view, and
+ *   unclamped it blows a Gaussian just beyond the near plane up into a footprint of
+ *   thousands of pixels.  A clamped coordinate passes no gradient through J; the
+ *   screen mean itself is never clamped.
  *
  * Two compositing modes give the same numbers by construction: brute force (every
  * pixel walks every surviving Gaussian) and culled (every pixel walks only the
@@ -69,7 +75,7 @@ typedef struct {
 } og_camera;
 
 typedef struct {
-    double alpha_min, alpha_max, t_min, dilation, z_near, sil_thresh;
+    double alpha_min, alpha_max, t_min, dilation, z_near, jac_clip, sil_thresh;
     double w_rgb, w_depth, w_vis, w_prior;
     double beta1, beta2, eps, lr_rot, lr_trans;
     double amb_alpha, amb_t, amb_sil, amb_resid, amb_effect;
@@ -196,10 +202,12 @@ typedef struct {
     double qn[4], qnorm, Rg[9], s[3];
     double Sigma[9], Sigma_c[9], J[6];
     double xc[3];
+    double tan_c[2];  /* image-plane tangent at which J is taken (clamped x_c / z, y_c / z) */
+    int free_t[2];    /* 1 where that tangent is not clamped (J depends on x_c, y_c there) */
 } og_geom;
 
 static void geom_one(const og_scene *sc, int64_t i, const og_camera *cam, const double R[9],
-                     const double t[3], og_geom *g) {
+                     const double t[3], double jac_clip, og_geom *g) {
     const double *m = sc->means + 3 * i;
     for (int r = 0; r < 3; ++r) g->xc[r] = R[3 * r] * m[0] + R[3 * r + 1] * m[1] + R[3 * r + 2] * m[2] + t[r];
     const double *q = sc->quats + 4 * i;
@@ -219,21 +227,27 @@ static void geom_one(const og_scene *sc, int64_t i, const og_camera *cam, const 
     mat3_mul(R, g->Sigma, RS);
     mat3_transpose(R, Rt);
     mat3_mul(RS, Rt, g->Sigma_c);
-    /* Jacobian of pi_m at the camera-frame mean */
-    const double x = g->xc[0], y = g->xc[1], z = g->xc[2];
+    /* Jacobian of pi_m at the camera-frame mean, its tangent clamped (jac_clip > 0) */
+    const double z = g->xc[2];
+    const double lim[2] = {jac_clip * 0.5 * cam->width / cam->fx, jac_clip * 0.5 * cam->height / cam->fy};
+    for (int k = 0; k < 2; ++k) {
+        const double tk = g->xc[k] / z;
+        g->free_t[k] = !(jac_clip > 0.0) || fabs(tk) <= lim[k];
+        g->tan_c[k] = g->free_t[k] ? tk : copysign(lim[k], tk);
+    }
     g->J[0] = cam->fx / z;
     g->J[1] = 0.0;
-    g->J[2] = -cam->fx * x / (z * z);
+    g->J[2] = -cam->fx * g->tan_c[0] / z;
     g->J[3] = 0.0;
     g->J[4] = cam->fy / z;
-    g->J[5] = -cam->fy * y / (z * z);
+    g->J[5] = -cam->fy * g->tan_c[1] / z;
 }
 
 static void project_one(const og_scene *sc, int64_t i, const og_camera *cam, const double R[9], const double t[3],
                         const float Rf[9], const float tf[3], const og_params *p, og_proj *pr) {
     og_geom g;
     memset(pr, 0, sizeof(*pr));
-    geom_one(sc, i, cam, R, t, &g);
+    geom_one(sc, i, cam, R, t, p->jac_clip, &g);
     for (int k = 0; k < 3; ++k) pr->xc[k] = g.xc[k];
     const double z = g.xc[2];
     pr->zkey = depth_key(Rf, tf, sc->means + 3 * i);
@@ -711,7 +725,7 @@ static void backward_pixel(int px, int py, const og_contrib *cb, int64_t nc, con
 static void chain_one(const og_scene *sc, int64_t i, const og_camera *cam, const double R[9], const double t[3],
                       const og_params *p, const double *a, double *g14, double pose6[6]) {
     og_geom g;
-    geom_one(sc, i, cam, R, t, &g);
+    geom_one(sc, i, cam, R, t, p->jac_clip, &g);
     const double z = g.xc[2], x = g.xc[0], y = g.xc[1];
     /* Sigma' and its inverse (same formulas as the projection) */
     double JS[6];
@@ -753,16 +767,19 @@ static void chain_one(const og_scene *sc, int64_t i, const og_camera *cam, const
             for (int u = 0; u < 2; ++u) v += Gs[2 * r + u] * JS[3 * u + c];
             dJ[3 * r + c] = 2.0 * v;
         }
-    /* camera-frame mean: through pi_m (d mu' = J d x_c), the depth channel and J itself */
-    double dxc[3];
-    dxc[0] = g.J[0] * a[G_MX] + g.J[3] * a[G_MY];
-    dxc[1] = g.J[1] * a[G_MX] + g.J[4] * a[G_MY];
-    dxc[2] = g.J[2] * a[G_MX] + g.J[5] * a[G_MY] + a[G_Z];
+    /* camera-frame mean: through pi_m (d mu' = (f / z, -f x / z^2) d x_c, never clamped),
+     * the depth channel and J itself: J02 = -fx tan_x / z with tan_x = x / z where free,
+     * so dJ02/dx = -fx / z^2 and dJ02/dz = fx tan_x / z^2 + fx x / z^3 there, and
+     * dJ02/dx = 0, dJ02/dz = fx tan_x / z^2 where clamped (J12 likewise) */
     const double fx = cam->fx, fy = cam->fy;
-    dxc[0] += dJ[2] * (-fx / (z * z));
-    dxc[1] += dJ[5] * (-fy / (z * z));
-    dxc[2] += dJ[0] * (-fx / (z * z)) + dJ[2] * (2.0 * fx * x / (z * z * z)) + dJ[4] * (-fy / (z * z)) +
-              dJ[5] * (2.0 * fy * y / (z * z * z));
+    double dxc[3];
+    dxc[0] = fx / z * a[G_MX];
+    dxc[1] = fy / z * a[G_MY];
+    dxc[2] = -fx * x / (z * z) * a[G_MX] - fy * y / (z * z) * a[G_MY] + a[G_Z];
+    if (g.free_t[0]) dxc[0] += dJ[2] * (-fx / (z * z));
+    if (g.free_t[1]) dxc[1] += dJ[5] * (-fy / (z * z));
+    dxc[2] += dJ[0] * (-fx / (z * z)) + dJ[2] * (fx * g.tan_c[0] / (z * z) + (g.free_t[0] ? fx * x / (z * z * z) : 0.0)) +
+              dJ[4] * (-fy / (z * z)) + dJ[5] * (fy * g.tan_c[1] / (z * z) + (g.free_t[1] ? fy * y / (z * z * z) : 0.0));
     /* x_c = W m + t */
     double dm[3];
     for (int c = 0; c < 3; ++c) dm[c] = R[c] * dxc[0] + R[3 + c] * dxc[1] + R[6 + c] * dxc[2];

@@ -97,6 +97,30 @@ def test_projection_covariance_monte_carlo():
     np.testing.assert_allclose(np.array([[a, b], [b, c]]) @ np.array([[A, B], [B, C]]), np.eye(2), atol=1e-12)
 
 
+def test_jacobian_clamp_beyond_view():
+    """Beyond +-jac_clip half-extents the Jacobian is frozen: sliding a Gaussian sideways
+    at a fixed depth moves its screen mean as pi_m says but leaves Sigma' unchanged, and
+    Sigma' is continuous where the clamp begins; inside the clamp it equals the unclamped
+    Sigma'."""
+    cam = oracle.camera(200, 200, 160, 120, 320, 240)
+    lim = 1.3 * 160 / 200  # tangent limit along x at the default jac_clip
+    z = 1.0
+    xs = np.array([0.5 * lim, lim * (1 - 1e-9), lim * (1 + 1e-9), 1.5 * lim, 4.0 * lim, 9.0 * lim])
+    n = xs.size
+    q = np.tile([0.9, 0.2, -0.3, 0.25], (n, 1))
+    sc = oracle.Scene(np.stack([xs * z, np.full(n, 0.1), np.full(n, z)], 1), q, np.tile(np.log([0.01, 0.03, 0.2]), (n, 1)),
+                      np.zeros(n), np.full((n, 3), 0.5))
+    pr = oracle.project(sc, cam, scenes.identity_pose(), oracle.Params(alpha_min=0.0))
+    free = oracle.project(sc, cam, scenes.identity_pose(), oracle.Params(alpha_min=0.0, jac_clip=0.0))
+    np.testing.assert_allclose(pr["mu"][:, 0], 200 * xs + 160, rtol=1e-12)
+    np.testing.assert_allclose(pr["cov2"][:2], free["cov2"][:2], rtol=1e-12)
+    np.testing.assert_allclose(pr["cov2"][1], pr["cov2"][2], rtol=1e-7)
+    for k in (3, 4, 5):
+        np.testing.assert_allclose(pr["cov2"][k], pr["cov2"][2], rtol=1e-12)
+    # unclamped, the footprint of the far mean is stretched many times over
+    assert free["cov2"][5, 0] > 20 * pr["cov2"][5, 0]
+
+
 def test_near_plane_culls():
     sc = oracle.Scene(np.array([[0, 0, 0.15], [0, 0, 1.0]]), np.tile([1.0, 0, 0, 0], (2, 1)),
                       np.full((2, 3), -3.0), np.zeros(2), np.full((2, 3), 0.5))
@@ -238,14 +262,20 @@ def _with(sc, name, i, k, val):
     return oracle.Scene(**arrs)
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
-def test_backward_matches_finite_differences(seed):
+@pytest.mark.parametrize("seed,jac_clip", [(0, 1.3), (1, 1.3), (2, 1.3), (3, 0.35)])
+def test_backward_matches_finite_differences(seed, jac_clip):
     """Hand-derived reverse compositing and chain rule vs central finite differences of
-    F = sum_p w . (C, D, S) with random weights, thresholds off (smooth maps), FP64."""
+    F = sum_p w . (C, D, S) with random weights, thresholds off (smooth maps), FP64.  The
+    last case clamps the Jacobian's tangent for most Gaussians (no gradient through a
+    clamped coordinate, the 1 / z factors still differentiated)."""
     sc, rng = _tiny_scene(seed)
     cam = oracle.camera(40, 40, 11.5, 8.5, 24, 18)
     pose = scenes.perturb_pose(scenes.identity_pose(), rng, 4.0, 0.05)
-    p = _smooth_params(dilation=0.1 * seed)
+    p = _smooth_params(dilation=0.1 * seed, jac_clip=jac_clip)
+    R0, t0 = scenes.pose_rt(pose)
+    xc = sc.means @ R0.T + t0
+    clamped = (np.abs(xc[:, 0] / xc[:, 2]) > jac_clip * 12 / 40) | (np.abs(xc[:, 1] / xc[:, 2]) > jac_clip * 9 / 40)
+    assert clamped.sum() >= (3 if jac_clip < 1 else 0)
     w = rng.normal(size=(5, 18, 24))
     b = oracle.backward(sc, cam, pose, p, w[:3], w[3], w[4])
     g = b["grads"]
