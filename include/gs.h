@@ -99,6 +99,9 @@ typedef struct {
     float t_min;            /* stop before the Gaussian that takes T below t_min (1e-4)*/
     float dilation;         /* eps added to the diagonal of Sigma' in px^2 (0)         */
     float z_near;           /* Gaussians with camera depth <= z_near are dropped (0.2) */
+    float jac_clip;         /* J of Sigma' is taken at the mean's image-plane tangent
+                               clamped to +-jac_clip * (W / 2 fx, H / 2 fy); no gradient
+                               flows through a clamped coordinate; 0 disables (1.3)   */
     float sil_thresh;       /* loss mask: S > sil_thresh and depth > 0 (0.99)          */
     float w_rgb, w_depth, w_vis, w_prior; /* loss weights (0.5, 1, 0.1, 0.5)           */
     double lr_rot, lr_trans;              /* Adam step sizes, rad and m (2e-3, 2e-3)   */

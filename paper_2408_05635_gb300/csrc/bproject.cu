@@ -162,8 +162,13 @@ __global__ void __launch_bounds__(kBlock) k_bproject(BprojLaunch L) {
             for (int c = 0; c < 3; ++c)
                 M[3 * r + c] = sRt[3 * r] * Bm[c] + sRt[3 * r + 1] * Bm[3 + c] + sRt[3 * r + 2] * Bm[6 + c];
         const float iz = 1.f / z, iz2 = iz * iz;
-        const float J00 = vi.fx * iz, J02 = -vi.fx * x * iz2;
-        const float J11 = vi.fy * iz, J12 = -vi.fy * y * iz2;
+        // J as the projection took it: tangent clamped to the view's limits
+        const float txr = x * iz, tyr = y * iz;
+        const float tx = fminf(fmaxf(txr, -vi.tan_lim_x), vi.tan_lim_x);
+        const float ty = fminf(fmaxf(tyr, -vi.tan_lim_y), vi.tan_lim_y);
+        const bool free_x = tx == txr, free_y = ty == tyr;
+        const float J00 = vi.fx * iz, J02 = -vi.fx * tx * iz;
+        const float J11 = vi.fy * iz, J12 = -vi.fy * ty * iz;
         float N0[3], N1[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -196,10 +201,14 @@ __global__ void __launch_bounds__(kBlock) k_bproject(BprojLaunch L) {
         }
         const float dmu_x = gg.g0.x, dmu_y = gg.g0.y, dd = gg.g0.z;
         const float fx = vi.fx, fy = vi.fy;
-        const float dxc0 = dmu_x * J00 - dJ02 * fx * iz2;
-        const float dxc1 = dmu_y * J11 - dJ12 * fy * iz2;
-        const float dxc2 = dmu_x * J02 + dmu_y * J12 + dd - dJ00 * fx * iz2 + dJ02 * 2.f * fx * x * iz2 * iz -
-                           dJ11 * fy * iz2 + dJ12 * 2.f * fy * y * iz2 * iz;
+        // d mu' / d x_c is the unclamped (f / z, -f x / z^2); J02 = -fx t_x / z passes
+        // dJ02/dx = -fx / z^2 and dJ02/dz = fx (t_x + x / z) / z^2 where t_x is free, and
+        // only dJ02/dz = fx t_x / z^2 where it is clamped (J12 likewise)
+        const float dxc0 = dmu_x * J00 - (free_x ? dJ02 * fx * iz2 : 0.f);
+        const float dxc1 = dmu_y * J11 - (free_y ? dJ12 * fy * iz2 : 0.f);
+        const float dxc2 = -(dmu_x * fx * txr + dmu_y * fy * tyr) * iz + dd - dJ00 * fx * iz2 +
+                           dJ02 * fx * iz2 * (tx + (free_x ? txr : 0.f)) - dJ11 * fy * iz2 +
+                           dJ12 * fy * iz2 * (ty + (free_y ? tyr : 0.f));
         if (L.want_pose) {
             // translation, and rotation about the camera centre (mean and covariance parts)
             float P[9];  // dM M^T

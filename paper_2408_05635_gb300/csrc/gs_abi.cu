@@ -199,6 +199,8 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
         vi.tiles_y = (c.height + kTile - 1) / kTile;
         vi.tile_base = (uint32_t)T;
         vi.pix_base = (uint32_t)P;
+        vi.tan_lim_x = jacobian_tangent_limit(ctx->cfg.jac_clip, c.width, c.fx);
+        vi.tan_lim_y = jacobian_tangent_limit(ctx->cfg.jac_clip, c.height, c.fy);
         T += (uint64_t)vi.tiles_x * vi.tiles_y;
         P += (uint64_t)c.width * c.height;
         if (T >= (1ull << 27) || 5 * P >= (1ull << 32))
@@ -340,6 +342,7 @@ void gs_default_config(gs_config *c) {
     c->t_min = 1e-4f;
     c->dilation = 0.0f;
     c->z_near = 0.2f;
+    c->jac_clip = 1.3f;
     c->sil_thresh = 0.99f;
     c->w_rgb = 0.5f;
     c->w_depth = 1.0f;
@@ -375,7 +378,7 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg) {
     if (cfg) c = *cfg;
     if (c.tile_w != kTile || c.tile_h != kTile) return GS_ERR_UNSUPPORTED;
     if (!(c.alpha_min >= 0.f) || !(c.alpha_max > c.alpha_min) || !(c.alpha_max <= 1.f) || !(c.t_min >= 0.f) ||
-        !(c.t_min < 1.f) || !(c.dilation >= 0.f) || !(c.z_near > 0.f) || !(c.lr_rot >= 0) || !(c.lr_trans >= 0) ||
+        !(c.t_min < 1.f) || !(c.dilation >= 0.f) || !(c.z_near > 0.f) || !(c.jac_clip >= 0.f) || !(c.lr_rot >= 0) || !(c.lr_trans >= 0) ||
         !(c.beta1 >= 0 && c.beta1 < 1) || !(c.beta2 >= 0 && c.beta2 < 1) || !(c.eps > 0))
         return GS_ERR_INVALID_ARG;
     gs_ctx *ctx = new (std::nothrow) gs_ctx();

@@ -37,8 +37,14 @@ struct ViewInfo {
     int32_t width, height, tiles_x, tiles_y;
     uint32_t tile_base;  // first global tile index of the view
     uint32_t pix_base;   // first pixel of the view in the concatenated planes
-    uint32_t pad0, pad1;
+    float tan_lim_x, tan_lim_y;  // clamp of the image-plane tangent at which J is taken
 };
+
+// Tangent limit of the EWA Jacobian along one image axis: jac_clip half-extents of the
+// view (the mean's x_c / z beyond it is clamped for J only); infinite when disabled.
+inline float jacobian_tangent_limit(float jac_clip, int32_t extent, double focal) {
+    return jac_clip > 0.f ? (float)((double)jac_clip * 0.5 * (double)extent / focal) : INFINITY;
+}
 static_assert(sizeof(ViewInfo) == 48, "ViewInfo layout");
 
 // Small counters at the start of the workspace (cleared before every projection).

@@ -87,6 +87,8 @@ extern "C" gs_status gs_render_static(const gs_config *cfg, const gs_gaussians *
     vi.height = cam->height;
     vi.tiles_x = (cam->width + kTile - 1) / kTile;
     vi.tiles_y = (cam->height + kTile - 1) / kTile;
+    vi.tan_lim_x = jacobian_tangent_limit(cfg->jac_clip, cam->width, cam->fx);
+    vi.tan_lim_y = jacobian_tangent_limit(cfg->jac_clip, cam->height, cam->fy);
     Dims d{};
     d.n = g->n;
     d.V = 1;

@@ -321,8 +321,11 @@ __global__ void __launch_bounds__(kBlock, 5) k_project(ProjectLaunch L) {
                 M[3 * r + 2] = (sRt[3 * r] * Rg[2] + sRt[3 * r + 1] * Rg[5] + sRt[3 * r + 2] * Rg[8]) * s2;
             }
             const float iz = __fdividef(1.f, z);
-            const float J00 = vi.fx * iz, J02 = -vi.fx * x * iz * iz;
-            const float J11 = vi.fy * iz, J12 = -vi.fy * y * iz * iz;
+            // J at the mean's image-plane tangent, clamped to the view's limits
+            const float tx = fminf(fmaxf(x * iz, -vi.tan_lim_x), vi.tan_lim_x);
+            const float ty = fminf(fmaxf(y * iz, -vi.tan_lim_y), vi.tan_lim_y);
+            const float J00 = vi.fx * iz, J02 = -vi.fx * tx * iz;
+            const float J11 = vi.fy * iz, J12 = -vi.fy * ty * iz;
             // N = J M, Sigma' = N N^T + dilation I
             float N0[3], N1[3];
 #pragma unroll

@@ -55,7 +55,7 @@ class gs_targets(ctypes.Structure):
 
 class gs_config(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32)] + [
-        (n, c_float) for n in ("alpha_min", "alpha_max", "t_min", "dilation", "z_near", "sil_thresh",
+        (n, c_float) for n in ("alpha_min", "alpha_max", "t_min", "dilation", "z_near", "jac_clip", "sil_thresh",
                                "w_rgb", "w_depth", "w_vis", "w_prior")] + [
         (n, c_double) for n in ("lr_rot", "lr_trans", "beta1", "beta2", "eps")]
 
@@ -262,6 +262,7 @@ class Config:
     t_min: float = 1e-4
     dilation: float = 0.0
     z_near: float = 0.2
+    jac_clip: float = 1.3
     sil_thresh: float = 0.99
     w_rgb: float = 0.5
     w_depth: float = 1.0
