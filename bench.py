@@ -53,6 +53,8 @@ def _args():
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--batched-steps", type=int, default=10,
                     help="timed steps of the batched BF16 hypothesis leg (0 skips it)")
+    ap.add_argument("--mapping-steps", type=int, default=5,
+                    help="timed windows of the mapping leg (0 skips it)")
     return ap.parse_args()
 
 
@@ -89,6 +91,72 @@ def batched_workload(seed: int = 0):
         rgb, depth = scenes.raycast_room(gts[f], frame_cams[f], seed=seed)
         frames.append((rgb, depth, scenes.prior_from_depth(depth, rng, 0.02, 0.05)))
     return g, cams, poses, frame_of, frames
+
+
+N_MAP_GAUSS = 1_000_000
+MAP_VIEWS = 8
+
+
+def mapping_workload(seed: int = 0):
+    """A mapping window (Sec. III-C: keyframe poses fixed, Gaussians optimised): 8 keyframes
+    of 1200 x 680 on a circle around the room centre, 45 deg of yaw apart, over a 1M-Gaussian
+    room; RGB-D targets ray-cast from the keyframe poses, depth priors (x (1 + N(0, 0.03)),
+    8% holes)."""
+    from paper_2408_05635_gb300 import scenes
+    g = scenes.room_scene(N_MAP_GAUSS, seed=seed)
+    poses = np.asarray(scenes.mapping_keyframes(MAP_VIEWS))
+    cams = [scenes.WIDE_CAM] * MAP_VIEWS
+    rng = np.random.default_rng(seed + 3)
+    frames = []
+    for v in range(MAP_VIEWS):
+        rgb, depth = scenes.raycast_room(poses[v], cams[v], seed=seed)
+        frames.append((rgb, depth, scenes.prior_from_depth(depth, rng, 0.03, 0.08)))
+    return g, cams, poses, frames
+
+
+def run_mapping(a, dev, stream):
+    """Map-gradient windows: the combined loss of every keyframe of the window rendered and
+    differentiated to all 14 parameters of every Gaussian, `chunk` views per call through
+    one workspace (a larger chunk fills the GPU better, a smaller one needs less memory)."""
+    import torch
+    from paper_2408_05635_gb300 import gs
+    g, cams, poses_np, frames = mapping_workload()
+    poses = torch.tensor(poses_np, dtype=torch.float64, device=dev)
+    targets = [tuple(torch.from_numpy(x).to(dev) for x in f) for f in frames]
+    gt = gs.GaussianTensors.from_numpy(g, device=dev)
+    P = sum(c.width * c.height for c in cams)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    res, loss_v = {}, None
+    for chunk in (1, 2, 4, 8):
+        R = gs.Rasterizer(gs.Config(), device=dev)
+        probs = [R.plan(gt, cams[v0:v0 + chunk], poses[v0:v0 + chunk].contiguous(), margin=1.25)
+                 for v0 in range(0, MAP_VIEWS, chunk)]
+        ws_bytes = max(gs.gs_workspace_size(R.ctx, pr) for pr in probs)
+        grads = None
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                out = R.mapping_grads(gt, cams, poses, targets, chunk=chunk, probs=probs, stream=stream)
+                grads = out["grads"]
+            torch.cuda.synchronize(dev)
+            ev[0].record(stream)
+            for _ in range(a.mapping_steps):
+                for t in grads.values():
+                    t.zero_()
+                out = R.mapping_grads(gt, cams, poses, targets, chunk=chunk, grads=grads, probs=probs, stream=stream)
+            ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        R.sync(stream)
+        ms = ev[0].elapsed_time(ev[1]) / a.mapping_steps
+        res[chunk] = {"ms_per_window": round(ms, 3), "mpix_per_s": round(P / ms / 1e3, 1),
+                      "workspace_gb": round(ws_bytes / 1e9, 2)}
+        loss_v = out["loss"].cpu().numpy()
+        R.close()
+    best = min(res, key=lambda c: res[c]["ms_per_window"])
+    return {"workload": f"{MAP_VIEWS} keyframes 1200x680, {N_MAP_GAUSS // 1000}k room Gaussians, fp32, "
+                        "gradients of all 14 parameters",
+            "pixels_per_window": P, "chunks": {str(c): v for c, v in res.items()}, "best_chunk": best,
+            "loss_per_view": [round(float(x), 5) for x in loss_v],
+            "l2": "working set far above L2 (no flush)"}
 
 
 def run_batched(a, dev, stream):
@@ -497,6 +565,8 @@ def main():
         }
         if world == 1 and a.batched_steps > 0:
             line["batched"] = run_batched(a, dev, stream)
+        if world == 1 and a.mapping_steps > 0:
+            line["mapping"] = run_mapping(a, dev, stream)
         if world == 1 and not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, cam, start, rgb, depth, prior, a.cpu_sample_seconds)
         print(json.dumps(line), flush=True)
