@@ -423,10 +423,13 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
                             sqrt(gx * gx + gy * gy) * pr->dmu;
         const double margin = fmax(p->amb_alpha, dexp);
         /* skipping or keeping an alpha ~ alpha_min Gaussian moves the pixel by at most about
-         * 2 alpha_min T max(1, z): only a decision that can matter is ambiguous */
-        if (araw > 0.0 && fabs(log(araw / p->alpha_min)) <= margin &&
-            2.0 * p->alpha_min * T * fmax(1.0, fabs(pr->xc[2])) > p->amb_effect)
-            a = 1;
+         * 2 alpha_min T max(1, z): only a decision that can matter is ambiguous.  Either way
+         * it scales the transmittance of everything behind by 1 - alpha, which an FP32
+         * renderer may therefore hold off by alpha / (1 - alpha): a later t_min decision
+         * inherits that uncertainty. */
+        const int near_min = araw > 0.0 && fabs(log(araw / p->alpha_min)) <= margin;
+        if (near_min && 2.0 * p->alpha_min * T * fmax(1.0, fabs(pr->xc[2])) > p->amb_effect) a = 1;
+        if (near_min) eT += araw / (1.0 - araw);
         if (araw < p->alpha_min) continue;
         const int clamped = araw >= p->alpha_max;
         const double alpha = clamped ? p->alpha_max : araw;
