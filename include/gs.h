@@ -251,6 +251,91 @@ gs_status gs_set_profiling_mask(gs_ctx *ctx, uint32_t mask);
  * number available.  Errors: STATE (profiling off or nothing recorded), CUDA. */
 gs_status gs_kernel_times(gs_ctx *ctx, gs_kernel_time *out, int32_t cap, int32_t *count);
 
+/* ------------------------------------------------------------------ scene optimisation */
+
+/* The map as the scene optimisation holds it (Sec. III-C).  Device arrays with room for
+ * `capacity` Gaussians, of which the first n are live; n is a device int64 that the calls
+ * below read and update, so a sequence of them needs no host synchronisation.
+ *   means, quats, log_scales, opacity_logits, rgb: FP32, the shapes of gs_gaussians, the
+ *     optimiser's master copy (a render reads them as a gs_gaussians with GS_F32);
+ *   lowp_*: NULL, or a copy of the four attribute arrays in lowp_dtype (GS_BF16 or
+ *     GS_F16, rounded to nearest) that every call below refreshes where it changes the
+ *     FP32 values, for renders with that dtype (they share the FP32 means);
+ *   adam_state: NULL, or the Adam moments, 28 x capacity FP32: the first moments of the
+ *     groups means (3 capacity floats), quats (4), log_scales (3), opacity_logits (1),
+ *     rgb (3), then the second moments in the same layout; a Gaussian's entries are the
+ *     rows of its index in each group.
+ * Every pointer must be 16-byte aligned and capacity a multiple of 4. */
+typedef struct {
+    float *means;
+    float *quats;
+    float *log_scales;
+    float *opacity_logits;
+    float *rgb;
+    void *lowp_quats;
+    void *lowp_log_scales;
+    void *lowp_opacity_logits;
+    void *lowp_rgb;
+    int32_t lowp_dtype; /* gs_dtype of the lowp arrays (ignored when they are NULL) */
+    int32_t reserved;
+    int64_t capacity;
+    float *adam_state;
+} gs_map;
+
+/* Settings of the scene optimisation.  The paper gives none; gs_default_map_config fills
+ * the readings beside each field. */
+typedef struct {
+    double lr_means, lr_quats, lr_log_scales, lr_opacity_logits, lr_rgb; /* Adam step sizes per
+                                  group (1e-4, 1e-3, 1e-3, 5e-2, 2.5e-3)                    */
+    double beta1, beta2, eps;  /* Adam moments and denominator guard (0.9, 0.999, 1e-15)    */
+    float sil_add;             /* a keyframe pixel gets a Gaussian where S < sil_add (0.5)  */
+    float opacity_min;         /* gs_map_prune drops Gaussians with opacity < this (0.005)  */
+} gs_map_config;
+
+void gs_default_map_config(gs_map_config *cfg);
+
+/* Device scratch, in bytes, that gs_map_add (items = the view's pixels) and gs_map_prune
+ * (items = the source map's capacity) need. */
+size_t gs_map_scratch_bytes(int64_t items);
+
+/* New Gaussians from one RGB-D observation: every Gaussian of the first frame (Sec. III-A)
+ * and, on a keyframe, the pixels its silhouette shows as new observations (Sec. III-C; the
+ * silhouette is the mask of where Gaussians are added, Sec. V).  A pixel with depth d > 0
+ * (and S < sil_add when sil is given) becomes a Gaussian centred on its sample point
+ * (u, v) unprojected with d through the pose, with its colour, opacity 0.5 (logit 0), the
+ * identity rotation and the isotropic scale d / f, f = (fx + fy) / 2 (one pixel wide in
+ * the image).  They are appended after the live Gaussians in row-major pixel order; their
+ * Adam moments are zeroed.
+ *   cam: host; pose: device, 7 doubles (world->camera); rgb, depth: device planes of the
+ *   view; sil: device plane or NULL (every pixel with depth); n: device int64, the live
+ *   count, updated; scratch: device, gs_map_scratch_bytes(W H) bytes, 256-byte aligned;
+ *   err_flags: device uint32 or NULL, bit 0 set when the map was full (the Gaussians
+ *   that fit were added, n = capacity).
+ * Errors: INVALID_ARG (NULL or misaligned pointer, bad camera, scratch too small), CUDA. */
+gs_status gs_map_add(const gs_map_config *cfg, const gs_map *map, int64_t *n, const gs_camera *cam,
+                     const double *pose, const float *rgb, const float *depth, const float *sil, void *scratch,
+                     size_t scratch_bytes, uint32_t *err_flags, void *stream);
+
+/* One Adam step on every parameter of the live Gaussians, keyframe poses fixed
+ * (Sec. III-C): per group, m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), in FP32.
+ *   grads: the gradients of the loss summed over the window (gs_backward's), FP32 device
+ *   arrays of capacity rows (rows >= n are not read); map->adam_state is required;
+ *   n: device int64 live count; step: t >= 1.
+ * Errors: INVALID_ARG, CUDA. */
+gs_status gs_map_adam_step(const gs_map_config *cfg, const gs_map *map, const int64_t *n,
+                           const gs_gaussians_grad *grads, int64_t step, void *stream);
+
+/* Duplicate removal (Sec. III-C): the live Gaussians of src whose opacity is at least
+ * opacity_min (decided on the FP32 logit against logit(opacity_min) rounded to FP32) are
+ * copied, in order, to dst with their Adam moments and lowp copies (each moved only where
+ * both maps have them); n_dst receives their count.  src and dst must not overlap and
+ * dst->capacity must be at least src->capacity.
+ *   n_src, n_dst: device int64; scratch: device, gs_map_scratch_bytes(src->capacity).
+ * Errors: INVALID_ARG, CUDA. */
+gs_status gs_map_prune(const gs_map_config *cfg, const gs_map *src, const int64_t *n_src, const gs_map *dst,
+                       int64_t *n_dst, void *scratch, size_t scratch_bytes, void *stream);
+
 /* ------------------------------------------------------------------ no-allocation render */
 
 /* Limits of gs_render_static. */

@@ -60,6 +60,17 @@ class gs_config(ctypes.Structure):
         (n, c_double) for n in ("lr_rot", "lr_trans", "beta1", "beta2", "eps")]
 
 
+class gs_map(ctypes.Structure):
+    _fields_ = [(n, c_void_p) for n in ("means", "quats", "log_scales", "opacity_logits", "rgb", "lowp_quats",
+                                         "lowp_log_scales", "lowp_opacity_logits", "lowp_rgb")] + [
+        ("lowp_dtype", c_int32), ("reserved", c_int32), ("capacity", c_int64), ("adam_state", c_void_p)]
+
+
+class gs_map_config(ctypes.Structure):
+    _fields_ = [(n, c_double) for n in ("lr_means", "lr_quats", "lr_log_scales", "lr_opacity_logits", "lr_rgb",
+                                        "beta1", "beta2", "eps")] + [("sil_add", c_float), ("opacity_min", c_float)]
+
+
 class gs_problem(ctypes.Structure):
     _fields_ = [("n_gaussians", c_int64), ("n_views", c_int32), ("reserved", c_int32),
                 ("cameras", ctypes.POINTER(gs_camera)), ("pair_capacity", c_int64),
@@ -118,6 +129,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "gs_render_static": (c_int32, [P(gs_config), P(gs_gaussians), P(gs_camera), c_void_p, P(gs_targets),
                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
             "gs_kernel_times": (c_int32, [c_void_p, P(gs_kernel_time), c_int32, P(c_int32)]),
+            "gs_default_map_config": (None, [P(gs_map_config)]),
+            "gs_map_scratch_bytes": (c_size_t, [c_int64]),
+            "gs_map_add": (c_int32, [P(gs_map_config), P(gs_map), c_void_p, P(gs_camera), c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_size_t, c_void_p, c_void_p]),
+            "gs_map_adam_step": (c_int32, [P(gs_map_config), P(gs_map), c_void_p, P(gs_gaussians_grad), c_int64,
+                                           c_void_p]),
+            "gs_map_prune": (c_int32, [P(gs_map_config), P(gs_map), c_void_p, P(gs_map), c_void_p, c_void_p,
+                                       c_size_t, c_void_p]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -318,6 +337,121 @@ class GaussianTensors:
             return torch.as_tensor(a, dtype=torch.float32).to(device=device, dtype=dt).contiguous()
         return GaussianTensors(t(g.means, torch.float32), t(g.quats, attr_dtype), t(g.log_scales, attr_dtype),
                                t(g.logits, attr_dtype), t(g.rgb, attr_dtype))
+
+
+def gs_default_map_config() -> gs_map_config:
+    c = gs_map_config()
+    load().gs_default_map_config(ctypes.byref(c))
+    return c
+
+
+def gs_map_scratch_bytes(items: int) -> int:
+    return int(load().gs_map_scratch_bytes(int(items)))
+
+
+def _map_check(st, what):
+    if st:
+        raise GsError(st, what)
+
+
+def gs_map_add(cfg: gs_map_config, m: gs_map, n: torch.Tensor, cam, pose: torch.Tensor, rgb, depth, sil, scratch,
+               scratch_bytes: int, err=None, stream=None) -> None:
+    _map_check(load().gs_map_add(ctypes.byref(cfg), ctypes.byref(m), _ptr(n), ctypes.byref(cam), _ptr(pose), _ptr(rgb),
+                                 _ptr(depth), _ptr(sil), _ptr(scratch), scratch_bytes, _ptr(err), _stream(stream)),
+               "gs_map_add")
+
+
+def gs_map_adam_step(cfg: gs_map_config, m: gs_map, n: torch.Tensor, grads: gs_gaussians_grad, step: int,
+                     stream=None) -> None:
+    _map_check(load().gs_map_adam_step(ctypes.byref(cfg), ctypes.byref(m), _ptr(n), ctypes.byref(grads), int(step),
+                                       _stream(stream)), "gs_map_adam_step")
+
+
+def gs_map_prune(cfg: gs_map_config, src: gs_map, n_src: torch.Tensor, dst: gs_map, n_dst: torch.Tensor, scratch,
+                 scratch_bytes: int, stream=None) -> None:
+    _map_check(load().gs_map_prune(ctypes.byref(cfg), ctypes.byref(src), _ptr(n_src), ctypes.byref(dst), _ptr(n_dst),
+                                   _ptr(scratch), scratch_bytes, _stream(stream)), "gs_map_prune")
+
+
+class Map:
+    """The map as the scene optimisation holds it (gs_map): FP32 master arrays with room
+    for `capacity` Gaussians (rounded up to a multiple of 4), the live count on the device,
+    the Adam moments and, with lowp_dtype, a BF16 / F16 render copy of the attributes."""
+
+    GROUPS = ("means", "quats", "log_scales", "logits", "rgb")
+    WIDTH = {"means": 3, "quats": 4, "log_scales": 3, "logits": 1, "rgb": 3}
+
+    def __init__(self, capacity: int, device="cuda", lowp_dtype: torch.dtype | None = None, adam: bool = True,
+                 config: gs_map_config | None = None):
+        load()
+        cap = (int(capacity) + 3) // 4 * 4
+        self.capacity, self.device = cap, torch.device(device)
+        self.p = {k: torch.zeros((cap, self.WIDTH[k]) if k != "logits" else (cap,), dtype=torch.float32, device=device)
+                  for k in self.GROUPS}
+        self.lowp_dtype = lowp_dtype
+        self.lp = None if lowp_dtype is None else {
+            k: torch.zeros_like(self.p[k], dtype=lowp_dtype) for k in self.GROUPS[1:]}
+        self.state = torch.zeros(28 * cap, dtype=torch.float32, device=device) if adam else None
+        self.count = torch.zeros(1, dtype=torch.int64, device=device)
+        self.err = torch.zeros(1, dtype=torch.int32, device=device)
+        self.config = config or gs_default_map_config()
+        self._scratch = None
+
+    def c(self) -> gs_map:
+        lp = self.lp or {}
+        return gs_map(_ptr(self.p["means"]), _ptr(self.p["quats"]), _ptr(self.p["log_scales"]), _ptr(self.p["logits"]),
+                      _ptr(self.p["rgb"]), _ptr(lp.get("quats")), _ptr(lp.get("log_scales")), _ptr(lp.get("logits")),
+                      _ptr(lp.get("rgb")), _DT.get(self.lowp_dtype, 0), 0, self.capacity, _ptr(self.state))
+
+    @property
+    def n(self) -> int:
+        """Live count (synchronises with the device)."""
+        return int(self.count.item())
+
+    def scratch(self, items: int) -> tuple[torch.Tensor, int]:
+        need = gs_map_scratch_bytes(items)
+        if self._scratch is None or self._scratch.numel() < need + 256:
+            self._scratch = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
+        off = (-self._scratch.data_ptr()) % 256
+        return self._scratch[off:off + need], need
+
+    def gaussians(self, n: int | None = None, lowp: bool = False) -> GaussianTensors:
+        """The first n live Gaussians as a render input (FP32, or the low-precision copy)."""
+        n = self.n if n is None else n
+        src = self.lp if lowp else self.p
+        return GaussianTensors(self.p["means"][:n], src["quats"][:n], src["log_scales"][:n], src["logits"][:n],
+                               src["rgb"][:n])
+
+    def load(self, g) -> None:
+        """Fill the map with arrays (numpy or tensors, rows = Gaussians); moments zeroed."""
+        n = len(g.means)
+        if n > self.capacity:
+            raise ValueError("more Gaussians than capacity")
+        for k in self.GROUPS:
+            self.p[k][:n] = torch.as_tensor(getattr(g, k), dtype=torch.float32, device=self.device).reshape(
+                self.p[k][:n].shape)
+            if self.lp is not None and k != "means":
+                self.lp[k][:n] = self.p[k][:n].to(self.lowp_dtype)
+        if self.state is not None:
+            self.state.zero_()
+        self.count.fill_(n)
+
+    def add_from_frame(self, cam, pose: torch.Tensor, rgb, depth, sil=None, stream=None) -> None:
+        """gs_map_add: Gaussians for the frame's pixels with depth (and S < sil_add)."""
+        cc = gs_camera(float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy), int(cam.width), int(cam.height))
+        scr, nb = self.scratch(int(cam.width) * int(cam.height))
+        gs_map_add(self.config, self.c(), self.count, cc, pose, rgb, depth, sil, scr, nb, self.err, stream)
+
+    def adam_step(self, grads: dict, step: int, stream=None) -> None:
+        """gs_map_adam_step with gradient tensors of capacity rows (keys of GROUPS)."""
+        G = gs_gaussians_grad(_ptr(grads.get("means")), _ptr(grads.get("quats")), _ptr(grads.get("log_scales")),
+                              _ptr(grads.get("logits")), _ptr(grads.get("rgb")))
+        gs_map_adam_step(self.config, self.c(), self.count, G, step, stream)
+
+    def prune_into(self, dst: "Map", stream=None) -> None:
+        """gs_map_prune: the Gaussians of this map with opacity >= opacity_min, into dst."""
+        scr, nb = self.scratch(self.capacity)
+        gs_map_prune(self.config, self.c(), self.count, dst.c(), dst.count, scr, nb, stream)
 
 
 def cameras_c(cams: Sequence) -> ctypes.Array:
