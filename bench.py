@@ -55,6 +55,8 @@ def _args():
                     help="timed steps of the batched BF16 hypothesis leg (0 skips it)")
     ap.add_argument("--mapping-steps", type=int, default=5,
                     help="timed windows of the mapping leg (0 skips it)")
+    ap.add_argument("--sequence-frames", type=int, default=200,
+                    help="frames of the long-sequence leg (0 skips it)")
     return ap.parse_args()
 
 
@@ -157,6 +159,96 @@ def run_mapping(a, dev, stream):
             "pixels_per_window": P, "chunks": {str(c): v for c, v in res.items()}, "best_chunk": best,
             "loss_per_view": [round(float(x), 5) for x in loss_v],
             "l2": "working set far above L2 (no flush)"}
+
+
+N_SEQ_GAUSS = 2_000_000
+
+
+def sequence_workload(dev, n_frames: int, seed: int = 0):
+    """The long sequence: 640 x 480 frames along a closed spline around the room (1.8 deg
+    and 4 cm per frame on average), each an RGB-D frame ray-cast from the true pose (on the
+    GPU) with a depth prior (x (1 + N(0, 0.02)), 5% holes); the 2M-Gaussian room as the
+    fixed map for the tracking-only run, with FP16 attributes."""
+    import torch
+    from paper_2408_05635_gb300 import scenes
+    g = scenes.room_scene(N_SEQ_GAUSS, seed=seed)
+    cam = scenes.TUM_CAM
+    poses = scenes.spline_trajectory(n_frames, seed=seed)
+    gen = torch.Generator(device=dev).manual_seed(seed + 5)
+    frames = []
+    for p in poses:
+        rgb, depth = scenes.raycast_room_torch(p, cam, seed=seed, device=dev)
+        noise = torch.randn(depth.shape, generator=gen, device=dev) * 0.02
+        holes = torch.rand(depth.shape, generator=gen, device=dev) < 0.05
+        prior = torch.where(holes, torch.zeros_like(depth), depth * (1 + noise))
+        frames.append((rgb, depth, prior))
+    return g, cam, poses, frames
+
+
+def _trajectory_report(est, gt):
+    from paper_2408_05635_gb300 import scenes, slam
+    ce, cg = slam.camera_centres(est), slam.camera_centres(gt)
+    d = np.linalg.norm(ce - cg, axis=1)
+    ang = []
+    for a, b in zip(est, gt):
+        Ra, Rb = scenes.pose_rt(a)[0], scenes.pose_rt(b)[0]
+        ang.append(np.degrees(np.arccos(np.clip((np.trace(Ra @ Rb.T) - 1) / 2, -1, 1))))
+    return {"ate_rmse_cm": round(100 * float(np.sqrt(np.mean(d * d))), 3), "max_trans_err_cm": round(100 * float(d.max()), 3),
+            "final_trans_err_cm": round(100 * float(d[-1]), 3), "max_rot_err_deg": round(float(np.max(ang)), 4)}
+
+
+def run_sequence(a, dev, stream):
+    """Tracking over a long sequence: on the fixed true map (every frame started from the
+    previous estimate, 100 iterations in one graph launch), and the whole loop from an
+    empty map (first-frame Gaussians, tracking, keyframe additions, window optimisation
+    and removal)."""
+    import time
+    import torch
+    from paper_2408_05635_gb300 import gs, slam
+    g, cam, gt_poses, frames = sequence_workload(dev, a.sequence_frames)
+    F = len(gt_poses)
+    P = cam.width * cam.height
+    out = {"workload": f"{F} frames 640x480 along a spline around the room, 100 tracking iterations per frame"}
+    # (1) tracking on the fixed 2M-Gaussian map, FP16 attributes
+    gt = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=torch.float16)
+    tr = slam.Tracker(cam, 100, device=dev)
+    pose = torch.tensor(gt_poses[0], dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        tr.track(gt, pose, *frames[1], stream=stream)  # plan and capture
+        torch.cuda.synchronize(dev)
+        est = [pose.clone()]
+        t0 = time.perf_counter()
+        for k in range(1, F):
+            pose = tr.track(gt, est[-1], *frames[k], stream=stream)
+            est.append(pose)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    tr.close()
+    rep = _trajectory_report(torch.stack(est).cpu().numpy(), gt_poses)
+    out["tracking_fixed_map"] = {"map": f"{N_SEQ_GAUSS // 1000}k room Gaussians, fp16 attributes",
+                                 "ms_per_frame": round(1e3 * wall / (F - 1), 3),
+                                 "tracking_iters_per_s": round(100 * (F - 1) / wall, 1),
+                                 "mpix_per_s": round(100 * (F - 1) * P / wall / 1e6, 1), "replans": tr.replans, **rep}
+    del gt
+    # (2) the whole loop from an empty map
+    cfg = slam.SlamConfig(lowp=torch.float16)
+    S = slam.Slam(cam, cfg, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(F):
+            S.process(k, *frames[k], first_pose=gt_poses[0] if k == 0 else None, stream=stream)
+        torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    rep = _trajectory_report(torch.stack(S.poses).cpu().numpy(), gt_poses)
+    q = S.evaluate(frames, stream)
+    out["slam_from_empty_map"] = {"ms_per_frame": round(1e3 * wall / F, 3), "frames_per_s": round(F / wall, 2),
+                                  "keyframes": S.stats["keyframes"], "map_iters_per_keyframe": cfg.map_iters, "first_frame_map_iters": cfg.first_map_iters,
+                                  "window": cfg.window, "final_map_gaussians": S.n,
+                                  "added_total": int(sum(S.stats["added"])), "pruned_total": int(sum(S.stats["pruned"])),
+                                  "replans": S.tracker.replans, **rep, **{k: round(v, 3) for k, v in q.items()}}
+    S.close()
+    return out
 
 
 def run_batched(a, dev, stream):
@@ -567,6 +659,8 @@ def main():
             line["batched"] = run_batched(a, dev, stream)
         if world == 1 and a.mapping_steps > 0:
             line["mapping"] = run_mapping(a, dev, stream)
+        if world == 1 and a.sequence_frames > 0:
+            line["sequence"] = run_sequence(a, dev, stream)
         if world == 1 and not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, cam, start, rgb, depth, prior, a.cpu_sample_seconds)
         print(json.dumps(line), flush=True)

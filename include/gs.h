@@ -336,6 +336,15 @@ gs_status gs_map_adam_step(const gs_map_config *cfg, const gs_map *map, const in
 gs_status gs_map_prune(const gs_map_config *cfg, const gs_map *src, const int64_t *n_src, const gs_map *dst,
                        int64_t *n_dst, void *scratch, size_t scratch_bytes, void *stream);
 
+/* Image-quality sums of one rendered view against its observation, behind the evaluation
+ * of Sec. IV (PSNR of the colour, the average depth error).  rgb / depth: the render,
+ * rgb_t / depth_t: the observation, planar FP32 device arrays of `pixels` pixels; out:
+ * device, 4 doubles = (sum of squared colour errors over every pixel and channel,
+ * sum |D - D*| over the pixels with D* > 0, their count, sum (D - D*)^2 over them),
+ * accumulated in FP64 in a fixed order.  Errors: INVALID_ARG, CUDA. */
+gs_status gs_image_metrics(const float *rgb, const float *depth, const float *rgb_t, const float *depth_t,
+                           int64_t pixels, double *out, void *stream);
+
 /* ------------------------------------------------------------------ no-allocation render */
 
 /* Limits of gs_render_static. */

@@ -129,6 +129,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "gs_render_static": (c_int32, [P(gs_config), P(gs_gaussians), P(gs_camera), c_void_p, P(gs_targets),
                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
             "gs_kernel_times": (c_int32, [c_void_p, P(gs_kernel_time), c_int32, P(c_int32)]),
+            "gs_image_metrics": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
             "gs_default_map_config": (None, [P(gs_map_config)]),
             "gs_map_scratch_bytes": (c_size_t, [c_int64]),
             "gs_map_add": (c_int32, [P(gs_map_config), P(gs_map), c_void_p, P(gs_camera), c_void_p, c_void_p,
@@ -337,6 +338,13 @@ class GaussianTensors:
             return torch.as_tensor(a, dtype=torch.float32).to(device=device, dtype=dt).contiguous()
         return GaussianTensors(t(g.means, torch.float32), t(g.quats, attr_dtype), t(g.log_scales, attr_dtype),
                                t(g.logits, attr_dtype), t(g.rgb, attr_dtype))
+
+
+def gs_image_metrics(rgb, depth, rgb_t, depth_t, out: torch.Tensor, stream=None) -> None:
+    """out (device, 4 doubles) <- (sum sq. colour error, sum |D - D*| where D* > 0, that
+    pixel count, sum (D - D*)^2 there)."""
+    _map_check(load().gs_image_metrics(_ptr(rgb), _ptr(depth), _ptr(rgb_t), _ptr(depth_t), int(depth.numel()), _ptr(out),
+                                       _stream(stream)), "gs_image_metrics")
 
 
 def gs_default_map_config() -> gs_map_config:

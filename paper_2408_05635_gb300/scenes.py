@@ -12,7 +12,9 @@ frames); that dataset is not available here, so these scenes stand in for it:
   batched-hypothesis and long-sequence cases).
 * ``raycast_room``: an RGB-D "sensor" frame of the same room, made by intersecting
   pixel rays with the room's rectangles (plain geometry, not splatting). The benchmark
-  uses it as its target frame.
+  uses it as its target frame; ``raycast_room_torch`` is the same in torch, for the
+  long sequence's 200 frames on the GPU.
+* ``spline_trajectory``: the long sequence's camera path around the room.
 
 All floating-point attributes are returned as float32. That is what the GPU consumes;
 the oracle receives the same values widened to float64.  Quaternions are (w, x, y, z);
@@ -239,6 +241,38 @@ def raycast_room(pose, cam: Cam, seed: int = 0) -> tuple[np.ndarray, np.ndarray]
     return rgb.astype(np.float32), depth.reshape(H, W).astype(np.float32)
 
 
+def raycast_room_torch(pose, cam: Cam, seed: int = 0, device="cpu"):
+    """raycast_room in float64 torch on `device` (a GPU makes a long sequence's frames in
+    milliseconds each): the same rays, rectangles and texture; returns float32 tensors
+    rgb (3 x H x W) and depth (H x W)."""
+    import torch
+    f64 = dict(dtype=torch.float64, device=device)
+    R, t = pose_rt(pose)
+    H, W = cam.height, cam.width
+    v, u = torch.meshgrid(torch.arange(H, **f64), torch.arange(W, **f64), indexing="ij")
+    dc = torch.stack([(u - cam.cx) / cam.fx, (v - cam.cy) / cam.fy, torch.ones_like(u)], -1).reshape(-1, 3)
+    Rt = torch.as_tensor(R, **f64)
+    dw = dc @ Rt
+    ow = -Rt.T @ torch.as_tensor(t, **f64)
+    best = torch.full((dw.shape[0],), float("inf"), **f64)
+    col = torch.zeros(dw.shape[0], 3, **f64)
+    for r in room_rects(seed):
+        nrm, org = torch.as_tensor(r.normal, **f64), torch.as_tensor(r.origin, **f64)
+        ru, rv = torch.as_tensor(r.u, **f64), torch.as_tensor(r.v, **f64)
+        den = dw @ nrm
+        s = ((org - ow) @ nrm) / den
+        hit = ow[None, :] + s[:, None] * dw - org
+        aa, bb = hit @ ru, hit @ rv
+        ok = (den.abs() > 1e-12) & (s > 1e-6) & (aa >= 0) & (aa <= r.su) & (bb >= 0) & (bb <= r.sv) & (s < best)
+        best = torch.where(ok, s, best)
+        sn = 0.15 * torch.sin(2.0 * np.pi * aa / 1.7 + r.phase) * torch.sin(2.0 * np.pi * bb / 1.3 + 0.5 * r.phase)
+        chk = torch.remainder(torch.floor(aa / 0.5) + torch.floor(bb / 0.5), 2) * 0.12 - 0.06
+        c = (torch.as_tensor(r.base, **f64)[None, :] + (sn + chk)[:, None]).clamp(0.0, 1.0)
+        col = torch.where(ok[:, None], c, col)
+    depth = torch.where(torch.isfinite(best), best, torch.zeros_like(best))
+    return col.T.reshape(3, H, W).float().contiguous(), depth.reshape(H, W).float().contiguous()
+
+
 def prior_from_depth(depth: np.ndarray, rng: np.random.Generator, sigma: float, hole_frac: float) -> np.ndarray:
     """Depth prior = depth x (1 + N(0, sigma)) with a random `hole_frac` of pixels set to 0."""
     noise = rng.normal(0.0, sigma, size=depth.shape)
@@ -273,13 +307,16 @@ def mapping_keyframes(n_views: int = 8) -> list:
 
 def spline_trajectory(n_frames: int, seed: int = 0, n_ctrl: int = 8) -> list:
     """Camera poses along a closed Catmull-Rom spline through `n_ctrl` seeded control
-    points at least 0.5 m from every wall, each looking along the direction of travel
-    tilted toward the room centre."""
+    points that loop once around the room centre (ordered by azimuth, radius 0.7-1.5 m,
+    height 0.9-2.1 m, so at least 0.5 m from every wall), each camera looking outward from
+    the centre, nearly level: the heading turns about 360 / n_frames degrees per frame."""
     rng = np.random.default_rng(seed + 104729)
     X, Y, Z = ROOM
-    ctrl = np.stack([rng.uniform(0.5, X - 0.5, n_ctrl), rng.uniform(0.8, Y - 0.8, n_ctrl),
-                     rng.uniform(0.5, Z - 0.5, n_ctrl)], axis=1)
-    centre = np.array([X / 2, 1.2, Z / 2])
+    centre = np.array([X / 2, 1.5, Z / 2])
+    az = np.sort(rng.uniform(0.0, 2 * np.pi, n_ctrl))
+    az = (az + np.linspace(0.0, 2 * np.pi, n_ctrl, endpoint=False)) / 2.0  # spread the azimuths
+    rad = rng.uniform(0.7, 1.5, n_ctrl)
+    ctrl = np.stack([centre[0] + rad * np.sin(az), rng.uniform(0.9, 2.1, n_ctrl), centre[2] + rad * np.cos(az)], 1)
     poses = []
     for f in range(n_frames):
         s = f * n_ctrl / n_frames
@@ -288,8 +325,8 @@ def spline_trajectory(n_frames: int, seed: int = 0, n_ctrl: int = 8) -> list:
         p0, p1, p2, p3 = (ctrl[(i + k - 1) % n_ctrl] for k in range(4))
         pos = 0.5 * ((2 * p1) + (-p0 + p2) * u + (2 * p0 - 5 * p1 + 4 * p2 - p3) * u * u
                      + (-p0 + 3 * p1 - 3 * p2 + p3) * u ** 3)
-        look = centre - pos
-        look[1] *= 0.3
+        look = pos - centre
+        look[1] *= 0.2
         poses.append(look_at(pos, look))
     return poses
 

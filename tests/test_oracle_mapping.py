@@ -134,3 +134,44 @@ def test_prune_keeps_order_and_threshold():
     assert np.all(o[out["row"]] >= 0.005 * (1 - 1e-6)) and np.all(o[removed] < 0.005 * (1 + 1e-6))
     assert 0 < out["row"].size < n
     np.testing.assert_array_equal(out["logit"], logits[out["row"]])
+
+
+# ---------------------------------------------------------------------------- evaluation
+
+def test_image_sums_and_psnr_closed_forms():
+    from oracle import metrics as omx
+    rng = np.random.default_rng(10)
+    H, W = 12, 17
+    rgb_t = rng.uniform(size=(3, H, W))
+    depth_t = rng.uniform(0.5, 3.0, (H, W))
+    depth_t[rng.uniform(size=(H, W)) < 0.3] = 0.0
+    s = omx.image_sums(rgb_t + 0.1, depth_t + 0.02, rgb_t, depth_t)
+    valid = int((depth_t > 0).sum())
+    np.testing.assert_allclose(s, [3 * H * W * 0.01, 0.02 * valid, valid, 0.0004 * valid], rtol=1e-12)
+    assert omx.psnr(s[0], 3 * H * W) == pytest.approx(20.0, abs=1e-9)
+    assert omx.psnr(0.0, 10) == float("inf")
+
+
+def test_trajectory_errors_closed_forms():
+    from oracle import metrics as omx
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(11)
+    gt = [scenes.perturb_pose(scenes.identity_pose(), rng, 30.0, 1.0) for _ in range(5)]
+    e = omx.trajectory_errors(gt, gt)
+    assert e["ate_rmse"] == 0.0 and np.allclose(e["rot"], 0.0, atol=1e-7)
+    # moving every camera centre by a: world->camera t' = t - R a
+    a = np.array([0.03, -0.04, 0.0])
+    shifted = []
+    for p in gt:
+        R, t = scenes.pose_rt(p)
+        shifted.append(scenes.pose_from_rt(R, t - R @ a))
+    assert omx.trajectory_errors(shifted, gt)["ate_rmse"] == pytest.approx(0.05, rel=1e-9)
+    # turning every camera by 0.1 rad about its own centre
+    turned = []
+    for p in gt:
+        R, t = scenes.pose_rt(p)
+        Q = Rotation.from_rotvec(0.1 * np.array([0.6, 0.0, 0.8])).as_matrix()
+        turned.append(scenes.pose_from_rt(Q @ R, Q @ t))
+    e = omx.trajectory_errors(turned, gt)
+    np.testing.assert_allclose(e["rot"], 0.1, rtol=1e-9)
+    assert e["ate_rmse"] == pytest.approx(0.0, abs=1e-12)
