@@ -251,6 +251,48 @@ def run_sequence(a, dev, stream):
     return out
 
 
+def run_isotropic(dev, stream, steps: int = 400):
+    """The same tracking iteration with the room stored as isotropic Gaussians (Eq. 1 as
+    written: 32 bytes per Gaussian instead of 56; radius = geometric mean of the scales),
+    beside the anisotropic store, each warm and with the L2 flushed between steps."""
+    import torch
+    from paper_2408_05635_gb300 import gs, scenes
+    g, cam, gt_pose, start, rgb, depth, prior = workload()
+    iso = scenes.Gaussians(g.means, None, g.log_scales.mean(axis=1, keepdims=True).astype(np.float32), g.logits, g.rgb)
+    tg_t = [torch.tensor(x.reshape(-1), device=dev) for x in (rgb, depth, prior)]
+    tg = gs.gs_targets(*(x.data_ptr() for x in tg_t))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for name, gg in (("anisotropic", g), ("isotropic", iso)):
+        R = gs.Rasterizer(gs.Config(), device=dev)
+        gt = gs.GaussianTensors.from_numpy(gg, device=dev)
+        poses = torch.tensor(np.asarray(start)[None], dtype=torch.float64, device=dev)
+        prob = R.plan(gt, [cam], poses, margin=1.5)
+        ws, nb = R.workspace(prob)
+        adam = torch.zeros(1, 16, dtype=torch.float64, device=dev)
+        loss = torch.zeros(1, 1, dtype=torch.float64, device=dev)
+        s0 = poses.clone()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+        for k in range(steps + 5):
+            if k % ITERS_PER_FRAME == 0:
+                poses.copy_(s0)
+                adam.zero_()
+            flush.fill_(float(k))
+            j = k - 5
+            if j >= 0:
+                ev[2 * j].record(stream)
+            gs.gs_track_step(R.ctx, prob, gt.c(), tg, poses, adam, loss, 1, ws, nb, stream)
+            if j >= 0:
+                ev[2 * j + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        R.sync(stream)
+        us = 1e3 * sum(ev[2 * j].elapsed_time(ev[2 * j + 1]) for j in range(steps)) / steps
+        res[name] = {"us_per_iter": round(us, 2), "bytes_per_gaussian": 32 if name == "isotropic" else 56}
+        R.close()
+    res["workload"] = "tracking 640x480, the 200k room (isotropic: radius = geometric mean of the scales)"
+    return res
+
+
 def run_batched(a, dev, stream):
     """The batched / low-precision form beside the plain one, on the same views: all 512
     hypotheses tracked in one call with BF16 attributes, against the same keyframes'
@@ -655,6 +697,8 @@ def main():
                                f"the timed steps mark only {dominant}",
             "pairs_per_step": {k: v // a.steps for k, v in contrib.items()},
         }
+        if world == 1:
+            line["isotropic"] = run_isotropic(dev, stream)
         if world == 1 and a.batched_steps > 0:
             line["batched"] = run_batched(a, dev, stream)
         if world == 1 and a.mapping_steps > 0:

@@ -54,7 +54,10 @@ typedef struct gs_ctx gs_ctx;
 /* The map: n anisotropic Gaussians (Eq. 1 with the covariance Sigma = R s s^T R^T).
  * All arrays device, row-major, n rows.  means: float32 n x 3 (world frame, metres);
  * quats n x 4 (w, x, y, z), any non-zero norm; log_scales n x 3 (scale = exp);
- * opacity_logits n (opacity o = sigmoid); rgb n x 3.  The last four use dtype_attr. */
+ * opacity_logits n (opacity o = sigmoid); rgb n x 3.  The last four use dtype_attr.
+ * Isotropic Gaussians (Eq. 1 as written, eight values each: centre, radius, opacity,
+ * colour): quats NULL and log_scales n x 1 (radius = exp); Sigma = r^2 I.  Their
+ * gradients fill log_scales as n x 1 and leave the quats gradient untouched. */
 typedef struct {
     const float *means;
     const void *quats;

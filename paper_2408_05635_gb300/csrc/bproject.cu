@@ -116,8 +116,9 @@ __device__ __forceinline__ float warp_reduce8(float (&v)[8], int lane, int &idx)
     return v[0];
 }
 
-// One block per cell, one thread per record of the cell.
-template <int DT, bool PARAMS>
+// One block per cell, one thread per record of the cell.  ISO: isotropic Gaussians (Eq. 1
+// as written: one log-radius per Gaussian, no rotation), Sigma_c = s^2 I.
+template <int DT, bool PARAMS, bool ISO>
 __global__ void __launch_bounds__(kBlock) k_bproject(BprojLaunch L) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ float s_red[kWarps][8];
@@ -140,17 +141,25 @@ __global__ void __launch_bounds__(kBlock) k_bproject(BprojLaunch L) {
         const float x = cam_coord(sRt, 0, mx, my, mz);
         const float y = cam_coord(sRt, 1, mx, my, mz);
         const float z = cam_coord(sRt, 2, mx, my, mz);
-        const float q0 = ld_attr<DT>(L.g.quats, 4 * i), q1 = ld_attr<DT>(L.g.quats, 4 * i + 1);
-        const float q2 = ld_attr<DT>(L.g.quats, 4 * i + 2), q3 = ld_attr<DT>(L.g.quats, 4 * i + 3);
-        const float qn2 = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
-        const float qinv = rsqrtf(qn2);
-        const float w = q0 * qinv, qx = q1 * qinv, qy = q2 * qinv, qz = q3 * qinv;
-        float Rg[9];
-        quat_to_rot(w, qx, qy, qz, Rg);
+        float w = 1.f, qx = 0.f, qy = 0.f, qz = 0.f, qinv = 1.f;
+        float Rg[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
         float s[3];
-        s[0] = expf(ld_attr<DT>(L.g.log_scales, 3 * i));
-        s[1] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 1));
-        s[2] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 2));
+        if constexpr (ISO) {
+            s[0] = s[1] = s[2] = expf(ld_attr<DT>(L.g.log_scales, i));
+        } else {
+            const float q0 = ld_attr<DT>(L.g.quats, 4 * i), q1 = ld_attr<DT>(L.g.quats, 4 * i + 1);
+            const float q2 = ld_attr<DT>(L.g.quats, 4 * i + 2), q3 = ld_attr<DT>(L.g.quats, 4 * i + 3);
+            const float qn2 = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
+            qinv = rsqrtf(qn2);
+            w = q0 * qinv;
+            qx = q1 * qinv;
+            qy = q2 * qinv;
+            qz = q3 * qinv;
+            quat_to_rot(w, qx, qy, qz, Rg);
+            s[0] = expf(ld_attr<DT>(L.g.log_scales, 3 * i));
+            s[1] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 1));
+            s[2] = expf(ld_attr<DT>(L.g.log_scales, 3 * i + 2));
+        }
         float Bm[9], M[9];  // B = Rg diag(s), M = W B
 #pragma unroll
         for (int r = 0; r < 3; ++r)
@@ -239,13 +248,18 @@ __global__ void __launch_bounds__(kBlock) k_bproject(BprojLaunch L) {
                     for (int c = 0; c < 3; ++c)
                         dB[3 * r + c] = sRt[r] * dM[c] + sRt[3 + r] * dM[3 + c] + sRt[6 + r] * dM[6 + c];
                 if (G.log_scales) {
+                    if constexpr (ISO) {
+                        // one radius drives all three axes: d log s = s trace(W^T dM)
+                        atomicAdd(G.log_scales + i, (dB[0] + dB[4] + dB[8]) * s[0]);
+                    } else {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float ds = dB[c] * Rg[c] + dB[3 + c] * Rg[3 + c] + dB[6 + c] * Rg[6 + c];
-                        atomicAdd(G.log_scales + 3 * i + c, ds * s[c]);
+                        for (int c = 0; c < 3; ++c) {
+                            const float ds = dB[c] * Rg[c] + dB[3 + c] * Rg[3 + c] + dB[6 + c] * Rg[6 + c];
+                            atomicAdd(G.log_scales + 3 * i + c, ds * s[c]);
+                        }
                     }
                 }
-                if (G.quats) {
+                if (!ISO && G.quats) {
                     float dRg[9];
 #pragma unroll
                     for (int r = 0; r < 3; ++r)
@@ -376,11 +390,16 @@ cudaError_t launch_finalize(const FinalizeLaunch &L, cudaStream_t st) {
 cudaError_t launch_bproject(const BprojLaunch &L, cudaStream_t st) {
     const uint32_t grid = (uint32_t)L.d.V * (uint32_t)L.d.nblk;
     const bool params = L.grads.means || L.grads.quats || L.grads.log_scales || L.grads.opacity_logits || L.grads.rgb;
+    const bool iso = L.g.quats == nullptr;
 #define GS_BPROJ(DT)                                                   \
-    if (params)                                                        \
-        k_bproject<DT, true><<<grid, kBlock, 0, st>>>(L);              \
+    if (params && iso)                                                 \
+        k_bproject<DT, true, true><<<grid, kBlock, 0, st>>>(L);        \
+    else if (params)                                                   \
+        k_bproject<DT, true, false><<<grid, kBlock, 0, st>>>(L);       \
+    else if (iso)                                                      \
+        k_bproject<DT, false, true><<<grid, kBlock, 0, st>>>(L);       \
     else                                                               \
-        k_bproject<DT, false><<<grid, kBlock, 0, st>>>(L);
+        k_bproject<DT, false, false><<<grid, kBlock, 0, st>>>(L);
     switch (L.dtype) {
         case GS_F32: GS_BPROJ(GS_F32) break;
         case GS_BF16: GS_BPROJ(GS_BF16) break;

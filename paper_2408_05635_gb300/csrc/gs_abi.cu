@@ -273,7 +273,7 @@ gs_status check_gaussians(gs_ctx *ctx, const gs_gaussians *g, const Problem &pr)
     if (g->n != pr.d.n) return fail(ctx, GS_ERR_INVALID_ARG, "gaussians.n differs from problem.n_gaussians");
     if (g->dtype_attr != GS_F32 && g->dtype_attr != GS_BF16 && g->dtype_attr != GS_F16)
         return fail(ctx, GS_ERR_INVALID_ARG, "unknown dtype_attr");
-    if (g->n > 0 && (!g->means || !g->quats || !g->log_scales || !g->opacity_logits || !g->rgb))
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->opacity_logits || !g->rgb))
         return fail(ctx, GS_ERR_INVALID_ARG, "a Gaussian attribute pointer is NULL");
     return GS_OK;
 }

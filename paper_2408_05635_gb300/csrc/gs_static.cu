@@ -72,7 +72,7 @@ extern "C" gs_status gs_render_static(const gs_config *cfg, const gs_gaussians *
         !(cam->fy > 0))
         return GS_ERR_INVALID_ARG;
     if (g->dtype_attr != GS_F32 && g->dtype_attr != GS_BF16 && g->dtype_attr != GS_F16) return GS_ERR_INVALID_ARG;
-    if (g->n > 0 && (!g->means || !g->quats || !g->log_scales || !g->opacity_logits || !g->rgb))
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->opacity_logits || !g->rgb))
         return GS_ERR_INVALID_ARG;
     if (targets && (!targets->rgb || !targets->depth)) return GS_ERR_INVALID_ARG;
     if (loss && !targets) return GS_ERR_INVALID_ARG;

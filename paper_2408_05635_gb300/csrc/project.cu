@@ -274,7 +274,7 @@ cudaError_t launch_scan_tiles(const WsPtrs &ws, const Dims &d, cudaStream_t st) 
     return cudaGetLastError();
 }
 
-template <int DT>
+template <int DT, bool ISO>
 __global__ void __launch_bounds__(kBlock, 5) k_project(ProjectLaunch L) {
     const int v = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -302,23 +302,29 @@ __global__ void __launch_bounds__(kBlock, 5) k_project(ProjectLaunch L) {
         const float y = cam_coord(sRt, 1, mx, my, mz);
         const float z = cam_coord(sRt, 2, mx, my, mz);
         if (z > S.z_near) {
-            float qw = ld_attr<DT>(L.g.quats, 4 * i), qx = ld_attr<DT>(L.g.quats, 4 * i + 1);
-            float qy = ld_attr<DT>(L.g.quats, 4 * i + 2), qz = ld_attr<DT>(L.g.quats, 4 * i + 3);
-            const float qq = qw * qw + qx * qx + qy * qy + qz * qz;
-            const float qi = qq > 0.f ? rsqrtf(qq) : 0.f;
-            qw *= qi; qx *= qi; qy *= qi; qz *= qi;
-            float Rg[9];
-            quat_to_rot(qw, qx, qy, qz, Rg);
-            const float s0 = __expf(ld_attr<DT>(L.g.log_scales, 3 * i));
-            const float s1 = __expf(ld_attr<DT>(L.g.log_scales, 3 * i + 1));
-            const float s2 = __expf(ld_attr<DT>(L.g.log_scales, 3 * i + 2));
-            // M = W Rg diag(s): Sigma_c = M M^T
+            // M = W Rg diag(s): Sigma_c = M M^T (isotropic: M = s W)
             float M[9];
+            if constexpr (ISO) {
+                const float sc = __expf(ld_attr<DT>(L.g.log_scales, i));
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                M[3 * r + 0] = (sRt[3 * r] * Rg[0] + sRt[3 * r + 1] * Rg[3] + sRt[3 * r + 2] * Rg[6]) * s0;
-                M[3 * r + 1] = (sRt[3 * r] * Rg[1] + sRt[3 * r + 1] * Rg[4] + sRt[3 * r + 2] * Rg[7]) * s1;
-                M[3 * r + 2] = (sRt[3 * r] * Rg[2] + sRt[3 * r + 1] * Rg[5] + sRt[3 * r + 2] * Rg[8]) * s2;
+                for (int k = 0; k < 9; ++k) M[k] = sRt[k] * sc;
+            } else {
+                float qw = ld_attr<DT>(L.g.quats, 4 * i), qx = ld_attr<DT>(L.g.quats, 4 * i + 1);
+                float qy = ld_attr<DT>(L.g.quats, 4 * i + 2), qz = ld_attr<DT>(L.g.quats, 4 * i + 3);
+                const float qq = qw * qw + qx * qx + qy * qy + qz * qz;
+                const float qi = qq > 0.f ? rsqrtf(qq) : 0.f;
+                qw *= qi; qx *= qi; qy *= qi; qz *= qi;
+                float Rg[9];
+                quat_to_rot(qw, qx, qy, qz, Rg);
+                const float s0 = __expf(ld_attr<DT>(L.g.log_scales, 3 * i));
+                const float s1 = __expf(ld_attr<DT>(L.g.log_scales, 3 * i + 1));
+                const float s2 = __expf(ld_attr<DT>(L.g.log_scales, 3 * i + 2));
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    M[3 * r + 0] = (sRt[3 * r] * Rg[0] + sRt[3 * r + 1] * Rg[3] + sRt[3 * r + 2] * Rg[6]) * s0;
+                    M[3 * r + 1] = (sRt[3 * r] * Rg[1] + sRt[3 * r + 1] * Rg[4] + sRt[3 * r + 2] * Rg[7]) * s1;
+                    M[3 * r + 2] = (sRt[3 * r] * Rg[2] + sRt[3 * r + 1] * Rg[5] + sRt[3 * r + 2] * Rg[8]) * s2;
+                }
             }
             const float iz = __fdividef(1.f, z);
             // J at the mean's image-plane tangent, clamped to the view's limits
@@ -396,10 +402,20 @@ __global__ void __launch_bounds__(kBlock, 5) k_project(ProjectLaunch L) {
 
 cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st) {
     dim3 grid(L.d.nblk, L.d.V);
+    const bool iso = L.g.quats == nullptr;  // isotropic Gaussians: one log-radius, no rotation
     switch (L.dtype) {
-        case GS_F32: k_project<GS_F32><<<grid, kBlock, 0, st>>>(L); break;
-        case GS_BF16: k_project<GS_BF16><<<grid, kBlock, 0, st>>>(L); break;
-        case GS_F16: k_project<GS_F16><<<grid, kBlock, 0, st>>>(L); break;
+        case GS_F32:
+            if (iso) k_project<GS_F32, true><<<grid, kBlock, 0, st>>>(L);
+            else k_project<GS_F32, false><<<grid, kBlock, 0, st>>>(L);
+            break;
+        case GS_BF16:
+            if (iso) k_project<GS_BF16, true><<<grid, kBlock, 0, st>>>(L);
+            else k_project<GS_BF16, false><<<grid, kBlock, 0, st>>>(L);
+            break;
+        case GS_F16:
+            if (iso) k_project<GS_F16, true><<<grid, kBlock, 0, st>>>(L);
+            else k_project<GS_F16, false><<<grid, kBlock, 0, st>>>(L);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

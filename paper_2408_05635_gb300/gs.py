@@ -320,15 +320,22 @@ class GaussianTensors:
     def n(self) -> int:
         return self.means.shape[0]
 
+    @property
+    def isotropic(self) -> bool:
+        """Eq. 1 as written: no quaternions, one log-radius per Gaussian."""
+        return self.quats is None
+
     def c(self) -> gs_gaussians:
         if self.means.dtype != torch.float32:
             raise ValueError("means must be float32")
-        dt = self.quats.dtype
-        for t in (self.log_scales, self.logits, self.rgb):
+        dt = self.log_scales.dtype
+        for t in (self.logits, self.rgb) + (() if self.quats is None else (self.quats,)):
             if t.dtype != dt:
                 raise ValueError("quats, log_scales, logits and rgb must share one dtype")
         if dt not in _DT:
             raise ValueError(f"unsupported attribute dtype {dt}")
+        if self.quats is None and self.log_scales.numel() != self.n:
+            raise ValueError("isotropic Gaussians take one log-radius each")
         return gs_gaussians(_ptr(self.means), _ptr(self.quats), _ptr(self.log_scales), _ptr(self.logits),
                             _ptr(self.rgb), _DT[dt], 0, self.n)
 
@@ -336,8 +343,8 @@ class GaussianTensors:
     def from_numpy(g, device="cuda", attr_dtype=torch.float32) -> "GaussianTensors":
         def t(a, dt):
             return torch.as_tensor(a, dtype=torch.float32).to(device=device, dtype=dt).contiguous()
-        return GaussianTensors(t(g.means, torch.float32), t(g.quats, attr_dtype), t(g.log_scales, attr_dtype),
-                               t(g.logits, attr_dtype), t(g.rgb, attr_dtype))
+        return GaussianTensors(t(g.means, torch.float32), None if g.quats is None else t(g.quats, attr_dtype),
+                               t(g.log_scales, attr_dtype), t(g.logits, attr_dtype), t(g.rgb, attr_dtype))
 
 
 def gs_image_metrics(rgb, depth, rgb_t, depth_t, out: torch.Tensor, stream=None) -> None:
@@ -548,9 +555,9 @@ class Rasterizer:
         grads = None
         if params:
             out["grads"] = {k: torch.zeros(getattr(g, k).shape, dtype=torch.float32, device=self.device)
-                            for k in ("means", "quats", "log_scales", "logits", "rgb")}
+                            for k in ("means", "quats", "log_scales", "logits", "rgb") if getattr(g, k) is not None}
             G = out["grads"]
-            grads = gs_gaussians_grad(_ptr(G["means"]), _ptr(G["quats"]), _ptr(G["log_scales"]), _ptr(G["logits"]),
+            grads = gs_gaussians_grad(_ptr(G["means"]), _ptr(G.get("quats")), _ptr(G["log_scales"]), _ptr(G["logits"]),
                                       _ptr(G["rgb"]))
         if pose:
             out["pose_grad"] = torch.zeros(n_views, 6, dtype=torch.float64, device=self.device)
@@ -569,8 +576,8 @@ class Rasterizer:
         V = len(cams)
         if grads is None:
             grads = {k: torch.zeros(getattr(g, k).shape, dtype=torch.float32, device=self.device)
-                     for k in ("means", "quats", "log_scales", "logits", "rgb")}
-        G = gs_gaussians_grad(_ptr(grads["means"]), _ptr(grads["quats"]), _ptr(grads["log_scales"]),
+                     for k in ("means", "quats", "log_scales", "logits", "rgb") if getattr(g, k) is not None}
+        G = gs_gaussians_grad(_ptr(grads["means"]), _ptr(grads.get("quats")), _ptr(grads["log_scales"]),
                               _ptr(grads["logits"]), _ptr(grads["rgb"]))
         loss = torch.zeros(V, dtype=torch.float64, device=self.device)
         gc = g.c()
