@@ -532,6 +532,23 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The largest of every rank's value (the slowest replica sets the job's time); the
+    plain value with one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step: float, steps: int, world: int, ms_max: float) -> float:
+    """Units all ranks processed per second: every replica does `steps` steps of
+    `units_per_step` units, and the job takes the slowest replica's time (weak scaling)."""
+    return world * steps * units_per_step / (ms_max / 1e3)
+
+
 def main():
     a = _args()
     rank = int(os.environ.get("RANK", "0"))
@@ -622,12 +639,9 @@ def main():
     if st:
         raise SystemExit(f"device reported {gs._STATUS[st]} during the timed steps")
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     pix = cam.width * cam.height
-    iters_per_s = world * a.steps / (ms_max / 1e3)
+    iters_per_s = whole_job_rate(1, a.steps, world, ms_max)
     mpix = iters_per_s * pix / 1e6
 
     # end to end through the public call with host buffers: pinned frame in, pose and loss out
@@ -655,10 +669,7 @@ def main():
             e2e_e.append(s1)
     torch.cuda.synchronize(dev)
     e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e2e_s, e2e_e))
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_mpix = world * a.steps * pix / (float(te.item()) / 1e3) / 1e6
+    e2e_mpix = whole_job_rate(pix, a.steps, world, max_over_ranks(e2e_ms, world, dev)) / 1e6
 
     # roofline of the dominant kernel, from its CUDA-event time inside the timed steps
     avg = {k: v / a.steps for k, v in kern_ms.items()}
