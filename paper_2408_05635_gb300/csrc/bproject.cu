@@ -119,7 +119,7 @@ __device__ __forceinline__ float warp_reduce8(float (&v)[8], int lane, int &idx)
 // One block per cell, one thread per record of the cell.  ISO: isotropic Gaussians (Eq. 1
 // as written: one log-radius per Gaussian, no rotation), Sigma_c = s^2 I.
 template <int DT, bool PARAMS, bool ISO>
-__global__ void __launch_bounds__(kBlock) k_bproject(BprojLaunch L) {
+__global__ void __launch_bounds__(kBlock, PARAMS ? 4 : 6) k_bproject(BprojLaunch L) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ float s_red[kWarps][8];
     const uint32_t cell = blockIdx.x;

@@ -275,7 +275,7 @@ cudaError_t launch_scan_tiles(const WsPtrs &ws, const Dims &d, cudaStream_t st) 
 }
 
 template <int DT, bool ISO>
-__global__ void __launch_bounds__(kBlock, 5) k_project(ProjectLaunch L) {
+__global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
     const int v = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     __shared__ float sRt[12];
@@ -421,10 +421,17 @@ cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Resident blocks per SM the emission is compiled for: six fit a 200k-Gaussian view's 782
+// cells in one wave on 152 SMs (at the cost of a few spilled registers).
+#ifndef GS_EMIT_MIN_BLOCKS
+#define GS_EMIT_MIN_BLOCKS 6
+#endif
+constexpr int kEmitMinBlocks = GS_EMIT_MIN_BLOCKS;
+
 // One key per (record, tile met): depth bits (positive floats sort as unsigned ints) in
 // the high word, the record in the low word, stored at the next free slot of the tile's
 // sub-bucket.  One block per cell, one thread per record (record_tiles).
-__global__ void __launch_bounds__(kBlock) k_emit(WsPtrs ws, Dims d) {
+__global__ void __launch_bounds__(kBlock, kEmitMinBlocks) k_emit(WsPtrs ws, Dims d) {
     const uint32_t cell = blockIdx.x;
     const uint32_t cnt = ws.cell_cnt[cell];
     if ((uint32_t)(threadIdx.x & ~31u) >= cnt) return;  // whole warps without records leave
