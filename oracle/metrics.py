@@ -48,3 +48,72 @@ def trajectory_errors(est, gt) -> dict:
         Rd = _rotation(np.asarray(a)[:4]) @ _rotation(np.asarray(b)[:4]).T
         ang.append(np.arccos(np.clip((np.trace(Rd) - 1.0) / 2.0, -1.0, 1.0)))
     return {"trans": d, "rot": np.array(ang), "ate_rmse": float(np.sqrt(np.mean(d * d)))}
+
+
+# ---------------------------------------------------------------------------- MS-SSIM
+
+# Multi-scale structural similarity (Wang, Simoncelli and Bovik, 2003): per scale the
+# contrast-structure term cs = (2 s_xy + C2) / (s_x^2 + s_y^2 + C2) averaged over the
+# image, on the coarsest scale also the luminance term l = (2 m_x m_y + C1) /
+# (m_x^2 + m_y^2 + C1); local statistics under an 11 x 11 Gaussian window (sigma 1.5) over
+# the window positions that fit (valid); 2 x 2 average pooling between the five scales;
+# MS-SSIM = l_5^b5 prod_j cs_j^bj with the published exponents.  Readings: colours in
+# [0, 1] (L = 1), K1 = 0.01, K2 = 0.03; negative cs clamped at 0; computed per colour
+# channel and averaged over the channels.
+MSSSIM_WEIGHTS = (0.0448, 0.2856, 0.3001, 0.2363, 0.1333)
+
+
+def gaussian_window(size: int = 11, sigma: float = 1.5) -> np.ndarray:
+    x = np.arange(size, dtype=np.float64) - (size - 1) / 2.0
+    g = np.exp(-x * x / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def _filter_valid(img: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """Separable correlation with the window, valid positions only."""
+    k = g.size
+    H, W = img.shape
+    rows = np.zeros((H, W - k + 1))
+    for j in range(k):
+        rows += g[j] * img[:, j:j + W - k + 1]
+    out = np.zeros((H - k + 1, W - k + 1))
+    for i in range(k):
+        out += g[i] * rows[i:i + H - k + 1, :]
+    return out
+
+
+def ssim_terms(x: np.ndarray, y: np.ndarray, k1: float = 0.01, k2: float = 0.03) -> tuple[float, float]:
+    """(mean l, mean cs) of two single-channel images at one scale."""
+    g = gaussian_window()
+    c1, c2 = k1 * k1, k2 * k2
+    mx, my = _filter_valid(x, g), _filter_valid(y, g)
+    sxx = _filter_valid(x * x, g) - mx * mx
+    syy = _filter_valid(y * y, g) - my * my
+    sxy = _filter_valid(x * y, g) - mx * my
+    l = (2 * mx * my + c1) / (mx * mx + my * my + c1)
+    cs = (2 * sxy + c2) / (sxx + syy + c2)
+    return float(l.mean()), float(cs.mean())
+
+
+def _pool2(img: np.ndarray) -> np.ndarray:
+    H, W = img.shape[0] // 2, img.shape[1] // 2
+    return 0.25 * (img[0:2 * H:2, 0:2 * W:2] + img[1:2 * H:2, 0:2 * W:2] + img[0:2 * H:2, 1:2 * W:2]
+                   + img[1:2 * H:2, 1:2 * W:2])
+
+
+def ms_ssim(rgb, rgb_t) -> dict:
+    """MS-SSIM of two colour images (3 x H x W in [0, 1]): per channel and the mean."""
+    rgb, rgb_t = np.asarray(rgb, np.float64), np.asarray(rgb_t, np.float64)
+    per = []
+    for ch in range(rgb.shape[0]):
+        x, y = rgb[ch], rgb_t[ch]
+        val = 1.0
+        for j, b in enumerate(MSSSIM_WEIGHTS):
+            l, cs = ssim_terms(x, y)
+            val *= max(cs, 0.0) ** b
+            if j == len(MSSSIM_WEIGHTS) - 1:
+                val *= max(l, 0.0) ** b
+            else:
+                x, y = _pool2(x), _pool2(y)
+        per.append(val)
+    return {"ms_ssim": float(np.mean(per)), "per_channel": per}

@@ -175,3 +175,36 @@ def test_trajectory_errors_closed_forms():
     e = omx.trajectory_errors(turned, gt)
     np.testing.assert_allclose(e["rot"], 0.1, rtol=1e-9)
     assert e["ate_rmse"] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_ms_ssim_identities_and_closed_forms():
+    """MS-SSIM of an image with itself is 1; of two constant images (no structure, so
+    cs = 1 at every scale) it is l^b5 with l = (2 a b + C1) / (a^2 + b^2 + C1); it is
+    symmetric, falls with added noise, and the window is the normalised Gaussian."""
+    from oracle import metrics as omx
+    rng = np.random.default_rng(12)
+    img = rng.uniform(size=(3, 200, 260))
+    assert omx.ms_ssim(img, img)["ms_ssim"] == pytest.approx(1.0, abs=1e-12)
+    a, b = 0.3, 0.7
+    c = omx.ms_ssim(np.full((3, 180, 180), a), np.full((3, 180, 180), b))
+    lv = (2 * a * b + 1e-4) / (a * a + b * b + 1e-4)
+    assert c["ms_ssim"] == pytest.approx(lv ** 0.1333, rel=1e-12)
+    noisy = np.clip(img + rng.normal(0, 0.05, img.shape), 0, 1)
+    noisier = np.clip(img + rng.normal(0, 0.2, img.shape), 0, 1)
+    s1, s2 = omx.ms_ssim(img, noisy)["ms_ssim"], omx.ms_ssim(img, noisier)["ms_ssim"]
+    assert 1.0 > s1 > s2 > 0.0
+    assert omx.ms_ssim(noisy, img)["ms_ssim"] == pytest.approx(s1, rel=1e-12)
+    g = omx.gaussian_window()
+    assert g.sum() == pytest.approx(1.0) and np.argmax(g) == 5 and g[0] == pytest.approx(g[-1])
+    assert sum(omx.MSSSIM_WEIGHTS) == pytest.approx(1.0, abs=1e-3)
+
+
+def test_ms_ssim_window_filter_is_a_valid_correlation():
+    """The separable window filter equals scipy's 2-D correlation with the outer-product
+    window over the valid positions."""
+    from scipy.signal import correlate2d
+    from oracle import metrics as omx
+    rng = np.random.default_rng(13)
+    img = rng.uniform(size=(37, 52))
+    g = omx.gaussian_window()
+    np.testing.assert_allclose(omx._filter_valid(img, g), correlate2d(img, np.outer(g, g), mode="valid"), rtol=1e-12)
