@@ -348,6 +348,23 @@ gs_status gs_map_prune(const gs_map_config *cfg, const gs_map *src, const int64_
 gs_status gs_image_metrics(const float *rgb, const float *depth, const float *rgb_t, const float *depth_t,
                            int64_t pixels, double *out, void *stream);
 
+/* Device scratch, in bytes, that gs_msssim needs for a width x height image. */
+size_t gs_msssim_scratch_bytes(int32_t width, int32_t height);
+
+/* Multi-scale structural similarity (Wang, Simoncelli and Bovik, 2003) of a rendered
+ * colour image against its observation, the MS-SSIM of Sec. IV: per scale the mean
+ * contrast-structure term (and on the coarsest the mean luminance term) under an 11 x 11
+ * Gaussian window (sigma 1.5) at every position where it fits, constants K1 = 0.01,
+ * K2 = 0.03 for colours in [0, 1], five scales made by 2 x 2 average pooling (odd last
+ * row / column dropped), negative terms clamped at 0, combined with the published
+ * exponents (0.0448, 0.2856, 0.3001, 0.2363, 0.1333) per colour channel.
+ *   rgb, rgb_t: device, planar 3 x height x width FP32; width and height at least 176 (the
+ *   coarsest scale holds one window); out: device, 4 doubles = (mean over the channels,
+ *   red, green, blue); scratch: device, gs_msssim_scratch_bytes, 256-byte aligned.
+ * Errors: INVALID_ARG, CUDA. */
+gs_status gs_msssim(const float *rgb, const float *rgb_t, int32_t width, int32_t height, double *out, void *scratch,
+                    size_t scratch_bytes, void *stream);
+
 /* ------------------------------------------------------------------ no-allocation render */
 
 /* Limits of gs_render_static. */

@@ -130,6 +130,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
             "gs_kernel_times": (c_int32, [c_void_p, P(gs_kernel_time), c_int32, P(c_int32)]),
             "gs_image_metrics": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+            "gs_msssim_scratch_bytes": (c_size_t, [c_int32, c_int32]),
+            "gs_msssim": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
             "gs_default_map_config": (None, [P(gs_map_config)]),
             "gs_map_scratch_bytes": (c_size_t, [c_int64]),
             "gs_map_add": (c_int32, [P(gs_map_config), P(gs_map), c_void_p, P(gs_camera), c_void_p, c_void_p,
@@ -352,6 +354,16 @@ def gs_image_metrics(rgb, depth, rgb_t, depth_t, out: torch.Tensor, stream=None)
     pixel count, sum (D - D*)^2 there)."""
     _map_check(load().gs_image_metrics(_ptr(rgb), _ptr(depth), _ptr(rgb_t), _ptr(depth_t), int(depth.numel()), _ptr(out),
                                        _stream(stream)), "gs_image_metrics")
+
+
+def gs_msssim(rgb, rgb_t, width: int, height: int, out: torch.Tensor, stream=None) -> None:
+    """out (device, 4 doubles) <- MS-SSIM (channel mean, red, green, blue) of two planar
+    colour images; the scratch is allocated here."""
+    need = int(load().gs_msssim_scratch_bytes(int(width), int(height)))
+    scratch = torch.empty(need + 256, dtype=torch.uint8, device=out.device)
+    off = (-scratch.data_ptr()) % 256
+    _map_check(load().gs_msssim(_ptr(rgb), _ptr(rgb_t), int(width), int(height), _ptr(out),
+                                scratch[off:].data_ptr(), need, _stream(stream)), "gs_msssim")
 
 
 def gs_default_map_config() -> gs_map_config:

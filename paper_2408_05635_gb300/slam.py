@@ -178,18 +178,25 @@ class Slam:
         """Image quality of the final map at the keyframes' estimated poses (Sec. IV:
         PSNR of the colour, average depth error): gs_image_metrics per keyframe."""
         g = self.gaussians(lowp=False)
+        W, H = int(self.cam.width), int(self.cam.height)
+        ssim_ok = min(W, H) >= 176  # the coarsest of the five scales must hold one window
         sums = torch.zeros(len(self.keyframes), 4, dtype=torch.float64, device=self.dev)
+        ssim = torch.zeros(len(self.keyframes), 4, dtype=torch.float64, device=self.dev)
         for j, (pose, (rgb, depth, _)) in enumerate(self.keyframes):
             prob = self.mapper.plan(g, [self.cam], pose.reshape(1, 7), margin=self.cfg.plan_margin)
             out = self.mapper.render(prob, g, pose.reshape(1, 7), stream=stream)
             gs.gs_image_metrics(out["rgb"], out["depth"], rgb.reshape(-1), depth.reshape(-1), sums[j], stream)
+            if ssim_ok:
+                gs.gs_msssim(out["rgb"], rgb.reshape(-1), W, H, ssim[j], stream)
         self.mapper.sync(stream)
         s = sums.cpu().numpy()
-        P = int(self.cam.width) * int(self.cam.height)
-        mse = s[:, 0] / (3 * P)
-        return {"psnr_db": float(np.mean(10 * np.log10(1.0 / np.maximum(mse, 1e-30)))),
-                "depth_l1_cm": float(100 * s[:, 1].sum() / max(s[:, 2].sum(), 1.0)),
-                "depth_rmse_cm": float(100 * np.sqrt(s[:, 3].sum() / max(s[:, 2].sum(), 1.0)))}
+        mse = s[:, 0] / (3 * W * H)
+        res = {"psnr_db": float(np.mean(10 * np.log10(1.0 / np.maximum(mse, 1e-30)))),
+               "depth_l1_cm": float(100 * s[:, 1].sum() / max(s[:, 2].sum(), 1.0)),
+               "depth_rmse_cm": float(100 * np.sqrt(s[:, 3].sum() / max(s[:, 2].sum(), 1.0)))}
+        if ssim_ok:
+            res["ms_ssim"] = float(ssim[:, 0].mean().item())
+        return res
 
 
 def camera_centres(poses) -> np.ndarray:
