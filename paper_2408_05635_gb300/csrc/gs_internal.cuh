@@ -349,6 +349,57 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
     return __fadd_rn(f, e);
 }
 
+// Tiles [a0, a1] of row ty (within the record's tile columns [tx0, tx1]) that the support
+// ellipse q(d) <= R, R = dmax2 (1 + 1e-3) + 1e-3 (the margin of ellipse_meets_rect), meets.
+// The ellipse cut by the row's band of pixel centres [y0, y1] is convex, so its x-extent is
+// one interval: on the right boundary x = mx + (-b dy + sqrt(a R - det dy^2)) / a, concave
+// in dy = y - my, the maximum mx + sqrt(R c / det) is reached at dy = -b sqrt(R / (c det)),
+// and outside the band at the nearer band edge; the left boundary mirrors it.  A tile
+// meets the ellipse iff its pixel-centre columns overlap that interval, so this finds the
+// same tiles as testing each tile of the row, at the cost of one row.  The interval is
+// widened by 1e-3 px + 1e-6 |x| against the rounding of the square roots.  Explicitly
+// rounded operations: k_project and k_emit enumerate identical tiles.
+__device__ __forceinline__ void row_tiles(const ViewInfo &vi, float mx, float my, float a, float b, float c,
+                                          float dmax2, int ty, int tx0, int tx1, int &a0, int &a1) {
+    a0 = tx0;
+    a1 = tx1;
+    if (!(dmax2 < INFINITY)) return;
+    const float R = __fadd_rn(__fmul_rn(dmax2, 1.001f), 1e-3f);
+    const float det = diff_of_products(a, c, b, b);
+    const float yb0 = (float)(ty * kTile), yb1 = (float)min(ty * kTile + kTile - 1, vi.height - 1);
+    const float Y = __fsqrt_rn(__fdiv_rn(__fmul_rn(a, R), det));  // y half-extent of the ellipse
+    const float ly = fmaxf(__fsub_rn(yb0, my), -Y), hy = fminf(__fsub_rn(yb1, my), Y);
+    if (!(ly <= hy)) {
+        a0 = 1;
+        a1 = 0;
+        return;
+    }
+    const float X = __fsqrt_rn(__fdiv_rn(__fmul_rn(R, c), det));    // x half-extent of the ellipse
+    const float t = __fmul_rn(b, __fsqrt_rn(__fdiv_rn(R, __fmul_rn(c, det))));  // |dy| of the x-extremes
+    const float ia = __fdiv_rn(1.f, a);
+    // boundary offsets at the band edges: -b dy / a -+ sqrt(a R - det dy^2) / a
+    const float rl = __fsqrt_rn(fmaxf(__fsub_rn(__fmul_rn(a, R), __fmul_rn(det, __fmul_rn(ly, ly))), 0.f));
+    const float rh = __fsqrt_rn(fmaxf(__fsub_rn(__fmul_rn(a, R), __fmul_rn(det, __fmul_rn(hy, hy))), 0.f));
+    const float cl = __fmul_rn(__fmul_rn(-b, ly), ia), ch = __fmul_rn(__fmul_rn(-b, hy), ia);
+    float xr, xl;
+    if (-t >= ly && -t <= hy)
+        xr = X;
+    else
+        xr = fmaxf(__fadd_rn(cl, __fmul_rn(rl, ia)), __fadd_rn(ch, __fmul_rn(rh, ia)));
+    if (t >= ly && t <= hy)
+        xl = -X;
+    else
+        xl = fminf(__fsub_rn(cl, __fmul_rn(rl, ia)), __fsub_rn(ch, __fmul_rn(rh, ia)));
+    xl = __fsub_rn(__fadd_rn(mx, xl), __fadd_rn(1e-3f, __fmul_rn(1e-6f, fabsf(__fadd_rn(mx, xl)))));
+    xr = __fadd_rn(__fadd_rn(mx, xr), __fadd_rn(1e-3f, __fmul_rn(1e-6f, fabsf(__fadd_rn(mx, xr)))));
+    // tile tx spans pixel centres [16 tx, 16 tx + 15]: it meets [xl, xr] iff
+    // 16 tx + 15 >= xl and 16 tx <= xr
+    const float lo = fmaxf(ceilf(__fdiv_rn(__fsub_rn(xl, (float)(kTile - 1)), (float)kTile)), -1.f);
+    const float hi = fminf(floorf(__fdiv_rn(xr, (float)kTile)), 1.0e7f);
+    a0 = max(tx0, (int)lo);
+    a1 = min(tx1, (int)hi);
+}
+
 __device__ __forceinline__ float4 stage_box(const float4 B, float cu, float cv) {
     const float detc = diff_of_products(B.x, B.z, B.y, B.y);
     if (!(detc > 0.f) || !(B.w < INFINITY)) return make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);

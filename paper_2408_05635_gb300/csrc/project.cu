@@ -51,10 +51,10 @@ __device__ __forceinline__ void record_tiles(bool mine, const ViewInfo &vi, floa
     const int rw = tx1 - tx0 + 1;
     const int count = has ? rw * (ty1 - ty0 + 1) : 0;
     if (SOLO && has && count <= kSoloTiles) {
-        const float ia = __fdividef(1.f, B.x), ic = __fdividef(1.f, B.z);
-        for (int t = 0; t < count; ++t) {
-            const int ty = ty0 + t / rw, tx = tx0 + t % rw;
-            if (tile_hit(vi, A, B, ia, ic, tx, ty)) body(lane, vi.tile_base + (uint32_t)(ty * vi.tiles_x + tx), A, tag);
+        for (int ty = ty0; ty <= ty1; ++ty) {
+            int a0, a1;
+            row_tiles(vi, A.x, A.y, B.x, B.y, B.z, B.w, ty, tx0, tx1, a0, a1);
+            for (int tx = a0; tx <= a1; ++tx) body(lane, vi.tile_base + (uint32_t)(ty * vi.tiles_x + tx), A, tag);
         }
     }
     uint32_t big = __ballot_sync(0xffffffffu, count > kSoloTiles);
@@ -456,10 +456,12 @@ __global__ void __launch_bounds__(kBlock, kEmitMinBlocks) k_emit(WsPtrs ws, Dims
     const int rw = tx1 - tx0 + 1;
     const int count = has ? rw * (ty1 - ty0 + 1) : 0;
     if (has && count <= kSoloTiles) {
-        const float ia = __fdividef(1.f, B.x), ic = __fdividef(1.f, B.z);
-        uint32_t hits = 0;
-        for (int t = 0; t < count; ++t)
-            if (tile_hit(vi, A, B, ia, ic, tx0 + t % rw, ty0 + t / rw)) hits |= 1u << t;
+        uint32_t hits = 0;  // bit (ty - ty0) rw + (tx - tx0) for every tile met
+        for (int ty = ty0; ty <= ty1; ++ty) {
+            int a0, a1;
+            row_tiles(vi, A.x, A.y, B.x, B.y, B.z, B.w, ty, tx0, tx1, a0, a1);
+            if (a0 <= a1) hits |= ((1u << (a1 - a0 + 1)) - 1u) << ((ty - ty0) * rw + (a0 - tx0));
+        }
         const unsigned long long key = ((unsigned long long)__float_as_uint(A.z) << 32) | r;
         while (hits) {
             uint32_t bucket[8], slot[8];
