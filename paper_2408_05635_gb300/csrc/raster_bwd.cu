@@ -19,7 +19,8 @@
 // Each warp owns an 8 x 4 patch of the tile and walks, back to front, only the staged
 // Gaussians whose support box meets the patch and that precede its last contributor.
 // Reduction: every (pixel, Gaussian) term is summed over the warp with a butterfly
-// reduce-scatter (6 values in 8 shuffles for the pose-only walk, 16 in 16 otherwise),
+// reduce-scatter (for the pose-only walk 6 values in 8 shuffles, or two Gaussians' 12 in
+// 13 when it steps two at a time; 16 values in 16 otherwise),
 // added by the owning lanes into a per-batch shared-memory accumulator, and flushed once
 // per (tile, Gaussian) with vector float4 atomics into the record's global accumulator.
 // Lanes whose pixel the Gaussian does not reach take a = 0, which leaves T and g.B
@@ -69,6 +70,27 @@ __device__ __forceinline__ float warp_reduce_scatter6(float v0, float v1, float 
     const float b = u2 + __shfl_xor_sync(0xffffffffu, u2, 8);
     float c = (h2 ? b : a) + __shfl_xor_sync(0xffffffffu, h2 ? a : b, 4);
     c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
+// Joint reduce-scatter of two Gaussians' six values (a: the first, b: the second) in 13
+// shuffles instead of two times eight: six exchanges over lane bit 4 (the bit-4 half keeps
+// b), three over bit 3, two over bit 2 (the third value of each half is summed by both
+// partners), one over bit 1 and a plain sum over bit 0.  Value 3 * b3 + (b1 ? 2 : b2) of
+// Gaussian b4 ends in the lane; owners are the lanes with bit 0 clear and not both of
+// bits 2, 1 set (twelve of them).
+__device__ __forceinline__ float warp_reduce_scatter12(const float (&a)[6], const float (&b)[6], int lane) {
+    const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0, h2 = (lane & 4) != 0, h1 = (lane & 2) != 0;
+    float u[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) u[k] = (h4 ? b[k] : a[k]) + __shfl_xor_sync(0xffffffffu, h4 ? a[k] : b[k], 16);
+    float w[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) w[m] = (h3 ? u[3 + m] : u[m]) + __shfl_xor_sync(0xffffffffu, h3 ? u[m] : u[3 + m], 8);
+    const float x = (h2 ? w[1] : w[0]) + __shfl_xor_sync(0xffffffffu, h2 ? w[0] : w[1], 4);
+    const float y = w[2] + __shfl_xor_sync(0xffffffffu, w[2], 4);
+    float c = (h1 ? y : x) + __shfl_xor_sync(0xffffffffu, h1 ? x : y, 2);
     c += __shfl_xor_sync(0xffffffffu, c, 1);
     return c;
 }
@@ -127,8 +149,13 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     const Settings &S = L.s;
     const float thr = S.log2_alpha_min;
     // the accumulator slot this lane adds after a reduction, or -1
-    int my_slot = -1;
+    int my_slot = -1, pair_slot = -1;
     if (POSE) {
+        // the paired steps' joint reduction: value 3 b3 + (b1 ? 2 : b2) of Gaussian b4
+        if ((lane & 1) == 0 && !((lane & 2) && (lane & 4))) {
+            const int k = ((lane & 8) ? 3 : 0) + ((lane & 2) ? 2 : ((lane & 4) ? 1 : 0));
+            pair_slot = k < 3 ? k : k + 1;  // values 0..5 -> slots 0, 1, 2, 4, 5, 6
+        }
         if ((lane & 3) == 0 && !((lane & 8) && (lane & 4))) {
             const int k = ((lane & 16) ? 3 : 0) + ((lane & 4) ? 2 : ((lane & 8) ? 1 : 0));
             my_slot = k < 3 ? k : k + 1;  // values 0..5 -> slots 0, 1, 2, 4, 5, 6
@@ -221,12 +248,8 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
                 float vA[6], vB[6];
                 bwd_step6(cA, pA, sC[jA], g0, g1, g2, gD, gS, S.alpha_max, T, GB, vA);
                 bwd_step6(cB, pB, sC[jB], g0, g1, g2, gD, gS, S.alpha_max, T, GB, vB);
-                const float sA = warp_reduce_scatter6(vA[0], vA[1], vA[2], vA[3], vA[4], vA[5], lane);
-                const float sB = warp_reduce_scatter6(vB[0], vB[1], vB[2], vB[3], vB[4], vB[5], lane);
-                if (my_slot >= 0) {
-                    if (sA != 0.f) atomicAdd(&sAcc[jA * kAccStride + my_slot], sA);
-                    if (sB != 0.f) atomicAdd(&sAcc[jB * kAccStride + my_slot], sB);
-                }
+                const float s2 = warp_reduce_scatter12(vA, vB, lane);
+                if (pair_slot >= 0 && s2 != 0.f) atomicAdd(&sAcc[((lane & 16) ? jB : jA) * kAccStride + pair_slot], s2);
             }
         }
         for (; e >= 0; --e) {
