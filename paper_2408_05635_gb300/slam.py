@@ -69,7 +69,7 @@ class Tracker:
         if has_prior:
             self.t_prior.copy_(prior.reshape(-1), non_blocking=True)
         tg = gs.gs_targets(self.t_rgb.data_ptr(), self.t_depth.data_ptr(), self.t_prior.data_ptr() if has_prior else None)
-        key = (g.means.data_ptr(), g.n, g.quats.dtype)
+        key = (g.means.data_ptr(), g.n, g.log_scales.dtype, g.isotropic)
         for _ in range(4):
             self.pose.copy_(start.reshape(1, 7))
             self.adam.zero_()

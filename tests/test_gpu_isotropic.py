@@ -79,3 +79,29 @@ def test_isotropic_equals_anisotropic_with_equal_scales():
     R.sync()
     for k in ("rgb", "depth", "sil"):
         assert np.abs(outs[0][k] - outs[1][k]).max() < 1e-5, k
+
+
+def test_isotropic_map_tracks_like_equal_scale_anisotropic():
+    """Frame tracking (slam.Tracker, gs_track_step) on an isotropic map and on the same map
+    stored anisotropically with equal scales: the same trajectory to FP32 rounding, and it
+    moves toward the true pose."""
+    from paper_2408_05635_gb300 import slam
+    g = scenes.room_scene(40_000, seed=4)
+    log_r = g.log_scales.mean(axis=1, keepdims=True).astype(np.float32)
+    iso = scenes.Gaussians(g.means, None, log_r, g.logits, g.rgb)
+    ident = np.tile(np.array([1.0, 0.0, 0.0, 0.0], np.float32), (g.n, 1))
+    aniso = scenes.Gaussians(g.means, ident, np.repeat(log_r, 3, axis=1), g.logits, g.rgb)
+    cam = scenes.Cam(262.5, 262.5, 159.5, 119.5, 320, 240)
+    truth = scenes.tracking_gt_pose()
+    start = scenes.perturb_pose(truth, np.random.default_rng(5), 1.0, 0.03)
+    rgb, depth = scenes.raycast_room(truth, cam, seed=4)
+    frame = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (rgb, depth)]
+    out = []
+    for gg in (iso, aniso):
+        tr = slam.Tracker(cam, 40)
+        p = tr.track(gs.GaussianTensors.from_numpy(gg), torch.tensor(start, dtype=torch.float64, device="cuda"), *frame)
+        out.append(p.cpu().numpy())
+        tr.close()
+    centre = lambda q: -scenes.pose_rt(q)[0].T @ scenes.pose_rt(q)[1]
+    assert np.linalg.norm(centre(out[0]) - centre(out[1])) < 1e-4
+    assert np.linalg.norm(centre(out[0]) - centre(truth)) < np.linalg.norm(centre(start) - centre(truth))
