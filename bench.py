@@ -230,24 +230,27 @@ def run_sequence(a, dev, stream):
                                  "tracking_iters_per_s": round(100 * (F - 1) / wall, 1),
                                  "mpix_per_s": round(100 * (F - 1) * P / wall / 1e6, 1), "replans": tr.replans, **rep}
     del gt
-    # (2) the whole loop from an empty map
-    cfg = slam.SlamConfig(lowp=torch.float16)
-    S = slam.Slam(cam, cfg, device=dev)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for k in range(F):
-            S.process(k, *frames[k], first_pose=gt_poses[0] if k == 0 else None, stream=stream)
+    # (2) the whole loop from an empty map, with anisotropic Gaussians and with the
+    # isotropic ones of Eq. 1 as written
+    for key, iso in (("slam_from_empty_map", False), ("slam_from_empty_map_isotropic", True)):
+        cfg = slam.SlamConfig(lowp=torch.float16, isotropic=iso)
+        S = slam.Slam(cam, cfg, device=dev)
         torch.cuda.synchronize(dev)
-    wall = time.perf_counter() - t0
-    rep = _trajectory_report(torch.stack(S.poses).cpu().numpy(), gt_poses)
-    q = S.evaluate(frames, stream)
-    out["slam_from_empty_map"] = {"ms_per_frame": round(1e3 * wall / F, 3), "frames_per_s": round(F / wall, 2),
-                                  "keyframes": S.stats["keyframes"], "map_iters_per_keyframe": cfg.map_iters, "first_frame_map_iters": cfg.first_map_iters,
-                                  "window": cfg.window, "final_map_gaussians": S.n,
-                                  "added_total": int(sum(S.stats["added"])), "pruned_total": int(sum(S.stats["pruned"])),
-                                  "replans": S.tracker.replans, **rep, **{k: round(v, 3) for k, v in q.items()}}
-    S.close()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(F):
+                S.process(k, *frames[k], first_pose=gt_poses[0] if k == 0 else None, stream=stream)
+            torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        rep = _trajectory_report(torch.stack(S.poses).cpu().numpy(), gt_poses)
+        q = S.evaluate(frames, stream)
+        out[key] = {"ms_per_frame": round(1e3 * wall / F, 3), "frames_per_s": round(F / wall, 2),
+                    "keyframes": S.stats["keyframes"], "map_iters_per_keyframe": cfg.map_iters,
+                    "first_frame_map_iters": cfg.first_map_iters, "window": cfg.window, "final_map_gaussians": S.n,
+                    "added_total": int(sum(S.stats["added"])), "pruned_total": int(sum(S.stats["pruned"])),
+                    "replans": S.tracker.replans, **rep, **{k: round(v, 3) for k, v in q.items()}}
+        S.close()
+        del S
     return out
 
 

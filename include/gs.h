@@ -268,6 +268,9 @@ gs_status gs_kernel_times(gs_ctx *ctx, gs_kernel_time *out, int32_t cap, int32_t
  *     groups means (3 capacity floats), quats (4), log_scales (3), opacity_logits (1),
  *     rgb (3), then the second moments in the same layout; a Gaussian's entries are the
  *     rows of its index in each group.
+ * An isotropic map (Eq. 1 as written) has quats = lowp_quats = NULL and log_scales of
+ * capacity x 1; its moments are 16 x capacity floats (means 3, log_scales 1,
+ * opacity_logits 1, rgb 3, then the second moments).
  * Every pointer must be 16-byte aligned and capacity a multiple of 4. */
 typedef struct {
     float *means;

@@ -69,11 +69,12 @@ def gaussians_from_frame(cam, pose, rgb, depth, sil=None, sil_add: float = 0.5) 
 
 
 def adam_step(params: dict, grads: dict, m: dict, v: dict, step: int, lrs: dict, beta1: float, beta2: float,
-              eps: float) -> tuple[dict, dict, dict]:
+              eps: float, groups=GROUPS) -> tuple[dict, dict, dict]:
     """One Adam step on every group (Sec. III-C: gradient-based optimisation of the
-    Gaussians).  All dicts map a group name to an array; step is the 1-based t."""
+    Gaussians).  All dicts map a group name to an array; step is the 1-based t; `groups`
+    lists the groups present (an isotropic map has no quaternions)."""
     out_p, out_m, out_v = {}, {}, {}
-    for k in GROUPS:
+    for k in groups:
         g = np.asarray(grads[k], np.float64)
         mk = beta1 * np.asarray(m[k], np.float64) + (1.0 - beta1) * g
         vk = beta2 * np.asarray(v[k], np.float64) + (1.0 - beta2) * g * g

@@ -20,15 +20,23 @@ namespace {
 
 constexpr int kCompactThreads = 1024;
 constexpr int kGroups = 5;  // means, quats, log_scales, opacity_logits, rgb
-__host__ __device__ constexpr int group_width(int s) { return s == 1 ? 4 : (s == 3 ? 1 : 3); }
-__host__ __device__ constexpr int group_offset(int s) { return s == 0 ? 0 : (s == 1 ? 3 : (s == 2 ? 7 : (s == 3 ? 10 : 11))); }
+// Values per Gaussian of each group, and the group's first row in a moment array (in units
+// of capacity); isotropic maps (Eq. 1 as written) have no quaternion and one log-radius.
+__host__ __device__ constexpr int group_width(int s, bool iso) {
+    return s == 1 ? (iso ? 0 : 4) : (s == 2 ? (iso ? 1 : 3) : (s == 3 ? 1 : 3));
+}
+__host__ __device__ constexpr int group_offset(int s, bool iso) {
+    return iso ? (s == 0 ? 0 : (s <= 2 ? 3 : (s == 3 ? 4 : 5))) : (s == 0 ? 0 : (s == 1 ? 3 : (s == 2 ? 7 : (s == 3 ? 10 : 11))));
+}
+__host__ __device__ constexpr int values_per_gaussian(bool iso) { return iso ? 8 : 14; }
 
 struct MapView {
     float *p[kGroups];
     void *lp[kGroups];  // lp[0] is always NULL (the means have no low-precision copy)
     int32_t lowp_dt;
+    bool iso;      // no quaternions, one log-radius
     int64_t cap;
-    float *state;  // m: groups at cap * group_offset; v: 14 cap further
+    float *state;  // m: groups at cap * group_offset; v: values_per_gaussian cap further
 };
 
 MapView view_of(const gs_map &m) {
@@ -44,6 +52,7 @@ MapView view_of(const gs_map &m) {
     v.lp[3] = m.lowp_opacity_logits;
     v.lp[4] = m.lowp_rgb;
     v.lowp_dt = m.lowp_dtype;
+    v.iso = m.quats == nullptr;
     v.cap = m.capacity;
     v.state = m.adam_state;
     return v;
@@ -168,28 +177,32 @@ __global__ void __launch_bounds__(kCompactThreads) k_add_emit(AddLaunch L) {
         const float ls = (float)log(d / (0.5 * (L.fx + L.fy)));
         const float q[4] = {1.f, 0.f, 0.f, 0.f};
         const float c[3] = {L.rgb[p], L.rgb[P + p], L.rgb[2 * P + p]};
+        const int wl = group_width(2, M.iso);
+        if (!M.iso) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) M.p[1][4 * i + k] = q[k];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) M.p[2][3 * i + k] = ls;
+            for (int k = 0; k < 4; ++k) M.p[1][4 * i + k] = q[k];
+        }
+        for (int k = 0; k < wl; ++k) M.p[2][wl * i + k] = ls;
         M.p[3][i] = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) M.p[4][3 * i + k] = c[k];
-        if (M.lp[1]) {
+        if (M.lp[2]) {
+            if (M.lp[1]) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) store_lowp(M.lp[1], 4 * i + k, q[k], M.lowp_dt);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) store_lowp(M.lp[2], 3 * i + k, ls, M.lowp_dt);
+                for (int k = 0; k < 4; ++k) store_lowp(M.lp[1], 4 * i + k, q[k], M.lowp_dt);
+            }
+            for (int k = 0; k < wl; ++k) store_lowp(M.lp[2], wl * i + k, ls, M.lowp_dt);
             store_lowp(M.lp[3], i, 0.f, M.lowp_dt);
 #pragma unroll
             for (int k = 0; k < 3; ++k) store_lowp(M.lp[4], 3 * i + k, c[k], M.lowp_dt);
         }
         if (M.state) {
+            const int vp = values_per_gaussian(M.iso);
 #pragma unroll
             for (int s = 0; s < kGroups; ++s) {
-                const int w = group_width(s);
-                float *m = M.state + M.cap * group_offset(s);
-                float *vv = m + 14 * M.cap;
+                const int w = group_width(s, M.iso);
+                float *m = M.state + M.cap * group_offset(s, M.iso);
+                float *vv = m + vp * M.cap;
                 for (int k = 0; k < w; ++k) {
                     m[w * i + k] = 0.f;
                     vv[w * i + k] = 0.f;
@@ -215,6 +228,7 @@ struct AdamLaunch {
     void *lp[kGroups];
     float *m[kGroups], *v[kGroups];
     float lr[kGroups];
+    int width[kGroups];
     float b1, b2, omb1, omb2, c1, c2, eps;
     int32_t lowp_dt;
     const int64_t *n;
@@ -232,8 +246,8 @@ __device__ __forceinline__ float adam_one(float &p, float g, float &m, float &v,
 // tail (fewer than four values) taken by block 0.
 __global__ void __launch_bounds__(256) k_map_adam(AdamLaunch L) {
     const int s = blockIdx.y;
-    if (L.g[s] == nullptr) return;
-    const int64_t len = (int64_t)group_width(s) * (*L.n);
+    if (L.g[s] == nullptr || L.width[s] == 0) return;
+    const int64_t len = (int64_t)L.width[s] * (*L.n);
     const float lr = L.lr[s];
     float *p = L.p[s], *m = L.m[s], *v = L.v[s];
     const float *g = L.g[s];
@@ -306,18 +320,19 @@ __global__ void __launch_bounds__(kCompactThreads) k_prune_emit(PruneLaunch L) {
     const MapView &S = L.src, &D = L.dst;
     if (keep) {
         const int64_t j = (int64_t)before + r;
+        const int vp = values_per_gaussian(S.iso);
 #pragma unroll
         for (int s = 0; s < kGroups; ++s) {
-            const int w = group_width(s);
+            const int w = group_width(s, S.iso);
             for (int k = 0; k < w; ++k) D.p[s][w * j + k] = S.p[s][w * i + k];
             if (s > 0 && S.lp[s] && D.lp[s] && S.lowp_dt == D.lowp_dt)
                 for (int k = 0; k < w; ++k) copy_lowp(S.lp[s], w * i + k, D.lp[s], w * j + k, D.lowp_dt);
             if (S.state && D.state) {
-                const float *sm = S.state + S.cap * group_offset(s);
-                float *dm = D.state + D.cap * group_offset(s);
+                const float *sm = S.state + S.cap * group_offset(s, S.iso);
+                float *dm = D.state + D.cap * group_offset(s, S.iso);
                 for (int k = 0; k < w; ++k) {
                     dm[w * j + k] = sm[w * i + k];
-                    dm[14 * D.cap + w * j + k] = sm[14 * S.cap + w * i + k];
+                    dm[vp * D.cap + w * j + k] = sm[vp * S.cap + w * i + k];
                 }
             }
         }
@@ -333,10 +348,13 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 bool map_ok(const gs_map *m) {
     if (!m || m->capacity < 0 || (m->capacity & 3) != 0) return false;
-    const float *f[5] = {m->means, m->quats, m->log_scales, m->opacity_logits, m->rgb};
+    const bool iso = m->quats == nullptr;  // isotropic: no quaternions anywhere
+    const float *f[5] = {m->means, iso ? m->means : m->quats, m->log_scales, m->opacity_logits, m->rgb};
     for (const float *q : f)
         if (!q || !aligned16(q)) return false;
-    const void *l[4] = {m->lowp_quats, m->lowp_log_scales, m->lowp_opacity_logits, m->lowp_rgb};
+    if (iso && m->lowp_quats) return false;
+    const void *l[4] = {iso ? m->lowp_log_scales : m->lowp_quats, m->lowp_log_scales, m->lowp_opacity_logits,
+                        m->lowp_rgb};
     const bool any = l[0] || l[1] || l[2] || l[3];
     if (any) {
         if (m->lowp_dtype != GS_BF16 && m->lowp_dtype != GS_F16) return false;
@@ -419,9 +437,10 @@ gs_status gs_map_adam_step(const gs_map_config *cfg, const gs_map *map, const in
         L.p[s] = M.p[s];
         L.g[s] = gp[s];
         L.lp[s] = M.lp[s];
-        L.m[s] = M.state + M.cap * group_offset(s);
-        L.v[s] = L.m[s] + 14 * M.cap;
+        L.m[s] = M.state + M.cap * group_offset(s, M.iso);
+        L.v[s] = L.m[s] + values_per_gaussian(M.iso) * M.cap;
         L.lr[s] = (float)lr[s];
+        L.width[s] = group_width(s, M.iso);
     }
     L.b1 = (float)cfg->beta1;
     L.b2 = (float)cfg->beta2;
@@ -451,7 +470,7 @@ gs_status gs_map_prune(const gs_map_config *cfg, const gs_map *src, const int64_
         return GS_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(scratch) & 255u) != 0 || scratch_bytes < scratch_bytes_for(src->capacity))
         return GS_ERR_INVALID_ARG;
-    if (src->means == dst->means) return GS_ERR_INVALID_ARG;
+    if (src->means == dst->means || (src->quats == nullptr) != (dst->quats == nullptr)) return GS_ERR_INVALID_ARG;
     PruneLaunch L{};
     L.src = view_of(*src);
     L.dst = view_of(*dst);

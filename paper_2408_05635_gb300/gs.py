@@ -403,22 +403,24 @@ def gs_map_prune(cfg: gs_map_config, src: gs_map, n_src: torch.Tensor, dst: gs_m
 class Map:
     """The map as the scene optimisation holds it (gs_map): FP32 master arrays with room
     for `capacity` Gaussians (rounded up to a multiple of 4), the live count on the device,
-    the Adam moments and, with lowp_dtype, a BF16 / F16 render copy of the attributes."""
-
-    GROUPS = ("means", "quats", "log_scales", "logits", "rgb")
-    WIDTH = {"means": 3, "quats": 4, "log_scales": 3, "logits": 1, "rgb": 3}
+    the Adam moments and, with lowp_dtype, a BF16 / F16 render copy of the attributes.
+    isotropic: Eq. 1 as written (no quaternions, one log-radius per Gaussian)."""
 
     def __init__(self, capacity: int, device="cuda", lowp_dtype: torch.dtype | None = None, adam: bool = True,
-                 config: gs_map_config | None = None):
+                 config: gs_map_config | None = None, isotropic: bool = False):
         load()
         cap = (int(capacity) + 3) // 4 * 4
-        self.capacity, self.device = cap, torch.device(device)
+        self.capacity, self.device, self.isotropic = cap, torch.device(device), isotropic
+        self.GROUPS = ("means", "log_scales", "logits", "rgb") if isotropic else ("means", "quats", "log_scales",
+                                                                                  "logits", "rgb")
+        self.WIDTH = {"means": 3, "quats": 4, "log_scales": 1 if isotropic else 3, "logits": 1, "rgb": 3}
         self.p = {k: torch.zeros((cap, self.WIDTH[k]) if k != "logits" else (cap,), dtype=torch.float32, device=device)
                   for k in self.GROUPS}
         self.lowp_dtype = lowp_dtype
         self.lp = None if lowp_dtype is None else {
-            k: torch.zeros_like(self.p[k], dtype=lowp_dtype) for k in self.GROUPS[1:]}
-        self.state = torch.zeros(28 * cap, dtype=torch.float32, device=device) if adam else None
+            k: torch.zeros_like(self.p[k], dtype=lowp_dtype) for k in self.GROUPS if k != "means"}
+        per = sum(self.WIDTH[k] for k in self.GROUPS)
+        self.state = torch.zeros(2 * per * cap, dtype=torch.float32, device=device) if adam else None
         self.count = torch.zeros(1, dtype=torch.int64, device=device)
         self.err = torch.zeros(1, dtype=torch.int32, device=device)
         self.config = config or gs_default_map_config()
@@ -426,7 +428,7 @@ class Map:
 
     def c(self) -> gs_map:
         lp = self.lp or {}
-        return gs_map(_ptr(self.p["means"]), _ptr(self.p["quats"]), _ptr(self.p["log_scales"]), _ptr(self.p["logits"]),
+        return gs_map(_ptr(self.p["means"]), _ptr(self.p.get("quats")), _ptr(self.p["log_scales"]), _ptr(self.p["logits"]),
                       _ptr(self.p["rgb"]), _ptr(lp.get("quats")), _ptr(lp.get("log_scales")), _ptr(lp.get("logits")),
                       _ptr(lp.get("rgb")), _DT.get(self.lowp_dtype, 0), 0, self.capacity, _ptr(self.state))
 
@@ -446,8 +448,8 @@ class Map:
         """The first n live Gaussians as a render input (FP32, or the low-precision copy)."""
         n = self.n if n is None else n
         src = self.lp if lowp else self.p
-        return GaussianTensors(self.p["means"][:n], src["quats"][:n], src["log_scales"][:n], src["logits"][:n],
-                               src["rgb"][:n])
+        q = None if self.isotropic else src["quats"][:n]
+        return GaussianTensors(self.p["means"][:n], q, src["log_scales"][:n], src["logits"][:n], src["rgb"][:n])
 
     def load(self, g) -> None:
         """Fill the map with arrays (numpy or tensors, rows = Gaussians); moments zeroed."""
@@ -455,8 +457,10 @@ class Map:
         if n > self.capacity:
             raise ValueError("more Gaussians than capacity")
         for k in self.GROUPS:
-            self.p[k][:n] = torch.as_tensor(getattr(g, k), dtype=torch.float32, device=self.device).reshape(
-                self.p[k][:n].shape)
+            a = torch.as_tensor(getattr(g, k), dtype=torch.float32, device=self.device)
+            if k == "log_scales" and self.isotropic and a.dim() == 2 and a.shape[1] == 3:
+                a = a.mean(dim=1)
+            self.p[k][:n] = a.reshape(self.p[k][:n].shape)
             if self.lp is not None and k != "means":
                 self.lp[k][:n] = self.p[k][:n].to(self.lowp_dtype)
         if self.state is not None:

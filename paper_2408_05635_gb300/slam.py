@@ -18,9 +18,6 @@ import torch
 
 from . import gs
 
-GROUPS = ("means", "quats", "log_scales", "logits", "rgb")
-
-
 @dataclasses.dataclass
 class SlamConfig:
     """Readings where the paper is silent (its keyframes follow feature parallax, which a
@@ -36,6 +33,7 @@ class SlamConfig:
     lowp: torch.dtype | None = None  # track on a BF16 / F16 render copy of the map
     capacity: int = 4_000_000     # Gaussians the map can hold
     prune: bool = True            # remove Gaussians with opacity < opacity_min after mapping
+    isotropic: bool = False       # Eq. 1 as written: no rotation, one radius per Gaussian
 
 
 class Tracker:
@@ -100,11 +98,11 @@ class Slam:
         self.cam, self.cfg = cam, cfg or SlamConfig()
         self.dev = torch.device(device)
         c = self.cfg
-        self.map = gs.Map(c.capacity, device, lowp_dtype=c.lowp)
-        self.spare = gs.Map(c.capacity, device, lowp_dtype=c.lowp) if c.prune else None
+        self.map = gs.Map(c.capacity, device, lowp_dtype=c.lowp, isotropic=c.isotropic)
+        self.spare = gs.Map(c.capacity, device, lowp_dtype=c.lowp, isotropic=c.isotropic) if c.prune else None
         self.tracker = Tracker(cam, c.track_iters, config, device, c.plan_margin)
         self.mapper = gs.Rasterizer(config or gs.Config(), device)
-        self.grads = {k: torch.zeros_like(self.map.p[k]) for k in GROUPS}
+        self.grads = {k: torch.zeros_like(self.map.p[k]) for k in self.map.GROUPS}
         self.keyframes: list[tuple[torch.Tensor, tuple]] = []
         self.poses: list[torch.Tensor] = []
         self.n = 0
@@ -157,7 +155,7 @@ class Slam:
         g = self.map.gaussians(n, lowp=False)
         probs = [self.mapper.plan(g, cams[v0:v0 + c.map_chunk], poses[v0:v0 + c.map_chunk].contiguous(),
                                   margin=c.plan_margin) for v0 in range(0, len(win), c.map_chunk)]
-        views = {k: self.grads[k][:n] for k in GROUPS}
+        views = {k: self.grads[k][:n] for k in self.map.GROUPS}
         self.map.state.zero_()
         iters = c.first_map_iters if len(self.keyframes) == 1 else c.map_iters
         for it in range(1, iters + 1):

@@ -26,12 +26,22 @@ def _lrs(cfg):
             "logits": cfg.lr_opacity_logits, "rgb": cfg.lr_rgb}
 
 
-def _state_views(state, cap):
+def _groups(iso):
+    return ("means", "log_scales", "logits", "rgb") if iso else om.GROUPS
+
+
+def _width(iso):
+    return dict(om.WIDTH, log_scales=1) if iso else om.WIDTH
+
+
+def _state_views(state, cap, iso=False):
     """Split the flat Adam state into per-group (m, v) arrays of capacity rows."""
     off, out = 0, {}
-    for k in om.GROUPS:
-        w = om.WIDTH[k]
-        out[k] = (state[off * cap:(off + w) * cap].reshape(cap, w), state[(14 + off) * cap:(14 + off + w) * cap].reshape(cap, w))
+    per = sum(_width(iso)[k] for k in _groups(iso))
+    for k in _groups(iso):
+        w = _width(iso)[k]
+        out[k] = (state[off * cap:(off + w) * cap].reshape(cap, w),
+                  state[(per + off) * cap:(per + off + w) * cap].reshape(cap, w))
         off += w
     return out
 
@@ -43,20 +53,21 @@ def _frame(pose, cam=CAM, seed=0):
 
 # ---------------------------------------------------------------------------- Adam
 
-@pytest.mark.parametrize("lowp", [None, torch.bfloat16])
-def test_adam_steps_match_oracle(lowp):
+@pytest.mark.parametrize("lowp,iso", [(None, False), (torch.bfloat16, False), (torch.float16, True)])
+def test_adam_steps_match_oracle(lowp, iso):
     rng = np.random.default_rng(1)
     n, cap = 1001, 1004
-    M = gs.Map(cap, lowp_dtype=lowp)
+    M = gs.Map(cap, lowp_dtype=lowp, isotropic=iso)
     cap = M.capacity
-    p0 = {k: rng.normal(size=(cap, om.WIDTH[k])).astype(np.float32) for k in om.GROUPS}
-    for k in om.GROUPS:
+    G, Wd = _groups(iso), _width(iso)
+    p0 = {k: rng.normal(size=(cap, Wd[k])).astype(np.float32) for k in G}
+    for k in G:
         M.p[k].copy_(torch.from_numpy(p0[k].reshape(M.p[k].shape)))
         if M.lp is not None and k != "means":
             M.lp[k].copy_(M.p[k].to(lowp))
     M.count.fill_(n)
     cfg = M.config
-    p = {k: p0[k][:n].astype(np.float64) for k in om.GROUPS}
+    p = {k: p0[k][:n].astype(np.float64) for k in G}
     m = {k: np.zeros_like(a) for k, a in p.items()}
     v = {k: np.zeros_like(a) for k, a in p.items()}
     # error bounds of the FP32 recursion (u = 2^-24): m sums terms of either sign, so its
@@ -66,15 +77,15 @@ def test_adam_steps_match_oracle(lowp):
     m_abs = {k: np.zeros_like(a) for k, a in p.items()}
     p_err = {k: np.zeros_like(a) for k, a in p.items()}
     for t in range(1, 4):
-        g = {k: (rng.normal(size=(cap, om.WIDTH[k])) * 10.0 ** rng.uniform(-4, 1, (cap, 1))).astype(np.float32)
-             for k in om.GROUPS}
-        gt = {k: torch.from_numpy(g[k].reshape(M.p[k].shape)).cuda() for k in om.GROUPS}
+        g = {k: (rng.normal(size=(cap, Wd[k])) * 10.0 ** rng.uniform(-4, 1, (cap, 1))).astype(np.float32)
+             for k in G}
+        gt = {k: torch.from_numpy(g[k].reshape(M.p[k].shape)).cuda() for k in G}
         if t == 3:
             gt.pop("rgb")  # a group without a gradient is left alone
         M.adam_step(gt, t)
-        gg = {k: g[k][:n].astype(np.float64) for k in om.GROUPS}
-        q, m2, v2 = om.adam_step(p, gg, m, v, t, _lrs(cfg), cfg.beta1, cfg.beta2, cfg.eps)
-        for k in om.GROUPS:
+        gg = {k: g[k][:n].astype(np.float64) for k in G}
+        q, m2, v2 = om.adam_step(p, gg, m, v, t, _lrs(cfg), cfg.beta1, cfg.beta2, cfg.eps, groups=G)
+        for k in G:
             if t == 3 and k == "rgb":
                 continue
             m_abs[k] = cfg.beta1 * m_abs[k] + (1 - cfg.beta1) * np.abs(gg[k])
@@ -86,8 +97,8 @@ def test_adam_steps_match_oracle(lowp):
             q["rgb"], m2["rgb"], v2["rgb"] = p["rgb"], m["rgb"], v["rgb"]
         p, m, v = q, m2, v2
     torch.cuda.synchronize()
-    st = _state_views(M.state.cpu().numpy(), cap)
-    for k in om.GROUPS:
+    st = _state_views(M.state.cpu().numpy(), cap, iso)
+    for k in G:
         got = M.p[k].cpu().numpy().reshape(cap, -1)
         lr = _lrs(cfg)[k]
         assert np.all(np.abs(got[:n] - p[k]) <= p_err[k] + 1e-7 * lr), k
@@ -105,30 +116,35 @@ def _check_added(M, n0, ref, state_before=None):
     n1 = M.n
     k = ref["pixel"].size
     assert n1 == n0 + k
-    got = {key: M.p[key][n0:n1].cpu().numpy().reshape(k, -1).astype(np.float64) for key in om.GROUPS}
+    iso = M.isotropic
+    got = {key: M.p[key][n0:n1].cpu().numpy().reshape(k, -1).astype(np.float64) for key in M.GROUPS}
     np.testing.assert_array_equal(got["rgb"], ref["rgb"].astype(np.float32).astype(np.float64))
     np.testing.assert_allclose(got["means"], ref["means"], rtol=0, atol=1e-6)
-    np.testing.assert_allclose(got["log_scales"], ref["log_scales"], rtol=0, atol=1e-6)
-    np.testing.assert_array_equal(got["quats"], ref["quats"])
+    np.testing.assert_allclose(got["log_scales"], ref["log_scales"][:, :1] if iso else ref["log_scales"], rtol=0,
+                               atol=1e-6)
+    if not iso:
+        np.testing.assert_array_equal(got["quats"], ref["quats"])
     np.testing.assert_array_equal(got["logits"], ref["logits"])
     if M.state is not None:
-        st = _state_views(M.state.cpu().numpy(), M.capacity)
-        for key in om.GROUPS:
+        st = _state_views(M.state.cpu().numpy(), M.capacity, iso)
+        for key in M.GROUPS:
             assert not st[key][0][n0:n1].any() and not st[key][1][n0:n1].any()
             if state_before is not None:
-                sb = _state_views(state_before, M.capacity)
+                sb = _state_views(state_before, M.capacity, iso)
                 np.testing.assert_array_equal(st[key][0][:n0], sb[key][0][:n0])
     if M.lp is not None:
-        for key in om.GROUPS[1:]:
+        for key in M.GROUPS[1:]:
             np.testing.assert_array_equal(M.lp[key][n0:n1].float().cpu().numpy(),
                                           M.p[key][n0:n1].to(M.lowp_dtype).float().cpu().numpy())
 
 
-def test_first_frame_gaussians_match_oracle():
-    """Sec. III-A: one Gaussian per pixel with depth, in pixel order, at the start of an empty map."""
+@pytest.mark.parametrize("iso", [False, True])
+def test_first_frame_gaussians_match_oracle(iso):
+    """Sec. III-A: one Gaussian per pixel with depth, in pixel order, at the start of an
+    empty map (anisotropic, or isotropic as Eq. 1 is written)."""
     pose = scenes.look_at((2.5, 1.5, 0.8), (0.2, -0.1, 1.0))
     rgb, depth = _frame(pose)
-    M = gs.Map(CAM.width * CAM.height, lowp_dtype=torch.float16)
+    M = gs.Map(CAM.width * CAM.height, lowp_dtype=torch.float16, isotropic=iso)
     M.add_from_frame(CAM, torch.tensor(pose, dtype=torch.float64, device="cuda"), torch.from_numpy(rgb).cuda(),
                      torch.from_numpy(depth).cuda())
     ref = om.gaussians_from_frame(ocam(CAM), pose, rgb, depth)
@@ -171,15 +187,16 @@ def test_add_overflow_fills_to_capacity_and_flags():
 
 # ---------------------------------------------------------------------------- removal
 
-@pytest.mark.parametrize("n", [0, 1, 5000])
-def test_prune_matches_oracle(n):
+@pytest.mark.parametrize("n,iso", [(0, False), (1, False), (5000, False), (5000, True)])
+def test_prune_matches_oracle(n, iso):
     rng = np.random.default_rng(3)
     cap = 5004
-    A, B = gs.Map(cap, lowp_dtype=torch.bfloat16), gs.Map(cap, lowp_dtype=torch.bfloat16)
-    for k in om.GROUPS:
+    A = gs.Map(cap, lowp_dtype=torch.bfloat16, isotropic=iso)
+    B = gs.Map(cap, lowp_dtype=torch.bfloat16, isotropic=iso)
+    for k in A.GROUPS:
         A.p[k].normal_()
     A.p["logits"].copy_(torch.from_numpy(rng.normal(-5.3, 0.6, cap).astype(np.float32)))
-    for k in om.GROUPS[1:]:
+    for k in A.GROUPS[1:]:
         A.lp[k].copy_(A.p[k].to(torch.bfloat16))
     A.state.normal_()
     A.count.fill_(n)
@@ -191,12 +208,12 @@ def test_prune_matches_oracle(n):
     assert B.n == k
     if n == 5000:
         assert 0 < k < n
-    for key in om.GROUPS:
+    for key in A.GROUPS:
         np.testing.assert_array_equal(B.p[key][:k].cpu().numpy(), A.p[key][:n].cpu().numpy()[keep])
         if key != "means":
             np.testing.assert_array_equal(B.lp[key][:k].float().cpu().numpy(), A.lp[key][:n].float().cpu().numpy()[keep])
-    sa, sb = _state_views(A.state.cpu().numpy(), A.capacity), _state_views(B.state.cpu().numpy(), B.capacity)
-    for key in om.GROUPS:
+    sa, sb = _state_views(A.state.cpu().numpy(), A.capacity, iso), _state_views(B.state.cpu().numpy(), B.capacity, iso)
+    for key in A.GROUPS:
         np.testing.assert_array_equal(sb[key][0][:k], sa[key][0][:n][keep])
         np.testing.assert_array_equal(sb[key][1][:k], sa[key][1][:n][keep])
 

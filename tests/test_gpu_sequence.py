@@ -67,18 +67,20 @@ def test_frame_to_frame_tracking_follows_oracle():
     tr.close()
 
 
-def test_slam_loop_builds_a_map_and_tracks():
+@pytest.mark.parametrize("iso", [False, True])
+def test_slam_loop_builds_a_map_and_tracks(iso):
     """Sec. III on the first 13 frames of the long sequence's path (QVGA): first-frame
     Gaussians, tracking, keyframes every 4 frames with silhouette-driven additions, 30
-    mapping iterations per keyframe (100 on the first), removal.  The trajectory stays
-    within a few cm of the truth, the map grows on the keyframes and renders the
-    keyframes back recognisably."""
+    mapping iterations per keyframe (100 on the first), removal; with anisotropic
+    Gaussians and with the isotropic ones of Eq. 1.  The trajectory stays within a few cm
+    of the truth, the map grows on the keyframes and renders the keyframes back
+    recognisably."""
     poses = scenes.spline_trajectory(200, seed=2)[:13]
     frames = []
     for p in poses:
         rgb, depth = scenes.raycast_room_torch(p, CAM, seed=2, device="cuda")
         frames.append((rgb, depth, None))
-    cfg = slam.SlamConfig(capacity=400_000, lowp=torch.float16)
+    cfg = slam.SlamConfig(capacity=400_000, lowp=torch.float16, isotropic=iso)
     S = slam.Slam(CAM, cfg)
     for k in range(len(poses)):
         S.process(k, *frames[k], first_pose=poses[0] if k == 0 else None)
