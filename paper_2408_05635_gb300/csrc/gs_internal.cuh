@@ -28,6 +28,10 @@ constexpr int kBlock = 256;               // threads per Gaussian-parallel block
 constexpr int kWarps = kBlock / 32;       // warps per Gaussian-parallel block
 constexpr int kCell = kBlock;             // Gaussians (and record slots) per cell
 constexpr int kBatch = 256;               // Gaussians staged per compositing batch
+// The compositors stage one Gaussian per thread of the tile block (shared arrays of
+// kBatch entries indexed by the thread) and zero one accumulator row per thread: the
+// batch depth must equal the block size.
+static_assert(kBatch == kTile * kTile, "compositor staging assumes one staged Gaussian per tile thread");
 
 enum ErrFlag : uint32_t { kErrRecords = 1u, kErrPairs = 2u, kErrTimeout = 4u };
 
