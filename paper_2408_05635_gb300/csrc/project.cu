@@ -301,7 +301,33 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
         const float x = cam_coord(sRt, 0, mx, my, mz);
         const float y = cam_coord(sRt, 1, mx, my, mz);
         const float z = cam_coord(sRt, 2, mx, my, mz);
-        if (z > S.z_near) {
+        bool reach = z > S.z_near;
+        if (reach && S.alpha_min > 0.f) {
+            // Early reject of a Gaussian whose support cannot reach the image, before the
+            // covariance (it pays off when a warp's Gaussians are spatial neighbours, as in a
+            // map built frame by frame): Sigma'_xx = |J0 M|^2 + e <= |J0|^2 s_max^2 + e
+            // (M = W Rg diag(s), W and Rg orthonormal; J0 the first row of the clamped
+            // Jacobian) and the support radius^2 is at most 2 ln(1 / alpha_min).  Widened by
+            // 1 % and 3 px, so a Gaussian dropped here would also fail record_rect's box test.
+            float lsm;
+            if constexpr (ISO) {
+                lsm = ld_attr<DT>(L.g.log_scales, i);
+            } else {
+                lsm = fmaxf(fmaxf(ld_attr<DT>(L.g.log_scales, 3 * i), ld_attr<DT>(L.g.log_scales, 3 * i + 1)),
+                            ld_attr<DT>(L.g.log_scales, 3 * i + 2));
+            }
+            const float sm2 = __expf(2.f * lsm);
+            const float iz = __fdividef(1.f, z);
+            const float tx = fminf(fmaxf(x * iz, -vi.tan_lim_x), vi.tan_lim_x);
+            const float ty = fminf(fmaxf(y * iz, -vi.tan_lim_y), vi.tan_lim_y);
+            const float r2 = -2.f * __logf(S.alpha_min);
+            const float hx = 1.01f * sqrtf(r2 * (vi.fx * vi.fx * iz * iz * (1.f + tx * tx) * sm2 + S.dilation)) + 3.f;
+            const float hy = 1.01f * sqrtf(r2 * (vi.fy * vi.fy * iz * iz * (1.f + ty * ty) * sm2 + S.dilation)) + 3.f;
+            const float mu_x = vi.fx * x * iz + vi.cx, mu_y = vi.fy * y * iz + vi.cy;
+            reach = mu_x + hx >= 0.f && mu_x - hx <= (float)(vi.width - 1) && mu_y + hy >= 0.f &&
+                    mu_y - hy <= (float)(vi.height - 1);
+        }
+        if (reach) {
             // M = W Rg diag(s): Sigma_c = M M^T (isotropic: M = s W)
             float M[9];
             if constexpr (ISO) {
@@ -421,25 +447,29 @@ cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Resident blocks per SM the emission is compiled for: six fit a 200k-Gaussian view's 782
-// cells in one wave on 152 SMs (at the cost of a few spilled registers).
-#ifndef GS_EMIT_MIN_BLOCKS
-#define GS_EMIT_MIN_BLOCKS 6
-#endif
-constexpr int kEmitMinBlocks = GS_EMIT_MIN_BLOCKS;
+// The emission runs kEmitThreads threads per block, kCell / kEmitThreads blocks per cell,
+// compiled for kEmitMinBlocks resident blocks per SM (64 registers a thread).
+constexpr int kEmitThreads = 64;
+constexpr int kEmitMinBlocks = 16;
+static_assert(kCell % kEmitThreads == 0 && kEmitThreads % 32 == 0, "emission blocks split cells into warps");
 
 // One key per (record, tile met): depth bits (positive floats sort as unsigned ints) in
 // the high word, the record in the low word, stored at the next free slot of the tile's
 // sub-bucket.  One block per cell, one thread per record (record_tiles).
-__global__ void __launch_bounds__(kBlock, kEmitMinBlocks) k_emit(WsPtrs ws, Dims d) {
-    const uint32_t cell = blockIdx.x;
+__global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws, Dims d) {
+    // kCell / kEmitThreads blocks per cell, each taking a quarter of the cell's slots: a
+    // cell full of visible Gaussians (neighbours in a map built frame by frame) is spread
+    // over several SMs instead of running as one long block, and empty quarters leave at once
+    const uint32_t cell = blockIdx.x / (uint32_t)(kCell / kEmitThreads);
+    const uint32_t first = (blockIdx.x % (uint32_t)(kCell / kEmitThreads)) * (uint32_t)kEmitThreads;
     const uint32_t cnt = ws.cell_cnt[cell];
-    if ((uint32_t)(threadIdx.x & ~31u) >= cnt) return;  // whole warps without records leave
+    const uint32_t slot_id = first + threadIdx.x;  // the record slot of this thread in the cell
+    if ((slot_id & ~31u) >= cnt) return;  // whole warps without records leave
     const int lane = threadIdx.x & 31;
     const int view = (int)(cell / (uint32_t)d.nblk);
     const ViewInfo vi = ws.views[view];
-    const uint32_t r = cell * kCell + threadIdx.x;
-    const bool mine = threadIdx.x < cnt;
+    const uint32_t r = cell * kCell + slot_id;
+    const bool mine = slot_id < cnt;
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A;
     uint32_t sub = 0;
     if (mine) {
@@ -448,7 +478,7 @@ __global__ void __launch_bounds__(kBlock, kEmitMinBlocks) k_emit(WsPtrs ws, Dims
         B = rec.b;
         sub = (uint32_t)((uint64_t)__float_as_uint(rec.c.w) % (uint64_t)d.n) & (d.S - 1);
     }
-    const uint32_t rbase = cell * kCell + (threadIdx.x & ~31u);
+    const uint32_t rbase = cell * kCell + (slot_id & ~31u);
     // small rectangles: this lane alone, slot atomics issued eight at a time before the
     // dependent stores, so a record waits for about one atomic round trip per eight tiles
     int tx0 = 1, tx1 = 0, ty0 = 1, ty1 = 0;
@@ -499,7 +529,8 @@ __global__ void __launch_bounds__(kBlock, kEmitMinBlocks) k_emit(WsPtrs ws, Dims
 }
 
 cudaError_t launch_emit(const WsPtrs &ws, const Dims &d, cudaStream_t st) {
-    k_emit<<<(uint32_t)d.V * (uint32_t)d.nblk, kBlock, 0, st>>>(ws, d);
+    const uint32_t cells = (uint32_t)d.V * (uint32_t)d.nblk;
+    k_emit<<<cells * (uint32_t)(kCell / kEmitThreads), kEmitThreads, 0, st>>>(ws, d);
     return cudaGetLastError();
 }
 

@@ -189,11 +189,29 @@ def _texture(rect: _Rect, a: np.ndarray, b: np.ndarray) -> np.ndarray:
     return np.clip(c, 0.0, 1.0)
 
 
+def morton_codes(points: np.ndarray, cell: float) -> np.ndarray:
+    """Morton (Z-order) codes of points quantised to `cell`-sized cubes (21 bits per axis)."""
+    q = np.clip(np.floor((points - points.min(axis=0)) / cell), 0, (1 << 21) - 1).astype(np.uint64)
+
+    def spread(x):
+        x = x & np.uint64(0x1FFFFF)
+        x = (x | (x << np.uint64(32))) & np.uint64(0x1F00000000FFFF)
+        x = (x | (x << np.uint64(16))) & np.uint64(0x1F0000FF0000FF)
+        x = (x | (x << np.uint64(8))) & np.uint64(0x100F00F00F00F00F)
+        x = (x | (x << np.uint64(4))) & np.uint64(0x10C30C30C30C30C3)
+        x = (x | (x << np.uint64(2))) & np.uint64(0x1249249249249249)
+        return x
+
+    return spread(q[:, 0]) | (spread(q[:, 1]) << np.uint64(1)) | (spread(q[:, 2]) << np.uint64(2))
+
+
 def room_scene(n: int, seed: int = 0, log_scale_mu: float = -4.0, log_scale_sigma: float = 0.4,
-               logit_mu: float = 2.0, logit_sigma: float = 1.0, jitter_m: float = 0.005) -> Gaussians:
+               logit_mu: float = 2.0, logit_sigma: float = 1.0, jitter_m: float = 0.005,
+               ordered: bool = True) -> Gaussians:
     """`n` Gaussians with means sampled area-uniformly on the room's surfaces plus
     N(0, 5 mm) jitter along the normal, log-scales N(-4, 0.4), random quaternions,
-    logits N(2, 1) and the room texture as colour."""
+    logits N(2, 1) and the room texture as colour; listed along a Morton curve of their
+    means (ordered=False keeps the sampling order)."""
     rng = np.random.default_rng(seed)
     rects = room_rects(seed)
     areas = np.array([r.su * r.sv for r in rects])
@@ -211,6 +229,11 @@ def room_scene(n: int, seed: int = 0, log_scale_mu: float = -4.0, log_scale_sigm
     log_scales = rng.normal(log_scale_mu, log_scale_sigma, size=(n, 3))
     quats = _random_quats(rng, n)
     logits = rng.normal(logit_mu, logit_sigma, size=n)
+    if ordered:
+        # a map built frame by frame lists neighbouring Gaussians together; so does this
+        # one, along a Morton curve of the means (1 cm cells)
+        order = np.argsort(morton_codes(means, 0.01), kind="stable")
+        means, rgb, log_scales, quats, logits = means[order], rgb[order], log_scales[order], quats[order], logits[order]
     return Gaussians(means.astype(np.float32), quats, log_scales.astype(np.float32),
                      logits.astype(np.float32), rgb.astype(np.float32))
 
