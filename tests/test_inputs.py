@@ -1,6 +1,7 @@
 """The seeded input generators: the torch ray-caster reproduces the numpy one, and the
 long sequence's camera path moves by trackable steps."""
 import numpy as np
+import pytest
 
 from paper_2408_05635_gb300 import scenes
 
@@ -25,3 +26,23 @@ def test_spline_steps_are_trackable():
     assert step.max() < 0.1 and max(ang) < 8.0
     X, Y, Z = scenes.ROOM
     assert np.all(c[:, 0] > 0.5) and np.all(c[:, 0] < X - 0.5) and np.all(c[:, 2] > 0.5) and np.all(c[:, 2] < Z - 0.5)
+
+
+def test_camera_centres_and_trajectory_report():
+    """The sequence driver's camera centres and the bench's trajectory report against the
+    metric oracle's independent definitions (closed forms of a shifted trajectory)."""
+    import bench
+    from oracle import metrics as omx
+    from paper_2408_05635_gb300 import slam
+    poses = np.asarray(scenes.spline_trajectory(30, seed=4))
+    np.testing.assert_allclose(slam.camera_centres(poses), [omx.camera_centre(p) for p in poses], atol=1e-12)
+    rep = bench._trajectory_report(poses, poses)
+    assert rep["ate_rmse_cm"] == 0.0 and rep["max_rot_err_deg"] == 0.0
+    shifted = []
+    for p in poses:
+        R, t = scenes.pose_rt(p)
+        shifted.append(scenes.pose_from_rt(R, t - R @ np.array([0.0, 0.03, 0.04])))
+    rep = bench._trajectory_report(np.asarray(shifted), poses)
+    ref = omx.trajectory_errors(shifted, poses)
+    assert rep["ate_rmse_cm"] == pytest.approx(5.0, abs=1e-6)
+    assert rep["ate_rmse_cm"] == pytest.approx(100 * ref["ate_rmse"], abs=1e-6)
