@@ -57,7 +57,26 @@ def _args():
                     help="timed windows of the mapping leg (0 skips it)")
     ap.add_argument("--sequence-frames", type=int, default=200,
                     help="frames of the long-sequence leg (0 skips it)")
+    ap.add_argument("--autotune-reps", type=int, default=10,
+                    help="passes per setting of the launch-schedule autotuner before the tracking and batched "
+                         "legs (0: the default schedule)")
+    ap.add_argument("--schedule", default=None,
+                    help="fixed launch schedule 'sub_buckets,fwd_batch,bwd_batch' instead of tuning")
     return ap.parse_args()
+
+
+def apply_schedule(a, R, prob, g, poses, targets) -> dict:
+    """The launch schedule of a leg: fixed by --schedule, else picked by the library's
+    autotuner on the leg's own problem (gs_autotune), else the default."""
+    if a.schedule:
+        sb, fb, bb = (int(x) for x in a.schedule.split(","))
+        R.set_schedule(sb, fb, bb)
+        return {"schedule": R.schedule, "tuned": False}
+    if a.autotune_reps > 0:
+        res = R.autotune(prob, g, poses, targets, pose_only=True, reps=a.autotune_reps)
+        res["tuned"] = True
+        return res
+    return {"schedule": R.schedule, "tuned": False}
 
 
 def workload(seed: int = 0):
@@ -320,6 +339,7 @@ def run_batched(a, dev, stream):
     gtb = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=torch.bfloat16)
     poses = start.clone()
     prob = R.plan(gtb, cams, poses, margin=1.5)
+    sched = apply_schedule(a, R, prob, gtb, poses, (t_rgb, t_depth, t_prior))
     ws, nb = R.workspace(prob)
     tg = gs.gs_targets(t_rgb.data_ptr(), t_depth.data_ptr(), t_prior.data_ptr())
     adam = torch.zeros(V, 16, dtype=torch.float64, device=dev)
@@ -354,6 +374,7 @@ def run_batched(a, dev, stream):
     # plain: one hypothesis per keyframe, one call per view, FP32 attributes
     gtf = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=torch.float32)
     Rp = gs.Rasterizer(gs.Config(), device=dev)
+    Rp_sched = Rp.schedule  # the default: the plain form is the untuned baseline
     sub = [int(np.flatnonzero(frame_of == f)[0]) for f in range(BATCH_FRAMES)]
     off = np.concatenate([[0], np.cumsum(pix)])
     plain_ms, rel = 0.0, []
@@ -387,10 +408,11 @@ def run_batched(a, dev, stream):
                     f"1200x680), {N_BATCH_GAUSS // 1000}k room Gaussians",
         "views": V, "pixels_per_step": P, "workspace_gb": round(ws_bytes / 1e9, 2),
         "batched_bf16": {"ms_per_step": b_ms, "view_iters_per_s": batched_view_its, "mpix_per_s": P / b_ms / 1e3,
-                         "launch": "one gs_track_step call (one CUDA graph) for all views", "kernels_us": kernels},
+                         "launch": "one gs_track_step call (one CUDA graph) for all views", "kernels_us": kernels,
+                         "launch_schedule": sched},
         "plain_fp32": {"views_timed": len(sub), "ms_per_view_iter": plain_ms / len(sub),
                        "view_iters_per_s": plain_view_its, "mpix_per_s": sub_pix / plain_ms / 1e3,
-                       "launch": "one gs_track_step call per view"},
+                       "launch": "one gs_track_step call per view", "launch_schedule": Rp_sched},
         "speedup_view_iters": batched_view_its / plain_view_its,
         "pose_grad_rel_diff_bf16_vs_fp32": {"max": max(rel), "median": float(np.median(rel))},
         "l2": "working set far above L2 (no flush)",
@@ -585,6 +607,7 @@ def main():
     frame_dev = torch.tensor(np.concatenate([rgb.reshape(-1), depth.reshape(-1), prior.reshape(-1)]), device=dev)
     t_rgb, t_depth, t_prior = frame_dev[:3 * P_px], frame_dev[3 * P_px:4 * P_px], frame_dev[4 * P_px:]
     targets = gs.gs_targets(t_rgb.data_ptr(), t_depth.data_ptr(), t_prior.data_ptr())
+    sched = apply_schedule(a, R, prob, gt, poses, (t_rgb, t_depth, t_prior))
     adam = torch.zeros(1, 16, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
     stream = torch.cuda.current_stream(dev)
@@ -697,7 +720,8 @@ def main():
             "config": {"workload": WORKLOAD, "width": cam.width, "height": cam.height, "gaussians": N_GAUSS,
                        "pairs": int(counts.n_pairs), "records": int(counts.n_records),
                        "max_tile_pairs": int(counts.max_tile),
-                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
+                       "launch_schedule": sched},
             "tracking_iters_per_s": iters_per_s,
             "e2e": {"value": e2e_mpix, "unit": "Mpix/s",
                     "h2d_bytes_per_step": int(h_frame.numel() * h_frame.element_size()),

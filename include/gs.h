@@ -254,6 +254,57 @@ gs_status gs_set_profiling_mask(gs_ctx *ctx, uint32_t mask);
  * number available.  Errors: STATE (profiling off or nothing recorded), CUDA. */
 gs_status gs_kernel_times(gs_ctx *ctx, gs_kernel_time *out, int32_t cap, int32_t *count);
 
+/* ------------------------------------------------------------------ launch schedule */
+
+/* How the context launches the binning and the two compositors.  None of these change
+ * a result beyond FP32 summation order: the sub-buckets only split where a tile's pairs
+ * are counted and placed (the tile's list is sorted whole), and the batch depth only
+ * sets how many of a tile's depth-sorted Gaussians the tile block stages into shared
+ * memory at a time (every pixel still composites them in the same order).  The tile is
+ * 16 x 16 with one thread per pixel in every schedule. */
+typedef struct {
+    int32_t sub_buckets; /* counters per tile for the pair count and key emission: 1, 2
+                            or 4 (4; fewer are used when tiles x 4 exceeds 2^22)       */
+    int32_t fwd_batch;   /* Gaussians staged per forward batch: 64, 128 or 256 (256)   */
+    int32_t bwd_batch;   /* Gaussians staged per backward batch: 64, 128 or 256 (256)  */
+    int32_t reserved;    /* 0 */
+} gs_schedule;
+
+/* Read the context's schedule (defaults after gs_create).  Errors: INVALID_ARG (NULL). */
+gs_status gs_get_schedule(const gs_ctx *ctx, gs_schedule *out);
+
+/* Set the schedule used by every later call on the context (a cached tracking graph is
+ * rebuilt on its next use).  The workspace size does not depend on it.  Errors:
+ * INVALID_ARG (NULL, or a value outside the sets above). */
+gs_status gs_set_schedule(gs_ctx *ctx, const gs_schedule *sched);
+
+/* One measurement of gs_autotune. */
+typedef struct {
+    int32_t stage; /* 0: binning (projection, scan, emission) timed per sub_buckets;
+                      1: forward compositing (with the fused loss) per fwd_batch;
+                      2: backward compositing per bwd_batch                          */
+    int32_t value; /* the sub_buckets / fwd_batch / bwd_batch setting timed          */
+    float ms;      /* mean device time of one pass of the stage (CUDA events on the
+                      stream, warm caches, after one untimed pass)                   */
+} gs_tune_entry;
+
+/* Autotuner of the launch schedule for one problem: on the given Gaussians, poses and
+ * targets it times, stage after stage, every sub-bucket count (binning), every forward
+ * batch depth and every backward batch depth (the pose-only walk of tracking when
+ * pose_only != 0, the walk for all Gaussian parameters otherwise), `reps` passes each,
+ * keeps the fastest setting of each stage for the next stage and sets it on the
+ * context.  It uses the workspace (sized by gs_workspace_size for `prob`) as gs_project
+ * does and synchronises `stream`, so it cannot be captured into a graph; afterwards no
+ * projection is bound (call gs_project or gs_track_step next).  table (host, cap
+ * entries, may be NULL) receives the measurements in order, *count (may be NULL) their
+ * number (9 at most); best (may be NULL) the chosen schedule.  A capacity overflow
+ * during the passes is reported as CAPACITY (the schedule is then left unchanged).
+ * Errors: INVALID_ARG (as gs_project; targets without rgb or depth; reps outside
+ * [1, 1000]), WORKSPACE, CAPACITY, CUDA. */
+gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const double *poses,
+                      const gs_targets *targets, int32_t pose_only, int32_t reps, void *ws, size_t ws_bytes,
+                      gs_tune_entry *table, int32_t cap, int32_t *count, gs_schedule *best, void *stream);
+
 /* ------------------------------------------------------------------ scene optimisation */
 
 /* The map as the scene optimisation holds it (Sec. III-C).  Device arrays with room for

@@ -41,10 +41,11 @@ struct GraphKey {
     std::vector<ViewInfo> views;
     uint32_t pair_cap = 0;
     uint32_t prof_mask = 0;
+    uint32_t sched[3] = {};  // sub-buckets, forward and backward batch depths
     bool operator==(const GraphKey &o) const {
         if (ws != o.ws || ws_bytes != o.ws_bytes || n != o.n || dtype != o.dtype || iters != o.iters ||
-            pair_cap != o.pair_cap || prof_mask != o.prof_mask ||
-            views.size() != o.views.size())
+            pair_cap != o.pair_cap || prof_mask != o.prof_mask || sched[0] != o.sched[0] ||
+            sched[1] != o.sched[1] || sched[2] != o.sched[2] || views.size() != o.views.size())
             return false;
         for (int k = 0; k < 12; ++k)
             if (ptrs[k] != o.ptrs[k]) return false;
@@ -57,6 +58,7 @@ struct GraphKey {
 struct gs_ctx {
     gs_config cfg{};
     Settings s{};
+    gs_schedule sched{gsk::kSubMax, gsk::kBatch, gsk::kBatch, 0};
     std::string err;
     // state bound by the last gs_project
     bool bound = false;
@@ -209,8 +211,13 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     }
     d.T = (uint32_t)T;
     d.P = (uint32_t)P;
-    d.S = 4;
-    while (d.S > 1 && (uint64_t)d.T * d.S > (1ull << 22)) d.S >>= 1;
+    // the layout has room for kSubMax counters per tile (fewer for huge tile counts), so
+    // the workspace size does not depend on the schedule, which may use fewer
+    uint32_t s_lay = kSubMax;
+    while (s_lay > 1 && (uint64_t)d.T * s_lay > (1ull << 22)) s_lay >>= 1;
+    d.S = std::min(s_lay, (uint32_t)ctx->sched.sub_buckets);
+    d.fwd_batch = (uint32_t)ctx->sched.fwd_batch;
+    d.bwd_batch = (uint32_t)ctx->sched.bwd_batch;
     out.d = d;
     Layout &L = out.lay;
     size_t o = 0;
@@ -222,14 +229,14 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     L.err = take(sizeof(uint32_t));
     // zeroed before every projection: [hdr, zero_end)
     L.hdr = take(sizeof(DevHeader));
-    L.tile_cnt = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
+    L.tile_cnt = take(sizeof(uint32_t) * ((size_t)d.T * s_lay + 1));
     L.zero_end = o;
     const size_t cells = (size_t)d.V * d.nblk;
     L.views = take(sizeof(ViewInfo) * d.V);
     L.view_rt = take(sizeof(float) * 12 * d.V);
     L.cell_cnt = take(sizeof(uint32_t) * cells);
-    L.tile_start = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
-    L.cursor = take(sizeof(uint32_t) * ((size_t)d.T * d.S + 1));
+    L.tile_start = take(sizeof(uint32_t) * ((size_t)d.T * s_lay + 1));
+    L.cursor = take(sizeof(uint32_t) * ((size_t)d.T * s_lay + 1));
     L.tile_order = take(sizeof(uint32_t) * (size_t)d.T);
     L.rec = take(sizeof(Rec) * cells * kCell);
     L.rec_grad = take(sizeof(RecGrad) * cells * kCell);
@@ -327,6 +334,34 @@ cudaError_t enqueue_forward(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, con
     if ((e = mark_begin(ctx, st, "k_forward")) != cudaSuccess) return e;
     if ((e = launch_forward(F, st)) != cudaSuccess) return e;
     return mark(ctx, st, "k_forward");
+}
+
+bool valid_batch(int32_t b) { return b == 64 || b == 128 || b == 256; }
+
+// Device time of one pass of `enqueue`, averaged over `reps` passes after one untimed
+// pass, with two events on the stream.
+template <class F>
+cudaError_t time_passes(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, int reps, F &&enqueue, float &ms) {
+    cudaError_t e = enqueue();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e0, s)) != cudaSuccess) return e;
+    for (int r = 0; r < reps; ++r)
+        if ((e = enqueue()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+    float t = 0.f;
+    if ((e = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) return e;
+    ms = t / (float)reps;
+    return cudaSuccess;
+}
+
+// The fastest candidate, unless it is within 1 % of the first (the default), which then
+// stays: timing noise does not move the schedule.
+int pick(const float *ms, int n) {
+    int b = 0;
+    for (int k = 1; k < n; ++k)
+        if (ms[k] < ms[b]) b = k;
+    return ms[b] < 0.99f * ms[0] ? b : 0;
 }
 
 }  // namespace
@@ -611,6 +646,9 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
         key.views = pr.views;
         key.pair_cap = pr.d.pair_cap;
         key.prof_mask = ctx->prof_mask;
+        key.sched[0] = pr.d.S;
+        key.sched[1] = pr.d.fwd_batch;
+        key.sched[2] = pr.d.bwd_batch;
         if (!ctx->graph_exec || !(ctx->graph_key == key)) {
             if (ctx->graph_exec) {
                 cudaGraphExecDestroy(ctx->graph_exec);
@@ -653,6 +691,142 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
     ctx->poses = poses;
     ctx->have_loss = true;
     ctx->grads_used = true;
+    return GS_OK;
+}
+
+gs_status gs_get_schedule(const gs_ctx *ctx, gs_schedule *out) {
+    if (!ctx || !out) return GS_ERR_INVALID_ARG;
+    *out = ctx->sched;
+    return GS_OK;
+}
+
+gs_status gs_set_schedule(gs_ctx *ctx, const gs_schedule *sched) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!sched) return fail(ctx, GS_ERR_INVALID_ARG, "schedule is NULL");
+    const int32_t sb = sched->sub_buckets;
+    if ((sb != 1 && sb != 2 && sb != 4) || !valid_batch(sched->fwd_batch) || !valid_batch(sched->bwd_batch) ||
+        sched->reserved != 0)
+        return fail(ctx, GS_ERR_INVALID_ARG, "sub_buckets must be 1, 2 or 4 and batch depths 64, 128 or 256");
+    ctx->sched = *sched;
+    return GS_OK;
+}
+
+gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const double *poses,
+                      const gs_targets *targets, int32_t pose_only, int32_t reps, void *ws, size_t ws_bytes,
+                      gs_tune_entry *table, int32_t cap, int32_t *count, gs_schedule *best, void *stream) {
+    if (!ctx) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (reps < 1 || reps > 1000) return fail(ctx, GS_ERR_INVALID_ARG, "reps must be in [1, 1000]");
+    if (cap < 0 || (cap > 0 && !table)) return fail(ctx, GS_ERR_INVALID_ARG, "table is NULL or cap negative");
+    if (!targets || !targets->rgb || !targets->depth) return fail(ctx, GS_ERR_INVALID_ARG, "targets need rgb and depth");
+    if (!poses) return fail(ctx, GS_ERR_INVALID_ARG, "poses is NULL");
+    Problem pr;
+    gs_status st = build_problem(ctx, prob, pr);
+    if (st != GS_OK) return st;
+    if ((st = check_gaussians(ctx, g, pr)) != GS_OK) return st;
+    if (!ws || ws_bytes < pr.lay.total || (reinterpret_cast<uintptr_t>(ws) % kAlign) != 0)
+        return fail(ctx, GS_ERR_WORKSPACE, "workspace NULL, smaller than gs_workspace_size or not 256-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &capst);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream query");
+    if (capst != cudaStreamCaptureStatusNone)
+        return fail(ctx, GS_ERR_INVALID_ARG, "gs_autotune synchronises and cannot be captured");
+    const WsPtrs w = ws_ptrs(ws, pr.lay);
+    const GaussPtrs gp{g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb};
+    // the passes overwrite whatever projection was bound; no profiling markers inside them
+    ctx->bound = false;
+    const uint32_t prof_saved = ctx->prof_mask;
+    ctx->prof_mask = 0;
+    reset_marks(ctx);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    gs_tune_entry ent[9];
+    int n_ent = 0;
+    gs_schedule chosen = ctx->sched;
+    // the layout's sub-bucket room: the most counters per tile this problem can use
+    uint32_t s_lay = kSubMax;
+    while (s_lay > 1 && (uint64_t)pr.d.T * s_lay > (1ull << 22)) s_lay >>= 1;
+    const int subs[3] = {4, 2, 1}, batches[3] = {256, 128, 64};  // the defaults first
+    Dims d = pr.d;
+    Problem run;
+    run.views = pr.views;
+    run.lay = pr.lay;
+    auto stage = [&](int which, const int *cand, int ncand, auto &&enqueue_for, int &pick_out) -> cudaError_t {
+        float ms[3];
+        int vals[3], nv = 0;
+        for (int k = 0; k < ncand; ++k) {
+            if (which == 0 && (uint32_t)cand[k] > s_lay) continue;
+            vals[nv] = cand[k];
+            cudaError_t r = time_passes(s, ev[0], ev[1], reps, [&]() { return enqueue_for(cand[k]); }, ms[nv]);
+            if (r != cudaSuccess) return r;
+            ent[n_ent++] = gs_tune_entry{which, cand[k], ms[nv]};
+            ++nv;
+        }
+        pick_out = vals[pick(ms, nv)];
+        return cudaSuccess;
+    };
+    e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (e == cudaSuccess) e = upload_views(pr, w, ws, s);
+    // stage 0: binning per sub-bucket count (the scan leaves every counter zero again)
+    if (e == cudaSuccess)
+        e = stage(0, subs, 3,
+                  [&](int S) {
+                      run.d = d;
+                      run.d.S = (uint32_t)S;
+                      return enqueue_project(ctx, run, w, gp, g->dtype_attr, poses, s);
+                  },
+                  chosen.sub_buckets);
+    if (e == cudaSuccess) {
+        d.S = (uint32_t)chosen.sub_buckets;
+        run.d = d;
+        e = enqueue_project(ctx, run, w, gp, g->dtype_attr, poses, s);
+    }
+    // stage 1: forward compositing with the fused loss per batch depth (idempotent passes)
+    if (e == cudaSuccess)
+        e = stage(1, batches, 3,
+                  [&](int nb) {
+                      run.d = d;
+                      run.d.fwd_batch = (uint32_t)nb;
+                      return enqueue_forward(ctx, run, w, targets, nullptr, nullptr, nullptr, s);
+                  },
+                  chosen.fwd_batch);
+    // stage 2: backward compositing per batch depth (the passes add into the record
+    // accumulators again and again; nothing reads them before the next projection)
+    if (e == cudaSuccess) {
+        d.fwd_batch = (uint32_t)chosen.fwd_batch;
+        e = stage(2, batches, 3,
+                  [&](int nb) {
+                      BackwardLaunch B;
+                      B.ws = w;
+                      B.d = d;
+                      B.d.bwd_batch = (uint32_t)nb;
+                      B.s = ctx->s;
+                      B.up_rgb = w.upstream;
+                      B.up_depth = w.upstream + 3u * d.P;
+                      B.up_sil = w.upstream + 4u * d.P;
+                      B.pose_only = pose_only != 0;
+                      return launch_backward(B, s);
+                  },
+                  chosen.bwd_batch);
+    }
+    uint32_t err = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&err, w.err, sizeof(err), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && err) e = cudaMemset(w.err, 0, sizeof(err));
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    ctx->prof_mask = prof_saved;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+    if (table)
+        for (int k = 0; k < n_ent && k < cap; ++k) table[k] = ent[k];
+    if (count) *count = n_ent;
+    if (err & (kErrRecords | kErrPairs | kErrTimeout))
+        return fail(ctx, (err & kErrTimeout) ? GS_ERR_TIMEOUT : GS_ERR_CAPACITY,
+                    "the problem overflowed its capacities during tuning; schedule unchanged");
+    ctx->sched = chosen;
+    if (best) *best = chosen;
     return GS_OK;
 }
 

@@ -27,11 +27,13 @@ constexpr int kTilePix = kTile * kTile;   // pixels (= threads) per tile block
 constexpr int kBlock = 256;               // threads per Gaussian-parallel block
 constexpr int kWarps = kBlock / 32;       // warps per Gaussian-parallel block
 constexpr int kCell = kBlock;             // Gaussians (and record slots) per cell
-constexpr int kBatch = 256;               // Gaussians staged per compositing batch
-// The compositors stage one Gaussian per thread of the tile block (shared arrays of
-// kBatch entries indexed by the thread) and zero one accumulator row per thread: the
-// batch depth must equal the block size.
-static_assert(kBatch == kTile * kTile, "compositor staging assumes one staged Gaussian per tile thread");
+constexpr int kBatch = 256;               // default (and largest) compositing batch depth
+// The compositors are compiled for batch depths 64, 128 and 256 (Gaussians staged into
+// shared memory per batch).  The first NB threads of the tile block stage one Gaussian
+// each and own one accumulator row each, and the per-warp lists hold batch positions as
+// bytes: NB must not exceed the block size nor 256.
+static_assert(kBatch <= kTilePix && kBatch <= 256, "a batch stages at most one Gaussian per tile thread");
+constexpr int kSubMax = 4;                // most per-tile sub-buckets a workspace is laid out for
 
 enum ErrFlag : uint32_t { kErrRecords = 1u, kErrPairs = 2u, kErrTimeout = 4u };
 
@@ -132,12 +134,14 @@ struct Dims {
     int32_t V;             // views
     int32_t nblk;          // ceil(n / kBlock): cells per view
     uint32_t T;            // tiles over all views
-    uint32_t S;            // sub-buckets per tile (power of two): a tile's pairs are counted and
+    uint32_t S;            // sub-buckets per tile (1, 2 or 4): a tile's pairs are counted and
                            // placed through S counters picked by Gaussian index, so no single
                            // counter takes every pair of a crowded tile; the S sub-ranges are
                            // contiguous, so the tile's list is still one range
     uint32_t P;            // pixels over all views
     uint32_t pair_cap;
+    uint32_t fwd_batch;    // Gaussians staged per forward batch: 64, 128 or 256 (0: kBatch)
+    uint32_t bwd_batch;    // Gaussians staged per backward batch: 64, 128 or 256 (0: kBatch)
 };
 
 struct Settings {

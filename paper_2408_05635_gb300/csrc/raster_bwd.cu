@@ -16,8 +16,10 @@
 // are taken of the moments dp (dx, dy, dx^2, dx dy, dy^2), dp = dL/dpower, and the conic is
 // applied once per (tile, Gaussian) when the sums are flushed.
 //
-// Each warp owns an 8 x 4 patch of the tile and walks, back to front, only the staged
-// Gaussians whose support box meets the patch and that precede its last contributor.
+// Batches of NB records (64, 128 or 256, the batch depth, picked per context) are staged
+// by the first NB threads, from the tile's last contributor backwards.  Each warp owns an
+// 8 x 4 patch of the tile and walks, back to front, only the staged Gaussians whose
+// support box meets the patch and that precede its last contributor.
 // Reduction: every (pixel, Gaussian) term is summed over the warp with a butterfly
 // reduce-scatter (for the pose-only walk 6 values in 8 shuffles, or two Gaussians' 12 in
 // 13 when it steps two at a time; 16 values in 16 otherwise),
@@ -120,12 +122,13 @@ __device__ __forceinline__ void bwd_step6(bool c, const PolyEval &pe, float4 Cc,
 // Shared accumulator slots per staged Gaussian: 0, 1 sum dp dx, dp dy; 2 sum a T g_D;
 // 3 sum dL/da a_raw; 4..6 sum dp dx^2, dp dx dy, dp dy^2; 8..10 sum a T g_C; 7, 11 unused.
 // POSE: only slots 0, 1, 2, 4, 5, 6 (what the pose gradient needs).
-template <bool POSE>
+template <bool POSE, int NB>
 __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
-    __shared__ float4 sP0[kBatch], sC[kBatch], sQ[kBatch], sBox[kBatch];
-    __shared__ float2 sP1[kBatch];
-    __shared__ float sAcc[kBatch * kAccStride];
-    __shared__ uint8_t sList[kTilePix / 32][kBatch];
+    static_assert(NB % 32 == 0 && NB <= kBatch, "batch depth: a multiple of 32, at most kBatch");
+    __shared__ float4 sP0[NB], sC[NB], sQ[NB], sBox[NB];
+    __shared__ float2 sP1[NB];
+    __shared__ float sAcc[NB * kAccStride];
+    __shared__ uint8_t sList[kTilePix / 32][NB];
     __shared__ int s_view;
     __shared__ uint32_t s_nmax;
     const uint32_t tile = L.ws.tile_order[blockIdx.x];
@@ -197,8 +200,8 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     float GB = 0.f;  // g . (colour, depth, 1) of everything behind, back-to-front
     uint32_t n_eval = 0, n_contrib = 0;
 
-    for (int64_t b0 = nmax ? (int64_t)((nmax - 1) / kBatch) * kBatch : -1; b0 >= 0; b0 -= kBatch) {
-        const int cnt = (int)min((uint32_t)kBatch, nmax - (uint32_t)b0);
+    for (int64_t b0 = nmax ? (int64_t)((nmax - 1) / NB) * NB : -1; b0 >= 0; b0 -= NB) {
+        const int cnt = (int)min((uint32_t)NB, nmax - (uint32_t)b0);
         if (tid < cnt) {
             const uint32_t r = L.ws.sorted[start + (uint32_t)b0 + tid];
             if (r < rec_slots(L.d)) {
@@ -213,8 +216,10 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
                 sBox[tid] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
             }
         }
+        if (tid < NB) {  // thread tid owns the accumulator row of batch position tid
 #pragma unroll
-        for (int k = 0; k < kAccStride; ++k) sAcc[tid * kAccStride + k] = 0.f;
+            for (int k = 0; k < kAccStride; ++k) sAcc[tid * kAccStride + k] = 0.f;
+        }
         __syncthreads();
         // this warp's list, limited to entries below its largest contributor count
         const int wcnt = (int)min((int64_t)cnt, (int64_t)wlast - b0);
@@ -308,12 +313,23 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     count_pairs(n_eval, n_contrib, &L.ws.hdr->bwd_evals, &L.ws.hdr->bwd_contrib);
 }
 
+template <int NB>
+void launch_backward_nb(const BackwardLaunch &L, cudaStream_t st) {
+    if (L.pose_only)
+        k_backward<true, NB><<<L.d.T, kTilePix, 0, st>>>(L);
+    else
+        k_backward<false, NB><<<L.d.T, kTilePix, 0, st>>>(L);
+}
+
 cudaError_t launch_backward(const BackwardLaunch &L, cudaStream_t st) {
     if (L.d.T == 0) return cudaSuccess;
-    if (L.pose_only)
-        k_backward<true><<<L.d.T, kTilePix, 0, st>>>(L);
-    else
-        k_backward<false><<<L.d.T, kTilePix, 0, st>>>(L);
+    switch (L.d.bwd_batch) {
+        case 0:
+        case 256: launch_backward_nb<256>(L, st); break;
+        case 128: launch_backward_nb<128>(L, st); break;
+        case 64: launch_backward_nb<64>(L, st); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -9,9 +9,12 @@
 // with a_i = min(alpha_max, o_i exp(power_i)) the 2-D footprint of Eq. 1 and
 // T_i = prod_{j<i} (1 - a_j).  Gaussians with a_i < alpha_min are skipped; the walk
 // stops before the Gaussian that would take T below t_min, and the block stops as soon
-// as all its pixels have stopped.  Batches of kBatch records are gathered into shared
-// memory by the whole block; each warp (an 8 x 4 patch of the tile) then lists the batch
-// Gaussians whose conservative support box meets its patch and walks only those.
+// as all its pixels have stopped.  Batches of NB records (64, 128 or 256, the batch
+// depth, picked per context) are gathered into shared memory by the first NB threads;
+// each warp (an 8 x 4 patch of the tile) then lists the batch Gaussians whose
+// conservative support box meets its patch and walks only those.  A smaller batch stages
+// fewer Gaussians past the point where every pixel of the tile has stopped; a larger one
+// takes fewer barriers.
 //
 // With targets, the combined loss of Sec. III-B (plus the depth-prior term) is
 // evaluated in the epilogue: its per-pixel gradient goes to the workspace for the
@@ -23,11 +26,12 @@ namespace gsk {
 
 __device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
-template <bool LOSS>
+template <bool LOSS, int NB>
 __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
-    __shared__ float4 sP0[kBatch], sC[kBatch], sBox[kBatch];
-    __shared__ float2 sP1[kBatch];
-    __shared__ uint8_t sList[kTilePix / 32][kBatch];
+    static_assert(NB % 32 == 0 && NB <= kBatch, "batch depth: a multiple of 32, at most kBatch");
+    __shared__ float4 sP0[NB], sC[NB], sBox[NB];
+    __shared__ float2 sP1[NB];
+    __shared__ uint8_t sList[kTilePix / 32][NB];
     __shared__ unsigned long long sKeys[kSortSmemKeys];
     __shared__ int s_view;
     __shared__ float s_loss[kTilePix / 32];
@@ -57,10 +61,10 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, D = 0.f;
     uint32_t last = 0, n_eval = 0, n_contrib = 0;
     bool done = !inside;
-    for (uint32_t b0 = 0; b0 < n; b0 += kBatch) {
+    for (uint32_t b0 = 0; b0 < n; b0 += NB) {
         if (__syncthreads_count(!done) == 0) break;
         const uint32_t idx = b0 + tid;
-        if (idx < n) {
+        if (tid < NB && idx < n) {  // thread tid stages batch position tid
             const uint32_t r = L.ws.sorted[start + idx];
             if (r < rec_slots(L.d)) {
                 const Rec rr = L.ws.rec[r];
@@ -74,7 +78,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
             }
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)kBatch, n - b0);
+        const int cnt = (int)min((uint32_t)NB, n - b0);
         if (__any_sync(0xffffffffu, !done)) {
             // this warp's list: the batch Gaussians whose support box meets its 8 x 4 patch
             int nl = 0;
@@ -188,12 +192,23 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     }
 }
 
+template <int NB>
+void launch_forward_nb(const ForwardLaunch &L, cudaStream_t st) {
+    if (L.t_rgb)
+        k_forward<true, NB><<<L.d.T, kTilePix, 0, st>>>(L);
+    else
+        k_forward<false, NB><<<L.d.T, kTilePix, 0, st>>>(L);
+}
+
 cudaError_t launch_forward(const ForwardLaunch &L, cudaStream_t st) {
     if (L.d.T == 0) return cudaSuccess;
-    if (L.t_rgb)
-        k_forward<true><<<L.d.T, kTilePix, 0, st>>>(L);
-    else
-        k_forward<false><<<L.d.T, kTilePix, 0, st>>>(L);
+    switch (L.d.fwd_batch) {
+        case 0:
+        case 256: launch_forward_nb<256>(L, st); break;
+        case 128: launch_forward_nb<128>(L, st); break;
+        case 64: launch_forward_nb<64>(L, st); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

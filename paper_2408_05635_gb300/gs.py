@@ -77,6 +77,14 @@ class gs_problem(ctypes.Structure):
                 ("record_capacity", c_int64)]
 
 
+class gs_schedule(ctypes.Structure):
+    _fields_ = [("sub_buckets", c_int32), ("fwd_batch", c_int32), ("bwd_batch", c_int32), ("reserved", c_int32)]
+
+
+class gs_tune_entry(ctypes.Structure):
+    _fields_ = [("stage", c_int32), ("value", c_int32), ("ms", ctypes.c_float)]
+
+
 class gs_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("ms", ctypes.c_float)]
 
@@ -129,6 +137,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "gs_render_static": (c_int32, [P(gs_config), P(gs_gaussians), P(gs_camera), c_void_p, P(gs_targets),
                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
             "gs_kernel_times": (c_int32, [c_void_p, P(gs_kernel_time), c_int32, P(c_int32)]),
+            "gs_get_schedule": (c_int32, [c_void_p, P(gs_schedule)]),
+            "gs_set_schedule": (c_int32, [c_void_p, P(gs_schedule)]),
+            "gs_autotune": (c_int32, [c_void_p, P(gs_problem), P(gs_gaussians), c_void_p, P(gs_targets), c_int32,
+                                      c_int32, c_void_p, c_size_t, P(gs_tune_entry), c_int32, P(c_int32),
+                                      P(gs_schedule), c_void_p]),
             "gs_image_metrics": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
             "gs_msssim_scratch_bytes": (c_size_t, [c_int32, c_int32]),
             "gs_msssim": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -261,6 +274,35 @@ def gs_kernel_times(ctx, cap: int = 4096) -> list[tuple[str, float]]:
     cnt = c_int32(0)
     _check(ctx, load().gs_kernel_times(ctx, arr, cap, ctypes.byref(cnt)), "gs_kernel_times")
     return [(arr[k].name.decode(), float(arr[k].ms)) for k in range(min(cap, cnt.value))]
+
+
+def gs_get_schedule(ctx) -> gs_schedule:
+    s = gs_schedule()
+    _check(ctx, load().gs_get_schedule(ctx, ctypes.byref(s)), "gs_get_schedule")
+    return s
+
+
+def gs_set_schedule(ctx, sub_buckets: int, fwd_batch: int, bwd_batch: int) -> None:
+    s = gs_schedule(int(sub_buckets), int(fwd_batch), int(bwd_batch), 0)
+    _check(ctx, load().gs_set_schedule(ctx, ctypes.byref(s)), "gs_set_schedule")
+
+
+TUNE_STAGES = ("sub_buckets", "fwd_batch", "bwd_batch")
+
+
+def gs_autotune(ctx, prob: gs_problem, g: gs_gaussians, poses, targets: gs_targets, ws, ws_bytes: int,
+                pose_only: bool = True, reps: int = 10, stream=None) -> tuple[gs_schedule, list[tuple[str, int, float]]]:
+    """Time every sub-bucket count and batch depth on this problem, set the fastest on
+    the context and return it with the measurements (setting name, value, ms per pass)."""
+    table = (gs_tune_entry * 9)()
+    cnt = c_int32(0)
+    best = gs_schedule()
+    st = load().gs_autotune(ctx, ctypes.byref(prob), ctypes.byref(g), _ptr(poses), ctypes.byref(targets),
+                            int(bool(pose_only)), int(reps), _ptr(ws), ws_bytes, table, 9, ctypes.byref(cnt),
+                            ctypes.byref(best), _stream(stream))
+    _check(ctx, st, "gs_autotune")
+    rows = [(TUNE_STAGES[table[k].stage], int(table[k].value), float(table[k].ms)) for k in range(min(9, cnt.value))]
+    return best, rows
 
 
 def gs_render_static(cfg: gs_config, g: gs_gaussians, cam: gs_camera, pose, targets: gs_targets | None = None,
@@ -613,6 +655,27 @@ class Rasterizer:
                        loss[sl], stream)
             gs_backward(self.ctx, None, None, None, G, None, stream)
         return {"grads": grads, "loss": loss}
+
+    # -- launch schedule -----------------------------------------------------------------
+    @property
+    def schedule(self) -> dict:
+        s = gs_get_schedule(self.ctx)
+        return {"sub_buckets": s.sub_buckets, "fwd_batch": s.fwd_batch, "bwd_batch": s.bwd_batch}
+
+    def set_schedule(self, sub_buckets: int = 4, fwd_batch: int = 256, bwd_batch: int = 256) -> None:
+        gs_set_schedule(self.ctx, sub_buckets, fwd_batch, bwd_batch)
+
+    def autotune(self, prob: gs_problem, g: GaussianTensors, poses: torch.Tensor, targets, pose_only: bool = True,
+                 reps: int = 10, stream=None) -> dict:
+        """gs_autotune on this problem; targets = (rgb, depth, prior-or-None) tensors
+        concatenated over the views.  Returns the chosen schedule and the timings."""
+        ws, nb = self.workspace(prob)
+        trgb, tdep, tprior = targets
+        tg = gs_targets(_ptr(trgb), _ptr(tdep), _ptr(tprior))
+        best, rows = gs_autotune(self.ctx, prob, g.c(), poses, tg, ws, nb, pose_only, reps, stream)
+        return {"schedule": {"sub_buckets": best.sub_buckets, "fwd_batch": best.fwd_batch,
+                             "bwd_batch": best.bwd_batch},
+                "timings_ms": [{"setting": k, "value": v, "ms": round(ms, 4)} for k, v, ms in rows]}
 
     def sync(self, stream=None) -> gs_counts:
         st, c = gs_sync_status(self.ctx, stream)
