@@ -61,19 +61,21 @@ def _args():
                     help="passes per setting of the launch-schedule autotuner before the tracking and batched "
                          "legs (0: the default schedule)")
     ap.add_argument("--schedule", default=None,
-                    help="fixed launch schedule 'sub_buckets,fwd_batch,bwd_batch' instead of tuning")
+                    help="fixed launch schedule 'tile_w,tile_h,sub_buckets,fwd_batch,bwd_batch' instead of tuning")
     return ap.parse_args()
 
 
-def apply_schedule(a, R, prob, g, poses, targets) -> dict:
+def apply_schedule(a, R, cams, g, poses, targets) -> dict:
     """The launch schedule of a leg: fixed by --schedule, else picked by the library's
-    autotuner on the leg's own problem (gs_autotune), else the default."""
+    autotuner on the leg's own views (gs_autotune), else the default.  The tuning problem
+    gets twice the usual pair-capacity margin, so that smaller tiles, which make more
+    (Gaussian, tile) pairs, are timed too; the leg plans its own problem afterwards."""
     if a.schedule:
-        sb, fb, bb = (int(x) for x in a.schedule.split(","))
-        R.set_schedule(sb, fb, bb)
+        R.set_schedule(*(int(x) for x in a.schedule.split(",")))
         return {"schedule": R.schedule, "tuned": False}
     if a.autotune_reps > 0:
-        res = R.autotune(prob, g, poses, targets, pose_only=True, reps=a.autotune_reps)
+        tprob = R.plan(g, cams, poses, margin=3.0)
+        res = R.autotune(tprob, g, poses, targets, pose_only=True, reps=a.autotune_reps)
         res["tuned"] = True
         return res
     return {"schedule": R.schedule, "tuned": False}
@@ -338,8 +340,8 @@ def run_batched(a, dev, stream):
     R = gs.Rasterizer(gs.Config(), device=dev)
     gtb = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=torch.bfloat16)
     poses = start.clone()
+    sched = apply_schedule(a, R, cams, gtb, poses, (t_rgb, t_depth, t_prior))
     prob = R.plan(gtb, cams, poses, margin=1.5)
-    sched = apply_schedule(a, R, prob, gtb, poses, (t_rgb, t_depth, t_prior))
     ws, nb = R.workspace(prob)
     tg = gs.gs_targets(t_rgb.data_ptr(), t_depth.data_ptr(), t_prior.data_ptr())
     adam = torch.zeros(V, 16, dtype=torch.float64, device=dev)
@@ -601,13 +603,13 @@ def main():
     poses = out8[:7].view(1, 7)
     poses.copy_(torch.tensor(np.asarray(start)[None], dtype=torch.float64))
     loss = out8[7:].view(1, 1)
-    prob = R.plan(gt, [cam], poses, margin=1.5)
-    ws, nb = R.workspace(prob)
     P_px = cam.width * cam.height
     frame_dev = torch.tensor(np.concatenate([rgb.reshape(-1), depth.reshape(-1), prior.reshape(-1)]), device=dev)
     t_rgb, t_depth, t_prior = frame_dev[:3 * P_px], frame_dev[3 * P_px:4 * P_px], frame_dev[4 * P_px:]
     targets = gs.gs_targets(t_rgb.data_ptr(), t_depth.data_ptr(), t_prior.data_ptr())
-    sched = apply_schedule(a, R, prob, gt, poses, (t_rgb, t_depth, t_prior))
+    sched = apply_schedule(a, R, [cam], gt, poses, (t_rgb, t_depth, t_prior))
+    prob = R.plan(gt, [cam], poses, margin=1.5)
+    ws, nb = R.workspace(prob)
     adam = torch.zeros(1, 16, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
     stream = torch.cuda.current_stream(dev)

@@ -96,7 +96,8 @@ typedef struct {
 /* Renderer, loss and pose-optimiser settings.  The paper states none of these values;
  * gs_default_config fills the readings documented beside each field. */
 typedef struct {
-    int32_t tile_w, tile_h; /* screen tile, 16 x 16 (the only shape this build has)   */
+    int32_t tile_w, tile_h; /* initial screen tile of the context's launch schedule
+                               (gs_schedule; 16 x 16)                                  */
     float alpha_min;        /* a Gaussian with alpha < alpha_min is skipped (1/255)    */
     float alpha_max;        /* alpha = min(alpha_max, o G) (0.99)                      */
     float t_min;            /* stop before the Gaussian that takes T below t_min (1e-4)*/
@@ -256,49 +257,64 @@ gs_status gs_kernel_times(gs_ctx *ctx, gs_kernel_time *out, int32_t cap, int32_t
 
 /* ------------------------------------------------------------------ launch schedule */
 
-/* How the context launches the binning and the two compositors.  None of these change
- * a result beyond FP32 summation order: the sub-buckets only split where a tile's pairs
- * are counted and placed (the tile's list is sorted whole), and the batch depth only
- * sets how many of a tile's depth-sorted Gaussians the tile block stages into shared
- * memory at a time (every pixel still composites them in the same order).  The tile is
- * 16 x 16 with one thread per pixel in every schedule. */
+/* How the context launches the binning and the two compositors.  Every pixel composites
+ * the same Gaussians in the same (depth, index) order under every schedule (a tile's list
+ * holds every Gaussian whose support reaches one of its pixels).  The sub-buckets only
+ * split where a tile's pairs are counted and placed (the tile's list is sorted whole) and
+ * the batch depth only sets how many of a tile's depth-sorted Gaussians the tile block
+ * stages into shared memory at a time: with the tile shape fixed, images are bit-identical
+ * and gradients differ by FP32 summation order.  The footprints are evaluated relative to
+ * the tile origin, so another tile shape changes their rounding (and may flip an
+ * alpha_min or t_min decision that sits within rounding of its threshold).  A tile block
+ * has one thread per pixel, so the tile shape also sets the threads per tile. */
 typedef struct {
-    int32_t sub_buckets; /* counters per tile for the pair count and key emission: 1, 2
-                            or 4 (4; fewer are used when tiles x 4 exceeds 2^22)       */
-    int32_t fwd_batch;   /* Gaussians staged per forward batch: 64, 128 or 256 (256)   */
-    int32_t bwd_batch;   /* Gaussians staged per backward batch: 64, 128 or 256 (256)  */
-    int32_t reserved;    /* 0 */
+    int32_t tile_w, tile_h; /* screen tile in pixels: tile_w in {8, 16, 32}, tile_h in
+                               {4, 8, 16, 32}, 64 <= tile_w tile_h <= 256 (16 x 16)    */
+    int32_t sub_buckets;    /* counters per tile for the pair count and key emission:
+                               1, 2 or 4 (4; fewer are used when tiles x 4 exceeds 2^22) */
+    int32_t fwd_batch;      /* Gaussians staged per forward batch: 64, 128 or 256, at
+                               most tile_w tile_h (256)                                 */
+    int32_t bwd_batch;      /* Gaussians staged per backward batch: the same (256)      */
+    int32_t reserved;       /* 0 */
 } gs_schedule;
 
 /* Read the context's schedule (defaults after gs_create).  Errors: INVALID_ARG (NULL). */
 gs_status gs_get_schedule(const gs_ctx *ctx, gs_schedule *out);
 
 /* Set the schedule used by every later call on the context (a cached tracking graph is
- * rebuilt on its next use).  The workspace size does not depend on it.  Errors:
- * INVALID_ARG (NULL, or a value outside the sets above). */
+ * rebuilt on its next use).  The workspace size does not depend on it (it has room for
+ * the tiles of the smallest shape), but a smaller tile can make more (Gaussian, tile)
+ * pairs than the problem's pair_capacity holds (reported as CAPACITY by gs_sync_status).
+ * Errors: INVALID_ARG (NULL, or a value outside the sets above). */
 gs_status gs_set_schedule(gs_ctx *ctx, const gs_schedule *sched);
 
 /* One measurement of gs_autotune. */
 typedef struct {
-    int32_t stage; /* 0: binning (projection, scan, emission) timed per sub_buckets;
-                      1: forward compositing (with the fused loss) per fwd_batch;
-                      2: backward compositing per bwd_batch                          */
-    int32_t value; /* the sub_buckets / fwd_batch / bwd_batch setting timed          */
-    float ms;      /* mean device time of one pass of the stage (CUDA events on the
-                      stream, warm caches, after one untimed pass)                   */
+    int32_t stage;        /* 0: tile shape, timed as a whole pass (projection, scan,
+                             emission, forward with the fused loss, backward);
+                             1: binning (projection, scan, emission) per sub_buckets;
+                             2: forward compositing per fwd_batch;
+                             3: backward compositing per bwd_batch                     */
+    float ms;             /* mean device time of one pass of the stage (CUDA events on
+                             the stream, warm caches, after one untimed pass); -1 when
+                             the setting made more pairs than pair_capacity (not timed) */
+    gs_schedule schedule; /* the schedule of the timed passes                          */
 } gs_tune_entry;
 
 /* Autotuner of the launch schedule for one problem: on the given Gaussians, poses and
- * targets it times, stage after stage, every sub-bucket count (binning), every forward
- * batch depth and every backward batch depth (the pose-only walk of tracking when
- * pose_only != 0, the walk for all Gaussian parameters otherwise), `reps` passes each,
- * keeps the fastest setting of each stage for the next stage and sets it on the
- * context.  It uses the workspace (sized by gs_workspace_size for `prob`) as gs_project
+ * targets it times, stage after stage, the tile shapes 16 x 16, 32 x 8, 16 x 8 and 8 x 8
+ * (one whole pass each, batch depths capped at the tile's threads), every sub-bucket
+ * count (binning), every forward batch depth and every backward batch depth that the
+ * chosen tile allows (the pose-only walk of tracking when pose_only != 0, the walk for
+ * all Gaussian parameters otherwise), `reps` passes each, keeps the fastest setting of
+ * each stage for the next stage (the first candidate, the context's current setting for
+ * the tile, unless another is at least 1 % faster) and sets it on the context.  It uses the workspace (sized by gs_workspace_size for `prob`) as gs_project
  * does and synchronises `stream`, so it cannot be captured into a graph; afterwards no
  * projection is bound (call gs_project or gs_track_step next).  table (host, cap
  * entries, may be NULL) receives the measurements in order, *count (may be NULL) their
- * number (9 at most); best (may be NULL) the chosen schedule.  A capacity overflow
- * during the passes is reported as CAPACITY (the schedule is then left unchanged).
+ * number (13 at most); best (may be NULL) the chosen schedule.  A tile shape whose pairs
+ * overflow pair_capacity is skipped (ms = -1); an overflow of the context's current
+ * schedule is reported as CAPACITY (the schedule is then left unchanged).
  * Errors: INVALID_ARG (as gs_project; targets without rgb or depth; reps outside
  * [1, 1000]), WORKSPACE, CAPACITY, CUDA. */
 gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const double *poses,

@@ -19,6 +19,25 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// Tile shapes a schedule may use (one thread per pixel, 8 x 4 warp patches).
+bool valid_tile(int32_t w, int32_t h) {
+    const bool wok = w == 8 || w == 16 || w == 32, hok = h == 4 || h == 8 || h == 16 || h == 32;
+    return wok && hok && w * h >= 64 && w * h <= kTilePix;
+}
+
+int ilog2(int32_t v) {
+    int l = 0;
+    while ((1 << (l + 1)) <= v) ++l;
+    return l;
+}
+
+// Most sub-buckets a problem of T tiles uses: T x sub-buckets stays within 2^22 counters.
+uint32_t max_sub(uint64_t T) {
+    uint32_t s = kSubMax;
+    while (s > 1 && T * s > (1ull << 22)) s >>= 1;
+    return s;
+}
+
 struct Layout {
     size_t err, hdr, tile_cnt, zero_end;
     size_t views, view_rt, cell_cnt, tile_start, cursor, tile_order, rec, rec_grad, keys, sorted, t_final, n_last,
@@ -58,7 +77,7 @@ struct GraphKey {
 struct gs_ctx {
     gs_config cfg{};
     Settings s{};
-    gs_schedule sched{gsk::kSubMax, gsk::kBatch, gsk::kBatch, 0};
+    gs_schedule sched{gsk::kTile, gsk::kTile, gsk::kSubMax, gsk::kBatch, gsk::kBatch, 0};
     std::string err;
     // state bound by the last gs_project
     bool bound = false;
@@ -185,6 +204,7 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
         return fail(ctx, GS_ERR_INVALID_ARG, "n_gaussians * n_views too large for 32-bit record slots");
     d.pair_cap = (uint32_t)p->pair_capacity;
     out.views.resize(p->n_views);
+    const int32_t tw = ctx->sched.tile_w, th = ctx->sched.tile_h;
     uint64_t T = 0, P = 0;
     for (int v = 0; v < p->n_views; ++v) {
         const gs_camera &c = p->cameras[v];
@@ -197,8 +217,10 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
         vi.cy = (float)c.cy;
         vi.width = c.width;
         vi.height = c.height;
-        vi.tiles_x = (c.width + kTile - 1) / kTile;
-        vi.tiles_y = (c.height + kTile - 1) / kTile;
+        vi.tiles_x = (c.width + tw - 1) / tw;
+        vi.tiles_y = (c.height + th - 1) / th;
+        vi.tile_lw = ilog2(tw);
+        vi.tile_lh = ilog2(th);
         vi.tile_base = (uint32_t)T;
         vi.pix_base = (uint32_t)P;
         vi.tan_lim_x = jacobian_tangent_limit(ctx->cfg.jac_clip, c.width, c.fx);
@@ -209,15 +231,26 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
             return fail(ctx, GS_ERR_INVALID_ARG, "too many pixels or tiles in one call");
         out.views[v] = vi;
     }
+    // the layout has room for the tiles and tile counters of every allowed tile shape, so
+    // the workspace size does not depend on the schedule
+    uint64_t lay_tiles = 0, lay_cnt = 0;
+    for (int32_t w = 8; w <= 32; w *= 2)
+        for (int32_t h = 4; h <= 32; h *= 2) {
+            if (!valid_tile(w, h)) continue;
+            uint64_t t = 0;
+            for (int v = 0; v < p->n_views; ++v)
+                t += (uint64_t)((p->cameras[v].width + w - 1) / w) * (uint64_t)((p->cameras[v].height + h - 1) / h);
+            lay_tiles = std::max(lay_tiles, t);
+            lay_cnt = std::max(lay_cnt, t * max_sub(t));
+        }
+    if (lay_tiles >= (1ull << 27)) return fail(ctx, GS_ERR_INVALID_ARG, "too many pixels or tiles in one call");
     d.T = (uint32_t)T;
     d.P = (uint32_t)P;
-    // the layout has room for kSubMax counters per tile (fewer for huge tile counts), so
-    // the workspace size does not depend on the schedule, which may use fewer
-    uint32_t s_lay = kSubMax;
-    while (s_lay > 1 && (uint64_t)d.T * s_lay > (1ull << 22)) s_lay >>= 1;
-    d.S = std::min(s_lay, (uint32_t)ctx->sched.sub_buckets);
+    d.S = std::min(max_sub(T), (uint32_t)ctx->sched.sub_buckets);
     d.fwd_batch = (uint32_t)ctx->sched.fwd_batch;
     d.bwd_batch = (uint32_t)ctx->sched.bwd_batch;
+    d.tile_threads = (uint32_t)(tw * th);
+    d.tile_lw = (uint32_t)ilog2(tw);
     out.d = d;
     Layout &L = out.lay;
     size_t o = 0;
@@ -229,15 +262,15 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     L.err = take(sizeof(uint32_t));
     // zeroed before every projection: [hdr, zero_end)
     L.hdr = take(sizeof(DevHeader));
-    L.tile_cnt = take(sizeof(uint32_t) * ((size_t)d.T * s_lay + 1));
+    L.tile_cnt = take(sizeof(uint32_t) * ((size_t)lay_cnt + 1));
     L.zero_end = o;
     const size_t cells = (size_t)d.V * d.nblk;
     L.views = take(sizeof(ViewInfo) * d.V);
     L.view_rt = take(sizeof(float) * 12 * d.V);
     L.cell_cnt = take(sizeof(uint32_t) * cells);
-    L.tile_start = take(sizeof(uint32_t) * ((size_t)d.T * s_lay + 1));
-    L.cursor = take(sizeof(uint32_t) * ((size_t)d.T * s_lay + 1));
-    L.tile_order = take(sizeof(uint32_t) * (size_t)d.T);
+    L.tile_start = take(sizeof(uint32_t) * ((size_t)lay_cnt + 1));
+    L.cursor = take(sizeof(uint32_t) * ((size_t)lay_cnt + 1));
+    L.tile_order = take(sizeof(uint32_t) * (size_t)lay_tiles);
     L.rec = take(sizeof(Rec) * cells * kCell);
     L.rec_grad = take(sizeof(RecGrad) * cells * kCell);
     L.keys = take(sizeof(unsigned long long) * (size_t)d.pair_cap);
@@ -245,7 +278,7 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     L.t_final = take(sizeof(float) * (size_t)d.P);
     L.n_last = take(sizeof(uint32_t) * (size_t)d.P);
     L.upstream = take(sizeof(float) * 5 * (size_t)d.P);
-    L.tile_loss = take(sizeof(float2) * (size_t)d.T);
+    L.tile_loss = take(sizeof(float2) * (size_t)lay_tiles);
     L.pose_part = take(sizeof(float2) * 6 * cells);
     L.total = o;
     return GS_OK;
@@ -338,6 +371,12 @@ cudaError_t enqueue_forward(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, con
 
 bool valid_batch(int32_t b) { return b == 64 || b == 128 || b == 256; }
 
+bool valid_schedule(const gs_schedule &sc) {
+    const int32_t sb = sc.sub_buckets, px = sc.tile_w * sc.tile_h;
+    return valid_tile(sc.tile_w, sc.tile_h) && (sb == 1 || sb == 2 || sb == 4) && valid_batch(sc.fwd_batch) &&
+           valid_batch(sc.bwd_batch) && sc.fwd_batch <= px && sc.bwd_batch <= px && sc.reserved == 0;
+}
+
 // Device time of one pass of `enqueue`, averaged over `reps` passes after one untimed
 // pass, with two events on the stream.
 template <class F>
@@ -371,7 +410,7 @@ extern "C" {
 void gs_default_config(gs_config *c) {
     if (!c) return;
     c->tile_w = kTile;
-    c->tile_h = kTile;
+    c->tile_h = kTile;  // the default schedule's tile
     c->alpha_min = 1.0f / 255.0f;
     c->alpha_max = 0.99f;
     c->t_min = 1e-4f;
@@ -411,7 +450,7 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg) {
     gs_config c;
     gs_default_config(&c);
     if (cfg) c = *cfg;
-    if (c.tile_w != kTile || c.tile_h != kTile) return GS_ERR_UNSUPPORTED;
+    if (!valid_tile(c.tile_w, c.tile_h)) return GS_ERR_UNSUPPORTED;
     if (!(c.alpha_min >= 0.f) || !(c.alpha_max > c.alpha_min) || !(c.alpha_max <= 1.f) || !(c.t_min >= 0.f) ||
         !(c.t_min < 1.f) || !(c.dilation >= 0.f) || !(c.z_near > 0.f) || !(c.jac_clip >= 0.f) || !(c.lr_rot >= 0) || !(c.lr_trans >= 0) ||
         !(c.beta1 >= 0 && c.beta1 < 1) || !(c.beta2 >= 0 && c.beta2 < 1) || !(c.eps > 0))
@@ -420,6 +459,9 @@ gs_status gs_create(gs_ctx **out, const gs_config *cfg) {
     if (!ctx) return GS_ERR_OOM;
     ctx->cfg = c;
     ctx->s = settings_of(c);
+    ctx->sched.tile_w = c.tile_w;
+    ctx->sched.tile_h = c.tile_h;
+    ctx->sched.fwd_batch = ctx->sched.bwd_batch = std::min(kBatch, c.tile_w * c.tile_h);
     *out = ctx;
     return GS_OK;
 }
@@ -704,10 +746,10 @@ gs_status gs_set_schedule(gs_ctx *ctx, const gs_schedule *sched) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (!sched) return fail(ctx, GS_ERR_INVALID_ARG, "schedule is NULL");
-    const int32_t sb = sched->sub_buckets;
-    if ((sb != 1 && sb != 2 && sb != 4) || !valid_batch(sched->fwd_batch) || !valid_batch(sched->bwd_batch) ||
-        sched->reserved != 0)
-        return fail(ctx, GS_ERR_INVALID_ARG, "sub_buckets must be 1, 2 or 4 and batch depths 64, 128 or 256");
+    if (!valid_schedule(*sched))
+        return fail(ctx, GS_ERR_INVALID_ARG,
+                    "tile_w in {8, 16, 32}, tile_h in {4, 8, 16, 32} with 64 to 256 pixels, sub_buckets 1, 2 or 4, "
+                    "batch depths 64, 128 or 256 and at most the tile's pixels");
     ctx->sched = *sched;
     return GS_OK;
 }
@@ -738,95 +780,138 @@ gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g
     // the passes overwrite whatever projection was bound; no profiling markers inside them
     ctx->bound = false;
     const uint32_t prof_saved = ctx->prof_mask;
+    const gs_schedule sched_saved = ctx->sched;
     ctx->prof_mask = 0;
     reset_marks(ctx);
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    gs_tune_entry ent[9];
+    gs_tune_entry ent[13];
     int n_ent = 0;
-    gs_schedule chosen = ctx->sched;
-    // the layout's sub-bucket room: the most counters per tile this problem can use
-    uint32_t s_lay = kSubMax;
-    while (s_lay > 1 && (uint64_t)pr.d.T * s_lay > (1ull << 22)) s_lay >>= 1;
-    const int subs[3] = {4, 2, 1}, batches[3] = {256, 128, 64};  // the defaults first
-    Dims d = pr.d;
-    Problem run;
-    run.views = pr.views;
-    run.lay = pr.lay;
-    auto stage = [&](int which, const int *cand, int ncand, auto &&enqueue_for, int &pick_out) -> cudaError_t {
-        float ms[3];
-        int vals[3], nv = 0;
-        for (int k = 0; k < ncand; ++k) {
-            if (which == 0 && (uint32_t)cand[k] > s_lay) continue;
-            vals[nv] = cand[k];
-            cudaError_t r = time_passes(s, ev[0], ev[1], reps, [&]() { return enqueue_for(cand[k]); }, ms[nv]);
-            if (r != cudaSuccess) return r;
-            ent[n_ent++] = gs_tune_entry{which, cand[k], ms[nv]};
-            ++nv;
+    gs_schedule cur = ctx->sched;
+    bool overflow = false;  // the context's own schedule overflowed the pair capacity
+
+    // The problem (views, tile grid, sizes) of schedule `sc`, on the same workspace layout.
+    auto problem_for = [&](const gs_schedule &sc, Problem &out) -> gs_status {
+        ctx->sched = sc;
+        const gs_status r = build_problem(ctx, prob, out);
+        ctx->sched = sched_saved;
+        return r;
+    };
+    // One pass of stage `which` (0: all, 1: binning, 2: forward, 3: backward).
+    auto enqueue_stage = [&](int which, const Problem &q) -> cudaError_t {
+        cudaError_t r = cudaSuccess;
+        if (which <= 1) r = enqueue_project(ctx, q, w, gp, g->dtype_attr, poses, s);
+        if (r == cudaSuccess && (which == 0 || which == 2))
+            r = enqueue_forward(ctx, q, w, targets, nullptr, nullptr, nullptr, s);
+        if (r == cudaSuccess && (which == 0 || which == 3)) {
+            BackwardLaunch B;
+            B.ws = w;
+            B.d = q.d;
+            B.s = ctx->s;
+            B.up_rgb = w.upstream;
+            B.up_depth = w.upstream + 3u * q.d.P;
+            B.up_sil = w.upstream + 4u * q.d.P;
+            B.pose_only = pose_only != 0;
+            r = launch_backward(B, s);
         }
-        pick_out = vals[pick(ms, nv)];
+        return r;
+    };
+    // Did the work enqueued since the last check overflow a capacity?  Clears the flag.
+    auto overflowed = [&](bool &flag) -> cudaError_t {
+        uint32_t err = 0;
+        cudaError_t r = cudaStreamSynchronize(s);
+        if (r == cudaSuccess) r = cudaMemcpy(&err, w.err, sizeof(err), cudaMemcpyDeviceToHost);
+        if (r == cudaSuccess && err) r = cudaMemset(w.err, 0, sizeof(err));
+        flag = (err & (kErrRecords | kErrPairs | kErrTimeout)) != 0;
+        return r;
+    };
+    // Time the candidates of one stage (the first is the current setting) and keep the
+    // fastest in `cur`; candidates that overflow are recorded with ms = -1.
+    auto stage = [&](int which, const gs_schedule *cand, int ncand) -> cudaError_t {
+        float ms[4];
+        int idx[4], nv = 0;
+        for (int k = 0; k < ncand; ++k) {
+            Problem q;
+            if (problem_for(cand[k], q) != GS_OK) continue;
+            // an untimed pass through the whole chain (binning, forward, backward) leaves
+            // the state this stage's passes read, then the overflow check
+            cudaError_t r = upload_views(q, w, ws, s);
+            if (r == cudaSuccess) r = enqueue_stage(0, q);
+            bool of = false;
+            if (r == cudaSuccess) r = overflowed(of);
+            if (r != cudaSuccess) return r;
+            if (of) {
+                if (k == 0) overflow = true;
+                ent[n_ent++] = gs_tune_entry{which, -1.f, cand[k]};
+                continue;
+            }
+            float t = 0.f;
+            r = time_passes(s, ev[0], ev[1], reps, [&]() { return enqueue_stage(which, q); }, t);
+            if (r != cudaSuccess) return r;
+            ent[n_ent++] = gs_tune_entry{which, t, cand[k]};
+            ms[nv] = t;
+            idx[nv++] = k;
+        }
+        if (nv > 0 && idx[0] == 0) cur = cand[idx[pick(ms, nv)]];
+        else if (nv > 0) {  // the current setting overflowed: the fastest of the others
+            int b = 0;
+            for (int k = 1; k < nv; ++k)
+                if (ms[k] < ms[b]) b = k;
+            cur = cand[idx[b]];
+        }
         return cudaSuccess;
     };
+
     e = cudaEventCreate(&ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
-    if (e == cudaSuccess) e = upload_views(pr, w, ws, s);
-    // stage 0: binning per sub-bucket count (the scan leaves every counter zero again)
-    if (e == cudaSuccess)
-        e = stage(0, subs, 3,
-                  [&](int S) {
-                      run.d = d;
-                      run.d.S = (uint32_t)S;
-                      return enqueue_project(ctx, run, w, gp, g->dtype_attr, poses, s);
-                  },
-                  chosen.sub_buckets);
+    // stage 0: tile shapes (the current one first), batch depths capped at the threads
     if (e == cudaSuccess) {
-        d.S = (uint32_t)chosen.sub_buckets;
-        run.d = d;
-        e = enqueue_project(ctx, run, w, gp, g->dtype_attr, poses, s);
+        const int32_t shapes[4][2] = {{16, 16}, {32, 8}, {16, 8}, {8, 8}};
+        gs_schedule cand[4];
+        int nc = 0;
+        cand[nc++] = cur;
+        for (const auto &sh : shapes) {
+            if (sh[0] == cur.tile_w && sh[1] == cur.tile_h) continue;
+            gs_schedule c = cur;
+            c.tile_w = sh[0];
+            c.tile_h = sh[1];
+            c.fwd_batch = std::min(c.fwd_batch, c.tile_w * c.tile_h);
+            c.bwd_batch = std::min(c.bwd_batch, c.tile_w * c.tile_h);
+            if (nc < 4 && valid_schedule(c)) cand[nc++] = c;
+        }
+        e = stage(0, cand, nc);
     }
-    // stage 1: forward compositing with the fused loss per batch depth (idempotent passes)
-    if (e == cudaSuccess)
-        e = stage(1, batches, 3,
-                  [&](int nb) {
-                      run.d = d;
-                      run.d.fwd_batch = (uint32_t)nb;
-                      return enqueue_forward(ctx, run, w, targets, nullptr, nullptr, nullptr, s);
-                  },
-                  chosen.fwd_batch);
-    // stage 2: backward compositing per batch depth (the passes add into the record
-    // accumulators again and again; nothing reads them before the next projection)
-    if (e == cudaSuccess) {
-        d.fwd_batch = (uint32_t)chosen.fwd_batch;
-        e = stage(2, batches, 3,
-                  [&](int nb) {
-                      BackwardLaunch B;
-                      B.ws = w;
-                      B.d = d;
-                      B.d.bwd_batch = (uint32_t)nb;
-                      B.s = ctx->s;
-                      B.up_rgb = w.upstream;
-                      B.up_depth = w.upstream + 3u * d.P;
-                      B.up_sil = w.upstream + 4u * d.P;
-                      B.pose_only = pose_only != 0;
-                      return launch_backward(B, s);
-                  },
-                  chosen.bwd_batch);
+    // stage 1: sub-buckets; stages 2 and 3: batch depths up to the tile's threads
+    const int32_t subs[3] = {4, 2, 1}, batches[3] = {256, 128, 64};
+    for (int which = 1; which <= 3 && e == cudaSuccess; ++which) {
+        gs_schedule cand[4];
+        int nc = 0;
+        cand[nc++] = cur;
+        for (int k = 0; k < 3; ++k) {
+            gs_schedule c = cur;
+            int32_t &field = which == 1 ? c.sub_buckets : (which == 2 ? c.fwd_batch : c.bwd_batch);
+            const int32_t v = which == 1 ? subs[k] : batches[k];
+            if (v == field) continue;
+            field = v;
+            if (which == 1) {  // the problem may allow fewer sub-buckets than asked
+                Problem q;
+                if (problem_for(c, q) != GS_OK || q.d.S != (uint32_t)v) continue;
+            }
+            if (valid_schedule(c)) cand[nc++] = c;
+        }
+        e = stage(which, cand, nc);
     }
-    uint32_t err = 0;
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) e = cudaMemcpy(&err, w.err, sizeof(err), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && err) e = cudaMemset(w.err, 0, sizeof(err));
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
     ctx->prof_mask = prof_saved;
+    ctx->sched = sched_saved;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
     if (table)
         for (int k = 0; k < n_ent && k < cap; ++k) table[k] = ent[k];
     if (count) *count = n_ent;
-    if (err & (kErrRecords | kErrPairs | kErrTimeout))
-        return fail(ctx, (err & kErrTimeout) ? GS_ERR_TIMEOUT : GS_ERR_CAPACITY,
-                    "the problem overflowed its capacities during tuning; schedule unchanged");
-    ctx->sched = chosen;
-    if (best) *best = chosen;
+    if (overflow)
+        return fail(ctx, GS_ERR_CAPACITY, "the problem overflowed its capacities during tuning; schedule unchanged");
+    ctx->sched = cur;
+    if (best) *best = cur;
     return GS_OK;
 }
 

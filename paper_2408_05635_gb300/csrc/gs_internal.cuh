@@ -22,8 +22,11 @@
 
 namespace gsk {
 
-constexpr int kTile = 16;                 // tile edge in pixels
-constexpr int kTilePix = kTile * kTile;   // pixels (= threads) per tile block
+constexpr int kTile = 16;                 // default tile edge in pixels
+constexpr int kTilePix = kTile * kTile;   // most pixels (= threads) per tile block
+// A screen tile is tile_w x tile_h pixels, one thread each: tile_w in {8, 16, 32},
+// tile_h in {4, 8, 16, 32}, 64 <= tile_w tile_h <= kTilePix (16 x 16 by default).  The
+// warps of a tile block own 8 x 4 patches, tile_w / 8 of them per patch row.
 constexpr int kBlock = 256;               // threads per Gaussian-parallel block
 constexpr int kWarps = kBlock / 32;       // warps per Gaussian-parallel block
 constexpr int kCell = kBlock;             // Gaussians (and record slots) per cell
@@ -31,7 +34,7 @@ constexpr int kBatch = 256;               // default (and largest) compositing b
 // The compositors are compiled for batch depths 64, 128 and 256 (Gaussians staged into
 // shared memory per batch).  The first NB threads of the tile block stage one Gaussian
 // each and own one accumulator row each, and the per-warp lists hold batch positions as
-// bytes: NB must not exceed the block size nor 256.
+// bytes: NB must not exceed 256 nor the tile's thread count (the host checks the latter).
 static_assert(kBatch <= kTilePix && kBatch <= 256, "a batch stages at most one Gaussian per tile thread");
 constexpr int kSubMax = 4;                // most per-tile sub-buckets a workspace is laid out for
 
@@ -44,6 +47,7 @@ struct ViewInfo {
     uint32_t tile_base;  // first global tile index of the view
     uint32_t pix_base;   // first pixel of the view in the concatenated planes
     float tan_lim_x, tan_lim_y;  // clamp of the image-plane tangent at which J is taken
+    int32_t tile_lw, tile_lh;    // log2 of the tile width and height in pixels
 };
 
 // Tangent limit of the EWA Jacobian along one image axis: jac_clip half-extents of the
@@ -51,7 +55,7 @@ struct ViewInfo {
 inline float jacobian_tangent_limit(float jac_clip, int32_t extent, double focal) {
     return jac_clip > 0.f ? (float)((double)jac_clip * 0.5 * (double)extent / focal) : INFINITY;
 }
-static_assert(sizeof(ViewInfo) == 48, "ViewInfo layout");
+static_assert(sizeof(ViewInfo) == 56, "ViewInfo layout");
 
 // Small counters at the start of the workspace (cleared before every projection).
 struct DevHeader {
@@ -142,6 +146,8 @@ struct Dims {
     uint32_t pair_cap;
     uint32_t fwd_batch;    // Gaussians staged per forward batch: 64, 128 or 256 (0: kBatch)
     uint32_t bwd_batch;    // Gaussians staged per backward batch: 64, 128 or 256 (0: kBatch)
+    uint32_t tile_threads; // threads (= pixels) of a tile block: tile_w x tile_h (0: kTilePix)
+    uint32_t tile_lw;      // log2 of the tile width, 3 to 5 (0: 16-pixel tiles)
 };
 
 struct Settings {
@@ -256,8 +262,8 @@ __device__ __forceinline__ void tile_rect(const ViewInfo &vi, float mx, float my
         tx0 = 1; tx1 = 0; ty0 = 1; ty1 = 0;
         return;
     }
-    tx0 = px0 / kTile; tx1 = px1 / kTile;
-    ty0 = py0 / kTile; ty1 = py1 / kTile;
+    tx0 = px0 >> vi.tile_lw; tx1 = px1 >> vi.tile_lw;  // px, py >= 0: shifts divide
+    ty0 = py0 >> vi.tile_lh; ty1 = py1 >> vi.tile_lh;
 }
 
 // Does the support ellipse q(d) = a dx^2 + 2 b dx dy + c dy^2 <= dmax2 meet the
@@ -292,13 +298,13 @@ __device__ __forceinline__ bool ellipse_meets_rect(float mx, float my, float a, 
     return best <= __fadd_rn(__fmul_rn(dmax2, 1.001f), 1e-3f);
 }
 
-// Pixel-centre rectangle of tile (tx, ty), clipped to the image.
+// Pixel-centre rectangle of tile (tx, ty) >= 0, clipped to the image.
 __device__ __forceinline__ void tile_bounds(const ViewInfo &vi, int tx, int ty, float &x0, float &x1, float &y0,
                                             float &y1) {
-    x0 = (float)(tx * kTile);
-    y0 = (float)(ty * kTile);
-    x1 = (float)min(tx * kTile + kTile - 1, vi.width - 1);
-    y1 = (float)min(ty * kTile + kTile - 1, vi.height - 1);
+    x0 = (float)(tx << vi.tile_lw);
+    y0 = (float)(ty << vi.tile_lh);
+    x1 = (float)min(((tx + 1) << vi.tile_lw) - 1, vi.width - 1);
+    y1 = (float)min(((ty + 1) << vi.tile_lh) - 1, vi.height - 1);
 }
 
 // ------------------------------------------------------------------ per-tile footprint
@@ -374,7 +380,7 @@ __device__ __forceinline__ void row_tiles(const ViewInfo &vi, float mx, float my
     if (!(dmax2 < INFINITY)) return;
     const float R = __fadd_rn(__fmul_rn(dmax2, 1.001f), 1e-3f);
     const float det = diff_of_products(a, c, b, b);
-    const float yb0 = (float)(ty * kTile), yb1 = (float)min(ty * kTile + kTile - 1, vi.height - 1);
+    const float yb0 = (float)(ty << vi.tile_lh), yb1 = (float)min(((ty + 1) << vi.tile_lh) - 1, vi.height - 1);
     const float Y = __fsqrt_rn(__fdiv_rn(__fmul_rn(a, R), det));  // y half-extent of the ellipse
     const float ly = fmaxf(__fsub_rn(yb0, my), -Y), hy = fminf(__fsub_rn(yb1, my), Y);
     if (!(ly <= hy)) {
@@ -400,10 +406,11 @@ __device__ __forceinline__ void row_tiles(const ViewInfo &vi, float mx, float my
         xl = fminf(__fsub_rn(cl, __fmul_rn(rl, ia)), __fsub_rn(ch, __fmul_rn(rh, ia)));
     xl = __fsub_rn(__fadd_rn(mx, xl), __fadd_rn(1e-3f, __fmul_rn(1e-6f, fabsf(__fadd_rn(mx, xl)))));
     xr = __fadd_rn(__fadd_rn(mx, xr), __fadd_rn(1e-3f, __fmul_rn(1e-6f, fabsf(__fadd_rn(mx, xr)))));
-    // tile tx spans pixel centres [16 tx, 16 tx + 15]: it meets [xl, xr] iff
-    // 16 tx + 15 >= xl and 16 tx <= xr
-    const float lo = fmaxf(ceilf(__fdiv_rn(__fsub_rn(xl, (float)(kTile - 1)), (float)kTile)), -1.f);
-    const float hi = fminf(floorf(__fdiv_rn(xr, (float)kTile)), 1.0e7f);
+    // tile tx spans pixel centres [TW tx, TW tx + TW - 1]: it meets [xl, xr] iff
+    // TW tx + TW - 1 >= xl and TW tx <= xr (TW a power of two: the divisions are exact)
+    const float TW = (float)(1 << vi.tile_lw);
+    const float lo = fmaxf(ceilf(__fdiv_rn(__fsub_rn(xl, __fsub_rn(TW, 1.f)), TW)), -1.f);
+    const float hi = fminf(floorf(__fdiv_rn(xr, TW)), 1.0e7f);
     a0 = max(tx0, (int)lo);
     a1 = min(tx1, (int)hi);
 }
@@ -416,8 +423,8 @@ __device__ __forceinline__ float4 stage_box(const float4 B, float cu, float cv) 
     return make_float4(cu - hx, cu + hx, cv - hy, cv + hy);
 }
 
-// Pixel layout of a 16 x 16 tile block: warp w owns the 8 x 4 patch at
-// ((w & 1) * 8, (w >> 1) * 4); lane l its pixel (l & 7, l >> 3) inside the patch.
+// Pixel layout of a tile block of width 2^lw: warp w owns the 8 x 4 patch at
+// ((w mod 2^(lw-3)) * 8, (w >> (lw-3)) * 4); lane l its pixel (l & 7, l >> 3) inside it.
 constexpr int kPatchW = 8, kPatchH = 4;
 
 struct PolyEval {
@@ -457,6 +464,14 @@ __device__ __forceinline__ uint32_t tile_entries(const WsPtrs &ws, const Dims &d
 __device__ __host__ __forceinline__ uint32_t rec_slots(const Dims &d) {
     return (uint32_t)d.V * (uint32_t)d.nblk * (uint32_t)kCell;
 }
+
+// Threads (= pixels) of a tile block.
+__device__ __host__ __forceinline__ uint32_t tile_threads(const Dims &d) {
+    return d.tile_threads ? d.tile_threads : (uint32_t)kTilePix;
+}
+
+// log2 of the tile width (the compositors are compiled per tile width).
+__device__ __host__ __forceinline__ uint32_t tile_lw(const Dims &d) { return d.tile_lw ? d.tile_lw : 4u; }
 
 // ------------------------------------------------------------------ host-side launchers
 

@@ -87,6 +87,8 @@ extern "C" gs_status gs_render_static(const gs_config *cfg, const gs_gaussians *
     vi.height = cam->height;
     vi.tiles_x = (cam->width + kTile - 1) / kTile;
     vi.tiles_y = (cam->height + kTile - 1) / kTile;
+    static_assert(kTile == 16, "the static render uses 16 x 16 tiles");
+    vi.tile_lw = vi.tile_lh = 4;  // 16 x 16 tiles
     vi.tan_lim_x = jacobian_tangent_limit(cfg->jac_clip, cam->width, cam->fx);
     vi.tan_lim_y = jacobian_tangent_limit(cfg->jac_clip, cam->height, cam->fy);
     Dims d{};
@@ -96,6 +98,8 @@ extern "C" gs_status gs_render_static(const gs_config *cfg, const gs_gaussians *
     if (d.nblk == 0) d.nblk = 1;
     d.T = (uint32_t)(vi.tiles_x * vi.tiles_y);
     d.S = 4;
+    d.tile_threads = kTilePix;
+    d.tile_lw = 4;
     d.P = (uint32_t)(cam->width * cam->height);
     d.pair_cap = (uint32_t)kMaxPairs;
     if ((int64_t)d.T > kMaxTiles) return GS_ERR_INVALID_ARG;

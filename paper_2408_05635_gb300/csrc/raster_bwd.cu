@@ -122,9 +122,10 @@ __device__ __forceinline__ void bwd_step6(bool c, const PolyEval &pe, float4 Cc,
 // Shared accumulator slots per staged Gaussian: 0, 1 sum dp dx, dp dy; 2 sum a T g_D;
 // 3 sum dL/da a_raw; 4..6 sum dp dx^2, dp dx dy, dp dy^2; 8..10 sum a T g_C; 7, 11 unused.
 // POSE: only slots 0, 1, 2, 4, 5, 6 (what the pose gradient needs).
-template <bool POSE, int NB>
+template <bool POSE, int NB, int LW>
 __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     static_assert(NB % 32 == 0 && NB <= kBatch, "batch depth: a multiple of 32, at most kBatch");
+    static_assert(LW >= 3 && (1 << LW) * kPatchH <= kTilePix, "tile width: 8 to 32 pixels");
     __shared__ float4 sP0[NB], sC[NB], sQ[NB], sBox[NB];
     __shared__ float2 sP1[NB];
     __shared__ float sAcc[NB * kAccStride];
@@ -141,11 +142,12 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     const ViewInfo vi = L.ws.views[s_view];
     const uint32_t local = tile - vi.tile_base;
     const int tx = (int)(local % (uint32_t)vi.tiles_x), ty = (int)(local / (uint32_t)vi.tiles_x);
-    const int pu0 = (warp & 1) * kPatchW, pv0 = (warp >> 1) * kPatchH;
+    constexpr int kPPR = (1 << LW) / kPatchW;  // 8 x 4 patches per patch row (tile width 2^LW)
+    const int pu0 = (warp % kPPR) * kPatchW, pv0 = (warp / kPPR) * kPatchH;
     const int lu = pu0 + (lane & (kPatchW - 1)), lv = pv0 + lane / kPatchW;
-    const int px = tx * kTile + lu, py = ty * kTile + lv;
+    const int px = (tx << LW) + lu, py = (ty << vi.tile_lh) + lv;
     const bool inside = px < vi.width && py < vi.height;
-    const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
+    const float x0 = (float)(tx << LW), y0 = (float)(ty << vi.tile_lh);
     const float fu = (float)lu, fv = (float)lv;
     const float pu_lo = (float)pu0, pu_hi = (float)(pu0 + kPatchW - 1);
     const float pv_lo = (float)pv0, pv_hi = (float)(pv0 + kPatchH - 1);
@@ -313,24 +315,39 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     count_pairs(n_eval, n_contrib, &L.ws.hdr->bwd_evals, &L.ws.hdr->bwd_contrib);
 }
 
-template <int NB>
+template <int NB, int LW>
 void launch_backward_nb(const BackwardLaunch &L, cudaStream_t st) {
     if (L.pose_only)
-        k_backward<true, NB><<<L.d.T, kTilePix, 0, st>>>(L);
+        k_backward<true, NB, LW><<<L.d.T, tile_threads(L.d), 0, st>>>(L);
     else
-        k_backward<false, NB><<<L.d.T, kTilePix, 0, st>>>(L);
+        k_backward<false, NB, LW><<<L.d.T, tile_threads(L.d), 0, st>>>(L);
+}
+
+template <int NB>
+cudaError_t launch_backward_lw(const BackwardLaunch &L, cudaStream_t st) {
+    switch (tile_lw(L.d)) {
+        case 3: launch_backward_nb<NB, 3>(L, st); break;
+        case 4: launch_backward_nb<NB, 4>(L, st); break;
+        case 5: launch_backward_nb<NB, 5>(L, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_backward(const BackwardLaunch &L, cudaStream_t st) {
     if (L.d.T == 0) return cudaSuccess;
+    // a batch stages at most one Gaussian per thread of the tile block
+    const uint32_t nb = L.d.bwd_batch ? L.d.bwd_batch : (uint32_t)kBatch;
+    if (nb > tile_threads(L.d)) return cudaErrorInvalidValue;
+    cudaError_t e;
     switch (L.d.bwd_batch) {
         case 0:
-        case 256: launch_backward_nb<256>(L, st); break;
-        case 128: launch_backward_nb<128>(L, st); break;
-        case 64: launch_backward_nb<64>(L, st); break;
+        case 256: e = launch_backward_lw<256>(L, st); break;
+        case 128: e = launch_backward_lw<128>(L, st); break;
+        case 64: e = launch_backward_lw<64>(L, st); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace gsk

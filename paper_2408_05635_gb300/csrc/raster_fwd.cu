@@ -1,6 +1,6 @@
 // raster_fwd.cu -- front-to-back compositing of colour, depth and silhouette.
 //
-// One block per 16 x 16 tile, one thread per pixel.  The block first sorts its tile's
+// One block per tile (16 x 16 by default), one thread per pixel.  The block first sorts its tile's
 // list (tile_sort.cuh).  For pixel p and the tile's
 // Gaussians in (depth, index) order:
 //   C(p) = sum_i c_i a_i T_i   (Eq. 2)
@@ -26,9 +26,10 @@ namespace gsk {
 
 __device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
-template <bool LOSS, int NB>
+template <bool LOSS, int NB, int LW>
 __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     static_assert(NB % 32 == 0 && NB <= kBatch, "batch depth: a multiple of 32, at most kBatch");
+    static_assert(LW >= 3 && (1 << LW) * kPatchH <= kTilePix, "tile width: 8 to 32 pixels");
     __shared__ float4 sP0[NB], sC[NB], sBox[NB];
     __shared__ float2 sP1[NB];
     __shared__ uint8_t sList[kTilePix / 32][NB];
@@ -44,11 +45,12 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     const ViewInfo vi = L.ws.views[view];
     const uint32_t local = tile - vi.tile_base;
     const int tx = (int)(local % (uint32_t)vi.tiles_x), ty = (int)(local / (uint32_t)vi.tiles_x);
-    const int pu0 = (warp & 1) * kPatchW, pv0 = (warp >> 1) * kPatchH;
+    constexpr int kPPR = (1 << LW) / kPatchW;  // 8 x 4 patches per patch row (tile width 2^LW)
+    const int pu0 = (warp % kPPR) * kPatchW, pv0 = (warp / kPPR) * kPatchH;
     const int lu = pu0 + (lane & (kPatchW - 1)), lv = pv0 + lane / kPatchW;
-    const int px = tx * kTile + lu, py = ty * kTile + lv;
+    const int px = (tx << LW) + lu, py = (ty << vi.tile_lh) + lv;
     const bool inside = px < vi.width && py < vi.height;
-    const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
+    const float x0 = (float)(tx << LW), y0 = (float)(ty << vi.tile_lh);
     const float fu = (float)lu, fv = (float)lv;
     const float pu_lo = (float)pu0, pu_hi = (float)(pu0 + kPatchW - 1);
     const float pv_lo = (float)pv0, pv_hi = (float)(pv0 + kPatchH - 1);
@@ -186,30 +188,45 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
         __syncthreads();
         if (tid == 0) {
             DF s{0.f, 0.f};
-            for (int w = 0; w < kTilePix / 32; ++w) s = df_add(s, DF{s_loss[w], 0.f});
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = df_add(s, DF{s_loss[w], 0.f});
             L.ws.tile_loss[tile] = df_pack(s);
         }
     }
 }
 
-template <int NB>
+template <int NB, int LW>
 void launch_forward_nb(const ForwardLaunch &L, cudaStream_t st) {
     if (L.t_rgb)
-        k_forward<true, NB><<<L.d.T, kTilePix, 0, st>>>(L);
+        k_forward<true, NB, LW><<<L.d.T, tile_threads(L.d), 0, st>>>(L);
     else
-        k_forward<false, NB><<<L.d.T, kTilePix, 0, st>>>(L);
+        k_forward<false, NB, LW><<<L.d.T, tile_threads(L.d), 0, st>>>(L);
+}
+
+template <int NB>
+cudaError_t launch_forward_lw(const ForwardLaunch &L, cudaStream_t st) {
+    switch (tile_lw(L.d)) {
+        case 3: launch_forward_nb<NB, 3>(L, st); break;
+        case 4: launch_forward_nb<NB, 4>(L, st); break;
+        case 5: launch_forward_nb<NB, 5>(L, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_forward(const ForwardLaunch &L, cudaStream_t st) {
     if (L.d.T == 0) return cudaSuccess;
+    // a batch stages at most one Gaussian per thread of the tile block
+    const uint32_t nb = L.d.fwd_batch ? L.d.fwd_batch : (uint32_t)kBatch;
+    if (nb > tile_threads(L.d)) return cudaErrorInvalidValue;
+    cudaError_t e;
     switch (L.d.fwd_batch) {
         case 0:
-        case 256: launch_forward_nb<256>(L, st); break;
-        case 128: launch_forward_nb<128>(L, st); break;
-        case 64: launch_forward_nb<64>(L, st); break;
+        case 256: e = launch_forward_lw<256>(L, st); break;
+        case 128: e = launch_forward_lw<128>(L, st); break;
+        case 64: e = launch_forward_lw<64>(L, st); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace gsk

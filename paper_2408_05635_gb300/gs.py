@@ -78,11 +78,19 @@ class gs_problem(ctypes.Structure):
 
 
 class gs_schedule(ctypes.Structure):
-    _fields_ = [("sub_buckets", c_int32), ("fwd_batch", c_int32), ("bwd_batch", c_int32), ("reserved", c_int32)]
+    _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("sub_buckets", c_int32), ("fwd_batch", c_int32),
+                ("bwd_batch", c_int32), ("reserved", c_int32)]
 
 
 class gs_tune_entry(ctypes.Structure):
-    _fields_ = [("stage", c_int32), ("value", c_int32), ("ms", ctypes.c_float)]
+    _fields_ = [("stage", c_int32), ("ms", ctypes.c_float), ("schedule", gs_schedule)]
+
+
+SCHEDULE_FIELDS = ("tile_w", "tile_h", "sub_buckets", "fwd_batch", "bwd_batch")
+
+
+def schedule_dict(s: gs_schedule) -> dict:
+    return {k: int(getattr(s, k)) for k in SCHEDULE_FIELDS}
 
 
 class gs_kernel_time(ctypes.Structure):
@@ -282,26 +290,29 @@ def gs_get_schedule(ctx) -> gs_schedule:
     return s
 
 
-def gs_set_schedule(ctx, sub_buckets: int, fwd_batch: int, bwd_batch: int) -> None:
-    s = gs_schedule(int(sub_buckets), int(fwd_batch), int(bwd_batch), 0)
+def gs_set_schedule(ctx, tile_w: int, tile_h: int, sub_buckets: int, fwd_batch: int, bwd_batch: int) -> None:
+    s = gs_schedule(int(tile_w), int(tile_h), int(sub_buckets), int(fwd_batch), int(bwd_batch), 0)
     _check(ctx, load().gs_set_schedule(ctx, ctypes.byref(s)), "gs_set_schedule")
 
 
-TUNE_STAGES = ("sub_buckets", "fwd_batch", "bwd_batch")
+TUNE_STAGES = ("tile", "sub_buckets", "fwd_batch", "bwd_batch")
+TUNE_MAX = 13
 
 
 def gs_autotune(ctx, prob: gs_problem, g: gs_gaussians, poses, targets: gs_targets, ws, ws_bytes: int,
-                pose_only: bool = True, reps: int = 10, stream=None) -> tuple[gs_schedule, list[tuple[str, int, float]]]:
-    """Time every sub-bucket count and batch depth on this problem, set the fastest on
-    the context and return it with the measurements (setting name, value, ms per pass)."""
-    table = (gs_tune_entry * 9)()
+                pose_only: bool = True, reps: int = 10, stream=None) -> tuple[gs_schedule, list[tuple[str, dict, float]]]:
+    """Time the tile shapes, sub-bucket counts and batch depths on this problem, set the
+    fastest on the context and return it with the measurements (stage, schedule timed,
+    ms per pass; -1 where the setting overflowed the pair capacity)."""
+    table = (gs_tune_entry * TUNE_MAX)()
     cnt = c_int32(0)
     best = gs_schedule()
     st = load().gs_autotune(ctx, ctypes.byref(prob), ctypes.byref(g), _ptr(poses), ctypes.byref(targets),
-                            int(bool(pose_only)), int(reps), _ptr(ws), ws_bytes, table, 9, ctypes.byref(cnt),
-                            ctypes.byref(best), _stream(stream))
+                            int(bool(pose_only)), int(reps), _ptr(ws), ws_bytes, table, TUNE_MAX,
+                            ctypes.byref(cnt), ctypes.byref(best), _stream(stream))
     _check(ctx, st, "gs_autotune")
-    rows = [(TUNE_STAGES[table[k].stage], int(table[k].value), float(table[k].ms)) for k in range(min(9, cnt.value))]
+    rows = [(TUNE_STAGES[table[k].stage], schedule_dict(table[k].schedule), float(table[k].ms))
+            for k in range(min(TUNE_MAX, cnt.value))]
     return best, rows
 
 
@@ -659,11 +670,11 @@ class Rasterizer:
     # -- launch schedule -----------------------------------------------------------------
     @property
     def schedule(self) -> dict:
-        s = gs_get_schedule(self.ctx)
-        return {"sub_buckets": s.sub_buckets, "fwd_batch": s.fwd_batch, "bwd_batch": s.bwd_batch}
+        return schedule_dict(gs_get_schedule(self.ctx))
 
-    def set_schedule(self, sub_buckets: int = 4, fwd_batch: int = 256, bwd_batch: int = 256) -> None:
-        gs_set_schedule(self.ctx, sub_buckets, fwd_batch, bwd_batch)
+    def set_schedule(self, tile_w: int = 16, tile_h: int = 16, sub_buckets: int = 4, fwd_batch: int = 256,
+                     bwd_batch: int = 256) -> None:
+        gs_set_schedule(self.ctx, tile_w, tile_h, sub_buckets, fwd_batch, bwd_batch)
 
     def autotune(self, prob: gs_problem, g: GaussianTensors, poses: torch.Tensor, targets, pose_only: bool = True,
                  reps: int = 10, stream=None) -> dict:
@@ -673,9 +684,8 @@ class Rasterizer:
         trgb, tdep, tprior = targets
         tg = gs_targets(_ptr(trgb), _ptr(tdep), _ptr(tprior))
         best, rows = gs_autotune(self.ctx, prob, g.c(), poses, tg, ws, nb, pose_only, reps, stream)
-        return {"schedule": {"sub_buckets": best.sub_buckets, "fwd_batch": best.fwd_batch,
-                             "bwd_batch": best.bwd_batch},
-                "timings_ms": [{"setting": k, "value": v, "ms": round(ms, 4)} for k, v, ms in rows]}
+        return {"schedule": schedule_dict(best),
+                "timings_ms": [{"stage": k, "schedule": sc, "ms": round(ms, 4)} for k, sc, ms in rows]}
 
     def sync(self, stream=None) -> gs_counts:
         st, c = gs_sync_status(self.ctx, stream)
