@@ -232,7 +232,7 @@ def run_sequence(a, dev, stream):
     out = {"workload": f"{F} frames 640x480 along a spline around the room, 100 tracking iterations per frame"}
     # (1) tracking on the fixed 2M-Gaussian map, FP16 attributes
     gt = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=torch.float16)
-    tr = slam.Tracker(cam, 100, device=dev)
+    tr = slam.Tracker(cam, 100, device=dev, autotune_reps=a.autotune_reps)
     pose = torch.tensor(gt_poses[0], dtype=torch.float64, device=dev)
     with torch.cuda.stream(stream):
         tr.track(gt, pose, *frames[1], stream=stream)  # plan and capture
@@ -249,12 +249,13 @@ def run_sequence(a, dev, stream):
     out["tracking_fixed_map"] = {"map": f"{N_SEQ_GAUSS // 1000}k room Gaussians, fp16 attributes",
                                  "ms_per_frame": round(1e3 * wall / (F - 1), 3),
                                  "tracking_iters_per_s": round(100 * (F - 1) / wall, 1),
-                                 "mpix_per_s": round(100 * (F - 1) * P / wall / 1e6, 1), "replans": tr.replans, **rep}
+                                 "mpix_per_s": round(100 * (F - 1) * P / wall / 1e6, 1), "replans": tr.replans,
+                                 "launch_schedule": tr.tune["schedule"] if tr.tune else tr.R.schedule, **rep}
     del gt
     # (2) the whole loop from an empty map, with anisotropic Gaussians and with the
     # isotropic ones of Eq. 1 as written
     for key, iso in (("slam_from_empty_map", False), ("slam_from_empty_map_isotropic", True)):
-        cfg = slam.SlamConfig(lowp=torch.float16, isotropic=iso)
+        cfg = slam.SlamConfig(lowp=torch.float16, isotropic=iso, autotune_reps=a.autotune_reps)
         S = slam.Slam(cam, cfg, device=dev)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -269,7 +270,8 @@ def run_sequence(a, dev, stream):
                     "keyframes": S.stats["keyframes"], "map_iters_per_keyframe": cfg.map_iters,
                     "first_frame_map_iters": cfg.first_map_iters, "window": cfg.window, "final_map_gaussians": S.n,
                     "added_total": int(sum(S.stats["added"])), "pruned_total": int(sum(S.stats["pruned"])),
-                    "replans": S.tracker.replans, **rep, **{k: round(v, 3) for k, v in q.items()}}
+                    "replans": S.tracker.replans, "schedule_tunings": S.tracker.tunes,
+                    "launch_schedule": S.tracker.R.schedule, **rep, **{k: round(v, 3) for k, v in q.items()}}
         S.close()
         del S
     return out

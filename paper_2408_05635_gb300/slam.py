@@ -34,16 +34,23 @@ class SlamConfig:
     capacity: int = 4_000_000     # Gaussians the map can hold
     prune: bool = True            # remove Gaussians with opacity < opacity_min after mapping
     isotropic: bool = False       # Eq. 1 as written: no rotation, one radius per Gaussian
+    autotune_reps: int = 0        # > 0: the tracker tunes its launch schedule (gs_autotune,
+                                  # that many passes per setting) on the first frame and
+                                  # again whenever the map has doubled since
 
 
 class Tracker:
     """Tracking with the map fixed (Sec. III-B): `iters` decoupled rotation / translation
     iterations in one gs_track_step call (one CUDA graph), starting from a given pose
     (the previous frame's estimate in a sequence).  The frame is copied into fixed device
-    buffers so the graph is reused from frame to frame."""
+    buffers so the graph is reused from frame to frame.  With autotune_reps > 0 the launch
+    schedule is tuned on the first frame and re-tuned when the map has doubled."""
 
-    def __init__(self, cam, iters: int, config: gs.Config | None = None, device="cuda", margin: float = 1.5):
+    def __init__(self, cam, iters: int, config: gs.Config | None = None, device="cuda", margin: float = 1.5,
+                 autotune_reps: int = 0):
         self.cam, self.iters, self.margin = cam, int(iters), margin
+        self.autotune_reps = int(autotune_reps)
+        self.tuned_n, self.tune, self.tunes = None, None, 0
         self.dev = torch.device(device)
         self.R = gs.Rasterizer(config or gs.Config(), device)
         P = int(cam.width) * int(cam.height)
@@ -72,6 +79,15 @@ class Tracker:
             self.pose.copy_(start.reshape(1, 7))
             self.adam.zero_()
             if self.prob is None or key != self.key:
+                if self.autotune_reps > 0 and (self.tuned_n is None or g.n > 2 * self.tuned_n):
+                    # tuned on a problem with twice the pair margin, so that the smaller
+                    # tiles (more pairs) are timed too
+                    tprob = self.R.plan(g, [self.cam], self.pose, margin=2 * self.margin)
+                    tgt = (self.t_rgb, self.t_depth, self.t_prior if has_prior else None)
+                    self.tune = self.R.autotune(tprob, g, self.pose, tgt, pose_only=True, reps=self.autotune_reps,
+                                                stream=stream)
+                    self.tuned_n = g.n
+                    self.tunes += 1
                 self.prob = self.R.plan(g, [self.cam], self.pose, margin=self.margin)
                 self.key = key
             ws, nb = self.R.workspace(self.prob)
@@ -100,7 +116,7 @@ class Slam:
         c = self.cfg
         self.map = gs.Map(c.capacity, device, lowp_dtype=c.lowp, isotropic=c.isotropic)
         self.spare = gs.Map(c.capacity, device, lowp_dtype=c.lowp, isotropic=c.isotropic) if c.prune else None
-        self.tracker = Tracker(cam, c.track_iters, config, device, c.plan_margin)
+        self.tracker = Tracker(cam, c.track_iters, config, device, c.plan_margin, c.autotune_reps)
         self.mapper = gs.Rasterizer(config or gs.Config(), device)
         self.grads = {k: torch.zeros_like(self.map.p[k]) for k in self.map.GROUPS}
         self.keyframes: list[tuple[torch.Tensor, tuple]] = []

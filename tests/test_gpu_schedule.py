@@ -178,3 +178,34 @@ def test_tracking_graph_follows_the_schedule():
     # the backward's atomics make even two runs of one schedule differ at rounding level
     assert np.abs(out[0] - out[2]).max() < 1e-6, np.abs(out[0] - out[2]).max()
     assert np.abs(out[0] - out[1]).max() < 1e-5, np.abs(out[0] - out[1]).max()
+
+
+def test_tracker_tunes_on_the_first_frame_and_when_the_map_doubles():
+    """slam.Tracker with autotune_reps: one gs_autotune on the first frame, none while the
+    map keeps its size, another once it has doubled; the tracked pose matches an untuned
+    tracker's to rounding (the tuned schedule may move the tile origins)."""
+    g = scenes.room_scene(30_000, seed=6)
+    cam = scenes.Cam(262.5, 262.5, 159.5, 119.5, 320, 240)
+    truth = scenes.tracking_gt_pose()
+    start = scenes.perturb_pose(truth, np.random.default_rng(7), 1.0, 0.03)
+    rgb, depth = scenes.raycast_room(truth, cam, seed=6)
+    frame = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (rgb, depth)]
+    gt = gs.GaussianTensors.from_numpy(g)
+    s0 = torch.tensor(start, dtype=torch.float64, device="cuda")
+    plain = slam.Tracker(cam, 5)
+    p_plain = plain.track(gt, s0, *frame).cpu().numpy()
+    plain.close()
+    tr = slam.Tracker(cam, 5, autotune_reps=2)
+    p1 = tr.track(gt, s0, *frame).cpu().numpy()
+    assert tr.tunes == 1 and tr.tune["schedule"] == tr.R.schedule
+    assert len(tr.tune["timings_ms"]) >= 7 and all(r["ms"] > 0 for r in tr.tune["timings_ms"])
+    tr.track(gt, s0, *frame)
+    assert tr.tunes == 1
+    doubled = scenes.Gaussians(*(None if a is None else np.concatenate([a, a]) for a in g.arrays()))
+    tr.track(gs.GaussianTensors.from_numpy(doubled), s0, *frame)
+    assert tr.tunes == 1  # exactly twice the size: not more than double
+    tripled = scenes.Gaussians(*(np.concatenate([a, a, a]) for a in g.arrays()))
+    tr.track(gs.GaussianTensors.from_numpy(tripled), s0, *frame)
+    assert tr.tunes == 2
+    tr.close()
+    assert np.abs(p1 - p_plain).max() < 1e-4, np.abs(p1 - p_plain).max()
