@@ -38,6 +38,7 @@ N_GAUSS = 200_000
 # the forward: the per-unit algorithmic work of the two compositing kernels.
 FLOP_BWD_PAIR = 58
 FLOP_FWD_PAIR = 23
+FLOP_BPROJ_REC = 300  # about: the chain rule of one record to the pose (k_bproject, pose only)
 N_SM, FP32_LANES = 152, 128  # GB300: FP32 FMA lanes per SM
 ITERS_PER_FRAME = 40  # tracking iterations per frame (the 640 x 480 tracking workload); the
                       # pose and Adam state restart from the frame's start pose every 40 steps
@@ -319,7 +320,7 @@ def run_isotropic(dev, stream, steps: int = 400):
     return res
 
 
-def run_batched(a, dev, stream):
+def run_batched(a, dev, stream, mhz: float = 2070.0):
     """The batched / low-precision form beside the plain one, on the same views: all 512
     hypotheses tracked in one call with BF16 attributes, against the same keyframes'
     views tracked one call per view with FP32 attributes (one hypothesis per keyframe)."""
@@ -352,8 +353,13 @@ def run_batched(a, dev, stream):
         track(R, gtb, prob, ws, nb, poses, adam, loss, tg)
     gs.gs_set_profiling(R.ctx, True)
     track(R, gtb, prob, ws, nb, poses, adam, loss, tg)
-    kernels = {k: round(1e3 * ms, 1) for k, ms in gs.gs_kernel_times(R.ctx)}
+    kms = dict(gs.gs_kernel_times(R.ctx))
+    kernels = {k: round(1e3 * ms, 1) for k, ms in kms.items()}
     gs.gs_set_profiling(R.ctx, False)
+    _, cb = gs.gs_sync_status(R.ctx, stream)  # the work of that iteration, counted on the device
+    rl_kernels = kernel_rooflines(kms, N_BATCH_GAUSS, V, 22, int(cb.n_records), int(cb.n_pairs),
+                                  tile_counters(cams, sched["schedule"]), int(cb.fwd_contrib), int(cb.bwd_contrib),
+                                  mhz)
     poses.copy_(start)
     adam.zero_()
     torch.cuda.synchronize(dev)
@@ -413,7 +419,7 @@ def run_batched(a, dev, stream):
         "views": V, "pixels_per_step": P, "workspace_gb": round(ws_bytes / 1e9, 2),
         "batched_bf16": {"ms_per_step": b_ms, "view_iters_per_s": batched_view_its, "mpix_per_s": P / b_ms / 1e3,
                          "launch": "one gs_track_step call (one CUDA graph) for all views", "kernels_us": kernels,
-                         "launch_schedule": sched},
+                         "roofline_kernels": rl_kernels, "launch_schedule": sched},
         "plain_fp32": {"views_timed": len(sub), "ms_per_view_iter": plain_ms / len(sub),
                        "view_iters_per_s": plain_view_its, "mpix_per_s": sub_pix / plain_ms / 1e3,
                        "launch": "one gs_track_step call per view", "launch_schedule": Rp_sched},
@@ -559,6 +565,62 @@ def run_reference(a, rank, world):
                              "sample": sample},
             "e2e": {"value": mpix, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def hbm_peak_gbs() -> tuple[float, str]:
+    """Measured HBM copy bandwidth of this GPU type (MEASURED_PEAKS.json), else the
+    fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def tile_counters(cams, sched: dict) -> int:
+    """Per-(tile, sub-bucket) counters the scan reads: tiles of the schedule's shape
+    over all views times the sub-buckets in use (at most 2^22 counters)."""
+    tw, th = sched["tile_w"], sched["tile_h"]
+    T = sum(-(-c.width // tw) * -(-c.height // th) for c in cams)
+    S = sched["sub_buckets"]
+    while S > 1 and T * S > (1 << 22):
+        S //= 2
+    return T * S
+
+
+def kernel_rooflines(kern_ms: dict, n_gauss: int, views: int, attr_bytes: int, records: int, pairs: int,
+                     counters: int, fwd_contrib: int, bwd_contrib: int, mhz: float) -> dict:
+    """Every kernel of a tracking iteration against the roofline that bounds it: its
+    algorithmic bytes or FLOPs per launch (from the work counted on the device) over its
+    CUDA-event time (markers around every kernel, so each time includes its launch gap),
+    as a fraction of the measured HBM copy bandwidth or of the FP32 FMA peak at the
+    sampled SM clock.  k_finalize is a chain of dependent steps (latency, no roofline)."""
+    hbm, hbm_from = hbm_peak_gbs()
+    fp32 = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    work = {
+        "k_project": ("hbm", 12 * n_gauss * views + (attr_bytes + 96) * records,
+                      f"12 B of means per (Gaussian, view); {attr_bytes} B of other parameters and a 96 B record "
+                      "per visible (Gaussian, view)"),
+        "k_scan_tiles": ("hbm", 12 * counters, "12 B per (tile, sub-bucket) counter"),
+        "k_emit": ("hbm", 12 * pairs, "12 B per (Gaussian, tile) pair"),
+        "k_forward": ("alu", FLOP_FWD_PAIR * fwd_contrib, f"{FLOP_FWD_PAIR} FLOP per contributing pair"),
+        "k_backward": ("alu", FLOP_BWD_PAIR * bwd_contrib, f"{FLOP_BWD_PAIR} FLOP per differentiated pair"),
+        "k_bproject": ("alu", FLOP_BPROJ_REC * records, f"about {FLOP_BPROJ_REC} FLOP per record"),
+    }
+    out = {}
+    for k, ms in kern_ms.items():
+        if k not in work or ms <= 0:
+            out[k] = {"bound": "latency", "us": round(1e3 * ms, 2)}
+            continue
+        bound, units, what = work[k]
+        if bound == "hbm":
+            achieved, peak, unit = units / (ms / 1e3) / 1e9, hbm, "GB/s"
+        else:
+            achieved, peak, unit = units / (ms / 1e3) / 1e12, fp32, "TFLOP/s"
+        out[k] = {"bound": bound, "us": round(1e3 * ms, 2), "achieved": float(f"{achieved:.4g}"),
+                  "peak": round(peak, 1), "unit": unit, "frac": float(f"{achieved / peak:.3g}"), "work": what}
+    out["peaks_from"] = f"HBM {hbm:.0f} GB/s ({hbm_from}); FP32 {fp32:.1f} TFLOP/s at {mhz:.0f} MHz"
+    return out
 
 
 def max_over_ranks(value: float, world: int, device) -> float:
@@ -737,11 +799,15 @@ def main():
             "kernels_us_note": f"{n_break} steps with event markers around every kernel (they add a few us each); "
                                f"the timed steps mark only {dominant}",
             "pairs_per_step": {k: v // a.steps for k, v in contrib.items()},
+            "roofline_kernels": kernel_rooflines(breakdown, N_GAUSS, 1, 44, int(counts.n_records), int(counts.n_pairs),
+                                                 tile_counters([cam], sched["schedule"]),
+                                                 contrib["fwd_contrib"] // a.steps, contrib["bwd_contrib"] // a.steps,
+                                                 mhz),
         }
         if world == 1:
             line["isotropic"] = run_isotropic(dev, stream)
         if world == 1 and a.batched_steps > 0:
-            line["batched"] = run_batched(a, dev, stream)
+            line["batched"] = run_batched(a, dev, stream, mhz)
         if world == 1 and a.mapping_steps > 0:
             line["mapping"] = run_mapping(a, dev, stream)
         if world == 1 and a.sequence_frames > 0:
