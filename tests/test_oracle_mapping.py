@@ -196,6 +196,10 @@ def test_ms_ssim_identities_and_closed_forms():
     assert omx.ms_ssim(noisy, img)["ms_ssim"] == pytest.approx(s1, rel=1e-12)
     g = omx.gaussian_window()
     assert g.sum() == pytest.approx(1.0) and np.argmax(g) == 5 and g[0] == pytest.approx(g[-1])
+    # the 11-tap window samples a Gaussian of sigma 1.5: its second moment is sigma^2 less
+    # the tails beyond +-5 px (0.3 %)
+    x = np.arange(11) - 5.0
+    assert float(np.sum(g * x * x)) == pytest.approx(1.5 ** 2, rel=5e-3)
     assert sum(omx.MSSSIM_WEIGHTS) == pytest.approx(1.0, abs=1e-3)
 
 
