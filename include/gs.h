@@ -143,7 +143,8 @@ typedef struct {
 void gs_default_config(gs_config *cfg);
 
 /* Create a context with a copy of cfg (NULL = defaults).  *out receives the handle.
- * Errors: GS_ERR_INVALID_ARG (bad setting or NULL out), GS_ERR_OOM, GS_ERR_CUDA. */
+ * Errors: GS_ERR_INVALID_ARG (bad setting or NULL out), GS_ERR_UNSUPPORTED (a tile shape
+ * outside the set gs_schedule lists), GS_ERR_OOM, GS_ERR_CUDA. */
 gs_status gs_create(gs_ctx **out, const gs_config *cfg);
 
 /* Destroy a context (NULL is allowed).  Waits for nothing: the caller must make sure no
@@ -169,7 +170,8 @@ gs_status gs_workspace_size(const gs_ctx *ctx, const gs_problem *prob, size_t *b
  * For every view k and Gaussian i: camera-frame mean R_k x_i + t_k; drop it when its
  * depth is <= z_near; Sigma = Rg diag(s^2) Rg^T; Sigma' = J W Sigma W^T J^T (+ dilation);
  * mu' = pi_m; o = sigmoid(logit); the opacity-aware support o exp(-d^2/2) >= alpha_min;
- * then one (tile, depth) entry for every 16 x 16 tile the support ellipse meets.
+ * then one (tile, depth) entry for every tile the support ellipse meets (tiles of the
+ * context's schedule, 16 x 16 by default).
  * poses: device, n_views x 7 doubles, read on the device when the kernels run.
  * ws: device workspace of at least gs_workspace_size bytes, 256-byte aligned; it
  * holds the projected state that gs_forward / gs_backward consume.  The Gaussian
