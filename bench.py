@@ -799,6 +799,8 @@ def main():
             "kernels_us_note": f"{n_break} steps with event markers around every kernel (they add a few us each); "
                                f"the timed steps mark only {dominant}",
             "pairs_per_step": {k: v // a.steps for k, v in contrib.items()},
+            # (pixel, Gaussian) pairs that contributed to Eqs. 2-4 or were differentiated, per second
+            "useful_pair_evals_per_s": (contrib["fwd_contrib"] + contrib["bwd_contrib"]) / (ms / 1e3),
             "roofline_kernels": kernel_rooflines(breakdown, N_GAUSS, 1, 44, int(counts.n_records), int(counts.n_pairs),
                                                  tile_counters([cam], sched["schedule"]),
                                                  contrib["fwd_contrib"] // a.steps, contrib["bwd_contrib"] // a.steps,
