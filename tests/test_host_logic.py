@@ -116,3 +116,70 @@ def test_tracker_gives_up_after_repeated_overflows(fake):
     fake.append((6, 0))  # GS_ERR_TIMEOUT: not a capacity problem, so it is raised
     with pytest.raises(gs.GsError):
         tr.track(_map(10), start, *_frame())
+
+
+class FakeMapper(FakeRasterizer):
+    """The mapping side of the fake: renders a silhouette and records the gradient calls."""
+
+    sil_value = 1.0
+
+    def render(self, prob, g, poses, targets=None, stream=None, images=True):
+        self.log.append(("render", g.n))
+        return {"sil": torch.full((CAM.height * CAM.width,), self.sil_value)}
+
+    def sync(self, stream=None):
+        return SimpleNamespace(n_pairs=0)
+
+    def mapping_grads(self, g, cams, poses, targets, chunk=2, grads=None, probs=None, stream=None):
+        self.log.append(("grads", len(cams), chunk, len(probs)))
+        return {"grads": grads}
+
+
+def test_slam_keyframes_window_iterations_and_removal(fake, monkeypatch):
+    """slam.Slam on ten frames: keyframes at 0, 4 and 8; the first keyframe's Gaussians
+    from every pixel with depth, later ones only where the silhouette is low; 5 Adam
+    iterations on the first keyframe, 2 after, each over the last `window` keyframes in
+    chunks; removal into the spare map after every keyframe, the two maps swapping."""
+    monkeypatch.setattr(gs, "Rasterizer", FakeMapper)
+    monkeypatch.setattr(gs, "load", lambda *a, **k: None)
+    monkeypatch.setattr(gs, "gs_map_scratch_bytes", lambda items: 256)
+    monkeypatch.setattr(gs, "_ptr", lambda t: None if t is None else t.data_ptr())  # host tensors here
+    monkeypatch.setattr(gs, "gs_default_map_config", lambda: gs.gs_map_config(sil_add=0.5, opacity_min=0.005))
+    steps = []
+
+    def add(cfg, m, count, cam, pose, rgb, depth, sil, scr, nb, err, stream=None):
+        take = depth.reshape(-1) > 0
+        if sil is not None:
+            take &= sil.reshape(-1) < cfg.sil_add
+        count += int(take.sum())
+
+    def adam(cfg, m, count, grads, step, stream=None):
+        steps.append(int(step))
+
+    def prune(cfg, src, n_src, dst, n_dst, scr, nb, stream=None):
+        n_dst.fill_(int(n_src.item()) - 1)  # one Gaussian faded
+
+    monkeypatch.setattr(gs, "gs_map_add", add)
+    monkeypatch.setattr(gs, "gs_map_adam_step", adam)
+    monkeypatch.setattr(gs, "gs_map_prune", prune)
+    cfg = slam.SlamConfig(track_iters=3, keyframe_every=4, window=2, map_iters=2, first_map_iters=5, map_chunk=1,
+                          capacity=4096, prune=True)
+    S = slam.Slam(CAM, cfg, device="cpu")
+    first = S.map
+    P = CAM.width * CAM.height
+    rgb, depth = _frame()
+    depth[0, :5] = 0.0  # five pixels without a measurement
+    for k in range(10):
+        FakeMapper.sil_value = 0.2 if k == 8 else 1.0  # frame 8 sees new surface everywhere
+        S.process(k, rgb, depth, first_pose=[1.0, 0, 0, 0, 0, 0, 0] if k == 0 else None)
+    assert S.stats["keyframes"] == 3 and len(S.keyframes) == 3 and len(S.poses) == 10
+    # frame 0: every pixel with depth; frame 4: none (the silhouette covers it); frame 8: all again
+    assert S.stats["added"] == [P - 5, 0, P - 5]
+    assert S.stats["pruned"] == [1, 1, 1] and S.n == 2 * (P - 5) - 3
+    assert steps == [1, 2, 3, 4, 5, 1, 2, 1, 2]
+    grads = [e for e in S.mapper.log if e[0] == "grads"]
+    # the window holds at most 2 keyframes, one view per chunk
+    assert [e[1] for e in grads] == [1] * 5 + [2] * 2 + [2] * 2 and all(e[3] == e[1] for e in grads)
+    # three removals: the maps swapped three times
+    assert S.map is not first and S.spare is first
+    S.close()
