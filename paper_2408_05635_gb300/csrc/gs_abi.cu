@@ -912,6 +912,7 @@ gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g
         return fail(ctx, GS_ERR_CAPACITY, "the problem overflowed its capacities during tuning; schedule unchanged");
     ctx->sched = cur;
     if (best) *best = cur;
+    ctx->err.clear();  // a candidate the problem could not take left its message
     return GS_OK;
 }
 
