@@ -303,22 +303,26 @@ typedef struct {
     gs_schedule schedule; /* the schedule of the timed passes                          */
 } gs_tune_entry;
 
-/* Autotuner of the launch schedule for one problem: on the given Gaussians, poses and
- * targets it times, stage after stage, the tile shapes 16 x 16, 32 x 8, 16 x 8 and 8 x 8
- * (one whole pass each, batch depths capped at the tile's threads), every sub-bucket
- * count (binning), every forward batch depth and every backward batch depth that the
- * chosen tile allows (the pose-only walk of tracking when pose_only != 0, the walk for
- * all Gaussian parameters otherwise), `reps` passes each, keeps the fastest setting of
- * each stage for the next stage (the first candidate, the context's current setting for
- * the tile, unless another is at least 1 % faster) and sets it on the context.  It uses the workspace (sized by gs_workspace_size for `prob`) as gs_project
- * does and synchronises `stream`, so it cannot be captured into a graph; afterwards no
- * projection is bound (call gs_project or gs_track_step next).  table (host, cap
- * entries, may be NULL) receives the measurements in order, *count (may be NULL) their
- * number (13 at most); best (may be NULL) the chosen schedule.  A tile shape whose pairs
- * overflow pair_capacity is skipped (ms = -1); an overflow of the context's current
- * schedule is reported as CAPACITY (the schedule is then left unchanged).
+/* Autotuner of the launch schedule for one problem.  On the given Gaussians, poses and
+ * targets it times, stage after stage:
+ *   - the tile shapes 16 x 16, 32 x 8, 16 x 8 and 8 x 8, one whole pass each (batch
+ *     depths capped at the tile's threads);
+ *   - every sub-bucket count (the binning);
+ *   - every forward batch depth, then every backward batch depth the chosen tile allows
+ *     (the pose-only walk of tracking when pose_only != 0, the walk for all Gaussian
+ *     parameters otherwise);
+ * `reps` passes each.  Each stage starts from the previous stage's choice (first, the
+ * context's current schedule) and keeps it unless another setting is at least 1 % faster;
+ * the final choice is set on the context.  It uses the workspace (sized by
+ * gs_workspace_size for `prob`) as gs_project does and synchronises `stream`, so it
+ * cannot be captured into a graph; afterwards no projection is bound (call gs_project or
+ * gs_track_step next).  table (host, cap entries, may be NULL) receives the measurements
+ * in order, *count (may be NULL) their number (13 at most); best (may be NULL) the chosen
+ * schedule.  A setting whose pairs overflow pair_capacity is recorded with ms = -1 and
+ * not chosen; an overflow of the context's current schedule is reported as CAPACITY (the
+ * schedule is then left unchanged).
  * Errors: INVALID_ARG (as gs_project; targets without rgb or depth; reps outside
- * [1, 1000]), WORKSPACE, CAPACITY, CUDA. */
+ * [1, 1000]; a capturing stream), WORKSPACE, CAPACITY, CUDA. */
 gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const double *poses,
                       const gs_targets *targets, int32_t pose_only, int32_t reps, void *ws, size_t ws_bytes,
                       gs_tune_entry *table, int32_t cap, int32_t *count, gs_schedule *best, void *stream);
