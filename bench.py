@@ -358,8 +358,7 @@ def run_batched(a, dev, stream, mhz: float = 2070.0):
     gs.gs_set_profiling(R.ctx, False)
     _, cb = gs.gs_sync_status(R.ctx, stream)  # the work of that iteration, counted on the device
     rl_kernels = kernel_rooflines(kms, N_BATCH_GAUSS, V, 22, int(cb.n_records), int(cb.n_pairs),
-                                  tile_counters(cams, sched["schedule"]), int(cb.fwd_contrib), int(cb.bwd_contrib),
-                                  mhz)
+                                  int(cb.fwd_contrib), int(cb.bwd_contrib), mhz)
     poses.copy_(start)
     adam.zero_()
     torch.cuda.synchronize(dev)
@@ -577,31 +576,20 @@ def hbm_peak_gbs() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def tile_counters(cams, sched: dict) -> int:
-    """Per-(tile, sub-bucket) counters the scan reads: tiles of the schedule's shape
-    over all views times the sub-buckets in use (at most 2^22 counters)."""
-    tw, th = sched["tile_w"], sched["tile_h"]
-    T = sum(-(-c.width // tw) * -(-c.height // th) for c in cams)
-    S = sched["sub_buckets"]
-    while S > 1 and T * S > (1 << 22):
-        S //= 2
-    return T * S
-
-
 def kernel_rooflines(kern_ms: dict, n_gauss: int, views: int, attr_bytes: int, records: int, pairs: int,
-                     counters: int, fwd_contrib: int, bwd_contrib: int, mhz: float) -> dict:
+                     fwd_contrib: int, bwd_contrib: int, mhz: float) -> dict:
     """Every kernel of a tracking iteration against the roofline that bounds it: its
     algorithmic bytes or FLOPs per launch (from the work counted on the device) over its
     CUDA-event time (markers around every kernel, so each time includes its launch gap),
     as a fraction of the measured HBM copy bandwidth or of the FP32 FMA peak at the
-    sampled SM clock.  k_finalize is a chain of dependent steps (latency, no roofline)."""
+    sampled SM clock.  k_scan_tiles (one block) and k_finalize (a chain of dependent
+    steps) are latency-bound: their times are reported without a roofline."""
     hbm, hbm_from = hbm_peak_gbs()
     fp32 = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
     work = {
         "k_project": ("hbm", 12 * n_gauss * views + (attr_bytes + 96) * records,
                       f"12 B of means per (Gaussian, view); {attr_bytes} B of other parameters and a 96 B record "
                       "per visible (Gaussian, view)"),
-        "k_scan_tiles": ("hbm", 12 * counters, "12 B per (tile, sub-bucket) counter"),
         "k_emit": ("hbm", 12 * pairs, "12 B per (Gaussian, tile) pair"),
         "k_forward": ("alu", FLOP_FWD_PAIR * fwd_contrib, f"{FLOP_FWD_PAIR} FLOP per contributing pair"),
         "k_backward": ("alu", FLOP_BWD_PAIR * bwd_contrib, f"{FLOP_BWD_PAIR} FLOP per differentiated pair"),
@@ -802,7 +790,6 @@ def main():
             # (pixel, Gaussian) pairs that contributed to Eqs. 2-4 or were differentiated, per second
             "useful_pair_evals_per_s": (contrib["fwd_contrib"] + contrib["bwd_contrib"]) / (ms / 1e3),
             "roofline_kernels": kernel_rooflines(breakdown, N_GAUSS, 1, 44, int(counts.n_records), int(counts.n_pairs),
-                                                 tile_counters([cam], sched["schedule"]),
                                                  contrib["fwd_contrib"] // a.steps, contrib["bwd_contrib"] // a.steps,
                                                  mhz),
         }

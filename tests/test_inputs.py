@@ -52,12 +52,8 @@ def test_kernel_rooflines_arithmetic():
     """The bench's per-kernel roofline table: bytes or FLOPs per launch over the event
     time, against the measured HBM bandwidth or the FP32 FMA peak (hand-computed cases)."""
     import bench
-    sched = {"tile_w": 16, "tile_h": 16, "sub_buckets": 4, "fwd_batch": 256, "bwd_batch": 256}
-    cam = scenes.TUM_CAM
-    assert bench.tile_counters([cam], sched) == 40 * 30 * 4
-    assert bench.tile_counters([cam], dict(sched, tile_w=8, tile_h=8, sub_buckets=2)) == 80 * 60 * 2
-    ms = {"k_project": 0.01, "k_forward": 0.05, "k_finalize": 0.01}
-    r = bench.kernel_rooflines(ms, n_gauss=1000, views=2, attr_bytes=44, records=500, pairs=0, counters=0,
+    ms = {"k_project": 0.01, "k_forward": 0.05, "k_finalize": 0.01, "k_scan_tiles": 0.01}
+    r = bench.kernel_rooflines(ms, n_gauss=1000, views=2, attr_bytes=44, records=500, pairs=0,
                                fwd_contrib=10 ** 6, bwd_contrib=0, mhz=1000.0)
     hbm, _ = bench.hbm_peak_gbs()
     assert r["k_project"]["achieved"] == pytest.approx((12 * 2000 + 140 * 500) / 1e-5 / 1e9, rel=1e-3)
@@ -65,4 +61,4 @@ def test_kernel_rooflines_arithmetic():
     peak = 152 * 128 * 2 * 1e9 / 1e12
     assert r["k_forward"]["peak"] == pytest.approx(peak, rel=1e-3)
     assert r["k_forward"]["achieved"] == pytest.approx(23e6 / 5e-5 / 1e12, rel=1e-3)
-    assert r["k_finalize"]["bound"] == "latency"
+    assert r["k_finalize"]["bound"] == "latency" and r["k_scan_tiles"] == {"bound": "latency", "us": 10.0}
