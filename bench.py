@@ -511,6 +511,38 @@ def cpu_baseline(g, cam, start, rgb, depth, prior, budget_s: float):
             "sample": f"{iters} full tracking iterations of the 640x480 / 200k workload in {el:.1f} s"}
 
 
+def oracle_small_single_thread(budget_s: float = 3.0) -> dict:
+    """The oracle's tracking iteration on one host thread, on the small parity case
+    (160 x 120, 2,000 Gaussians in front of the camera, target rendered 2 deg / 3 cm away,
+    depth prior with 5 % holes), repeated until `budget_s` seconds have elapsed."""
+    import oracle
+    from paper_2408_05635_gb300 import scenes
+    g, cam = scenes.cube_scene()
+    threads_before = oracle.num_threads(oracle.Params())
+    p = oracle.Params(n_threads=1)
+    sc = oracle.Scene(*g.arrays())
+    oc = oracle.camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    rng = np.random.default_rng(0)
+    tgt = oracle.render(sc, oc, scenes.perturb_pose(scenes.identity_pose(), rng, 2.0, 0.03), p)
+    prior = scenes.prior_from_depth(tgt["depth"], rng, 0.02, 0.05)
+    pose, state = np.asarray(scenes.identity_pose(), np.float64).copy(), np.zeros(16)
+    iters, t0 = 0, time.perf_counter()
+    while True:
+        r = oracle.render(sc, oc, pose, p)
+        L = oracle.loss(oc, p, r["rgb"], r["depth"], r["sil"], tgt["rgb"], tgt["depth"], prior)
+        b = oracle.backward(sc, oc, pose, p, L["d_rgb"], L["d_depth"], L["d_sil"])
+        pose, state = oracle.adam_step(pose, state, b["pose6"], p)
+        iters += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    its = iters / el
+    cores = oracle.num_threads(p)
+    oracle.num_threads(oracle.Params(n_threads=threads_before))  # the oracle's thread count as it was
+    return {"value": its * cam.width * cam.height / 1e6, "unit": "Mpix/s", "iters_per_s": its, "cores": cores,
+            "sample": f"{iters} full tracking iterations of the 160x120 / 2k case in {el:.1f} s"}
+
+
 def ncu_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None once the
     kernel's sources differ from the ones the counters were taken on."""
@@ -803,6 +835,7 @@ def main():
             line["sequence"] = run_sequence(a, dev, stream)
         if world == 1 and not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, cam, start, rgb, depth, prior, a.cpu_sample_seconds)
+            line["cpu_baseline"]["single_thread_small_case"] = oracle_small_single_thread()
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

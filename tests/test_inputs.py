@@ -62,3 +62,13 @@ def test_kernel_rooflines_arithmetic():
     assert r["k_forward"]["peak"] == pytest.approx(peak, rel=1e-3)
     assert r["k_forward"]["achieved"] == pytest.approx(23e6 / 5e-5 / 1e12, rel=1e-3)
     assert r["k_finalize"]["bound"] == "latency" and r["k_scan_tiles"] == {"bound": "latency", "us": 10.0}
+
+
+def test_oracle_single_thread_small_case_rate():
+    """The bench's single-thread oracle sample runs on one thread and reports a rate."""
+    import bench
+    import oracle
+    before = oracle.num_threads(oracle.Params())
+    r = bench.oracle_small_single_thread(0.2)
+    assert r["cores"] == 1 and r["value"] > 0 and r["iters_per_s"] > 0
+    assert oracle.num_threads(oracle.Params()) == before  # restored for whatever runs next
