@@ -39,7 +39,7 @@ N_GAUSS = 200_000
 FLOP_BWD_PAIR = 58
 FLOP_FWD_PAIR = 23
 FLOP_BPROJ_REC = 300  # about: the chain rule of one record to the pose (k_bproject, pose only)
-N_SM, FP32_LANES = 152, 128  # GB300: FP32 FMA lanes per SM
+FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 ITERS_PER_FRAME = 40  # tracking iterations per frame (the 640 x 480 tracking workload); the
                       # pose and Adam state restart from the frame's start pose every 40 steps
 
@@ -560,21 +560,20 @@ def ncu_traffic(kernel):
     return None
 
 
-def run_reference(a, rank, world):
-    if rank != 0:
-        return
-    g, cam, gt, start, rgb, depth, prior = workload()
+def reference_steps(g, cam, start, rgb, depth, prior, steps: int, warmup: int, band: int = 64):
+    """Seconds of each timed oracle step: one full FP64 tracking iteration (render, loss,
+    backward, decoupled Adam) on a `band`-row band of the frame.  The bands step down the
+    frame and wrap around within it, so every band lies wholly inside the image."""
     import oracle
     p = oracle.Params()
     sc = oracle.Scene(*g.arrays())
-    oc = oracle.camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
     H, W = cam.height, cam.width
-    # each step: one oracle tracking iteration on a 64-row band of the frame (bounded sample)
-    band = 64
+    band = min(band, H)
+    nbands = H // band
     times = []
     pose, state = np.asarray(start, np.float64).copy(), np.zeros(16)
-    for it in range(a.warmup + a.steps):
-        y0 = (it * band) % H
+    for it in range(warmup + steps):
+        y0 = (it % nbands) * band
         sub = oracle.camera(cam.fx, cam.fy, cam.cx, cam.cy - y0, W, band)
         sl = slice(y0, y0 + band)
         t0 = time.perf_counter()
@@ -583,8 +582,17 @@ def run_reference(a, rank, world):
         b = oracle.backward(sc, sub, pose, p, L["d_rgb"], L["d_depth"], L["d_sil"])
         pose, state = oracle.adam_step(pose, state, b["pose6"], p)
         dt = time.perf_counter() - t0
-        if it >= a.warmup:
+        if it >= warmup:
             times.append(dt)
+    return times, oracle.num_threads(p)
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    g, cam, gt, start, rgb, depth, prior = workload()
+    W, band = cam.width, 64
+    times, cores = reference_steps(g, cam, start, rgb, depth, prior, a.steps, a.warmup, band)
     total = sum(times)
     mpix = a.steps * W * band / total / 1e6
     sample = f"each step: one full oracle tracking iteration on a {W}x{band} band of the 640x480 / 200k frame"
@@ -592,10 +600,16 @@ def run_reference(a, rank, world):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": oracle.num_threads(p), "kind": "oracle",
+            "cpu_baseline": {"value": mpix, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": mpix, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def sm_count() -> int:
+    """Streaming multiprocessors of the current GPU, read from the device."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
 
 
 def hbm_peak_gbs() -> tuple[float, str]:
@@ -609,7 +623,7 @@ def hbm_peak_gbs() -> tuple[float, str]:
 
 
 def kernel_rooflines(kern_ms: dict, n_gauss: int, views: int, attr_bytes: int, records: int, pairs: int,
-                     fwd_contrib: int, bwd_contrib: int, mhz: float) -> dict:
+                     fwd_contrib: int, bwd_contrib: int, mhz: float, n_sm: int | None = None) -> dict:
     """Every kernel of a tracking iteration against the roofline that bounds it: its
     algorithmic bytes or FLOPs per launch (from the work counted on the device) over its
     CUDA-event time (markers around every kernel, so each time includes its launch gap),
@@ -617,7 +631,8 @@ def kernel_rooflines(kern_ms: dict, n_gauss: int, views: int, attr_bytes: int, r
     sampled SM clock.  k_scan_tiles (one block) and k_finalize (a chain of dependent
     steps) are latency-bound: their times are reported without a roofline."""
     hbm, hbm_from = hbm_peak_gbs()
-    fp32 = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    n_sm = n_sm or sm_count()
+    fp32 = n_sm * FP32_LANES * 2 * mhz * 1e6 / 1e12
     work = {
         "k_project": ("hbm", 12 * n_gauss * views + (attr_bytes + 96) * records,
                       f"12 B of means per (Gaussian, view); {attr_bytes} B of other parameters and a 96 B record "
@@ -639,7 +654,7 @@ def kernel_rooflines(kern_ms: dict, n_gauss: int, views: int, attr_bytes: int, r
             achieved, peak, unit = units / (ms / 1e3) / 1e12, fp32, "TFLOP/s"
         out[k] = {"bound": bound, "us": round(1e3 * ms, 2), "achieved": float(f"{achieved:.4g}"),
                   "peak": round(peak, 1), "unit": unit, "frac": float(f"{achieved / peak:.3g}"), "work": what}
-    out["peaks_from"] = f"HBM {hbm:.0f} GB/s ({hbm_from}); FP32 {fp32:.1f} TFLOP/s at {mhz:.0f} MHz"
+    out["peaks_from"] = f"HBM {hbm:.0f} GB/s ({hbm_from}); FP32 {fp32:.1f} TFLOP/s ({n_sm} SMs at {mhz:.0f} MHz)"
     return out
 
 
@@ -786,7 +801,8 @@ def main():
     avg = {k: v / a.steps for k, v in kern_ms.items()}
     clocks = clk.summary()
     mhz = clocks.get("sm_mhz") or 2070.0
-    peak_tflops = N_SM * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    n_sm = sm_count()
+    peak_tflops = n_sm * FP32_LANES * 2 * mhz * 1e6 / 1e12
     per_pair = {"k_backward": (FLOP_BWD_PAIR, contrib["bwd_contrib"]), "k_forward": (FLOP_FWD_PAIR, contrib["fwd_contrib"])}
     roofline = None
     if dominant in per_pair:
@@ -797,7 +813,7 @@ def main():
                     "traffic_from": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold cache "
                                     "(profiles/k_backward_k_forward_tracking_640x480_200k.md)",
                     "work": f"{f} FP32 FLOP per differentiated (pixel, Gaussian) pair x {units // a.steps} pairs",
-                    "peak_from": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz (median SM clock, timed region)"}
+                    "peak_from": f"{n_sm} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz (median SM clock, timed region)"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": mpix, "unit": "Mpix/s", "n_gpus": world, "steps": a.steps,

@@ -317,3 +317,57 @@ def test_mapping_window_grads_sum_over_views():
         a = outs[1]["grads"][name].cpu().numpy()
         b = outs[4]["grads"][name].cpu().numpy()
         assert np.abs(a - b).max() <= 1e-5 * max(1e-30, np.abs(a).max()), name
+
+
+def _opaque_stacks(n_stacks=24, layers=4, seed=21):
+    """Stacks of nearly opaque Gaussians in front of the cube scene: each stack puts
+    `layers` Gaussians 5 cm apart in depth over nearly the same pixels, opacities from
+    sigmoid(6) = 0.9975 (clamped at alpha_max = 0.99) down to sigmoid(3) = 0.95, so the
+    reverse walk recovers the transmittance through factors 1 / (1 - alpha) of up to 100."""
+    g, _ = scenes.cube_scene(n=600, seed=seed)
+    rng = np.random.default_rng(seed)
+    xy = rng.uniform(-0.45, 0.45, size=(n_stacks, 2))
+    means, logits = [], []
+    for s in range(n_stacks):
+        for k in range(layers):
+            means.append([xy[s, 0] + rng.normal(0, 0.004), xy[s, 1] + rng.normal(0, 0.004), 1.2 + 0.05 * k])
+            logits.append([6.0, 4.0, 5.0, 3.0][k % 4])
+    m = len(means)
+    stack = scenes.Gaussians(np.asarray(means, np.float32), rng.normal(size=(m, 4)).astype(np.float32),
+                             rng.normal(-3.2, 0.15, size=(m, 3)).astype(np.float32), np.asarray(logits, np.float32),
+                             rng.uniform(0, 1, size=(m, 3)).astype(np.float32))
+    cat = lambda a, b: np.concatenate([a, b])
+    return scenes.Gaussians(*(cat(a, b) for a, b in zip(stack.arrays(), g.arrays())))
+
+
+@pytest.mark.parametrize("t_min", [1e-4, 1e-6])
+def test_backward_through_near_opaque_stacks(t_min):
+    """Images and all gradients where the transmittance is rebuilt by division through
+    stacks of alpha = 0.95 .. 0.99 Gaussians (relative error up to 100 u per layer), with
+    the default early stop and with t_min = 1e-6, which lets three clamped layers through."""
+    g = _opaque_stacks()
+    cam = scenes.Cam(100.0, 100.0, 47.5, 35.5, 96, 72)
+    pose = scenes.perturb_pose(scenes.identity_pose(), np.random.default_rng(8), 0.5, 0.01)
+    gcfg, op = params_pair(t_min=t_min)
+    sc, oc = oracle.Scene(*g.arrays()), ocam(cam)
+    ref = oracle.render(sc, oc, pose, op)
+    # the stacks really are opaque: many pixels end below 1e-3 transmittance
+    assert (ref["sil"] > 1 - 1e-3).mean() > 0.05
+    R = gs.Rasterizer(gcfg)
+    gt = gs.GaussianTensors.from_numpy(g)
+    out, prob, poses, _ = gpu_render(R, gt, [cam], [pose])
+    H, W = cam.height, cam.width
+    amb = ref["amb"]
+    assert_images_close(out["rgb"].reshape(3, H, W), ref["rgb"], amb, what="rgb")
+    assert_images_close(out["depth"].reshape(H, W), ref["depth"], amb, what="depth")
+    rng = np.random.default_rng(5)
+    up = [np.where(amb[None], 0.0, rng.normal(size=(3, H, W))), np.where(amb, 0.0, rng.normal(size=(H, W))),
+          np.where(amb, 0.0, rng.normal(size=(H, W)))]
+    ob = oracle.backward(sc, oc, pose, op, *up)
+    ups = tuple(torch.tensor(a.reshape(-1).astype(np.float32), device="cuda") for a in up)
+    b = R.backward(gt, upstream=ups)
+    R.sync()
+    for name, lo, hi in GRAD_KEYS:
+        got = b["grads"][name].cpu().numpy().reshape(g.n, -1)
+        assert_grads_close(got, ob["grads"][:, lo:hi], what=name)
+    assert_grads_close(b["pose_grad"].cpu().numpy()[0], ob["pose6"], what="pose")

@@ -54,7 +54,7 @@ def test_kernel_rooflines_arithmetic():
     import bench
     ms = {"k_project": 0.01, "k_forward": 0.05, "k_finalize": 0.01, "k_scan_tiles": 0.01}
     r = bench.kernel_rooflines(ms, n_gauss=1000, views=2, attr_bytes=44, records=500, pairs=0,
-                               fwd_contrib=10 ** 6, bwd_contrib=0, mhz=1000.0)
+                               fwd_contrib=10 ** 6, bwd_contrib=0, mhz=1000.0, n_sm=152)
     hbm, _ = bench.hbm_peak_gbs()
     assert r["k_project"]["achieved"] == pytest.approx((12 * 2000 + 140 * 500) / 1e-5 / 1e9, rel=1e-3)
     assert r["k_project"]["frac"] == pytest.approx(r["k_project"]["achieved"] / hbm, rel=1e-2)
