@@ -62,7 +62,8 @@ def _args():
                     help="passes per setting of the launch-schedule autotuner before the tracking and batched "
                          "legs (0: the default schedule)")
     ap.add_argument("--schedule", default=None,
-                    help="fixed launch schedule 'tile_w,tile_h,sub_buckets,fwd_batch,bwd_batch' instead of tuning")
+                    help="fixed launch schedule 'tile_w,tile_h,sub_buckets,fwd_batch,bwd_batch[,flags]' instead of "
+                         "tuning (flags 1: the fused tracking compositor)")
     return ap.parse_args()
 
 
@@ -743,6 +744,9 @@ def main():
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     kern_ms, contrib = {}, {"fwd_evals": 0, "fwd_contrib": 0, "bwd_evals": 0, "bwd_contrib": 0}
     launches = 0
+    # the view-table copy, the projection, scan and emission, the compositing (two kernels,
+    # or one fused), the back-projection and the finalize
+    per_iter_launches = 1 + 3 + (1 if R.schedule["flags"] & gs.GS_SCHED_FUSED else 2) + 2
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -758,7 +762,7 @@ def main():
             kt = gs.gs_kernel_times(R.ctx)  # waits for this step's markers
             for name, ms in kt:
                 kern_ms[name] = kern_ms.get(name, 0.0) + ms
-            launches += len(gs.KERNELS) + 1  # the seven kernels of an iteration and the view-table copy
+            launches += per_iter_launches
             st_k, c_k = gs.gs_sync_status(R.ctx, stream)
             for key in contrib:
                 contrib[key] += getattr(c_k, key)
@@ -803,16 +807,22 @@ def main():
     mhz = clocks.get("sm_mhz") or 2070.0
     n_sm = sm_count()
     peak_tflops = n_sm * FP32_LANES * 2 * mhz * 1e6 / 1e12
-    per_pair = {"k_backward": (FLOP_BWD_PAIR, contrib["bwd_contrib"]), "k_forward": (FLOP_FWD_PAIR, contrib["fwd_contrib"])}
+    per_pair = {"k_backward": (FLOP_BWD_PAIR, contrib["bwd_contrib"], f"{FLOP_BWD_PAIR} FP32 FLOP per differentiated "
+                                                                       "(pixel, Gaussian) pair"),
+                "k_forward": (FLOP_FWD_PAIR, contrib["fwd_contrib"], f"{FLOP_FWD_PAIR} FP32 FLOP per contributing "
+                                                                     "(pixel, Gaussian) pair"),
+                "k_track_tile": (1, FLOP_FWD_PAIR * contrib["fwd_contrib"] + FLOP_BWD_PAIR * contrib["bwd_contrib"],
+                                 f"{FLOP_FWD_PAIR} FP32 FLOP per contributing and {FLOP_BWD_PAIR} per differentiated "
+                                 "(pixel, Gaussian) pair")}
     roofline = None
     if dominant in per_pair:
-        f, units = per_pair[dominant]
+        f, units, what = per_pair[dominant]
         achieved = f * units / a.steps / (avg[dominant] / 1e3) / 1e12
         roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak_tflops,
                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": ncu_traffic(dominant),
                     "traffic_from": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold cache "
                                     "(profiles/k_backward_k_forward_tracking_640x480_200k.md)",
-                    "work": f"{f} FP32 FLOP per differentiated (pixel, Gaussian) pair x {units // a.steps} pairs",
+                    "work": f"{what}: {f * units // a.steps} FLOP per launch",
                     "peak_from": f"{n_sm} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz (median SM clock, timed region)"}
     if rank == 0:
         line = {

@@ -277,8 +277,15 @@ typedef struct {
     int32_t fwd_batch;      /* Gaussians staged per forward batch: 64, 128 or 256, at
                                most tile_w tile_h (256)                                 */
     int32_t bwd_batch;      /* Gaussians staged per backward batch: the same (256)      */
-    int32_t reserved;       /* 0 */
+    int32_t flags;          /* GS_SCHED_* bits (0)                                      */
 } gs_schedule;
+
+/* gs_schedule.flags: GS_SCHED_FUSED -- in gs_track_step, each tile's forward with the
+ * fused loss and its pose-only reverse walk run in one kernel (k_track_tile): the same
+ * arithmetic as the two compositing kernels, with the pixel state kept in registers
+ * between the walks and the last forward batch reused by the reverse walk.  Needs
+ * fwd_batch == bwd_batch.  Other calls are unaffected. */
+#define GS_SCHED_FUSED 1
 
 /* Read the context's schedule (defaults after gs_create).  Errors: INVALID_ARG (NULL). */
 gs_status gs_get_schedule(const gs_ctx *ctx, gs_schedule *out);
@@ -296,7 +303,9 @@ typedef struct {
                              emission, forward with the fused loss, backward);
                              1: binning (projection, scan, emission) per sub_buckets;
                              2: forward compositing per fwd_batch;
-                             3: backward compositing per bwd_batch                     */
+                             3: backward compositing per bwd_batch;
+                             4: (pose_only) both compositors, as two kernels or fused
+                                (GS_SCHED_FUSED)                                         */
     float ms;             /* mean device time of one pass of the stage (CUDA events on
                              the stream, warm caches, after one untimed pass); -1 when
                              the setting made more pairs than pair_capacity (not timed) */
@@ -311,13 +320,15 @@ typedef struct {
  *   - every forward batch depth, then every backward batch depth the chosen tile allows
  *     (the pose-only walk of tracking when pose_only != 0, the walk for all Gaussian
  *     parameters otherwise);
+ *   - with pose_only, the two compositors as two kernels against the fused tracking
+ *     kernel (GS_SCHED_FUSED, both batch depths set to the forward's);
  * `reps` passes each.  Each stage starts from the previous stage's choice (first, the
  * context's current schedule) and keeps it unless another setting is at least 1 % faster;
  * the final choice is set on the context.  It uses the workspace (sized by
  * gs_workspace_size for `prob`) as gs_project does and synchronises `stream`, so it
  * cannot be captured into a graph; afterwards no projection is bound (call gs_project or
  * gs_track_step next).  table (host, cap entries, may be NULL) receives the measurements
- * in order, *count (may be NULL) their number (13 at most); best (may be NULL) the chosen
+ * in order, *count (may be NULL) their number (15 at most); best (may be NULL) the chosen
  * schedule.  A setting whose pairs overflow pair_capacity is recorded with ms = -1 and
  * not chosen; an overflow of the context's current schedule is reported as CAPACITY (the
  * schedule is then left unchanged).

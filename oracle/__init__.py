@@ -122,8 +122,12 @@ def _load():
             lib.og_backward.argtypes = [sc, cam, d, par, d, d, d, d, d, d]
             lib.og_adam_step.argtypes = [d, d, d, par]
             lib.og_num_threads.argtypes = [par]
+            lib.og_render_perturbed.argtypes = [sc, cam, d, par, ctypes.c_uint64, ctypes.c_double, d, d, d, d]
+            lib.og_render_alternatives.argtypes = [sc, cam, d, par, i64, ctypes.c_int64, ctypes.c_int32, i32, d]
+            lib.og_depth_keys.argtypes = [sc, d, P(ctypes.c_float), d]
             for fn in (lib.og_project, lib.og_render, lib.og_render_pixels, lib.og_loss,
-                       lib.og_backward, lib.og_adam_step, lib.og_num_threads):
+                       lib.og_backward, lib.og_adam_step, lib.og_num_threads, lib.og_render_perturbed,
+                       lib.og_render_alternatives, lib.og_depth_keys):
                 fn.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -188,7 +192,10 @@ def project(scene: Scene, cam: Camera, pose, params: Params) -> dict:
 
 def render(scene: Scene, cam: Camera, pose, params: Params) -> dict:
     """Eqs. 2-4: colour (3 x H x W), depth and silhouette (H x W), final transmittance,
-    number of contributors and the ambiguity mask, every pixel."""
+    number of contributors and the ambiguity mask, every pixel.  amb_bits holds the
+    reasons a pixel is flagged: AMB_ALPHA_MIN (an alpha near alpha_min whose skip matters),
+    AMB_ALPHA_MAX (an alpha near the clamp; it changes gradients, not the maps) and
+    AMB_T_MIN (the transmittance reaches t_min within its margin)."""
     lib = _load()
     H, W = cam.height, cam.width
     rgb = np.zeros((3, H, W))
@@ -201,7 +208,54 @@ def render(scene: Scene, cam: Camera, pose, params: Params) -> dict:
     _check(lib.og_render(ctypes.byref(sc), ctypes.byref(cam), _dp(pose), ctypes.byref(par), _dp(rgb),
                          _dp(depth), _dp(sil), _dp(tf), nc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                          amb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))), "render")
-    return {"rgb": rgb, "depth": depth, "sil": sil, "t_final": tf, "n_contrib": nc, "amb": amb.astype(bool)}
+    return {"rgb": rgb, "depth": depth, "sil": sil, "t_final": tf, "n_contrib": nc, "amb": amb.astype(bool),
+            "amb_bits": amb}
+
+
+AMB_ALPHA_MIN, AMB_ALPHA_MAX, AMB_T_MIN = 1, 2, 4
+
+
+def render_perturbed(scene: Scene, cam: Camera, pose, params: Params, seed: int, scale: float) -> dict:
+    """A render within the FP32 error model the ambiguity mask assumes, for testing the
+    mask: the pose rounded to FP32 as the GPU applies it, and each (pixel, Gaussian)
+    exponent of Eq. 1 moved by scale x its modelled rounding error x a SplitMix64
+    uniform in [-1, 1) drawn from (seed, pixel, Gaussian)."""
+    lib = _load()
+    H, W = cam.height, cam.width
+    rgb, depth, sil, tf = np.zeros((3, H, W)), np.zeros((H, W)), np.zeros((H, W)), np.zeros((H, W))
+    sc, par, pose = scene._c(), params._c(), _f64(pose, (7,))
+    _check(lib.og_render_perturbed(ctypes.byref(sc), ctypes.byref(cam), _dp(pose), ctypes.byref(par),
+                                   ctypes.c_uint64(seed), float(scale), _dp(rgb), _dp(depth), _dp(sil), _dp(tf)),
+           "render_perturbed")
+    return {"rgb": rgb, "depth": depth, "sil": sil, "t_final": tf}
+
+
+def render_alternatives(scene: Scene, cam: Camera, pose, params: Params, pix, max_alt: int = 16) -> dict:
+    """Every outcome (C_r, C_g, C_b, D, S, T) an FP32 renderer may legitimately produce at
+    the selected pixels (flat index y * W + x): the walk of Eqs. 2-4 branched at each
+    decision the ambiguity mask flags.  n_alt[k] outcomes in alts[k, :n_alt[k]], or
+    n_alt[k] = -1 when the pixel needs more than max_alt."""
+    lib = _load()
+    pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int64))
+    n_alt = np.zeros(pix.size, dtype=np.int32)
+    alts = np.zeros((pix.size, max_alt, 6))
+    sc, par, pose = scene._c(), params._c(), _f64(pose, (7,))
+    _check(lib.og_render_alternatives(ctypes.byref(sc), ctypes.byref(cam), _dp(pose), ctypes.byref(par),
+                                      pix.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), pix.size, int(max_alt),
+                                      n_alt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(alts)),
+           "render_alternatives")
+    return {"n_alt": n_alt, "alts": alts}
+
+
+def depth_keys(scene: Scene, pose) -> tuple[np.ndarray, np.ndarray]:
+    """(FP32 depth key that orders Eqs. 2-4, FP64 camera-frame depth) of every Gaussian."""
+    lib = _load()
+    keys = np.zeros(scene.n, dtype=np.float32)
+    z = np.zeros(scene.n)
+    sc, pose = scene._c(), _f64(pose, (7,))
+    _check(lib.og_depth_keys(ctypes.byref(sc), _dp(pose), keys.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                             _dp(z)), "depth_keys")
+    return keys, z
 
 
 def render_pixels(scene: Scene, cam: Camera, pose, params: Params, pix) -> dict:

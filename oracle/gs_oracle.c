@@ -391,12 +391,77 @@ static int build_rows(const og_proj *P, const int64_t *order, int64_t m, int hei
 
 /* ------------------------------------------------------------------ step 2: Eqs. 2-4 */
 
+/* Reasons a pixel is flagged ambiguous (bits of the mask). */
+#define OG_AMB_ALPHA_MIN 1u /* an alpha within its margin of alpha_min, keeping or skipping it matters */
+#define OG_AMB_ALPHA_MAX 2u /* an alpha within its margin of alpha_max (the clamp; gradients only) */
+#define OG_AMB_T_MIN 4u     /* the transmittance reaches t_min within its margin */
+
+/* One Gaussian at one pixel: its footprint G and alpha_raw = o G (Eq. 1, 2-D form), and
+ * the relative error dexp with which an FP32 renderer can know alpha_raw there.  `noise`
+ * is added to the exponent (0 except in the perturbed render that tests the mask).
+ * |d exponent / d mu'| = |conic d| times the screen-mean error (its 24-bit rounding plus
+ * dmu, the FP32 camera transform), and the quadratic form's terms are rounded once
+ * each: a footprint evaluated thousands of pixels from its mean has an alpha known only
+ * to ~1e-3, an ordinary one to ~1e-5. */
+typedef struct {
+    double G, araw, dexp;
+} og_eval;
+
+static void eval_gaussian(const og_proj *pr, int px, int py, double noise, og_eval *e) {
+    const double dx = (double)px - pr->mu[0], dy = (double)py - pr->mu[1];
+    const double q = pr->conic[0] * dx * dx + 2.0 * pr->conic[1] * dx * dy + pr->conic[2] * dy * dy;
+    e->G = exp(-0.5 * q + noise);
+    e->araw = pr->o * e->G;
+    const double gx = pr->conic[0] * dx + pr->conic[1] * dy, gy = pr->conic[1] * dx + pr->conic[2] * dy;
+    const double terms =
+        fabs(pr->conic[0] * dx * dx) + 2.0 * fabs(pr->conic[1] * dx * dy) + fabs(pr->conic[2] * dy * dy);
+    const double mu_mag = fmax(fabs(pr->mu[0]), fabs(pr->mu[1]));
+    e->dexp = 4.0 * OG_FP32_ROUNDOFF * (sqrt(gx * gx + gy * gy) * mu_mag + terms) + sqrt(gx * gx + gy * gy) * pr->dmu;
+}
+
+/* The exponent error of the perturbed render: the part of dexp that comes from the
+ * rounding of the screen mean and of the quadratic form (the camera transform's part is
+ * realised instead by rendering with the pose rounded to FP32). */
+static double rounding_dexp(const og_proj *pr, int px, int py) {
+    const double dx = (double)px - pr->mu[0], dy = (double)py - pr->mu[1];
+    const double gx = pr->conic[0] * dx + pr->conic[1] * dy, gy = pr->conic[1] * dx + pr->conic[2] * dy;
+    const double terms =
+        fabs(pr->conic[0] * dx * dx) + 2.0 * fabs(pr->conic[1] * dx * dy) + fabs(pr->conic[2] * dy * dy);
+    const double mu_mag = fmax(fabs(pr->mu[0]), fabs(pr->mu[1]));
+    return 4.0 * OG_FP32_ROUNDOFF * (sqrt(gx * gx + gy * gy) * mu_mag + terms);
+}
+
+/* SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): the 64-bit finaliser applied to
+ * seed + counter times the golden-ratio increment; a uniform in [-1, 1) from its top
+ * 53 bits.  Used only by the perturbed render, which tests the ambiguity mask. */
+static double splitmix_unit(uint64_t seed, uint64_t counter) {
+    uint64_t z = seed + (counter + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+/* Exponent perturbation of the render that tests the mask: none when scale is 0. */
+typedef struct {
+    uint64_t seed;
+    double scale;
+    int64_t n;
+} og_noise;
+
+static double noise_at(const og_noise *nz, const og_proj *pr, int px, int py, int W, int64_t g) {
+    if (!nz || nz->scale == 0.0) return 0.0;
+    const uint64_t counter = ((uint64_t)py * (uint64_t)W + (uint64_t)px) * (uint64_t)nz->n + (uint64_t)g;
+    return nz->scale * rounding_dexp(pr, px, py) * splitmix_unit(nz->seed, counter);
+}
+
 /* Composite one pixel front to back.  out5 = (C_r, C_g, C_b, D, S).  When `contrib` is
  * given, every Gaussian that contributed is recorded with its alpha, its incoming
- * transmittance T and its Gaussian factor G (alpha = min(alpha_max, o G)). */
+ * transmittance T and its Gaussian factor G (alpha = min(alpha_max, o G)).  *amb gets
+ * the OG_AMB_* reasons for which an FP32 renderer may take another discrete decision. */
 static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, int use_bbox, const og_proj *P,
-                            const og_scene *sc, const og_params *p, double out5[5], double *t_final,
-                            og_contrib *contrib, int64_t *ncontrib, int *amb) {
+                            const og_scene *sc, const og_params *p, const og_noise *nz, int W, double out5[5],
+                            double *t_final, og_contrib *contrib, int64_t *ncontrib, int *amb) {
     double T = 1.0, C0 = 0, C1 = 0, C2 = 0, D = 0, S = 0;
     double eT = 0.0; /* bound of the relative error of an FP32 renderer's T so far */
     int64_t nc = 0;
@@ -405,41 +470,29 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
         const int64_t gi = list[k];
         const og_proj *pr = &P[gi];
         if (use_bbox && (px < pr->x0 || px > pr->x1 || py < pr->y0 || py > pr->y1)) continue;
-        const double dx = (double)px - pr->mu[0], dy = (double)py - pr->mu[1];
-        const double q = pr->conic[0] * dx * dx + 2.0 * pr->conic[1] * dx * dy + pr->conic[2] * dy * dy;
-        const double G = exp(-0.5 * q);
-        const double araw = pr->o * G;
-        /* Relative margin of the alpha decisions: the fixed amb_alpha, or the error with
-         * which an FP32 renderer can know the exponent of Eq. 1 at this pixel, whichever is
-         * larger.  |d exponent / d mu'| = |conic d| times the screen-mean error (its 24-bit
-         * rounding plus dmu, the FP32 camera transform), and the quadratic form's terms are
-         * rounded once each; a footprint evaluated thousands of pixels from its mean has an
-         * alpha known only to ~1e-3, an ordinary one to ~1e-5. */
-        const double gx = pr->conic[0] * dx + pr->conic[1] * dy, gy = pr->conic[1] * dx + pr->conic[2] * dy;
-        const double terms = fabs(pr->conic[0] * dx * dx) + 2.0 * fabs(pr->conic[1] * dx * dy) +
-                             fabs(pr->conic[2] * dy * dy);
-        const double mu_mag = fmax(fabs(pr->mu[0]), fabs(pr->mu[1]));
-        const double dexp = 4.0 * OG_FP32_ROUNDOFF * (sqrt(gx * gx + gy * gy) * mu_mag + terms) +
-                            sqrt(gx * gx + gy * gy) * pr->dmu;
-        const double margin = fmax(p->amb_alpha, dexp);
-        /* skipping or keeping an alpha ~ alpha_min Gaussian moves the pixel by at most about
-         * 2 alpha_min T max(1, z): only a decision that can matter is ambiguous.  Either way
-         * it scales the transmittance of everything behind by 1 - alpha, which an FP32
-         * renderer may therefore hold off by alpha / (1 - alpha): a later t_min decision
-         * inherits that uncertainty. */
+        og_eval e;
+        eval_gaussian(pr, px, py, noise_at(nz, pr, px, py, W, gi), &e);
+        const double araw = e.araw;
+        /* Relative margin of the alpha decisions: the fixed amb_alpha, or dexp, whichever is
+         * larger.  Skipping or keeping an alpha ~ alpha_min Gaussian moves the pixel by at
+         * most about 2 alpha_min T max(1, z): only a decision that can matter is ambiguous.
+         * Either way it scales the transmittance of everything behind by 1 - alpha, which
+         * an FP32 renderer may therefore hold off by alpha / (1 - alpha): a later t_min
+         * decision inherits that uncertainty. */
+        const double margin = fmax(p->amb_alpha, e.dexp);
         const int near_min = araw > 0.0 && fabs(log(araw / p->alpha_min)) <= margin;
-        if (near_min && 2.0 * p->alpha_min * T * fmax(1.0, fabs(pr->xc[2])) > p->amb_effect) a = 1;
+        if (near_min && 2.0 * p->alpha_min * T * fmax(1.0, fabs(pr->xc[2])) > p->amb_effect) a |= OG_AMB_ALPHA_MIN;
         if (near_min) eT += araw / (1.0 - araw);
         if (araw < p->alpha_min) continue;
         const int clamped = araw >= p->alpha_max;
         const double alpha = clamped ? p->alpha_max : araw;
-        if (araw > 0.0 && fabs(log(araw / p->alpha_max)) <= margin) a = 1;
+        if (araw > 0.0 && fabs(log(araw / p->alpha_max)) <= margin) a |= OG_AMB_ALPHA_MAX;
         const double z = pr->xc[2];
         const double Tn = T * (1.0 - alpha);
         /* an alpha known to a relative dexp gives 1 - alpha to alpha dexp / (1 - alpha): the
          * product T = prod (1 - alpha_i) compounds it (a clamped alpha is exact) */
-        if (!clamped) eT += alpha * dexp / (1.0 - alpha);
-        if (fabs(Tn - p->t_min) <= fmax(p->amb_t, eT) * p->t_min) a = 1;
+        if (!clamped) eT += alpha * e.dexp / (1.0 - alpha);
+        if (fabs(Tn - p->t_min) <= fmax(p->amb_t, eT) * p->t_min) a |= OG_AMB_T_MIN;
         if (Tn < p->t_min) break;
         const double w = alpha * T;
         const double *c = sc->rgb + 3 * gi;
@@ -452,7 +505,7 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
             contrib[nc].g = gi;
             contrib[nc].alpha = alpha;
             contrib[nc].T = T;
-            contrib[nc].G = G;
+            contrib[nc].G = e.G;
             contrib[nc].clamped = clamped;
         }
         ++nc;
@@ -466,6 +519,98 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
     *t_final = T;
     *ncontrib = nc;
     *amb = a;
+}
+
+/* Every outcome of one pixel that an FP32 renderer may legitimately produce: the walk of
+ * composite_pixel, branching at each decision it would flag (an alpha_min decision that
+ * matters: skip and keep; a t_min decision: stop and go on).  An alpha_max decision
+ * needs no branch here: the clamp min(alpha_max, alpha) is continuous, so both sides of
+ * it give the same maps.  Each finished walk appends (C_r, C_g, C_b, D, S, T) to alts;
+ * *overflow is set once more than max_alt outcomes would be needed. */
+typedef struct {
+    const int64_t *list;
+    int64_t nlist;
+    int use_bbox, px, py, max_alt, W;
+    const og_proj *P;
+    const og_scene *sc;
+    const og_params *p;
+    double *alts;
+    int nalt, overflow;
+} og_branch;
+
+static void branch_leaf(og_branch *b, const double st[6]) {
+    if (b->nalt >= b->max_alt) {
+        b->overflow = 1;
+        return;
+    }
+    memcpy(b->alts + 6 * b->nalt, st, 6 * sizeof(double));
+    b->nalt++;
+}
+
+/* st = (C_r, C_g, C_b, D, S, T); walks list entries k0.. with the transmittance-error
+ * bound eT carried as in composite_pixel. */
+static void branch_walk(og_branch *b, int64_t k0, const double st_in[6], double eT) {
+    double st[6];
+    memcpy(st, st_in, sizeof(st));
+    const og_params *p = b->p;
+    for (int64_t k = k0; k < b->nlist && !b->overflow; ++k) {
+        const int64_t gi = b->list[k];
+        const og_proj *pr = &b->P[gi];
+        if (b->use_bbox && (b->px < pr->x0 || b->px > pr->x1 || b->py < pr->y0 || b->py > pr->y1)) continue;
+        og_eval e;
+        eval_gaussian(pr, b->px, b->py, 0.0, &e);
+        const double araw = e.araw, T = st[5];
+        const double margin = fmax(p->amb_alpha, e.dexp);
+        const int near_min = araw > 0.0 && fabs(log(araw / p->alpha_min)) <= margin;
+        const int matters = near_min && 2.0 * p->alpha_min * T * fmax(1.0, fabs(pr->xc[2])) > p->amb_effect;
+        if (near_min) eT += araw / (1.0 - araw);
+        int keep = araw >= p->alpha_min;
+        if (matters) {
+            /* the other outcome of this alpha_min decision, walked on its own */
+            if (keep) {
+                branch_walk(b, k + 1, st, eT);
+            } else {
+                const double alpha = fmin(araw, p->alpha_max), Tn = T * (1.0 - alpha);
+                if (!(Tn < p->t_min)) {
+                    double s2[6];
+                    const double w = alpha * T, *c = b->sc->rgb + 3 * gi;
+                    s2[0] = st[0] + c[0] * w;
+                    s2[1] = st[1] + c[1] * w;
+                    s2[2] = st[2] + c[2] * w;
+                    s2[3] = st[3] + pr->xc[2] * w;
+                    s2[4] = st[4] + w;
+                    s2[5] = Tn;
+                    branch_walk(b, k + 1, s2, eT + alpha * e.dexp / (1.0 - alpha));
+                } else {
+                    branch_leaf(b, st);
+                }
+            }
+            if (b->overflow) return;
+        }
+        if (!keep) continue;
+        const int clamped = araw >= p->alpha_max;
+        const double alpha = clamped ? p->alpha_max : araw;
+        const double Tn = T * (1.0 - alpha);
+        if (!clamped) eT += alpha * e.dexp / (1.0 - alpha);
+        const int near_t = fabs(Tn - p->t_min) <= fmax(p->amb_t, eT) * p->t_min;
+        if (near_t) {
+            /* one outcome stops here, the other takes this Gaussian and goes on (whichever
+             * of the two the FP64 walk takes) */
+            branch_leaf(b, st);
+            if (b->overflow) return;
+        } else if (Tn < p->t_min) {
+            branch_leaf(b, st);
+            return;
+        }
+        const double w = alpha * T, *c = b->sc->rgb + 3 * gi;
+        st[0] += c[0] * w;
+        st[1] += c[1] * w;
+        st[2] += c[2] * w;
+        st[3] += pr->xc[2] * w;
+        st[4] += w;
+        st[5] = Tn;
+    }
+    if (!b->overflow) branch_leaf(b, st);
 }
 
 typedef struct {
@@ -485,14 +630,20 @@ static void frame_free(og_frame *f) {
     }
 }
 
+/* f32_pose: project with the pose an FP32 renderer applies (pose_rot_f32, then FP64
+ * arithmetic), as the render that tests the ambiguity mask does. */
 static int frame_setup(const og_scene *sc, const og_camera *cam, const double pose[7], const og_params *p,
-                       og_frame *f) {
+                       int f32_pose, og_frame *f) {
     memset(f, 0, sizeof(*f));
     if (!sc || !cam || !pose || !p || sc->n < 0 || cam->width <= 0 || cam->height <= 0) return OG_ERR_ARG;
     double R[9], t[3], qn[4];
     float Rf[9], tf[3];
     pose_unpack(pose, R, t, qn);
     pose_rot_f32(pose, Rf, tf);
+    if (f32_pose) {
+        for (int k = 0; k < 9; ++k) R[k] = (double)Rf[k];
+        for (int k = 0; k < 3; ++k) t[k] = (double)tf[k];
+    }
     f->P = (og_proj *)malloc(sizeof(og_proj) * (size_t)(sc->n > 0 ? sc->n : 1));
     if (!f->P) return OG_ERR_OOM;
     for (int64_t i = 0; i < sc->n; ++i) project_one(sc, i, cam, R, t, Rf, tf, p, &f->P[i]);
@@ -568,7 +719,7 @@ int og_project(const og_scene *sc, const og_camera *cam, const double pose[7], c
 int og_render(const og_scene *sc, const og_camera *cam, const double pose[7], const og_params *p, double *rgb,
               double *depth, double *sil, double *t_final, int32_t *n_contrib, uint8_t *amb) {
     og_frame f;
-    int st = frame_setup(sc, cam, pose, p, &f);
+    int st = frame_setup(sc, cam, pose, p, 0, &f);
     if (st) return st;
     const int W = cam->width, H = cam->height;
     const int64_t HW = (int64_t)W * H;
@@ -582,7 +733,7 @@ int og_render(const og_scene *sc, const og_camera *cam, const double pose[7], co
             double o5[5], tf;
             int64_t nc;
             int a;
-            composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, o5, &tf, NULL, &nc, &a);
+            composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, NULL, W, o5, &tf, NULL, &nc, &a);
             const int64_t pix = (int64_t)py * W + px;
             if (rgb) {
                 rgb[pix] = o5[0];
@@ -605,7 +756,7 @@ int og_render_pixels(const og_scene *sc, const og_camera *cam, const double pose
                      const int64_t *pix, int64_t npix, double *out5, double *t_final, uint8_t *amb) {
     if (!pix || npix < 0 || !out5) return OG_ERR_ARG;
     og_frame f;
-    int st = frame_setup(sc, cam, pose, p, &f);
+    int st = frame_setup(sc, cam, pose, p, 0, &f);
     if (st) return st;
     const int W = cam->width;
     set_threads(p);
@@ -618,11 +769,101 @@ int og_render_pixels(const og_scene *sc, const og_camera *cam, const double pose
         double tf;
         int64_t nc;
         int a;
-        composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, out5 + 5 * k, &tf, NULL, &nc, &a);
+        composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, NULL, W, out5 + 5 * k, &tf, NULL, &nc, &a);
         if (t_final) t_final[k] = tf;
         if (amb) amb[k] = (uint8_t)a;
     }
     frame_free(&f);
+    return OG_OK;
+}
+
+/* The render an FP32 renderer could produce under the error model behind the ambiguity
+ * mask, for testing that mask: the projection uses the pose rounded to FP32 (as the GPU
+ * kernels do), and every (pixel, Gaussian) exponent of Eq. 1 is moved by scale times
+ * its modelled rounding error times a SplitMix64 uniform in [-1, 1) drawn from
+ * (seed, pixel, Gaussian).  Outputs as og_render (any may be NULL). */
+int og_render_perturbed(const og_scene *sc, const og_camera *cam, const double pose[7], const og_params *p,
+                        uint64_t seed, double scale, double *rgb, double *depth, double *sil, double *t_final) {
+    og_frame f;
+    int st = frame_setup(sc, cam, pose, p, 1, &f);
+    if (st) return st;
+    const int W = cam->width, H = cam->height;
+    const int64_t HW = (int64_t)W * H;
+    const og_noise nz = {seed, scale, sc->n};
+    set_threads(p);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int py = 0; py < H; ++py) {
+        const int64_t *list;
+        int64_t nl;
+        frame_pixel_list(&f, py, &list, &nl);
+        for (int px = 0; px < W; ++px) {
+            double o5[5], tf;
+            int64_t nc;
+            int a;
+            composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, &nz, W, o5, &tf, NULL, &nc, &a);
+            const int64_t pix = (int64_t)py * W + px;
+            if (rgb) {
+                rgb[pix] = o5[0];
+                rgb[HW + pix] = o5[1];
+                rgb[2 * HW + pix] = o5[2];
+            }
+            if (depth) depth[pix] = o5[3];
+            if (sil) sil[pix] = o5[4];
+            if (t_final) t_final[pix] = tf;
+        }
+    }
+    frame_free(&f);
+    return OG_OK;
+}
+
+/* Every outcome an FP32 renderer may produce at the selected pixels (index y * W + x):
+ * the front-to-back walk of Eqs. 2-4 branched at each decision the ambiguity mask flags
+ * (see branch_walk).  alts is npix x max_alt x 6 = (C_r, C_g, C_b, D, S, T) per outcome;
+ * n_alt[k] is the number of outcomes of pixel k, or -1 when it would take more than
+ * max_alt. */
+int og_render_alternatives(const og_scene *sc, const og_camera *cam, const double pose[7], const og_params *p,
+                           const int64_t *pix, int64_t npix, int32_t max_alt, int32_t *n_alt, double *alts) {
+    if (!pix || npix < 0 || max_alt < 1 || !n_alt || !alts) return OG_ERR_ARG;
+    og_frame f;
+    int st = frame_setup(sc, cam, pose, p, 0, &f);
+    if (st) return st;
+    const int W = cam->width;
+    set_threads(p);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < npix; ++k) {
+        og_branch b;
+        memset(&b, 0, sizeof(b));
+        b.px = (int)(pix[k] % W);
+        b.py = (int)(pix[k] / W);
+        frame_pixel_list(&f, b.py, &b.list, &b.nlist);
+        b.use_bbox = f.use_bbox;
+        b.max_alt = max_alt;
+        b.W = W;
+        b.P = f.P;
+        b.sc = sc;
+        b.p = p;
+        b.alts = alts + (size_t)k * (size_t)max_alt * 6;
+        const double st0[6] = {0, 0, 0, 0, 0, 1.0};
+        branch_walk(&b, 0, st0, 0.0);
+        n_alt[k] = b.overflow ? -1 : b.nalt;
+    }
+    frame_free(&f);
+    return OG_OK;
+}
+
+/* Per Gaussian: the FP32 depth key that orders Eqs. 2-4 (depth_key) and the FP64
+ * camera-frame depth of its mean, for pinning the key against the exact order. */
+int og_depth_keys(const og_scene *sc, const double pose[7], float *keys, double *z64) {
+    if (!sc || !pose || !keys || !z64) return OG_ERR_ARG;
+    double R[9], t[3], qn[4];
+    float Rf[9], tf[3];
+    pose_unpack(pose, R, t, qn);
+    pose_rot_f32(pose, Rf, tf);
+    for (int64_t i = 0; i < sc->n; ++i) {
+        const double *m = sc->means + 3 * i;
+        keys[i] = depth_key(Rf, tf, m);
+        z64[i] = R[6] * m[0] + R[7] * m[1] + R[8] * m[2] + t[2];
+    }
     return OG_OK;
 }
 
@@ -857,7 +1098,7 @@ int og_backward(const og_scene *sc, const og_camera *cam, const double pose[7], 
                 double *pose6) {
     if (!d_rgb || !d_depth || !d_sil) return OG_ERR_ARG;
     og_frame f;
-    int st = frame_setup(sc, cam, pose, p, &f);
+    int st = frame_setup(sc, cam, pose, p, 0, &f);
     if (st) return st;
     const int W = cam->width, H = cam->height;
     const int64_t HW = (int64_t)W * H;
@@ -898,7 +1139,7 @@ int og_backward(const og_scene *sc, const og_camera *cam, const double pose[7], 
                 double o5[5], tf;
                 int64_t nc;
                 int a;
-                composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, o5, &tf, cb, &nc, &a);
+                composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, NULL, W, o5, &tf, cb, &nc, &a);
                 backward_pixel(px, py, cb, nc, f.P, sc, g5, myacc);
             }
         }

@@ -60,11 +60,12 @@ struct GraphKey {
     std::vector<ViewInfo> views;
     uint32_t pair_cap = 0;
     uint32_t prof_mask = 0;
-    uint32_t sched[3] = {};  // sub-buckets, forward and backward batch depths
+    uint32_t sched[4] = {};  // sub-buckets, forward and backward batch depths, flags
     bool operator==(const GraphKey &o) const {
         if (ws != o.ws || ws_bytes != o.ws_bytes || n != o.n || dtype != o.dtype || iters != o.iters ||
             pair_cap != o.pair_cap || prof_mask != o.prof_mask || sched[0] != o.sched[0] ||
-            sched[1] != o.sched[1] || sched[2] != o.sched[2] || views.size() != o.views.size())
+            sched[1] != o.sched[1] || sched[2] != o.sched[2] || sched[3] != o.sched[3] ||
+            views.size() != o.views.size())
             return false;
         for (int k = 0; k < 12; ++k)
             if (ptrs[k] != o.ptrs[k]) return false;
@@ -117,7 +118,7 @@ gs_status cuda_fail(gs_ctx *ctx, cudaError_t e, const char *where) {
 }
 
 const char *const kKernelNames[] = {"k_project", "k_scan_tiles", "k_emit", "k_forward",
-                                    "k_backward", "k_bproject", "k_finalize"};
+                                    "k_backward", "k_bproject", "k_finalize", "k_track_tile"};
 constexpr uint32_t kAllKernels = (1u << (sizeof(kKernelNames) / sizeof(kKernelNames[0]))) - 1u;
 
 bool selected(const gs_ctx *ctx, const char *name) {
@@ -249,6 +250,7 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     d.S = std::min(max_sub(T), (uint32_t)ctx->sched.sub_buckets);
     d.fwd_batch = (uint32_t)ctx->sched.fwd_batch;
     d.bwd_batch = (uint32_t)ctx->sched.bwd_batch;
+    d.flags = (uint32_t)ctx->sched.flags;
     d.tile_threads = (uint32_t)(tw * th);
     d.tile_lw = (uint32_t)ilog2(tw);
     out.d = d;
@@ -369,12 +371,44 @@ cudaError_t enqueue_forward(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, con
     return mark(ctx, st, "k_forward");
 }
 
+// Both compositors of a pose-only tracking iteration with the fused loss: k_forward then
+// k_backward, or k_track_tile when the schedule fuses them (GS_SCHED_FUSED).
+cudaError_t enqueue_compositing(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, const gs_targets *t,
+                                cudaStream_t st) {
+    cudaError_t r;
+    if (pr.d.flags & GS_SCHED_FUSED) {
+        TrackTileLaunch K;
+        K.ws = w;
+        K.d = pr.d;
+        K.s = ctx->s;
+        K.t_rgb = t->rgb;
+        K.t_depth = t->depth;
+        K.t_prior = t->depth_prior;
+        if ((r = mark_begin(ctx, st, "k_track_tile")) != cudaSuccess) return r;
+        if ((r = launch_track_tile(K, st)) != cudaSuccess) return r;
+        return mark(ctx, st, "k_track_tile");
+    }
+    if ((r = enqueue_forward(ctx, pr, w, t, nullptr, nullptr, nullptr, st)) != cudaSuccess) return r;
+    BackwardLaunch B;
+    B.ws = w;
+    B.d = pr.d;
+    B.s = ctx->s;
+    B.up_rgb = w.upstream;
+    B.up_depth = w.upstream + 3u * pr.d.P;
+    B.up_sil = w.upstream + 4u * pr.d.P;
+    B.pose_only = true;
+    if ((r = mark_begin(ctx, st, "k_backward")) != cudaSuccess) return r;
+    if ((r = launch_backward(B, st)) != cudaSuccess) return r;
+    return mark(ctx, st, "k_backward");
+}
+
 bool valid_batch(int32_t b) { return b == 64 || b == 128 || b == 256; }
 
 bool valid_schedule(const gs_schedule &sc) {
     const int32_t sb = sc.sub_buckets, px = sc.tile_w * sc.tile_h;
     return valid_tile(sc.tile_w, sc.tile_h) && (sb == 1 || sb == 2 || sb == 4) && valid_batch(sc.fwd_batch) &&
-           valid_batch(sc.bwd_batch) && sc.fwd_batch <= px && sc.bwd_batch <= px && sc.reserved == 0;
+           valid_batch(sc.bwd_batch) && sc.fwd_batch <= px && sc.bwd_batch <= px &&
+           (sc.flags & ~GS_SCHED_FUSED) == 0 && (!(sc.flags & GS_SCHED_FUSED) || sc.fwd_batch == sc.bwd_batch);
 }
 
 // Device time of one pass of `enqueue`, averaged over `reps` passes after one untimed
@@ -629,18 +663,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
         for (int it = 0; it < iters; ++it) {
             cudaError_t r = enqueue_project(ctx, pr, w, gp, g->dtype_attr, poses, q);
             if (r != cudaSuccess) return r;
-            if ((r = enqueue_forward(ctx, pr, w, targets, nullptr, nullptr, nullptr, q)) != cudaSuccess) return r;
-            BackwardLaunch B;
-            B.ws = w;
-            B.d = pr.d;
-            B.s = ctx->s;
-            B.up_rgb = w.upstream;
-            B.up_depth = w.upstream + 3u * pr.d.P;
-            B.up_sil = w.upstream + 4u * pr.d.P;
-            B.pose_only = true;
-            if ((r = mark_begin(ctx, q, "k_backward")) != cudaSuccess) return r;
-            if ((r = launch_backward(B, q)) != cudaSuccess) return r;
-            if ((r = mark(ctx, q, "k_backward")) != cudaSuccess) return r;
+            if ((r = enqueue_compositing(ctx, pr, w, targets, q)) != cudaSuccess) return r;
             BprojLaunch J;
             J.ws = w;
             J.d = pr.d;
@@ -691,6 +714,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
         key.sched[0] = pr.d.S;
         key.sched[1] = pr.d.fwd_batch;
         key.sched[2] = pr.d.bwd_batch;
+        key.sched[3] = pr.d.flags;
         if (!ctx->graph_exec || !(ctx->graph_key == key)) {
             if (ctx->graph_exec) {
                 cudaGraphExecDestroy(ctx->graph_exec);
@@ -784,7 +808,7 @@ gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g
     ctx->prof_mask = 0;
     reset_marks(ctx);
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    gs_tune_entry ent[13];
+    gs_tune_entry ent[15];
     int n_ent = 0;
     gs_schedule cur = ctx->sched;
     bool overflow = false;  // the context's own schedule overflowed the pair capacity
@@ -796,9 +820,11 @@ gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g
         ctx->sched = sched_saved;
         return r;
     };
-    // One pass of stage `which` (0: all, 1: binning, 2: forward, 3: backward).
+    // One pass of stage `which` (0: all, 1: binning, 2: forward, 3: backward, 4: both
+    // compositors as the tracking step runs them).
     auto enqueue_stage = [&](int which, const Problem &q) -> cudaError_t {
         cudaError_t r = cudaSuccess;
+        if (which == 4) return enqueue_compositing(ctx, q, w, targets, s);
         if (which <= 1) r = enqueue_project(ctx, q, w, gp, g->dtype_attr, poses, s);
         if (r == cudaSuccess && (which == 0 || which == 2))
             r = enqueue_forward(ctx, q, w, targets, nullptr, nullptr, nullptr, s);
@@ -899,6 +925,14 @@ gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g
             if (valid_schedule(c)) cand[nc++] = c;
         }
         e = stage(which, cand, nc);
+    }
+    // stage 4 (tracking): the two compositors as two kernels or as one (GS_SCHED_FUSED)
+    if (e == cudaSuccess && pose_only) {
+        gs_schedule c = cur;
+        c.flags ^= GS_SCHED_FUSED;
+        if (c.flags & GS_SCHED_FUSED) c.bwd_batch = c.fwd_batch;
+        const gs_schedule cand[2] = {cur, c};
+        e = stage(4, cand, valid_schedule(c) ? 2 : 1);
     }
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);

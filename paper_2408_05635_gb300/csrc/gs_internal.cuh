@@ -148,6 +148,7 @@ struct Dims {
     uint32_t bwd_batch;    // Gaussians staged per backward batch: 64, 128 or 256 (0: kBatch)
     uint32_t tile_threads; // threads (= pixels) of a tile block: tile_w x tile_h (0: kTilePix)
     uint32_t tile_lw;      // log2 of the tile width, 3 to 5 (0: 16-pixel tiles)
+    uint32_t flags;        // GS_SCHED_* bits of the launch schedule
 };
 
 struct Settings {
@@ -508,6 +509,16 @@ struct BackwardLaunch {
     bool pose_only;                            // skip opacity / colour gradients
 };
 cudaError_t launch_backward(const BackwardLaunch &L, cudaStream_t st);
+
+// Forward with the fused loss and the pose-only reverse walk of each tile in one kernel
+// (the tracking step under GS_SCHED_FUSED); needs targets and fwd_batch == bwd_batch.
+struct TrackTileLaunch {
+    WsPtrs ws;
+    Dims d;
+    Settings s;
+    const float *t_rgb, *t_depth, *t_prior;
+};
+cudaError_t launch_track_tile(const TrackTileLaunch &L, cudaStream_t st);
 
 struct BprojLaunch {
     WsPtrs ws;

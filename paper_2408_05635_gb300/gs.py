@@ -79,14 +79,17 @@ class gs_problem(ctypes.Structure):
 
 class gs_schedule(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("sub_buckets", c_int32), ("fwd_batch", c_int32),
-                ("bwd_batch", c_int32), ("reserved", c_int32)]
+                ("bwd_batch", c_int32), ("flags", c_int32)]
+
+
+GS_SCHED_FUSED = 1  # gs_track_step: forward, fused loss and pose-only reverse walk in one kernel per tile
 
 
 class gs_tune_entry(ctypes.Structure):
     _fields_ = [("stage", c_int32), ("ms", ctypes.c_float), ("schedule", gs_schedule)]
 
 
-SCHEDULE_FIELDS = ("tile_w", "tile_h", "sub_buckets", "fwd_batch", "bwd_batch")
+SCHEDULE_FIELDS = ("tile_w", "tile_h", "sub_buckets", "fwd_batch", "bwd_batch", "flags")
 
 
 def schedule_dict(s: gs_schedule) -> dict:
@@ -265,7 +268,8 @@ def gs_set_profiling(ctx, enable: bool) -> None:
     _check(ctx, load().gs_set_profiling(ctx, int(bool(enable))), "gs_set_profiling")
 
 
-KERNELS = ("k_project", "k_scan_tiles", "k_emit", "k_forward", "k_backward", "k_bproject", "k_finalize")
+KERNELS = ("k_project", "k_scan_tiles", "k_emit", "k_forward", "k_backward", "k_bproject", "k_finalize",
+           "k_track_tile")
 
 
 def gs_set_profiling_mask(ctx, kernels) -> None:
@@ -290,13 +294,14 @@ def gs_get_schedule(ctx) -> gs_schedule:
     return s
 
 
-def gs_set_schedule(ctx, tile_w: int, tile_h: int, sub_buckets: int, fwd_batch: int, bwd_batch: int) -> None:
-    s = gs_schedule(int(tile_w), int(tile_h), int(sub_buckets), int(fwd_batch), int(bwd_batch), 0)
+def gs_set_schedule(ctx, tile_w: int, tile_h: int, sub_buckets: int, fwd_batch: int, bwd_batch: int,
+                    flags: int = 0) -> None:
+    s = gs_schedule(int(tile_w), int(tile_h), int(sub_buckets), int(fwd_batch), int(bwd_batch), int(flags))
     _check(ctx, load().gs_set_schedule(ctx, ctypes.byref(s)), "gs_set_schedule")
 
 
-TUNE_STAGES = ("tile", "sub_buckets", "fwd_batch", "bwd_batch")
-TUNE_MAX = 13
+TUNE_STAGES = ("tile", "sub_buckets", "fwd_batch", "bwd_batch", "fused")
+TUNE_MAX = 15
 
 
 def gs_autotune(ctx, prob: gs_problem, g: gs_gaussians, poses, targets: gs_targets, ws, ws_bytes: int,
@@ -673,8 +678,8 @@ class Rasterizer:
         return schedule_dict(gs_get_schedule(self.ctx))
 
     def set_schedule(self, tile_w: int = 16, tile_h: int = 16, sub_buckets: int = 4, fwd_batch: int = 256,
-                     bwd_batch: int = 256) -> None:
-        gs_set_schedule(self.ctx, tile_w, tile_h, sub_buckets, fwd_batch, bwd_batch)
+                     bwd_batch: int = 256, flags: int = 0) -> None:
+        gs_set_schedule(self.ctx, tile_w, tile_h, sub_buckets, fwd_batch, bwd_batch, flags)
 
     def autotune(self, prob: gs_problem, g: GaussianTensors, poses: torch.Tensor, targets, pose_only: bool = True,
                  reps: int = 10, stream=None) -> dict:

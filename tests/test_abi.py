@@ -95,7 +95,8 @@ def test_schedule_host_logic(libpath):
     assert st == 0
     s = gs.gs_schedule()
     assert lib.gs_get_schedule(h, ctypes.byref(s)) == 0
-    assert gs.schedule_dict(s) == {"tile_w": 16, "tile_h": 16, "sub_buckets": 4, "fwd_batch": 256, "bwd_batch": 256}
+    assert gs.schedule_dict(s) == {"tile_w": 16, "tile_h": 16, "sub_buckets": 4, "fwd_batch": 256, "bwd_batch": 256,
+                                   "flags": 0}
     cams = (gs.gs_camera * 3)(gs.gs_camera(525, 525, 319.5, 239.5, 640, 480), gs.gs_camera(100, 100, 10, 10, 37, 23),
                               gs.gs_camera(600, 600, 599.5, 339.5, 1200, 680))
     prob = gs.gs_problem(50000, 3, 0, ctypes.cast(cams, ctypes.POINTER(gs.gs_camera)), 1 << 20, 0)
@@ -104,7 +105,7 @@ def test_schedule_host_logic(libpath):
             (32, 4, 4, 128, 64), (16, 4, 1, 64, 64), (8, 16, 2, 128, 64)]
     for v in good:
         assert lib.gs_set_schedule(h, ctypes.byref(gs.gs_schedule(*v, 0))) == 0, v
-        assert lib.gs_get_schedule(h, ctypes.byref(s)) == 0 and tuple(gs.schedule_dict(s).values()) == v
+        assert lib.gs_get_schedule(h, ctypes.byref(s)) == 0 and tuple(gs.schedule_dict(s).values()) == v + (0,)
         n = ctypes.c_size_t(0)
         assert lib.gs_workspace_size(h, ctypes.byref(prob), ctypes.byref(n)) == 0
         sizes.add(n.value)
@@ -115,8 +116,12 @@ def test_schedule_host_logic(libpath):
     last = gs.gs_schedule(*good[-1], 0)
     for v in bad:
         assert lib.gs_set_schedule(h, ctypes.byref(gs.gs_schedule(*v, 0))) == 1, v
-    assert lib.gs_set_schedule(h, ctypes.byref(gs.gs_schedule(16, 16, 4, 256, 256, 7))) == 1  # reserved
+    assert lib.gs_set_schedule(h, ctypes.byref(gs.gs_schedule(16, 16, 4, 256, 256, 6))) == 1  # unknown flags
+    # the fused tracking kernel needs one batch depth for both walks
+    assert lib.gs_set_schedule(h, ctypes.byref(gs.gs_schedule(16, 16, 4, 256, 128, gs.GS_SCHED_FUSED))) == 1
     assert lib.gs_get_schedule(h, ctypes.byref(s)) == 0 and gs.schedule_dict(s) == gs.schedule_dict(last)
+    assert lib.gs_set_schedule(h, ctypes.byref(gs.gs_schedule(16, 8, 2, 128, 128, gs.GS_SCHED_FUSED))) == 0
+    assert lib.gs_get_schedule(h, ctypes.byref(s)) == 0 and s.flags == gs.GS_SCHED_FUSED
     assert lib.gs_destroy(h) == 0
 
 
@@ -139,5 +144,6 @@ def test_config_tile_sets_the_initial_schedule(libpath):
         s = gs.gs_schedule()
         assert lib.gs_get_schedule(h, ctypes.byref(s)) == 0
         nb = min(256, w * hgt)
-        assert gs.schedule_dict(s) == {"tile_w": w, "tile_h": hgt, "sub_buckets": 4, "fwd_batch": nb, "bwd_batch": nb}
+        assert gs.schedule_dict(s) == {"tile_w": w, "tile_h": hgt, "sub_buckets": 4, "fwd_batch": nb, "bwd_batch": nb,
+                                       "flags": 0}
         lib.gs_destroy(h)

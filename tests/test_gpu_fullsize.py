@@ -30,7 +30,7 @@ import torch
 
 import bench
 import oracle
-from gpu_common import assert_grads_close, assert_images_close, ocam
+from gpu_common import assert_grads_close, assert_images_close, ocam, rel_err
 from paper_2408_05635_gb300 import gs, scenes
 
 pytestmark = pytest.mark.gpu
@@ -94,15 +94,20 @@ def test_tracking_frame_gradients(tracking):
     assert_grads_close(b["pose_grad"].cpu().numpy()[0], ob["pose6"], what="pose")
 
 
-def test_tracking_graph_first_update(tracking):
-    """The bench's launch: gs_track_step (CUDA graph) from the start pose.  The first
-    decoupled Adam step moves each coordinate by lr * g / (|g| + eps), which the fused
-    loss's ambiguous pixels do not change unless a gradient component is near zero."""
+@pytest.mark.parametrize("flags", [0, gs.GS_SCHED_FUSED])
+def test_tracking_graph_first_update(tracking, flags):
+    """The bench's launch: gs_track_step (CUDA graph) from the start pose, with the two
+    compositing kernels and with the fused one (GS_SCHED_FUSED).  The first decoupled
+    Adam step moves each coordinate by lr * g / (|g| + eps), which the fused loss's
+    ambiguous pixels do not change unless a gradient component is near zero; the first
+    moments it leaves are (1 - beta1) g, the pose gradient itself, which must match the
+    oracle's through the same (unmasked) loss to the fused-loss bound 1e-2."""
     t = tracking
     L = t["L"]
     ob = oracle.backward(t["sc"], t["oc"], t["start"], t["op"], L["d_rgb"], L["d_depth"], L["d_sil"])
     o_pose, _ = oracle.adam_step(t["start"], np.zeros(16), ob["pose6"], t["op"])
     R = gs.Rasterizer(gs.Config())
+    R.set_schedule(16, 16, 4, 256, 256, flags)
     gt = gs.GaussianTensors.from_numpy(t["g"])
     poses = torch.tensor(np.asarray(t["start"])[None], dtype=torch.float64, device="cuda")
     prob = R.plan(gt, [t["cam"]], poses, margin=1.5)
@@ -114,6 +119,10 @@ def test_tracking_graph_first_update(tracking):
     R.sync()
     np.testing.assert_allclose(poses.cpu().numpy()[0], o_pose, atol=1e-9)
     assert hist.item() == pytest.approx(L["loss"], rel=2e-3)
+    st = adam.cpu().numpy()[0]
+    g6 = np.concatenate([st[0:3], st[6:9]]) / (1.0 - t["op"].beta1)
+    ri, r2 = rel_err(g6, ob["pose6"])
+    assert r2 < 1e-2, (ri, r2)
 
 
 # ---------------------------------------------------------------------------- batched hypotheses

@@ -29,8 +29,8 @@ SCHEDULES = [(16, 16, 4, 256, 256), (16, 16, 1, 64, 64), (16, 16, 2, 128, 128), 
              (32, 8, 2, 256, 64), (16, 8, 4, 128, 64), (8, 8, 1, 64, 64), (8, 32, 4, 256, 128),
              (32, 4, 2, 128, 128)]
 GRAD_KEYS = [("means", 0, 3), ("quats", 3, 7), ("log_scales", 7, 10), ("logits", 10, 11), ("rgb", 11, 14)]
-NAMES = ("tile_w", "tile_h", "sub_buckets", "fwd_batch", "bwd_batch")
-DEFAULT = dict(zip(NAMES, (16, 16, 4, 256, 256)))
+NAMES = ("tile_w", "tile_h", "sub_buckets", "fwd_batch", "bwd_batch", "flags")
+DEFAULT = dict(zip(NAMES, (16, 16, 4, 256, 256, 0)))
 
 
 @pytest.fixture(scope="module")
@@ -87,7 +87,7 @@ def test_schedule_results_match_default_and_oracle(case, default_run, sched):
     base, b0, c0 = default_run
     R = gs.Rasterizer(gcfg)
     R.set_schedule(*sched)
-    assert R.schedule == dict(zip(NAMES, sched))
+    assert R.schedule == dict(zip(NAMES, sched + (0,)))
     out, b, counts = _run(R, g, cam, pose, up)
     R.close()
     assert counts.err_flags == 0 and counts.max_tile > max(sched[3], sched[4])
@@ -171,13 +171,51 @@ def test_tracking_graph_follows_the_schedule():
     s0 = torch.tensor(start, dtype=torch.float64, device="cuda")
     tr = slam.Tracker(cam, 5)
     out = []
-    for sched in [(16, 16, 4, 256, 256), (16, 8, 1, 64, 128), (16, 16, 4, 256, 256)]:
+    for sched in [(16, 16, 4, 256, 256), (16, 8, 1, 64, 128), (16, 16, 4, 256, 256), (16, 16, 4, 256, 256, 1),
+                  (16, 8, 2, 128, 128, 1), (32, 8, 2, 64, 64, 1)]:
         tr.R.set_schedule(*sched)
         out.append(tr.track(gt, s0, *frame).cpu().numpy())
     tr.close()
     # the backward's atomics make even two runs of one schedule differ at rounding level
     assert np.abs(out[0] - out[2]).max() < 1e-6, np.abs(out[0] - out[2]).max()
     assert np.abs(out[0] - out[1]).max() < 1e-5, np.abs(out[0] - out[1]).max()
+    # the fused compositing kernel (GS_SCHED_FUSED): the same arithmetic in one launch
+    assert np.abs(out[0] - out[3]).max() < 1e-6, np.abs(out[0] - out[3]).max()
+    for k in (4, 5):
+        assert np.abs(out[0] - out[k]).max() < 1e-5, (k, np.abs(out[0] - out[k]).max())
+
+
+def test_fused_tracking_kernel_matches_the_two_kernels():
+    """One gs_track_step iteration with the forward and pose-only backward as two kernels
+    and as k_track_tile (GS_SCHED_FUSED), for every batch depth: the loss to FP32
+    summation order and the pose gradient (the first Adam moments over 1 - beta1) to 1e-5."""
+    g = scenes.room_scene(40_000, seed=8)
+    cam = scenes.Cam(262.5, 262.5, 159.5, 119.5, 320, 240)
+    truth = scenes.tracking_gt_pose()
+    start = scenes.perturb_pose(truth, np.random.default_rng(9), 1.0, 0.03)
+    rgb, depth = scenes.raycast_room(truth, cam, seed=8)
+    prior = scenes.prior_from_depth(depth, np.random.default_rng(3), 0.02, 0.05)
+    tt = [torch.tensor(np.ascontiguousarray(a).reshape(-1), device="cuda") for a in (rgb, depth, prior)]
+    tg = gs.gs_targets(*(x.data_ptr() for x in tt))
+    gt = gs.GaussianTensors.from_numpy(g)
+    for nb in (256, 128, 64):
+        res = []
+        for flags in (0, gs.GS_SCHED_FUSED):
+            R = gs.Rasterizer(gs.Config())
+            R.set_schedule(16, 16, 2, nb, nb, flags)
+            poses = torch.tensor(np.asarray(start)[None], dtype=torch.float64, device="cuda")
+            prob = R.plan(gt, [cam], poses, margin=1.5)
+            ws, nbytes = R.workspace(prob)
+            adam = torch.zeros(1, 16, dtype=torch.float64, device="cuda")
+            hist = torch.zeros(1, 1, dtype=torch.float64, device="cuda")
+            gs.gs_track_step(R.ctx, prob, gt.c(), tg, poses, adam, hist, 1, ws, nbytes)
+            R.sync()
+            st = adam.cpu().numpy()[0]
+            res.append((hist.item(), np.concatenate([st[0:3], st[6:9]]) / 0.1))
+            R.close()
+        (l0, g0), (l1, g1) = res
+        assert l1 == pytest.approx(l0, rel=1e-6)
+        assert np.abs(g1 - g0).max() <= 1e-5 * np.abs(g0).max(), (nb, g0, g1)
 
 
 def test_tracker_tunes_on_the_first_frame_and_when_the_map_doubles():

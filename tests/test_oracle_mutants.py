@@ -28,8 +28,8 @@ MUTANTS = {
                                      "mat3_transpose(R, Rt);\n    mat3_mul(Rt, g->Sigma, RS);\n"
                                      "    mat3_mul(RS, R, g->Sigma_c);"),
     # compositing (Eqs. 2-4)
-    "transmittance update": ("gs_oracle.c", "const double Tn = T * (1.0 - alpha);",
-                             "const double Tn = T * (1.0 - 0.5 * alpha);"),
+    "transmittance update": ("gs_oracle.c", "const double z = pr->xc[2];\n        const double Tn = T * (1.0 - alpha);",
+                             "const double z = pr->xc[2];\n        const double Tn = T * (1.0 - 0.5 * alpha);"),
     "depth weighted by T only": ("gs_oracle.c", "D += z * w;", "D += z * T;"),
     # reverse compositing and chain rule
     "behind-colour update": ("gs_oracle.c", "B[ch] = c->alpha * v[ch] + (1.0 - c->alpha) * B[ch];",
