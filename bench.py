@@ -512,6 +512,186 @@ def cpu_baseline(g, cam, start, rgb, depth, prior, budget_s: float):
             "sample": f"{iters} full tracking iterations of the 640x480 / 200k workload in {el:.1f} s"}
 
 
+def _check_view(sc, oc, pose, op, ref, rgb, depth, sil, max_alt=32):
+    """A GPU view (planar maps) against the oracle's: the largest error on pixels the oracle
+    does not flag, and on flagged pixels the distance to the nearest of the outcomes an
+    FP32 renderer may legitimately produce there (the walk of Eqs. 2-4 branched at each
+    flagged decision); pixels with more than max_alt outcomes are counted as unchecked."""
+    import oracle
+    H, W = oc.height, oc.width
+    rgb, depth, sil = rgb.reshape(3, H, W), depth.reshape(H, W), sil.reshape(H, W)
+    err = np.maximum(np.abs(rgb - ref["rgb"]).max(axis=0),
+                     np.maximum(np.abs(depth - ref["depth"]), np.abs(sil - ref["sil"])))
+    flagged = ref["amb"]
+    pix = np.flatnonzero(flagged.ravel())
+    near, unres = 0.0, 0
+    if pix.size:
+        A = oracle.render_alternatives(sc, oc, pose, op, pix, max_alt=max_alt)
+        got = np.stack([rgb[0].ravel()[pix], rgb[1].ravel()[pix], rgb[2].ravel()[pix], depth.ravel()[pix],
+                        sil.ravel()[pix]], 1)
+        for k, n in enumerate(A["n_alt"]):
+            if n < 1:
+                unres += 1
+            else:
+                near = max(near, float(np.abs(A["alts"][k, :n, :5] - got[k]).max(axis=1).min()))
+    return {"max_err_unflagged": float(err[~flagged].max()) if (~flagged).any() else 0.0,
+            "flagged_share": float(flagged.mean()), "max_err_flagged_nearest_outcome": near,
+            "unchecked_share": unres / (H * W)}
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    return {"inf": float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)),
+            "l2": float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))}
+
+
+def _masked_upstream(ref, L):
+    m = ref["amb"] | L["amb"]
+    return [np.where(m[None], 0.0, L["d_rgb"]), np.where(m, 0.0, L["d_depth"]), np.where(m, 0.0, L["d_sil"])], m
+
+
+def _view_accuracy(dev, stream, g_np, g_oracle, cam, pose, targets, attr_dtype, params_grads=False):
+    """One view rendered and differentiated by the GPU (attributes in attr_dtype) and by
+    the oracle on g_oracle (the attributes the GPU reads): images, loss, and the pose
+    gradient (and with params_grads every parameter gradient) for the oracle's loss
+    gradient with flagged pixels zeroed as the shared upstream; and the pose gradient
+    through each side's own fused loss."""
+    import torch
+    import oracle
+    from paper_2408_05635_gb300 import gs
+    op = oracle.Params()
+    sc = oracle.Scene(*g_oracle.arrays())
+    oc = oracle.camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    rgb_t, depth_t, prior_t = targets
+    ref = oracle.render(sc, oc, pose, op)
+    L = oracle.loss(oc, op, ref["rgb"], ref["depth"], ref["sil"], rgb_t, depth_t, prior_t)
+    ups, mask = _masked_upstream(ref, L)
+    ob = oracle.backward(sc, oc, pose, op, *ups)
+    of = oracle.backward(sc, oc, pose, op, L["d_rgb"], L["d_depth"], L["d_sil"])
+    R = gs.Rasterizer(gs.Config(), device=dev)
+    gt = gs.GaussianTensors.from_numpy(g_np, device=dev, attr_dtype=attr_dtype)
+    poses = torch.tensor(np.asarray(pose)[None], dtype=torch.float64, device=dev)
+    tt = tuple(torch.tensor(np.ascontiguousarray(x).reshape(-1), dtype=torch.float32, device=dev)
+               for x in (rgb_t, depth_t, prior_t))
+    prob = R.plan(gt, [cam], poses, margin=1.5)
+    out = R.render(prob, gt, poses, targets=tt, stream=stream)
+    fused = R.backward(gt, params=False, pose=True, stream=stream)["pose_grad"][0].cpu().numpy()
+    R.render(prob, gt, poses, stream=stream, images=False)
+    upt = tuple(torch.tensor(u.reshape(-1).astype(np.float32), device=dev) for u in ups)
+    b = R.backward(gt, upstream=upt, params=params_grads, pose=True, stream=stream)
+    parts = gs.gs_pose_partials(R.ctx, stream)
+    R.sync(stream)
+    res = _check_view(sc, oc, pose, op, ref, *(out[k].cpu().numpy().astype(np.float64) for k in ("rgb", "depth", "sil")))
+    res["loss_rel_err"] = abs(float(out["loss"][0]) - L["loss"]) / abs(L["loss"])
+    pg = b["pose_grad"][0].cpu().numpy()
+    res["pose_grad_rel_err"] = _rel(pg, ob["pose6"])
+    res["pose_grad_fused_loss_rel_err"] = _rel(fused, of["pose6"])
+    res["masked_upstream_share"] = float(mask.mean())
+    # the double-float pose reduction against an FP64 sum of the same per-cell partials
+    import math
+    exact = [math.fsum(float(h) + float(lo) for h, lo in parts[:, k, :]) for k in range(6)]
+    res["pose_reduction_df_vs_fp64_rel"] = _rel(pg, exact)["inf"]
+    if params_grads:
+        names = [("means", 0, 3), ("quats", 3, 7), ("log_scales", 7, 10), ("logits", 10, 11), ("rgb", 11, 14)]
+        res["param_grad_rel_err"] = {n: _rel(b["grads"][n].cpu().numpy().reshape(g_np.n, -1), ob["grads"][:, lo:hi])
+                                     for n, lo, hi in names}
+    R.close()
+    return res, fused
+
+
+def sequence_drift(dev, stream, frames_n: int = 10, iters: int = 100):
+    """Pose drift of the GPU tracker against the oracle's own tracking loop: the first
+    `frames_n` frames of the long sequence's spline path at 160 x 120, a 200k-Gaussian room
+    with FP16 attributes (the oracle on their FP32 values), `iters` decoupled Adam
+    iterations per frame, each frame started from that side's previous estimate."""
+    import torch
+    import oracle
+    from paper_2408_05635_gb300 import gs, scenes, slam
+    g = scenes.room_scene(200_000, seed=3)
+    cam = scenes.Cam(131.25, 131.25, 79.5, 59.5, 160, 120)
+    poses = scenes.spline_trajectory(frames_n + 1, seed=0)
+    gq = scenes.Gaussians(g.means, *(torch.tensor(a).to(torch.float16).float().numpy() for a in
+                                     (g.quats, g.log_scales, g.logits, g.rgb)))
+    rng = np.random.default_rng(11)
+    frames = []
+    for p in poses:
+        rgb, depth = scenes.raycast_room(p, cam, seed=3)
+        frames.append((rgb, depth, scenes.prior_from_depth(depth, rng, 0.02, 0.05)))
+    gt = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=torch.float16)
+    tr = slam.Tracker(cam, iters, device=dev)
+    est_gpu = [np.asarray(poses[0], np.float64)]
+    with torch.cuda.stream(stream):
+        for k in range(1, frames_n + 1):
+            f = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in frames[k]]
+            start = torch.tensor(est_gpu[-1], dtype=torch.float64, device=dev)
+            est_gpu.append(tr.track(gt, start, *f, stream=stream).cpu().numpy().reshape(7))
+    tr.close()
+    op = oracle.Params()
+    sc = oracle.Scene(*gq.arrays())
+    oc = oracle.camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+    est_o = [np.asarray(poses[0], np.float64)]
+    t0 = time.perf_counter()
+    for k in range(1, frames_n + 1):
+        pose, state = est_o[-1].copy(), np.zeros(16)
+        rgb, depth, prior = frames[k]
+        for _ in range(iters):
+            r = oracle.render(sc, oc, pose, op)
+            L = oracle.loss(oc, op, r["rgb"], r["depth"], r["sil"], rgb, depth, prior)
+            b = oracle.backward(sc, oc, pose, op, L["d_rgb"], L["d_depth"], L["d_sil"])
+            pose, state = oracle.adam_step(pose, state, b["pose6"], op)
+        est_o.append(pose)
+    el = time.perf_counter() - t0
+    ce_g, ce_o = slam.camera_centres(np.array(est_gpu)), slam.camera_centres(np.array(est_o))
+    dt = np.linalg.norm(ce_g - ce_o, axis=1)[1:]
+    ang = []
+    for a_, b_ in zip(est_gpu[1:], est_o[1:]):
+        Ra, Rb = scenes.pose_rt(a_)[0], scenes.pose_rt(b_)[0]
+        ang.append(float(np.degrees(np.arccos(np.clip((np.trace(Ra @ Rb.T) - 1) / 2, -1, 1)))))
+    truth = _trajectory_report(np.array(est_o), np.array(poses))
+    return {"workload": f"first {frames_n} frames of the spline path at 160x120, 200k room Gaussians (fp16), "
+                        f"{iters} iterations per frame; the oracle on the same FP16-rounded attributes",
+            "frames": frames_n, "trans_diff_mm_per_frame": [round(1e3 * float(x), 4) for x in dt],
+            "rot_diff_deg_per_frame": [round(x, 5) for x in ang],
+            "max_trans_diff_mm": round(1e3 * float(dt.max()), 4), "max_rot_diff_deg": round(max(ang), 5),
+            "oracle_ate_vs_truth_cm": truth["ate_rmse_cm"], "oracle_seconds": round(el, 1)}
+
+
+def accuracy_vs_oracle(dev, stream) -> dict:
+    """Every timed workload's error against the FP64 oracle, on samples the oracle finishes
+    on the host cores: the tracking frame, one batched view per resolution (BF16
+    attributes: against the oracle on the dequantized attributes, and through the fused
+    loss against the oracle on the FP32 attributes, the rounding of the storage included),
+    one mapping keyframe (every parameter gradient), and the drift of the sequence tracker
+    against the oracle's tracking loop."""
+    import torch
+    from paper_2408_05635_gb300 import scenes
+    out = {}
+    g, cam, gt_pose, start, rgb, depth, prior = workload()
+    out["tracking_frame"], _ = _view_accuracy(dev, stream, g, g, cam, start, (rgb, depth, prior), torch.float32)
+    gb, cams, poses0, frame_of, frames = batched_workload()
+    gq = scenes.Gaussians(gb.means, *(torch.tensor(a).to(torch.bfloat16).float().numpy() for a in
+                                      (gb.quats, gb.log_scales, gb.logits, gb.rgb)))
+    views = {}
+    for w in sorted({c.width for c in cams}):
+        v = next(v for v, c in enumerate(cams) if c.width == w)
+        res, fused_bf16 = _view_accuracy(dev, stream, gb, gq, cams[v], poses0[v], frames[frame_of[v]], torch.bfloat16)
+        import oracle
+        op = oracle.Params()
+        sc32 = oracle.Scene(*gb.arrays())
+        oc = oracle.camera(cams[v].fx, cams[v].fy, cams[v].cx, cams[v].cy, cams[v].width, cams[v].height)
+        r32 = oracle.render(sc32, oc, poses0[v], op)
+        L32 = oracle.loss(oc, op, r32["rgb"], r32["depth"], r32["sil"], *frames[frame_of[v]])
+        o32 = oracle.backward(sc32, oc, poses0[v], op, L32["d_rgb"], L32["d_depth"], L32["d_sil"])
+        res["bf16_pose_grad_vs_fp32_attribute_oracle_rel_err"] = _rel(fused_bf16, o32["pose6"])
+        views[f"{cams[v].width}x{cams[v].height} (view {v})"] = res
+    out["batched_bf16_views"] = views
+    gm, mcams, mposes, mframes = mapping_workload()
+    out["mapping_keyframe_1"], _ = _view_accuracy(dev, stream, gm, gm, mcams[1], mposes[1], mframes[1], torch.float32,
+                                                  params_grads=True)
+    out["sequence_drift"] = sequence_drift(dev, stream)
+    return out
+
+
 def oracle_small_single_thread(budget_s: float = 3.0) -> dict:
     """The oracle's tracking iteration on one host thread, on the small parity case
     (160 x 120, 2,000 Gaussians in front of the camera, target rendered 2 deg / 3 cm away,
@@ -746,7 +926,10 @@ def main():
     launches = 0
     # the view-table copy, the projection, scan and emission, the compositing (two kernels,
     # or one fused), the back-projection and the finalize
-    per_iter_launches = 1 + 3 + (1 if R.schedule["flags"] & gs.GS_SCHED_FUSED else 2) + 2
+    sch = R.schedule
+    tiles = -(-cam.width // sch["tile_w"]) * -(-cam.height // sch["tile_h"])
+    radix = 3 * gs.radix_passes(tiles) + 1 if sch["flags"] & gs.GS_SCHED_RADIX else 0  # passes x 3 + ties
+    per_iter_launches = 1 + 3 + radix + (1 if sch["flags"] & gs.GS_SCHED_FUSED else 2) + 2
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -862,6 +1045,11 @@ def main():
         if world == 1 and not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, cam, start, rgb, depth, prior, a.cpu_sample_seconds)
             line["cpu_baseline"]["single_thread_small_case"] = oracle_small_single_thread()
+            # the oracle run of the CPU-baseline leg also gives every timed workload's error
+            # against FP64
+            t0 = time.perf_counter()
+            line["cpu_baseline"]["accuracy_vs_oracle"] = accuracy_vs_oracle(dev, stream)
+            line["cpu_baseline"]["accuracy_vs_oracle"]["seconds"] = round(time.perf_counter() - t0, 1)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -257,6 +257,15 @@ gs_status gs_set_profiling_mask(gs_ctx *ctx, uint32_t mask);
  * number available.  Errors: STATE (profiling off or nothing recorded), CUDA. */
 gs_status gs_kernel_times(gs_ctx *ctx, gs_kernel_time *out, int32_t cap, int32_t *count);
 
+/* Instrumentation of the pose reduction (the FP64 summation the pose gradient of the
+ * decoupled update of Sec. III-B asks for): the per-cell partial sums the last pose
+ * backward left in the workspace, copied to `out` (host, cap floats) after synchronising
+ * `stream`.  Cell c of view v holds six double-float values (hi, lo pairs of FP32), at
+ * out[12 (v nblk + c) ..], nblk = ceil(n / 256); the pose gradient is their sum over the
+ * view's cells.  *count gets the number of floats (12 V nblk); nothing is copied when
+ * cap is smaller.  Errors: INVALID_ARG, STATE (nothing projected), CUDA. */
+gs_status gs_pose_partials(gs_ctx *ctx, float *out, int64_t cap, int64_t *count, void *stream);
+
 /* ------------------------------------------------------------------ launch schedule */
 
 /* How the context launches the binning and the two compositors.  Every pixel composites
@@ -286,6 +295,11 @@ typedef struct {
  * between the walks and the last forward batch reused by the reverse walk.  Needs
  * fwd_batch == bwd_batch.  Other calls are unaffected. */
 #define GS_SCHED_FUSED 1
+/* gs_schedule.flags: GS_SCHED_RADIX -- the front-to-back order of Eqs. 2-4 comes from one
+ * device-wide LSD radix sort of all (tile, depth) keys (eight-bit digits, stable passes,
+ * runs of equal keys then put in Gaussian order) run after the key emission, instead of
+ * the per-tile sort inside the forward.  Same order, same results. */
+#define GS_SCHED_RADIX 2
 
 /* Read the context's schedule (defaults after gs_create).  Errors: INVALID_ARG (NULL). */
 gs_status gs_get_schedule(const gs_ctx *ctx, gs_schedule *out);
@@ -305,7 +319,9 @@ typedef struct {
                              2: forward compositing per fwd_batch;
                              3: backward compositing per bwd_batch;
                              4: (pose_only) both compositors, as two kernels or fused
-                                (GS_SCHED_FUSED)                                         */
+                                (GS_SCHED_FUSED);
+                             5: the sort, per tile or device-wide (GS_SCHED_RADIX),
+                                timed as a whole pass                                    */
     float ms;             /* mean device time of one pass of the stage (CUDA events on
                              the stream, warm caches, after one untimed pass); -1 when
                              the setting made more pairs than pair_capacity (not timed) */
@@ -322,13 +338,15 @@ typedef struct {
  *     parameters otherwise);
  *   - with pose_only, the two compositors as two kernels against the fused tracking
  *     kernel (GS_SCHED_FUSED, both batch depths set to the forward's);
+ *   - the per-tile sort against the device-wide radix sort (GS_SCHED_RADIX), one whole
+ *     pass each;
  * `reps` passes each.  Each stage starts from the previous stage's choice (first, the
  * context's current schedule) and keeps it unless another setting is at least 1 % faster;
  * the final choice is set on the context.  It uses the workspace (sized by
  * gs_workspace_size for `prob`) as gs_project does and synchronises `stream`, so it
  * cannot be captured into a graph; afterwards no projection is bound (call gs_project or
  * gs_track_step next).  table (host, cap entries, may be NULL) receives the measurements
- * in order, *count (may be NULL) their number (15 at most); best (may be NULL) the chosen
+ * in order, *count (may be NULL) their number (17 at most); best (may be NULL) the chosen
  * schedule.  A setting whose pairs overflow pair_capacity is recorded with ms = -1 and
  * not chosen; an overflow of the context's current schedule is reported as CAPACITY (the
  * schedule is then left unchanged).

@@ -122,12 +122,13 @@ def _load():
             lib.og_backward.argtypes = [sc, cam, d, par, d, d, d, d, d, d]
             lib.og_adam_step.argtypes = [d, d, d, par]
             lib.og_num_threads.argtypes = [par]
-            lib.og_render_perturbed.argtypes = [sc, cam, d, par, ctypes.c_uint64, ctypes.c_double, d, d, d, d]
+            lib.og_render_perturbed.argtypes = [sc, cam, d, par, ctypes.c_uint64, ctypes.c_double, ctypes.c_int32, d, d, d, d]
             lib.og_render_alternatives.argtypes = [sc, cam, d, par, i64, ctypes.c_int64, ctypes.c_int32, i32, d]
             lib.og_depth_keys.argtypes = [sc, d, P(ctypes.c_float), d]
+            lib.og_render_tstats.argtypes = [sc, cam, d, par, d, d]
             for fn in (lib.og_project, lib.og_render, lib.og_render_pixels, lib.og_loss,
                        lib.og_backward, lib.og_adam_step, lib.og_num_threads, lib.og_render_perturbed,
-                       lib.og_render_alternatives, lib.og_depth_keys):
+                       lib.og_render_alternatives, lib.og_depth_keys, lib.og_render_tstats):
                 fn.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -215,17 +216,20 @@ def render(scene: Scene, cam: Camera, pose, params: Params) -> dict:
 AMB_ALPHA_MIN, AMB_ALPHA_MAX, AMB_T_MIN = 1, 2, 4
 
 
-def render_perturbed(scene: Scene, cam: Camera, pose, params: Params, seed: int, scale: float) -> dict:
+def render_perturbed(scene: Scene, cam: Camera, pose, params: Params, seed: int, scale: float,
+                     f32_pose: bool = False) -> dict:
     """A render within the FP32 error model the ambiguity mask assumes, for testing the
-    mask: the pose rounded to FP32 as the GPU applies it, and each (pixel, Gaussian)
-    exponent of Eq. 1 moved by scale x its modelled rounding error x a SplitMix64
-    uniform in [-1, 1) drawn from (seed, pixel, Gaussian)."""
+    mask: each screen mean moved by scale x up to dmu (the modelled camera-transform
+    error) in a direction drawn per Gaussian, each (pixel, Gaussian) exponent of Eq. 1 by
+    scale x up to its modelled rounding error (SplitMix64 uniforms from (seed, pixel,
+    Gaussian)); with f32_pose, also the pose rounded to FP32 as the GPU applies it."""
     lib = _load()
     H, W = cam.height, cam.width
     rgb, depth, sil, tf = np.zeros((3, H, W)), np.zeros((H, W)), np.zeros((H, W)), np.zeros((H, W))
     sc, par, pose = scene._c(), params._c(), _f64(pose, (7,))
     _check(lib.og_render_perturbed(ctypes.byref(sc), ctypes.byref(cam), _dp(pose), ctypes.byref(par),
-                                   ctypes.c_uint64(seed), float(scale), _dp(rgb), _dp(depth), _dp(sil), _dp(tf)),
+                                   ctypes.c_uint64(seed), float(scale), int(bool(f32_pose)), _dp(rgb), _dp(depth),
+                                   _dp(sil), _dp(tf)),
            "render_perturbed")
     return {"rgb": rgb, "depth": depth, "sil": sil, "t_final": tf}
 
@@ -245,6 +249,19 @@ def render_alternatives(scene: Scene, cam: Camera, pose, params: Params, pix, ma
                                       n_alt.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(alts)),
            "render_alternatives")
     return {"n_alt": n_alt, "alts": alts}
+
+
+def render_tstats(scene: Scene, cam: Camera, pose, params: Params) -> dict:
+    """Per pixel, where the walk stops on t_min: the transmittance-error bound it carried
+    (eT) and that step's size in log transmittance, -ln(1 - alpha) (0 where it does not
+    stop)."""
+    lib = _load()
+    H, W = cam.height, cam.width
+    eT, step = np.zeros((H, W)), np.zeros((H, W))
+    sc, par, pose = scene._c(), params._c(), _f64(pose, (7,))
+    _check(lib.og_render_tstats(ctypes.byref(sc), ctypes.byref(cam), _dp(pose), ctypes.byref(par), _dp(eT),
+                                _dp(step)), "render_tstats")
+    return {"eT": eT, "step": step}
 
 
 def depth_keys(scene: Scene, pose) -> tuple[np.ndarray, np.ndarray]:

@@ -407,10 +407,10 @@ typedef struct {
     double G, araw, dexp;
 } og_eval;
 
-static void eval_gaussian(const og_proj *pr, int px, int py, double noise, og_eval *e) {
-    const double dx = (double)px - pr->mu[0], dy = (double)py - pr->mu[1];
+static void eval_gaussian(const og_proj *pr, int px, int py, const double noise[3], og_eval *e) {
+    const double dx = (double)px - pr->mu[0] - noise[0], dy = (double)py - pr->mu[1] - noise[1];
     const double q = pr->conic[0] * dx * dx + 2.0 * pr->conic[1] * dx * dy + pr->conic[2] * dy * dy;
-    e->G = exp(-0.5 * q + noise);
+    e->G = exp(-0.5 * q + noise[2]);
     e->araw = pr->o * e->G;
     const double gx = pr->conic[0] * dx + pr->conic[1] * dy, gy = pr->conic[1] * dx + pr->conic[2] * dy;
     const double terms =
@@ -419,9 +419,8 @@ static void eval_gaussian(const og_proj *pr, int px, int py, double noise, og_ev
     e->dexp = 4.0 * OG_FP32_ROUNDOFF * (sqrt(gx * gx + gy * gy) * mu_mag + terms) + sqrt(gx * gx + gy * gy) * pr->dmu;
 }
 
-/* The exponent error of the perturbed render: the part of dexp that comes from the
- * rounding of the screen mean and of the quadratic form (the camera transform's part is
- * realised instead by rendering with the pose rounded to FP32). */
+/* The part of dexp that comes from the rounding of the screen mean and of the quadratic
+ * form (the camera transform's part, dmu, moves the whole footprint instead). */
 static double rounding_dexp(const og_proj *pr, int px, int py) {
     const double dx = (double)px - pr->mu[0], dy = (double)py - pr->mu[1];
     const double gx = pr->conic[0] * dx + pr->conic[1] * dy, gy = pr->conic[1] * dx + pr->conic[2] * dy;
@@ -449,10 +448,28 @@ typedef struct {
     int64_t n;
 } og_noise;
 
-static double noise_at(const og_noise *nz, const og_proj *pr, int px, int py, int W, int64_t g) {
-    if (!nz || nz->scale == 0.0) return 0.0;
+/* The perturbation of Gaussian g at one pixel: its screen mean moved by up to dmu (the
+ * camera transform's error, one draw per Gaussian, the same at every pixel) and the
+ * exponent of Eq. 1 by up to its rounding error (one draw per pixel and Gaussian). */
+static void noise_at(const og_noise *nz, const og_proj *pr, int px, int py, int W, int64_t g, double out[3]) {
+    out[0] = out[1] = out[2] = 0.0;
+    if (!nz || nz->scale == 0.0) return;
     const uint64_t counter = ((uint64_t)py * (uint64_t)W + (uint64_t)px) * (uint64_t)nz->n + (uint64_t)g;
-    return nz->scale * rounding_dexp(pr, px, py) * splitmix_unit(nz->seed, counter);
+    out[2] = nz->scale * rounding_dexp(pr, px, py) * splitmix_unit(nz->seed, counter);
+    const double ang = 3.14159265358979323846 * splitmix_unit(nz->seed ^ 0x5bd1e995u, 2u * (uint64_t)g);
+    const double r = nz->scale * pr->dmu * splitmix_unit(nz->seed ^ 0x5bd1e995u, 2u * (uint64_t)g + 1u);
+    out[0] = r * cos(ang);
+    out[1] = r * sin(ang);
+}
+
+/* Relative margin of an alpha decision (alpha_min skip, alpha_max clamp) at one pixel:
+ * the fixed floor amb_alpha or dexp, whichever is larger. */
+static double alpha_margin(const og_params *p, const og_eval *e) { return fmax(p->amb_alpha, e->dexp); }
+
+/* Is the transmittance Tn after a step within the margin of t_min (relative: the floor
+ * amb_t or the carried error bound eT)? */
+static int near_t_min(const og_params *p, double Tn, double eT) {
+    return fabs(Tn - p->t_min) <= fmax(p->amb_t, eT) * p->t_min;
 }
 
 /* Composite one pixel front to back.  out5 = (C_r, C_g, C_b, D, S).  When `contrib` is
@@ -461,17 +478,20 @@ static double noise_at(const og_noise *nz, const og_proj *pr, int px, int py, in
  * the OG_AMB_* reasons for which an FP32 renderer may take another discrete decision. */
 static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, int use_bbox, const og_proj *P,
                             const og_scene *sc, const og_params *p, const og_noise *nz, int W, double out5[5],
-                            double *t_final, og_contrib *contrib, int64_t *ncontrib, int *amb) {
+                            double *t_final, og_contrib *contrib, int64_t *ncontrib, int *amb, double *diag2) {
     double T = 1.0, C0 = 0, C1 = 0, C2 = 0, D = 0, S = 0;
     double eT = 0.0; /* bound of the relative error of an FP32 renderer's T so far */
     int64_t nc = 0;
     int a = 0;
+    if (diag2) diag2[0] = diag2[1] = 0.0;
     for (int64_t k = 0; k < nlist; ++k) {
         const int64_t gi = list[k];
         const og_proj *pr = &P[gi];
         if (use_bbox && (px < pr->x0 || px > pr->x1 || py < pr->y0 || py > pr->y1)) continue;
         og_eval e;
-        eval_gaussian(pr, px, py, noise_at(nz, pr, px, py, W, gi), &e);
+        double nzv[3];
+        noise_at(nz, pr, px, py, W, gi, nzv);
+        eval_gaussian(pr, px, py, nzv, &e);
         const double araw = e.araw;
         /* Relative margin of the alpha decisions: the fixed amb_alpha, or dexp, whichever is
          * larger.  Skipping or keeping an alpha ~ alpha_min Gaussian moves the pixel by at
@@ -479,7 +499,7 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
          * Either way it scales the transmittance of everything behind by 1 - alpha, which
          * an FP32 renderer may therefore hold off by alpha / (1 - alpha): a later t_min
          * decision inherits that uncertainty. */
-        const double margin = fmax(p->amb_alpha, e.dexp);
+        const double margin = alpha_margin(p, &e);
         const int near_min = araw > 0.0 && fabs(log(araw / p->alpha_min)) <= margin;
         if (near_min && 2.0 * p->alpha_min * T * fmax(1.0, fabs(pr->xc[2])) > p->amb_effect) a |= OG_AMB_ALPHA_MIN;
         if (near_min) eT += araw / (1.0 - araw);
@@ -492,8 +512,14 @@ static void composite_pixel(int px, int py, const int64_t *list, int64_t nlist, 
         /* an alpha known to a relative dexp gives 1 - alpha to alpha dexp / (1 - alpha): the
          * product T = prod (1 - alpha_i) compounds it (a clamped alpha is exact) */
         if (!clamped) eT += alpha * e.dexp / (1.0 - alpha);
-        if (fabs(Tn - p->t_min) <= fmax(p->amb_t, eT) * p->t_min) a |= OG_AMB_T_MIN;
-        if (Tn < p->t_min) break;
+        if (near_t_min(p, Tn, eT)) a |= OG_AMB_T_MIN;
+        if (Tn < p->t_min) {
+            if (diag2) {
+                diag2[0] = eT;
+                diag2[1] = -log1p(-alpha);
+            }
+            break;
+        }
         const double w = alpha * T;
         const double *c = sc->rgb + 3 * gi;
         C0 += c[0] * w;
@@ -558,9 +584,10 @@ static void branch_walk(og_branch *b, int64_t k0, const double st_in[6], double 
         const og_proj *pr = &b->P[gi];
         if (b->use_bbox && (b->px < pr->x0 || b->px > pr->x1 || b->py < pr->y0 || b->py > pr->y1)) continue;
         og_eval e;
-        eval_gaussian(pr, b->px, b->py, 0.0, &e);
+        const double zero[3] = {0.0, 0.0, 0.0};
+        eval_gaussian(pr, b->px, b->py, zero, &e);
         const double araw = e.araw, T = st[5];
-        const double margin = fmax(p->amb_alpha, e.dexp);
+        const double margin = alpha_margin(p, &e);
         const int near_min = araw > 0.0 && fabs(log(araw / p->alpha_min)) <= margin;
         const int matters = near_min && 2.0 * p->alpha_min * T * fmax(1.0, fabs(pr->xc[2])) > p->amb_effect;
         if (near_min) eT += araw / (1.0 - araw);
@@ -592,7 +619,7 @@ static void branch_walk(og_branch *b, int64_t k0, const double st_in[6], double 
         const double alpha = clamped ? p->alpha_max : araw;
         const double Tn = T * (1.0 - alpha);
         if (!clamped) eT += alpha * e.dexp / (1.0 - alpha);
-        const int near_t = fabs(Tn - p->t_min) <= fmax(p->amb_t, eT) * p->t_min;
+        const int near_t = near_t_min(p, Tn, eT);
         if (near_t) {
             /* one outcome stops here, the other takes this Gaussian and goes on (whichever
              * of the two the FP64 walk takes) */
@@ -733,7 +760,7 @@ int og_render(const og_scene *sc, const og_camera *cam, const double pose[7], co
             double o5[5], tf;
             int64_t nc;
             int a;
-            composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, NULL, W, o5, &tf, NULL, &nc, &a);
+            composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, NULL, W, o5, &tf, NULL, &nc, &a, NULL);
             const int64_t pix = (int64_t)py * W + px;
             if (rgb) {
                 rgb[pix] = o5[0];
@@ -769,7 +796,7 @@ int og_render_pixels(const og_scene *sc, const og_camera *cam, const double pose
         double tf;
         int64_t nc;
         int a;
-        composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, NULL, W, out5 + 5 * k, &tf, NULL, &nc, &a);
+        composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, NULL, W, out5 + 5 * k, &tf, NULL, &nc, &a, NULL);
         if (t_final) t_final[k] = tf;
         if (amb) amb[k] = (uint8_t)a;
     }
@@ -778,14 +805,17 @@ int og_render_pixels(const og_scene *sc, const og_camera *cam, const double pose
 }
 
 /* The render an FP32 renderer could produce under the error model behind the ambiguity
- * mask, for testing that mask: the projection uses the pose rounded to FP32 (as the GPU
- * kernels do), and every (pixel, Gaussian) exponent of Eq. 1 is moved by scale times
- * its modelled rounding error times a SplitMix64 uniform in [-1, 1) drawn from
- * (seed, pixel, Gaussian).  Outputs as og_render (any may be NULL). */
+ * mask, for testing that mask: every screen mean moves by scale times up to dmu (the
+ * modelled error of an FP32 camera transform, the pose's rounding included) in a
+ * direction drawn per Gaussian, and every (pixel, Gaussian) exponent of Eq. 1 by scale
+ * times up to its modelled rounding error, the draws SplitMix64 uniforms from (seed,
+ * pixel, Gaussian).  With f32_pose the projection also applies the pose rounded to FP32
+ * as the GPU kernels do.  Outputs as og_render (any may be NULL). */
 int og_render_perturbed(const og_scene *sc, const og_camera *cam, const double pose[7], const og_params *p,
-                        uint64_t seed, double scale, double *rgb, double *depth, double *sil, double *t_final) {
+                        uint64_t seed, double scale, int32_t f32_pose, double *rgb, double *depth, double *sil,
+                        double *t_final) {
     og_frame f;
-    int st = frame_setup(sc, cam, pose, p, 1, &f);
+    int st = frame_setup(sc, cam, pose, p, f32_pose, &f);
     if (st) return st;
     const int W = cam->width, H = cam->height;
     const int64_t HW = (int64_t)W * H;
@@ -800,7 +830,7 @@ int og_render_perturbed(const og_scene *sc, const og_camera *cam, const double p
             double o5[5], tf;
             int64_t nc;
             int a;
-            composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, &nz, W, o5, &tf, NULL, &nc, &a);
+            composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, &nz, W, o5, &tf, NULL, &nc, &a, NULL);
             const int64_t pix = (int64_t)py * W + px;
             if (rgb) {
                 rgb[pix] = o5[0];
@@ -810,6 +840,36 @@ int og_render_perturbed(const og_scene *sc, const og_camera *cam, const double p
             if (depth) depth[pix] = o5[3];
             if (sil) sil[pix] = o5[4];
             if (t_final) t_final[pix] = tf;
+        }
+    }
+    frame_free(&f);
+    return OG_OK;
+}
+
+/* Per pixel, for checking the share of pixels the t_min margin flags: at the step where
+ * the walk stops on t_min, the transmittance-error bound eT it carried and the step's
+ * size -ln(1 - alpha) in log transmittance (both 0 for a pixel whose walk does not stop). */
+int og_render_tstats(const og_scene *sc, const og_camera *cam, const double pose[7], const og_params *p,
+                     double *eT_stop, double *step_stop) {
+    if (!eT_stop || !step_stop) return OG_ERR_ARG;
+    og_frame f;
+    int st = frame_setup(sc, cam, pose, p, 0, &f);
+    if (st) return st;
+    const int W = cam->width, H = cam->height;
+    set_threads(p);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int py = 0; py < H; ++py) {
+        const int64_t *list;
+        int64_t nl;
+        frame_pixel_list(&f, py, &list, &nl);
+        for (int px = 0; px < W; ++px) {
+            double o5[5], tf, d2[2];
+            int64_t nc;
+            int a;
+            composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, NULL, W, o5, &tf, NULL, &nc, &a, d2);
+            const int64_t pix = (int64_t)py * W + px;
+            eT_stop[pix] = d2[0];
+            step_stop[pix] = d2[1];
         }
     }
     frame_free(&f);
@@ -1139,7 +1199,7 @@ int og_backward(const og_scene *sc, const og_camera *cam, const double pose[7], 
                 double o5[5], tf;
                 int64_t nc;
                 int a;
-                composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, NULL, W, o5, &tf, cb, &nc, &a);
+                composite_pixel(px, py, list, nl, f.use_bbox, f.P, sc, p, NULL, W, o5, &tf, cb, &nc, &a, NULL);
                 backward_pixel(px, py, cb, nc, f.P, sc, g5, myacc);
             }
         }

@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kBlock, PARAMS ? 4 : 6) k_bproject(BprojLaunch
 // thread always holds the same pair of components.  The block's partials are summed per
 // component by one warp (strided columns, then a butterfly).
 constexpr int kFinThreads = 384;
-constexpr int kFinUnroll = 4;
+constexpr int kFinUnroll = 8;
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeLaunch L) {
     const int v = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

@@ -41,7 +41,7 @@ uint32_t max_sub(uint64_t T) {
 struct Layout {
     size_t err, hdr, tile_cnt, zero_end;
     size_t views, view_rt, cell_cnt, tile_start, cursor, tile_order, rec, rec_grad, keys, sorted, t_final, n_last,
-        upstream, tile_loss, pose_part, total;
+        upstream, tile_loss, pose_part, rkeys, rvals, rhist, rtotal, total;
 };
 
 struct Problem {
@@ -118,7 +118,7 @@ gs_status cuda_fail(gs_ctx *ctx, cudaError_t e, const char *where) {
 }
 
 const char *const kKernelNames[] = {"k_project", "k_scan_tiles", "k_emit", "k_forward",
-                                    "k_backward", "k_bproject", "k_finalize", "k_track_tile"};
+                                    "k_backward", "k_bproject", "k_finalize", "k_track_tile", "k_radix_sort"};
 constexpr uint32_t kAllKernels = (1u << (sizeof(kKernelNames) / sizeof(kKernelNames[0]))) - 1u;
 
 bool selected(const gs_ctx *ctx, const char *name) {
@@ -282,6 +282,11 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     L.upstream = take(sizeof(float) * 5 * (size_t)d.P);
     L.tile_loss = take(sizeof(float2) * (size_t)lay_tiles);
     L.pose_part = take(sizeof(float2) * 6 * cells);
+    // the radix sort's second key / value buffers and digit counts (GS_SCHED_RADIX)
+    L.rkeys = take(sizeof(unsigned long long) * (size_t)d.pair_cap);
+    L.rvals = take(sizeof(uint32_t) * (size_t)d.pair_cap);
+    L.rhist = take(sizeof(uint32_t) * 256 * (size_t)radix_blocks(d.pair_cap));
+    L.rtotal = take(sizeof(uint32_t) * 256);
     L.total = o;
     return GS_OK;
 }
@@ -307,6 +312,10 @@ WsPtrs ws_ptrs(void *base, const Layout &L) {
     w.upstream = reinterpret_cast<float *>(b + L.upstream);
     w.tile_loss = reinterpret_cast<float2 *>(b + L.tile_loss);
     w.pose_part = reinterpret_cast<float2 *>(b + L.pose_part);
+    w.rkeys = reinterpret_cast<unsigned long long *>(b + L.rkeys);
+    w.rvals = reinterpret_cast<uint32_t *>(b + L.rvals);
+    w.rhist = reinterpret_cast<uint32_t *>(b + L.rhist);
+    w.rtotal = reinterpret_cast<uint32_t *>(b + L.rtotal);
     return w;
 }
 
@@ -350,7 +359,14 @@ cudaError_t enqueue_project(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, con
     if ((e = mark(ctx, st, "k_scan_tiles")) != cudaSuccess) return e;
     if ((e = mark_begin(ctx, st, "k_emit")) != cudaSuccess) return e;
     if ((e = launch_emit(w, pr.d, st)) != cudaSuccess) return e;
-    return mark(ctx, st, "k_emit");
+    if ((e = mark(ctx, st, "k_emit")) != cudaSuccess) return e;
+    if (!(pr.d.flags & GS_SCHED_RADIX)) return cudaSuccess;
+    RadixLaunch X;
+    X.ws = w;
+    X.d = pr.d;
+    if ((e = mark_begin(ctx, st, "k_radix_sort")) != cudaSuccess) return e;
+    if ((e = launch_radix_sort(X, st)) != cudaSuccess) return e;
+    return mark(ctx, st, "k_radix_sort");
 }
 
 cudaError_t enqueue_forward(gs_ctx *ctx, const Problem &pr, const WsPtrs &w, const gs_targets *t, float *rgb,
@@ -408,7 +424,8 @@ bool valid_schedule(const gs_schedule &sc) {
     const int32_t sb = sc.sub_buckets, px = sc.tile_w * sc.tile_h;
     return valid_tile(sc.tile_w, sc.tile_h) && (sb == 1 || sb == 2 || sb == 4) && valid_batch(sc.fwd_batch) &&
            valid_batch(sc.bwd_batch) && sc.fwd_batch <= px && sc.bwd_batch <= px &&
-           (sc.flags & ~GS_SCHED_FUSED) == 0 && (!(sc.flags & GS_SCHED_FUSED) || sc.fwd_batch == sc.bwd_batch);
+           (sc.flags & ~(GS_SCHED_FUSED | GS_SCHED_RADIX)) == 0 &&
+           (!(sc.flags & GS_SCHED_FUSED) || sc.fwd_batch == sc.bwd_batch);
 }
 
 // Device time of one pass of `enqueue`, averaged over `reps` passes after one untimed
@@ -808,7 +825,7 @@ gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g
     ctx->prof_mask = 0;
     reset_marks(ctx);
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    gs_tune_entry ent[15];
+    gs_tune_entry ent[17];
     int n_ent = 0;
     gs_schedule cur = ctx->sched;
     bool overflow = false;  // the context's own schedule overflowed the pair capacity
@@ -821,10 +838,16 @@ gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g
         return r;
     };
     // One pass of stage `which` (0: all, 1: binning, 2: forward, 3: backward, 4: both
-    // compositors as the tracking step runs them).
+    // compositors as the tracking step runs them, 5: binning, sort and both compositors as
+    // the caller will run them).
     auto enqueue_stage = [&](int which, const Problem &q) -> cudaError_t {
         cudaError_t r = cudaSuccess;
         if (which == 4) return enqueue_compositing(ctx, q, w, targets, s);
+        if (which == 5 && pose_only) {
+            r = enqueue_project(ctx, q, w, gp, g->dtype_attr, poses, s);
+            return r == cudaSuccess ? enqueue_compositing(ctx, q, w, targets, s) : r;
+        }
+        if (which == 5) which = 0;
         if (which <= 1) r = enqueue_project(ctx, q, w, gp, g->dtype_attr, poses, s);
         if (r == cudaSuccess && (which == 0 || which == 2))
             r = enqueue_forward(ctx, q, w, targets, nullptr, nullptr, nullptr, s);
@@ -934,6 +957,13 @@ gs_status gs_autotune(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g
         const gs_schedule cand[2] = {cur, c};
         e = stage(4, cand, valid_schedule(c) ? 2 : 1);
     }
+    // stage 5: the per-tile sort or the device-wide radix sort (GS_SCHED_RADIX)
+    if (e == cudaSuccess) {
+        gs_schedule c = cur;
+        c.flags ^= GS_SCHED_RADIX;
+        const gs_schedule cand[2] = {cur, c};
+        e = stage(5, cand, 2);
+    }
     for (cudaEvent_t x : ev)
         if (x) cudaEventDestroy(x);
     ctx->prof_mask = prof_saved;
@@ -986,6 +1016,20 @@ gs_status gs_kernel_times(gs_ctx *ctx, gs_kernel_time *out, int32_t cap, int32_t
         ++k;
     }
     *count = k;
+    return GS_OK;
+}
+
+gs_status gs_pose_partials(gs_ctx *ctx, float *out, int64_t cap, int64_t *count, void *stream) {
+    if (!ctx || !count || cap < 0 || (cap > 0 && !out)) return GS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!ctx->bound) return fail(ctx, GS_ERR_STATE, "no projection is bound");
+    const int64_t n = (int64_t)ctx->prob.d.V * (int64_t)ctx->prob.d.nblk * 12;
+    *count = n;
+    if (cap < n) return GS_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(out, ctx->ws.pose_part, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pose partials copy");
     return GS_OK;
 }
 

@@ -131,6 +131,10 @@ struct WsPtrs {
     float *upstream;       // 5 x P: dL/dC (planar like the images), dL/dD, dL/dS of the fused loss
     float2 *tile_loss;     // T, combined loss of each tile's pixels (fused loss), double-float
     float2 *pose_part;     // V x nblk x 6, pose-gradient sum of each cell's records, double-float
+    unsigned long long *rkeys;  // pair_capacity: the radix sort's second key buffer
+    uint32_t *rvals;       // pair_capacity: its second value buffer
+    uint32_t *rhist;       // 256 x radix_blocks(pair_capacity) digit counts
+    uint32_t *rtotal;      // 256 digit totals
 };
 
 struct Dims {
@@ -519,6 +523,16 @@ struct TrackTileLaunch {
     const float *t_rgb, *t_depth, *t_prior;
 };
 cudaError_t launch_track_tile(const TrackTileLaunch &L, cudaStream_t st);
+
+// The device-wide LSD radix sort of the (tile, depth) keys k_emit writes under
+// GS_SCHED_RADIX (radix_sort.cu); its result replaces the compositors' per-tile sort.
+struct RadixLaunch {
+    WsPtrs ws;
+    Dims d;
+};
+uint32_t radix_blocks(uint32_t pair_cap);
+int radix_passes(uint32_t tiles);
+cudaError_t launch_radix_sort(const RadixLaunch &L, cudaStream_t st);
 
 struct BprojLaunch {
     WsPtrs ws;

@@ -447,6 +447,19 @@ cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Write one (record, tile) pair at its slot: for the per-tile sort the key depth bits << 32 |
+// record; for the device-wide radix sort (GS_SCHED_RADIX) the key tile << 32 | depth bits
+// with the record as the value.  Depths are positive, so their bits order as unsigned.
+__device__ __forceinline__ void put_pair(const WsPtrs &ws, bool radix, uint32_t slot, uint32_t tile, uint32_t depth_bits,
+                                         uint32_t rec) {
+    if (radix) {
+        ws.keys[slot] = ((unsigned long long)tile << 32) | depth_bits;
+        ws.sorted[slot] = rec;
+    } else {
+        ws.keys[slot] = ((unsigned long long)depth_bits << 32) | rec;
+    }
+}
+
 // The emission runs kEmitThreads threads per block, kCell / kEmitThreads blocks per cell,
 // compiled for kEmitMinBlocks resident blocks per SM (64 registers a thread).
 constexpr int kEmitThreads = 64;
@@ -479,6 +492,7 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws
         sub = (uint32_t)((uint64_t)__float_as_uint(rec.c.w) % (uint64_t)d.n) & (d.S - 1);
     }
     const uint32_t rbase = cell * kCell + (slot_id & ~31u);
+    const bool radix = (d.flags & GS_SCHED_RADIX) != 0;
     // small rectangles: this lane alone, slot atomics issued eight at a time before the
     // dependent stores, so a record waits for about one atomic round trip per eight tiles
     int tx0 = 1, tx1 = 0, ty0 = 1, ty1 = 0;
@@ -492,7 +506,6 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws
             row_tiles(vi, A.x, A.y, B.x, B.y, B.z, B.w, ty, tx0, tx1, a0, a1);
             if (a0 <= a1) hits |= ((1u << (a1 - a0 + 1)) - 1u) << ((ty - ty0) * rw + (a0 - tx0));
         }
-        const unsigned long long key = ((unsigned long long)__float_as_uint(A.z) << 32) | r;
         while (hits) {
             uint32_t bucket[8], slot[8];
             bool live[8];
@@ -510,7 +523,7 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws
             for (int k = 0; k < 8; ++k)
                 if (live[k]) {
                     if (slot[k] < ws.tile_start[bucket[k] + 1] && slot[k] < d.pair_cap)
-                        ws.keys[slot[k]] = key;
+                        put_pair(ws, radix, slot[k], bucket[k] / d.S, __float_as_uint(A.z), r);
                     else
                         atomicOr(ws.err, (uint32_t)kErrPairs);
                 }
@@ -518,11 +531,10 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws
     }
     // large rectangles: the warp splits them
     record_tiles<false>(mine, vi, A, B, sub, lane, [&](int src, uint32_t tile, float4 As, uint32_t sb) {
-        const unsigned long long key = ((unsigned long long)__float_as_uint(As.z) << 32) | (rbase + (uint32_t)src);
         const uint32_t bucket = tile * d.S + sb;
         const uint32_t slot = atomicAdd(ws.cursor + bucket, 1u);
         if (slot < ws.tile_start[bucket + 1] && slot < d.pair_cap)
-            ws.keys[slot] = key;
+            put_pair(ws, radix, slot, tile, __float_as_uint(As.z), rbase + (uint32_t)src);
         else
             atomicOr(ws.err, (uint32_t)kErrPairs);
     });

@@ -102,7 +102,9 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
 
     uint32_t start;
     const uint32_t n = tile_entries(L.ws, L.d, tile, start);
-    sort_tile(L.ws, start, (int)n, sKeys);  // this tile's list in (depth, Gaussian) order
+    // this tile's list in (depth, Gaussian) order, unless the device-wide radix sort
+    // (GS_SCHED_RADIX) has already ordered it
+    if (!(L.d.flags & GS_SCHED_RADIX)) sort_tile(L.ws, start, (int)n, sKeys);
 
     // ---------------------------------------------------------------- forward (Eqs. 2-4)
     float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, D = 0.f;

@@ -18,6 +18,7 @@ import os
 import threading
 from typing import Sequence
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -83,6 +84,14 @@ class gs_schedule(ctypes.Structure):
 
 
 GS_SCHED_FUSED = 1  # gs_track_step: forward, fused loss and pose-only reverse walk in one kernel per tile
+GS_SCHED_RADIX = 2  # the depth order from one device-wide LSD radix sort of the (tile, depth) keys
+
+
+def radix_passes(tiles: int) -> int:
+    """Eight-bit passes of the radix sort over `tiles` tiles: four for the depth bits and
+    one per byte of the largest tile index."""
+    bits = max(0, int(tiles - 1).bit_length())
+    return 4 + (bits + 7) // 8
 
 
 class gs_tune_entry(ctypes.Structure):
@@ -149,6 +158,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                            c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
             "gs_kernel_times": (c_int32, [c_void_p, P(gs_kernel_time), c_int32, P(c_int32)]),
             "gs_get_schedule": (c_int32, [c_void_p, P(gs_schedule)]),
+            "gs_pose_partials": (c_int32, [c_void_p, c_void_p, c_int64, P(c_int64), c_void_p]),
             "gs_set_schedule": (c_int32, [c_void_p, P(gs_schedule)]),
             "gs_autotune": (c_int32, [c_void_p, P(gs_problem), P(gs_gaussians), c_void_p, P(gs_targets), c_int32,
                                       c_int32, c_void_p, c_size_t, P(gs_tune_entry), c_int32, P(c_int32),
@@ -269,7 +279,7 @@ def gs_set_profiling(ctx, enable: bool) -> None:
 
 
 KERNELS = ("k_project", "k_scan_tiles", "k_emit", "k_forward", "k_backward", "k_bproject", "k_finalize",
-           "k_track_tile")
+           "k_track_tile", "k_radix_sort")
 
 
 def gs_set_profiling_mask(ctx, kernels) -> None:
@@ -288,6 +298,17 @@ def gs_kernel_times(ctx, cap: int = 4096) -> list[tuple[str, float]]:
     return [(arr[k].name.decode(), float(arr[k].ms)) for k in range(min(cap, cnt.value))]
 
 
+def gs_pose_partials(ctx, stream=None) -> np.ndarray:
+    """The per-cell double-float pose partials of the last pose backward: an array of
+    shape (views, cells, 6, 2) of (hi, lo) FP32 pairs."""
+    cnt = c_int64(0)
+    _check(ctx, load().gs_pose_partials(ctx, None, 0, ctypes.byref(cnt), _stream(stream)), "gs_pose_partials")
+    out = np.zeros(cnt.value, dtype=np.float32)
+    _check(ctx, load().gs_pose_partials(ctx, out.ctypes.data, cnt.value, ctypes.byref(cnt), _stream(stream)),
+           "gs_pose_partials")
+    return out.reshape(-1, 6, 2)
+
+
 def gs_get_schedule(ctx) -> gs_schedule:
     s = gs_schedule()
     _check(ctx, load().gs_get_schedule(ctx, ctypes.byref(s)), "gs_get_schedule")
@@ -300,8 +321,8 @@ def gs_set_schedule(ctx, tile_w: int, tile_h: int, sub_buckets: int, fwd_batch: 
     _check(ctx, load().gs_set_schedule(ctx, ctypes.byref(s)), "gs_set_schedule")
 
 
-TUNE_STAGES = ("tile", "sub_buckets", "fwd_batch", "bwd_batch", "fused")
-TUNE_MAX = 15
+TUNE_STAGES = ("tile", "sub_buckets", "fwd_batch", "bwd_batch", "fused", "sort")
+TUNE_MAX = 17
 
 
 def gs_autotune(ctx, prob: gs_problem, g: gs_gaussians, poses, targets: gs_targets, ws, ws_bytes: int,

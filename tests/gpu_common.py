@@ -63,3 +63,38 @@ def rel_err(a, b):
 def assert_grads_close(gpu, ora, tol=GRAD_TOL, what=""):
     ri, r2 = rel_err(gpu, ora)
     assert ri <= tol and r2 <= tol, f"{what}: rel inf {ri:.2e}, rel l2 {r2:.2e} (tol {tol})"
+
+
+def check_images(rgb, depth, sil, ref, scene, cam, pose, op, tol=IMG_TOL, what="", max_alt=32) -> dict:
+    """GPU maps of one view (planar arrays) against the oracle (ref = oracle.render of the
+    same view).  Pixels the oracle does not flag must agree to `tol` in colour, depth and
+    silhouette; a flagged pixel must agree to `tol` with one of the outcomes an FP32
+    renderer may legitimately produce there (oracle.render_alternatives: the walk of
+    Eqs. 2-4 branched at each flagged decision).  Pixels with more outcomes than max_alt
+    stay unchecked; their share must stay below 0.01 %.  Returns the shares and errors."""
+    H, W = cam.height, cam.width
+    rgb, depth, sil = rgb.reshape(3, H, W), depth.reshape(H, W), sil.reshape(H, W)
+    err = np.maximum(np.abs(rgb - ref["rgb"]).max(axis=0),
+                     np.maximum(np.abs(depth - ref["depth"]), np.abs(sil - ref["sil"])))
+    flagged = ref["amb"]
+    worst = float(err[~flagged].max()) if (~flagged).any() else 0.0
+    assert worst <= tol, f"{what}: max |gpu - oracle| = {worst:.3e} on unflagged pixels (tol {tol})"
+    pix = np.flatnonzero(flagged.ravel())
+    worst_alt, unresolved = 0.0, 0
+    if pix.size:
+        alts = oracle.render_alternatives(scene, ocam(cam), pose, op, pix, max_alt=max_alt)
+        got = np.stack([rgb[0].ravel()[pix], rgb[1].ravel()[pix], rgb[2].ravel()[pix], depth.ravel()[pix],
+                        sil.ravel()[pix]], 1)
+        for k, n in enumerate(alts["n_alt"]):
+            if n < 1:
+                unresolved += 1
+                continue
+            d = float(np.abs(alts["alts"][k, :n, :5] - got[k]).max(axis=1).min())
+            worst_alt = max(worst_alt, d)
+            assert d <= tol, f"{what}: flagged pixel {pix[k]} is {d:.3e} from each of its {n} FP32 outcomes"
+    share_unres = unresolved / (H * W)
+    assert share_unres <= 1e-4, f"{what}: {unresolved} pixels with more than {max_alt} outcomes"
+    stats = {"flagged": float(flagged.mean()), "unresolved": share_unres, "max_err_unflagged": worst,
+             "max_err_flagged_nearest_outcome": worst_alt}
+    print(f"{what}: {stats}")
+    return stats

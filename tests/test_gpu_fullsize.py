@@ -30,7 +30,8 @@ import torch
 
 import bench
 import oracle
-from gpu_common import assert_grads_close, assert_images_close, ocam, rel_err
+import mask_model
+from gpu_common import assert_grads_close, assert_images_close, check_images, ocam, rel_err
 from paper_2408_05635_gb300 import gs, scenes
 
 pytestmark = pytest.mark.gpu
@@ -65,14 +66,13 @@ def test_tracking_frame_images_and_loss(tracking):
     prob = R.plan(gt, [t["cam"]], poses, margin=1.5)
     out = R.render(prob, gt, poses, targets=t["targets"])
     R.sync()
-    H, W = t["cam"].height, t["cam"].width
     ref = t["ref"]
-    amb = ref["amb"]
-    print(f"ambiguous pixels: {amb.mean():.4%}")
-    assert amb.mean() < 0.01
-    assert_images_close(out["rgb"].cpu().numpy().reshape(3, H, W), ref["rgb"], amb, what="rgb")
-    assert_images_close(out["depth"].cpu().numpy().reshape(H, W), ref["depth"], amb, what="depth")
-    assert_images_close(out["sil"].cpu().numpy().reshape(H, W), ref["sil"], amb, what="sil")
+    # the flagged share is what the mask's margins predict (closed forms, mask_model)
+    m = mask_model.mask_shares(t["sc"], t["cam"], t["start"], t["op"], ref)
+    print(f"tracking frame mask: {m}")
+    assert m["alpha_min"] <= m["alpha_min_bound"] and m["t_min"] <= m["t_min_bound"], m
+    check_images(out["rgb"].cpu().numpy(), out["depth"].cpu().numpy(), out["sil"].cpu().numpy(), ref, t["sc"],
+                 t["cam"], t["start"], t["op"], what="tracking frame")
     assert out["loss"].item() == pytest.approx(t["L"]["loss"], rel=2e-3)
 
 
@@ -166,17 +166,13 @@ def test_batched_sampled_views_images_and_loss(batched):
     for v in b["sample"]:
         oc, ref, L = b["refs"][v]
         H, W = oc.height, oc.width
-        amb = ref["amb"]
-        print(f"view {v} ({W}x{H}): ambiguous {amb.mean():.4%}")
-        # the mask follows the FP32 error of each decision (pose rounding, footprint
-        # exponent, compounded transmittance; gs_oracle.c)
-        assert amb.mean() < 0.05
-        rgb = out["rgb"][3 * off[v]:3 * off[v + 1]].cpu().numpy().reshape(3, H, W)
-        assert_images_close(rgb, ref["rgb"], amb, what=f"rgb view {v}")
-        assert_images_close(out["depth"][off[v]:off[v + 1]].cpu().numpy().reshape(H, W), ref["depth"], amb,
-                            what=f"depth view {v}")
-        assert_images_close(out["sil"][off[v]:off[v + 1]].cpu().numpy().reshape(H, W), ref["sil"], amb,
-                            what=f"sil view {v}")
+        # the flagged share is what the mask's margins predict (closed forms, mask_model)
+        m = mask_model.mask_shares(b["sc"], oc, b["poses0"][v], b["op"], ref)
+        print(f"view {v} ({W}x{H}) mask: {m}")
+        assert m["alpha_min"] <= m["alpha_min_bound"] and m["t_min"] <= m["t_min_bound"], m
+        check_images(out["rgb"][3 * off[v]:3 * off[v + 1]].cpu().numpy(), out["depth"][off[v]:off[v + 1]].cpu().numpy(),
+                     out["sil"][off[v]:off[v + 1]].cpu().numpy(), ref, b["sc"], oc, b["poses0"][v], b["op"],
+                     what=f"batched view {v}")
         assert out["loss"][v].item() == pytest.approx(L["loss"], rel=2e-3)
 
 
@@ -245,18 +241,17 @@ def test_mapping_keyframe_gradients():
     ref = oracle.render(sc, oc, pose, op)
     L = oracle.loss(oc, op, ref["rgb"], ref["depth"], ref["sil"], rgb, depth, prior)
     up_rgb, up_d, up_s, mask = _masked_upstream(ref, L)
-    print(f"mapping keyframe: ambiguous {mask.mean():.4%}")
-    assert mask.mean() < 0.05
+    m = mask_model.mask_shares(sc, cam, pose, op, ref)
+    print(f"mapping keyframe mask: {m}; with the loss mask's own decisions {mask.mean():.4%}")
+    assert m["alpha_min"] <= m["alpha_min_bound"] and m["t_min"] <= m["t_min_bound"], m
     ob = oracle.backward(sc, oc, pose, op, up_rgb, up_d, up_s)
     R = gs.Rasterizer(gs.Config())
     gt = gs.GaussianTensors.from_numpy(g)
     poses = torch.tensor(np.asarray(pose)[None], dtype=torch.float64, device="cuda")
     prob = R.plan(gt, [cam], poses, margin=1.25)
     out = R.render(prob, gt, poses)
-    H, W = cam.height, cam.width
-    assert_images_close(out["rgb"].cpu().numpy().reshape(3, H, W), ref["rgb"], ref["amb"], what="rgb")
-    assert_images_close(out["depth"].cpu().numpy().reshape(H, W), ref["depth"], ref["amb"], what="depth")
-    assert_images_close(out["sil"].cpu().numpy().reshape(H, W), ref["sil"], ref["amb"], what="sil")
+    check_images(out["rgb"].cpu().numpy(), out["depth"].cpu().numpy(), out["sil"].cpu().numpy(), ref, sc, cam, pose,
+                 op, what="mapping keyframe")
     ups = tuple(torch.tensor(a.reshape(-1).astype(np.float32), device="cuda") for a in (up_rgb, up_d, up_s))
     b = R.backward(gt, upstream=ups)
     R.sync()

@@ -9,7 +9,8 @@ import pytest
 import torch
 
 import oracle
-from gpu_common import (assert_grads_close, assert_images_close, gpu_render, ocam, params_pair, rel_err,
+import mask_model
+from gpu_common import (assert_grads_close, assert_images_close, check_images, gpu_render, ocam, params_pair, rel_err,
                         split_views)
 from paper_2408_05635_gb300 import gs, scenes
 
@@ -44,13 +45,11 @@ def test_forward_matches_oracle(case):
     gt = gs.GaussianTensors.from_numpy(g)
     pose = scenes.perturb_pose(scenes.identity_pose(), np.random.default_rng(5), 1.0, 0.02)
     out, prob, _, counts = gpu_render(R, gt, [cam], [pose])
-    ref = oracle.render(oracle.Scene(*g.arrays()), ocam(cam), pose, op)
-    amb = ref["amb"]
-    assert amb.mean() < 0.01
-    H, W = cam.height, cam.width
-    assert_images_close(out["rgb"].reshape(3, H, W), ref["rgb"], amb, what="rgb")
-    assert_images_close(out["depth"].reshape(H, W), ref["depth"], amb, what="depth")
-    assert_images_close(out["sil"].reshape(H, W), ref["sil"], amb, what="sil")
+    sc = oracle.Scene(*g.arrays())
+    ref = oracle.render(sc, ocam(cam), pose, op)
+    m = mask_model.mask_shares(sc, cam, pose, op, ref)
+    assert m["alpha_min"] <= m["alpha_min_bound"] and m["t_min"] <= m["t_min_bound"], m
+    check_images(out["rgb"], out["depth"], out["sil"], ref, sc, cam, pose, op, what=case)
     assert counts.n_pairs > 0 and counts.err_flags == 0
 
 
@@ -132,10 +131,11 @@ def test_multi_view_uneven_resolution():
     out, prob, _, _ = gpu_render(R, gt, cams, poses)
     rgbs = split_views(out["rgb"], cams, 3)
     deps = split_views(out["depth"], cams, 1)
+    sils = split_views(out["sil"], cams, 1)
+    sc = oracle.Scene(*g.arrays())
     for k, (cam, pose) in enumerate(zip(cams, poses)):
-        ref = oracle.render(oracle.Scene(*g.arrays()), ocam(cam), pose, op)
-        assert_images_close(rgbs[k], ref["rgb"], ref["amb"], what=f"rgb view {k}")
-        assert_images_close(deps[k][0], ref["depth"], ref["amb"], what=f"depth view {k}")
+        ref = oracle.render(sc, ocam(cam), pose, op)
+        check_images(rgbs[k], deps[k], sils[k], ref, sc, cam, pose, op, what=f"view {k}")
 
 
 def test_long_tile_list_uses_global_sort():

@@ -130,13 +130,14 @@ def test_autotune_times_every_setting_and_keeps_results(case, default_run):
     res = R.autotune(prob, gt, poses, tg, pose_only=False, reps=3)
     rows = res["timings_ms"]
     stages = [r["stage"] for r in rows]
-    assert stages == sorted(stages, key=("tile", "sub_buckets", "fwd_batch", "bwd_batch").index)
+    order = ("tile", "sub_buckets", "fwd_batch", "bwd_batch", "sort")  # no fused stage without pose_only
+    assert stages == sorted(stages, key=order.index)
     # the tile shapes first, the context's own (the default) leading
     assert [(r["schedule"]["tile_w"], r["schedule"]["tile_h"]) for r in rows[:4]] == [(16, 16), (32, 8), (16, 8), (8, 8)]
     assert rows[0]["schedule"] == DEFAULT
     assert all(r["ms"] > 0 for r in rows)
     assert R.schedule == res["schedule"]
-    for stage in ("tile", "sub_buckets", "fwd_batch", "bwd_batch"):
+    for stage in order:
         cand = [r for r in rows if r["stage"] == stage]
         assert cand, stage
         timed = [r for r in cand if r["ms"] > 0]
@@ -145,9 +146,9 @@ def test_autotune_times_every_setting_and_keeps_results(case, default_run):
         first = cand[0]
         won = min(timed, key=lambda r: r["ms"])
         pick = won if won["ms"] < 0.99 * first["ms"] else first
-        if stage == "bwd_batch":
+        if stage == order[-1]:
             assert pick["schedule"] == res["schedule"]
-        nxt = ("tile", "sub_buckets", "fwd_batch", "bwd_batch", None)
+        nxt = order + (None,)
         later = [r for r in rows if r["stage"] == nxt[nxt.index(stage) + 1]]
         if later:
             assert later[0]["schedule"] == pick["schedule"]
@@ -247,3 +248,89 @@ def test_tracker_tunes_on_the_first_frame_and_when_the_map_doubles():
     assert tr.tunes == 2
     tr.close()
     assert np.abs(p1 - p_plain).max() < 1e-4, np.abs(p1 - p_plain).max()
+
+
+def _sort_cases():
+    """Scenes for the two sorts: the parity cube; a map listed twice (every depth tied
+    with its copy, so the order of equal keys decides); a tile with 6,000 Gaussians (the
+    per-tile sort's global-memory path); three views of uneven resolution (tile ids past
+    eight bits, so the radix sort takes its second tile pass)."""
+    g, cam = scenes.cube_scene(n=3000, seed=12)
+    yield "cube", g, [cam], [scenes.perturb_pose(scenes.identity_pose(), np.random.default_rng(1), 1.0, 0.02)]
+    d = scenes.Gaussians(*(np.concatenate([a, a]) for a in g.arrays()))
+    yield "doubled", d, [cam], [scenes.identity_pose()]
+    rng = np.random.default_rng(2)
+    n = 6000
+    means = np.stack([rng.normal(0, 0.01, n), rng.normal(0, 0.01, n), rng.uniform(1.0, 3.0, n)], 1)
+    big = scenes.Gaussians(means.astype(np.float32), rng.normal(size=(n, 4)).astype(np.float32),
+                           rng.normal(-4.5, 0.2, (n, 3)).astype(np.float32),
+                           rng.normal(-3.0, 0.5, n).astype(np.float32), rng.uniform(size=(n, 3)).astype(np.float32))
+    yield "long tile", big, [scenes.Cam(60.0, 60.0, 23.5, 23.5, 48, 48)], [scenes.identity_pose()]
+    cams = [scenes.Cam(140.0, 140.0, 79.5, 59.5, 160, 120), scenes.Cam(70.0, 72.0, 39.5, 29.5, 80, 60),
+            scenes.Cam(300.0, 300.0, 250.0, 150.0, 500, 300)]
+    poses = [scenes.perturb_pose(scenes.identity_pose(), rng, 3.0, 0.05) for _ in cams]
+    yield "three views", g, cams, poses
+
+
+@pytest.mark.parametrize("case", list(_sort_cases()), ids=lambda c: c[0])
+def test_radix_sort_gives_the_per_tile_order(case):
+    """GS_SCHED_RADIX (one device-wide LSD radix sort of the (tile, depth) keys, ties put
+    in Gaussian order afterwards) against the per-tile sort: the same front-to-back order,
+    so bit-identical images, the same pair counts, and gradients equal to FP32 summation
+    order; images against the oracle on its unambiguous pixels."""
+    name, g, cams, poses = case
+    gcfg, op = params_pair()
+    runs = []
+    for flags in (0, gs.GS_SCHED_RADIX):
+        R = gs.Rasterizer(gcfg)
+        R.set_schedule(16, 16, 4, 256, 256, flags)
+        gt = gs.GaussianTensors.from_numpy(g)
+        pz = torch.tensor(np.asarray(poses, dtype=np.float64).reshape(-1, 7), device="cuda")
+        prob = R.plan(gt, cams, pz, margin=1.5)
+        out = R.render(prob, gt, pz)
+        P = sum(c.width * c.height for c in cams)
+        rng = np.random.default_rng(7)
+        ups = tuple(torch.tensor(rng.normal(size=k * P).astype(np.float32), device="cuda") for k in (3, 1, 1))
+        b = R.backward(gt, upstream=ups, n_views=len(cams))
+        counts = R.sync()
+        assert counts.err_flags == 0
+        runs.append(({k: v.cpu().numpy() for k, v in out.items()}, b, counts.n_pairs))
+        R.close()
+    (o0, b0, n0), (o1, b1, n1) = runs
+    assert n0 == n1 > 0
+    for k in ("rgb", "depth", "sil"):
+        np.testing.assert_array_equal(o1[k], o0[k], err_msg=f"{name}: {k}")
+    for gname in ("means", "quats", "log_scales", "logits", "rgb"):
+        ri, r2 = rel_err(b1["grads"][gname].cpu().numpy(), b0["grads"][gname].cpu().numpy())
+        assert ri < 1e-5 and r2 < 1e-5, (name, gname, ri, r2)
+    ri, r2 = rel_err(b1["pose_grad"].cpu().numpy(), b0["pose_grad"].cpu().numpy())
+    assert ri < 1e-5 and r2 < 1e-5, (name, "pose", ri, r2)
+    off = 0
+    for cam, pose in zip(cams, poses):
+        H, W = cam.height, cam.width
+        ref = oracle.render(oracle.Scene(*g.arrays()), ocam(cam), pose, op)
+        rgb = o1["rgb"][3 * off:3 * (off + H * W)].reshape(3, H, W)
+        assert_images_close(rgb, ref["rgb"], ref["amb"], what=f"{name} rgb")
+        assert_images_close(o1["depth"][off:off + H * W].reshape(H, W), ref["depth"], ref["amb"], what=f"{name} depth")
+        off += H * W
+
+
+def test_radix_sort_in_the_tracking_graph():
+    """gs_track_step with the radix sort, alone and with the fused compositor: the pose
+    after three iterations equals the per-tile sort's to rounding."""
+    g = scenes.room_scene(40_000, seed=4)
+    cam = scenes.Cam(262.5, 262.5, 159.5, 119.5, 320, 240)
+    truth = scenes.tracking_gt_pose()
+    start = scenes.perturb_pose(truth, np.random.default_rng(5), 1.0, 0.03)
+    rgb, depth = scenes.raycast_room(truth, cam, seed=4)
+    frame = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (rgb, depth)]
+    gt = gs.GaussianTensors.from_numpy(g)
+    s0 = torch.tensor(start, dtype=torch.float64, device="cuda")
+    tr = slam.Tracker(cam, 3)
+    out = []
+    for flags in (0, gs.GS_SCHED_RADIX, gs.GS_SCHED_RADIX | gs.GS_SCHED_FUSED):
+        tr.R.set_schedule(16, 16, 4, 256, 256, flags)
+        out.append(tr.track(gt, s0, *frame).cpu().numpy())
+    tr.close()
+    for k in (1, 2):
+        assert np.abs(out[0] - out[k]).max() < 1e-6, (k, np.abs(out[0] - out[k]).max())

@@ -16,7 +16,7 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PIN_SUITES = ("test_oracle.py", "test_oracle_mapping.py")
+PIN_SUITES = ("test_oracle.py", "test_oracle_mapping.py", "test_oracle_mask.py")
 
 # name: (file in oracle/, text, its replacement)
 MUTANTS = {
@@ -44,6 +44,17 @@ MUTANTS = {
     "pose Adam bias correction dropped": ("gs_oracle.c", "const double mh = *m / bc1, vh = *v / bc2;",
                                           "const double mh = *m, vh = *v / bc2;"),
     "pose rotation step direction": ("gs_oracle.c", "dq[1] = -step[0] * s;", "dq[1] = step[0] * s;"),
+    # the FP32-facing parts: the depth key and the ambiguity mask
+    "depth key from the wrong row": ("gs_oracle.c", "return fmaf(Rf[6], m0, fmaf(Rf[7], m1, fmaf(Rf[8], m2, tf[2])));",
+                                     "return fmaf(Rf[3], m0, fmaf(Rf[4], m1, fmaf(Rf[5], m2, tf[2])));"),
+    "depth key without translation": ("gs_oracle.c", "return fmaf(Rf[6], m0, fmaf(Rf[7], m1, fmaf(Rf[8], m2, tf[2])));",
+                                      "return fmaf(Rf[6], m0, fmaf(Rf[7], m1, Rf[8] * m2));"),
+    "alpha margin 100x too wide": ("gs_oracle.c", "return fmax(p->amb_alpha, e->dexp);",
+                                   "return fmax(100.0 * p->amb_alpha, e->dexp);"),
+    "t_min margin 30x too wide": ("gs_oracle.c", "return fabs(Tn - p->t_min) <= fmax(p->amb_t, eT) * p->t_min;",
+                                  "return fabs(Tn - p->t_min) <= 30.0 * fmax(p->amb_t, eT) * p->t_min;"),
+    "camera-transform error dropped from the margin": ("gs_oracle.c", "+ sqrt(gx * gx + gy * gy) * pr->dmu;",
+                                                       ";"),
     # map side (Sec. III-A, III-C) and metrics (Sec. IV)
     "unprojection rotation transposed": ("mapping.py", "means = (xc - t) @ R  #", "means = (xc - t) @ R.T  #"),
     "map Adam bias correction dropped": ("mapping.py", "m_hat = mk / (1.0 - beta1 ** step)", "m_hat = mk"),
@@ -71,7 +82,7 @@ def run_pins(work, mutant=None):
     in a fresh interpreter and return (failed, passed, pytest's output)."""
     _copy(os.path.join(ROOT, "oracle"), os.path.join(work, "oracle"),
           ("__init__.py", "gs_oracle.c", "mapping.py", "metrics.py"))
-    _copy(os.path.join(ROOT, "tests"), os.path.join(work, "tests"), ("conftest.py", "golden") + PIN_SUITES)
+    _copy(os.path.join(ROOT, "tests"), os.path.join(work, "tests"), ("conftest.py", "golden", "mask_model.py") + PIN_SUITES)
     _copy(os.path.join(ROOT, "paper_2408_05635_gb300"), os.path.join(work, "paper_2408_05635_gb300"),
           ("__init__.py", "scenes.py"))
     if mutant is not None:
