@@ -322,9 +322,11 @@ def run_isotropic(dev, stream, steps: int = 400):
 
 
 def run_batched(a, dev, stream, mhz: float = 2070.0):
-    """The batched / low-precision form beside the plain one, on the same views: all 512
-    hypotheses tracked in one call with BF16 attributes, against the same keyframes'
-    views tracked one call per view with FP32 attributes (one hypothesis per keyframe)."""
+    """The batched / low-precision form beside the plain one, on the same views, with the
+    two changes separated: all 512 hypotheses tracked in one call with BF16 attributes and
+    with FP32 attributes (each with its launch schedule tuned on the 512-view problem), and
+    the same keyframes' views tracked one call per view with FP32 attributes (one
+    hypothesis per keyframe), on the default schedule and tuned per resolution."""
     import torch
     from paper_2408_05635_gb300 import gs
     g, cams, poses0, frame_of, frames = batched_workload()
@@ -336,95 +338,121 @@ def run_batched(a, dev, stream, mhz: float = 2070.0):
     t_depth = torch.cat([torch.from_numpy(frames[f][1].reshape(-1)) for f in frame_of]).to(dev)
     t_prior = torch.cat([torch.from_numpy(frames[f][2].reshape(-1)) for f in frame_of]).to(dev)
     start = torch.tensor(np.asarray(poses0), dtype=torch.float64, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
     def track(R, gt, prob, ws, nb, poses, adam, loss, targets):
         gs.gs_track_step(R.ctx, prob, gt.c(), targets, poses, adam, loss, 1, ws, nb, stream)
 
-    # batched: one call over all views, BF16 attributes
-    R = gs.Rasterizer(gs.Config(), device=dev)
-    gtb = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=torch.bfloat16)
-    poses = start.clone()
-    sched = apply_schedule(a, R, cams, gtb, poses, (t_rgb, t_depth, t_prior))
-    prob = R.plan(gtb, cams, poses, margin=1.5)
-    ws, nb = R.workspace(prob)
-    tg = gs.gs_targets(t_rgb.data_ptr(), t_depth.data_ptr(), t_prior.data_ptr())
-    adam = torch.zeros(V, 16, dtype=torch.float64, device=dev)
-    loss = torch.zeros(1, V, dtype=torch.float64, device=dev)
-    for _ in range(3):
+    def batched(attr_dtype):
+        """One call over all views; returns the timings and the pose gradients at the start."""
+        R = gs.Rasterizer(gs.Config(), device=dev)
+        gtb = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=attr_dtype)
+        poses = start.clone()
+        sched = apply_schedule(a, R, cams, gtb, poses, (t_rgb, t_depth, t_prior))
+        prob = R.plan(gtb, cams, poses, margin=1.5)
+        ws, nb = R.workspace(prob)
+        tg = gs.gs_targets(t_rgb.data_ptr(), t_depth.data_ptr(), t_prior.data_ptr())
+        adam = torch.zeros(V, 16, dtype=torch.float64, device=dev)
+        loss = torch.zeros(1, V, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            track(R, gtb, prob, ws, nb, poses, adam, loss, tg)
+        gs.gs_set_profiling(R.ctx, True)
         track(R, gtb, prob, ws, nb, poses, adam, loss, tg)
-    gs.gs_set_profiling(R.ctx, True)
-    track(R, gtb, prob, ws, nb, poses, adam, loss, tg)
-    kms = dict(gs.gs_kernel_times(R.ctx))
-    kernels = {k: round(1e3 * ms, 1) for k, ms in kms.items()}
-    gs.gs_set_profiling(R.ctx, False)
-    _, cb = gs.gs_sync_status(R.ctx, stream)  # the work of that iteration, counted on the device
-    rl_kernels = kernel_rooflines(kms, N_BATCH_GAUSS, V, 22, int(cb.n_records), int(cb.n_pairs),
-                                  int(cb.fwd_contrib), int(cb.bwd_contrib), mhz)
-    poses.copy_(start)
-    adam.zero_()
-    torch.cuda.synchronize(dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    ev[0].record(stream)
-    for _ in range(a.batched_steps):
-        track(R, gtb, prob, ws, nb, poses, adam, loss, tg)
-    ev[1].record(stream)
-    torch.cuda.synchronize(dev)
-    st, c = gs.gs_sync_status(R.ctx, stream)
-    if st:
-        raise SystemExit(f"batched leg: device reported {gs._STATUS[st]}")
-    b_ms = ev[0].elapsed_time(ev[1]) / a.batched_steps
-    # the same start poses, pose gradient in BF16 (batched) for the accuracy comparison
-    poses.copy_(start)
-    out = R.render(prob, gtb, poses, targets=(t_rgb, t_depth, t_prior), stream=stream, images=False)
-    g_b = R.backward(gtb, params=False, pose=True, stream=stream, n_views=V)["pose_grad"].clone()
-    ws_bytes = nb
-    R.close()
-    del ws, R
+        kms = dict(gs.gs_kernel_times(R.ctx))
+        gs.gs_set_profiling(R.ctx, False)
+        _, cb = gs.gs_sync_status(R.ctx, stream)  # the work of that iteration, counted on the device
+        bytes_attr = 22 if attr_dtype == torch.bfloat16 else 44
+        rl = kernel_rooflines(kms, N_BATCH_GAUSS, V, bytes_attr, int(cb.n_records), int(cb.n_pairs),
+                              int(cb.fwd_contrib), int(cb.bwd_contrib), mhz)
+        poses.copy_(start)
+        adam.zero_()
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for _ in range(a.batched_steps):
+            track(R, gtb, prob, ws, nb, poses, adam, loss, tg)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        st, _ = gs.gs_sync_status(R.ctx, stream)
+        if st:
+            raise SystemExit(f"batched leg: device reported {gs._STATUS[st]}")
+        ms = ev[0].elapsed_time(ev[1]) / a.batched_steps
+        poses.copy_(start)
+        R.render(prob, gtb, poses, targets=(t_rgb, t_depth, t_prior), stream=stream, images=False)
+        grad = R.backward(gtb, params=False, pose=True, stream=stream, n_views=V)["pose_grad"].clone()
+        res = {"ms_per_step": ms, "view_iters_per_s": V / (ms / 1e3), "mpix_per_s": P / ms / 1e3,
+               "launch": "one gs_track_step call (one CUDA graph) for all views",
+               "kernels_us": {k: round(1e3 * v, 1) for k, v in kms.items()}, "roofline_kernels": rl,
+               "launch_schedule": sched, "pairs": int(cb.n_pairs), "workspace_gb": round(nb / 1e9, 2)}
+        R.close()
+        del ws
+        return res, grad
+
+    b16, g_b16 = batched(torch.bfloat16)
+    b32, g_b32 = batched(torch.float32)
 
     # plain: one hypothesis per keyframe, one call per view, FP32 attributes
     gtf = gs.GaussianTensors.from_numpy(g, device=dev, attr_dtype=torch.float32)
-    Rp = gs.Rasterizer(gs.Config(), device=dev)
-    Rp_sched = Rp.schedule  # the default: the plain form is the untuned baseline
     sub = [int(np.flatnonzero(frame_of == f)[0]) for f in range(BATCH_FRAMES)]
     off = np.concatenate([[0], np.cumsum(pix)])
-    plain_ms, rel = 0.0, []
-    reps = 10
-    for v in sub:
-        pv = start[v:v + 1].clone()
-        pr = Rp.plan(gtf, [cams[v]], pv, margin=1.5)
-        wsv, nbv = Rp.workspace(pr)
-        tr = (t_rgb[3 * off[v]:3 * off[v + 1]], t_depth[off[v]:off[v + 1]], t_prior[off[v]:off[v + 1]])
-        tgv = gs.gs_targets(tr[0].data_ptr(), tr[1].data_ptr(), tr[2].data_ptr())
-        av = torch.zeros(1, 16, dtype=torch.float64, device=dev)
-        lv = torch.zeros(1, 1, dtype=torch.float64, device=dev)
-        track(Rp, gtf, pr, wsv, nbv, pv, av, lv, tgv)  # captures this view's graph
-        torch.cuda.synchronize(dev)
-        ev[0].record(stream)
-        for _ in range(reps):
-            track(Rp, gtf, pr, wsv, nbv, pv, av, lv, tgv)
-        ev[1].record(stream)
-        torch.cuda.synchronize(dev)
-        plain_ms += ev[0].elapsed_time(ev[1]) / reps
-        pv.copy_(start[v:v + 1])
-        Rp.render(pr, gtf, pv, targets=tr, stream=stream, images=False)
-        g_f = Rp.backward(gtf, params=False, pose=True, stream=stream)["pose_grad"][0]
-        rel.append(float((g_b[v] - g_f).norm() / g_f.norm().clamp_min(1e-30)))
-    Rp.close()
     sub_pix = sum(pix[v] for v in sub)
-    plain_view_its = len(sub) / (plain_ms / 1e3)
-    batched_view_its = V / (b_ms / 1e3)
+
+    def plain(tuned):
+        Rs, scheds = {}, {}
+        total_ms, grads = 0.0, {}
+        reps = 10
+        for v in sub:
+            res_key = (cams[v].width, cams[v].height)
+            tr = (t_rgb[3 * off[v]:3 * off[v + 1]], t_depth[off[v]:off[v + 1]], t_prior[off[v]:off[v + 1]])
+            if res_key not in Rs:  # one context per resolution, tuned on its first view
+                Rs[res_key] = gs.Rasterizer(gs.Config(), device=dev)
+                if tuned and a.autotune_reps > 0:
+                    pv = start[v:v + 1].clone()
+                    tp = Rs[res_key].plan(gtf, [cams[v]], pv, margin=3.0)
+                    Rs[res_key].autotune(tp, gtf, pv, tr, pose_only=True, reps=a.autotune_reps)
+                scheds[f"{res_key[0]}x{res_key[1]}"] = Rs[res_key].schedule
+            Rp = Rs[res_key]
+            pv = start[v:v + 1].clone()
+            pr = Rp.plan(gtf, [cams[v]], pv, margin=1.5)
+            wsv, nbv = Rp.workspace(pr)
+            tgv = gs.gs_targets(tr[0].data_ptr(), tr[1].data_ptr(), tr[2].data_ptr())
+            av = torch.zeros(1, 16, dtype=torch.float64, device=dev)
+            lv = torch.zeros(1, 1, dtype=torch.float64, device=dev)
+            track(Rp, gtf, pr, wsv, nbv, pv, av, lv, tgv)  # captures this view's graph
+            torch.cuda.synchronize(dev)
+            ev[0].record(stream)
+            for _ in range(reps):
+                track(Rp, gtf, pr, wsv, nbv, pv, av, lv, tgv)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            total_ms += ev[0].elapsed_time(ev[1]) / reps
+            pv.copy_(start[v:v + 1])
+            Rp.render(pr, gtf, pv, targets=tr, stream=stream, images=False)
+            grads[v] = Rp.backward(gtf, params=False, pose=True, stream=stream)["pose_grad"][0].clone()
+        for Rp in Rs.values():
+            Rp.close()
+        return {"views_timed": len(sub), "ms_per_view_iter": total_ms / len(sub),
+                "view_iters_per_s": len(sub) / (total_ms / 1e3), "mpix_per_s": sub_pix / total_ms / 1e3,
+                "launch": "one gs_track_step call per view", "launch_schedule": scheds}, grads
+
+    p_def, g_f = plain(False)
+    p_tuned, _ = plain(True)
+
+    def rel(gb):
+        r = [float((gb[v] - g_f[v]).norm() / g_f[v].norm().clamp_min(1e-30)) for v in sub]
+        return {"max": max(r), "median": float(np.median(r))}
+
     return {
         "workload": f"{BATCH_FRAMES} keyframes x {BATCH_HYP} pose hypotheses (uneven 320x240 / 640x480 / "
                     f"1200x680), {N_BATCH_GAUSS // 1000}k room Gaussians",
-        "views": V, "pixels_per_step": P, "workspace_gb": round(ws_bytes / 1e9, 2),
-        "batched_bf16": {"ms_per_step": b_ms, "view_iters_per_s": batched_view_its, "mpix_per_s": P / b_ms / 1e3,
-                         "launch": "one gs_track_step call (one CUDA graph) for all views", "kernels_us": kernels,
-                         "roofline_kernels": rl_kernels, "launch_schedule": sched},
-        "plain_fp32": {"views_timed": len(sub), "ms_per_view_iter": plain_ms / len(sub),
-                       "view_iters_per_s": plain_view_its, "mpix_per_s": sub_pix / plain_ms / 1e3,
-                       "launch": "one gs_track_step call per view", "launch_schedule": Rp_sched},
-        "speedup_view_iters": batched_view_its / plain_view_its,
-        "pose_grad_rel_diff_bf16_vs_fp32": {"max": max(rel), "median": float(np.median(rel))},
+        "views": V, "pixels_per_step": P,
+        "batched_bf16": b16, "batched_fp32": b32,
+        "plain_fp32": p_def, "plain_fp32_tuned": p_tuned,
+        "speedup_batching": b32["view_iters_per_s"] / p_tuned["view_iters_per_s"],
+        "speedup_bf16_attributes": b16["view_iters_per_s"] / b32["view_iters_per_s"],
+        "speedup_view_iters": b16["view_iters_per_s"] / p_def["view_iters_per_s"],
+        "speedup_vs_tuned_plain": b16["view_iters_per_s"] / p_tuned["view_iters_per_s"],
+        "pose_grad_rel_diff_bf16_vs_fp32": rel(g_b16),
+        "pose_grad_rel_diff_batched_fp32_vs_plain_fp32": rel(g_b32),
         "l2": "working set far above L2 (no flush)",
     }
 
@@ -601,7 +629,7 @@ def _view_accuracy(dev, stream, g_np, g_oracle, cam, pose, targets, attr_dtype, 
 
 def sequence_drift(dev, stream, frames_n: int = 10, iters: int = 100):
     """Pose drift of the GPU tracker against the oracle's own tracking loop: the first
-    `frames_n` frames of the long sequence's spline path at 160 x 120, a 200k-Gaussian room
+    `frames_n` frames of the long sequence's 200-frame spline path at 160 x 120, a 200k-Gaussian room
     with FP16 attributes (the oracle on their FP32 values), `iters` decoupled Adam
     iterations per frame, each frame started from that side's previous estimate."""
     import torch
@@ -609,7 +637,7 @@ def sequence_drift(dev, stream, frames_n: int = 10, iters: int = 100):
     from paper_2408_05635_gb300 import gs, scenes, slam
     g = scenes.room_scene(200_000, seed=3)
     cam = scenes.Cam(131.25, 131.25, 79.5, 59.5, 160, 120)
-    poses = scenes.spline_trajectory(frames_n + 1, seed=0)
+    poses = scenes.spline_trajectory(200, seed=0)[:frames_n + 1]  # the 200-frame path's first frames
     gq = scenes.Gaussians(g.means, *(torch.tensor(a).to(torch.float16).float().numpy() for a in
                                      (g.quats, g.log_scales, g.logits, g.rgb)))
     rng = np.random.default_rng(11)
@@ -647,13 +675,15 @@ def sequence_drift(dev, stream, frames_n: int = 10, iters: int = 100):
     for a_, b_ in zip(est_gpu[1:], est_o[1:]):
         Ra, Rb = scenes.pose_rt(a_)[0], scenes.pose_rt(b_)[0]
         ang.append(float(np.degrees(np.arccos(np.clip((np.trace(Ra @ Rb.T) - 1) / 2, -1, 1)))))
-    truth = _trajectory_report(np.array(est_o), np.array(poses))
+    truth_o = _trajectory_report(np.array(est_o), np.array(poses))
+    truth_g = _trajectory_report(np.array(est_gpu), np.array(poses))
     return {"workload": f"first {frames_n} frames of the spline path at 160x120, 200k room Gaussians (fp16), "
                         f"{iters} iterations per frame; the oracle on the same FP16-rounded attributes",
             "frames": frames_n, "trans_diff_mm_per_frame": [round(1e3 * float(x), 4) for x in dt],
             "rot_diff_deg_per_frame": [round(x, 5) for x in ang],
             "max_trans_diff_mm": round(1e3 * float(dt.max()), 4), "max_rot_diff_deg": round(max(ang), 5),
-            "oracle_ate_vs_truth_cm": truth["ate_rmse_cm"], "oracle_seconds": round(el, 1)}
+            "ate_vs_truth_cm": {"oracle": truth_o["ate_rmse_cm"], "gpu": truth_g["ate_rmse_cm"]},
+            "oracle_seconds": round(el, 1)}
 
 
 def accuracy_vs_oracle(dev, stream) -> dict:

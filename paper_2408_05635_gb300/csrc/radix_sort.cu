@@ -5,7 +5,7 @@
 // k_emit (in this mode) writes each pair as the 64-bit key tile << 32 | bits(depth) (the
 // depth is positive, so its IEEE bits order as unsigned integers) with the record as the
 // value.  Eight-bit digits are sorted least significant first, each pass stable:
-//   k_radix_hist     per block of kRxTile keys, the count of each digit value;
+//   k_radix_hist     per block of 1,024 or 4,096 keys, the count of each digit value;
 //   k_radix_scan     per digit value, the exclusive prefix of its counts over the blocks
 //                    and its total;
 //   k_radix_scatter  per block, every key's destination: the keys of smaller digit values
@@ -26,9 +26,10 @@ namespace gsk {
 namespace {
 
 constexpr int kRxThreads = 256;
-constexpr int kRxItems = 16;
-constexpr int kRxTile = kRxThreads * kRxItems;
 constexpr int kRxDigits = 256;
+// Keys per thread per pass: 4 while that leaves at most kRxSmallBlocks blocks (small
+// problems then still spread over the GPU), 16 above.
+constexpr int kRxSmallBlocks = 4096;
 
 __device__ __forceinline__ uint32_t pair_count(const DevHeader *hdr, uint32_t cap) {
     const unsigned long long n = hdr->n_pairs;
@@ -58,6 +59,7 @@ __device__ __forceinline__ uint32_t block_scan256(uint32_t x, uint32_t *warp_sum
     return before + incl - x;
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kRxThreads) k_radix_hist(const unsigned long long *keys, const DevHeader *hdr,
                                                            uint32_t cap, int shift, uint32_t *hist, uint32_t nblk) {
     __shared__ uint32_t h[kRxDigits];
@@ -65,9 +67,9 @@ __global__ void __launch_bounds__(kRxThreads) k_radix_hist(const unsigned long l
     const uint32_t n = pair_count(hdr, cap);
     h[tid] = 0u;
     __syncthreads();
-    const uint32_t base = blockIdx.x * (uint32_t)kRxTile;
+    const uint32_t base = blockIdx.x * (uint32_t)(kRxThreads * ITEMS);
 #pragma unroll 4
-    for (int r = 0; r < kRxItems; ++r) {
+    for (int r = 0; r < ITEMS; ++r) {
         const uint32_t i = base + (uint32_t)(r * kRxThreads + tid);
         if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 0xffu], 1u);
     }
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(kRxThreads) k_radix_scan(uint32_t *hist, uint3
     if (threadIdx.x == 0) total_out[blockIdx.x] = run;
 }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kRxThreads) k_radix_scatter(const unsigned long long *src_k, const uint32_t *src_v,
                                                               unsigned long long *dst_k, uint32_t *dst_v,
                                                               const DevHeader *hdr, uint32_t cap, int shift,
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(kRxThreads) k_radix_scatter(const unsigned lon
     __shared__ uint32_t s_cnt[kRxThreads / 32][kRxDigits];  // per-warp counts of the current round
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n = pair_count(hdr, cap);
-    const uint32_t base = blockIdx.x * (uint32_t)kRxTile;
+    const uint32_t base = blockIdx.x * (uint32_t)(kRxThreads * ITEMS);
     if (base >= n) return;  // block-uniform
     {
         uint32_t all;
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(kRxThreads) k_radix_scatter(const unsigned lon
         s_base[tid] = before + hist[(size_t)tid * nblk + blockIdx.x];
     }
     const unsigned int lt = (1u << lane) - 1u;
-    for (int r = 0; r < kRxItems; ++r) {
+    for (int r = 0; r < ITEMS; ++r) {
         if (base + (uint32_t)(r * kRxThreads) >= n) break;  // block-uniform
 #pragma unroll
         for (int w = 0; w < kRxThreads / 32; ++w) s_cnt[w][tid] = 0u;
@@ -169,7 +172,14 @@ __global__ void __launch_bounds__(kRxThreads) k_radix_ties(const unsigned long l
 
 }  // namespace
 
-uint32_t radix_blocks(uint32_t pair_cap) { return (pair_cap + kRxTile - 1) / kRxTile; }
+int radix_items(uint32_t pair_cap) {
+    return (pair_cap + 4u * kRxThreads - 1) / (4u * kRxThreads) <= (uint32_t)kRxSmallBlocks ? 4 : 16;
+}
+
+uint32_t radix_blocks(uint32_t pair_cap) {
+    const uint32_t tile = (uint32_t)(kRxThreads * radix_items(pair_cap));
+    return (pair_cap + tile - 1) / tile;
+}
 
 int radix_passes(uint32_t tiles) {
     int tile_bits = 0;
@@ -181,15 +191,21 @@ cudaError_t launch_radix_sort(const RadixLaunch &L, cudaStream_t st) {
     const uint32_t nblk = radix_blocks(L.d.pair_cap);
     if (nblk == 0) return cudaSuccess;
     const int passes = radix_passes(L.d.T);
+    const bool small = radix_items(L.d.pair_cap) == 4;
     unsigned long long *k[2] = {L.ws.keys, L.ws.rkeys};
     uint32_t *v[2] = {L.ws.sorted, L.ws.rvals};
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         const int s = p & 1, t = s ^ 1;
-        k_radix_hist<<<nblk, kRxThreads, 0, st>>>(k[s], L.ws.hdr, L.d.pair_cap, shift, L.ws.rhist, nblk);
+        if (small) k_radix_hist<4><<<nblk, kRxThreads, 0, st>>>(k[s], L.ws.hdr, L.d.pair_cap, shift, L.ws.rhist, nblk);
+        else k_radix_hist<16><<<nblk, kRxThreads, 0, st>>>(k[s], L.ws.hdr, L.d.pair_cap, shift, L.ws.rhist, nblk);
         k_radix_scan<<<kRxDigits, kRxThreads, 0, st>>>(L.ws.rhist, nblk, L.ws.rtotal);
-        k_radix_scatter<<<nblk, kRxThreads, 0, st>>>(k[s], v[s], k[t], v[t], L.ws.hdr, L.d.pair_cap, shift, L.ws.rhist,
-                                                    L.ws.rtotal, nblk);
+        if (small)
+            k_radix_scatter<4><<<nblk, kRxThreads, 0, st>>>(k[s], v[s], k[t], v[t], L.ws.hdr, L.d.pair_cap, shift,
+                                                            L.ws.rhist, L.ws.rtotal, nblk);
+        else
+            k_radix_scatter<16><<<nblk, kRxThreads, 0, st>>>(k[s], v[s], k[t], v[t], L.ws.hdr, L.d.pair_cap, shift,
+                                                             L.ws.rhist, L.ws.rtotal, nblk);
     }
     const int f = passes & 1;
     k_radix_ties<<<(L.d.pair_cap + kRxThreads - 1) / kRxThreads, kRxThreads, 0, st>>>(k[f], v[f], L.ws.sorted,

@@ -61,8 +61,8 @@ __device__ __forceinline__ int build_list(const float4 *sBox, uint8_t *list, int
 
 }  // namespace
 
-constexpr int kFusedScratch = (kSortSmemKeys * 8 > kBatch * kAccStride * 4) ? kSortSmemKeys * 8
-                                                                           : kBatch * kAccStride * 4;
+constexpr int kFusedScratch = (2 * kSortSmemKeys * 8 > kBatch * kAccStride * 4) ? 2 * kSortSmemKeys * 8
+                                                                               : kBatch * kAccStride * 4;
 
 template <int NB, int LW>
 __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
     __shared__ float4 sP0[NB], sC[NB], sQ[NB], sBox[NB];
     __shared__ float2 sP1[NB];
     __shared__ uint8_t sList[kTilePix / 32][NB];
-    // the sort's keys, then (reverse walk) the per-batch accumulators
+    // the sort's two key buffers, then (reverse walk) the per-batch accumulators
     __shared__ __align__(16) unsigned char sScratch[kFusedScratch];
     unsigned long long *sKeys = reinterpret_cast<unsigned long long *>(sScratch);
     float *sAcc = reinterpret_cast<float *>(sScratch);

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     __shared__ float4 sP0[NB], sC[NB], sBox[NB];
     __shared__ float2 sP1[NB];
     __shared__ uint8_t sList[kTilePix / 32][NB];
-    __shared__ unsigned long long sKeys[kSortSmemKeys];
+    __shared__ unsigned long long sKeys[2 * kSortSmemKeys];  // the sort's two buffers
     __shared__ int s_view;
     __shared__ float s_loss[kTilePix / 32];
     const uint32_t tile = L.ws.tile_order[blockIdx.x];
