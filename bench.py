@@ -834,7 +834,8 @@ def hbm_peak_gbs() -> tuple[float, str]:
 
 
 def kernel_rooflines(kern_ms: dict, n_gauss: int, views: int, attr_bytes: int, records: int, pairs: int,
-                     fwd_contrib: int, bwd_contrib: int, mhz: float, n_sm: int | None = None) -> dict:
+                     fwd_contrib: int, bwd_contrib: int, mhz: float, n_sm: int | None = None,
+                     radix_passes: int = 6) -> dict:
     """Every kernel of a tracking iteration against the roofline that bounds it: its
     algorithmic bytes or FLOPs per launch (from the work counted on the device) over its
     CUDA-event time (markers around every kernel, so each time includes its launch gap),
@@ -851,6 +852,10 @@ def kernel_rooflines(kern_ms: dict, n_gauss: int, views: int, attr_bytes: int, r
         "k_emit": ("hbm", 12 * pairs, "12 B per (Gaussian, tile) pair"),
         "k_forward": ("alu", FLOP_FWD_PAIR * fwd_contrib, f"{FLOP_FWD_PAIR} FLOP per contributing pair"),
         "k_backward": ("alu", FLOP_BWD_PAIR * bwd_contrib, f"{FLOP_BWD_PAIR} FLOP per differentiated pair"),
+        "k_track_tile": ("alu", FLOP_FWD_PAIR * fwd_contrib + FLOP_BWD_PAIR * bwd_contrib,
+                         f"{FLOP_FWD_PAIR} FLOP per contributing and {FLOP_BWD_PAIR} per differentiated pair"),
+        "k_radix_sort": ("hbm", 24 * radix_passes * pairs,
+                         f"{radix_passes} passes x 24 B per (Gaussian, tile) pair (key and value read and written)"),
         "k_bproject": ("alu", FLOP_BPROJ_REC * records, f"about {FLOP_BPROJ_REC} FLOP per record"),
     }
     out = {}

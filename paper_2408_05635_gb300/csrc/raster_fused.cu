@@ -121,7 +121,49 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
         if (__any_sync(0xffffffffu, !done)) {
             const int nl = build_list(sBox, sList[warp], cnt, lane, pu_lo, pu_hi, pv_lo, pv_hi);
             if (!done) {
-                for (int e = 0; e < nl; ++e) {
+                // two list entries per step: both footprints are evaluated before the
+                // pixel state is updated with the front one, then the back one (alpha 0
+                // for an entry that misses the pixel, which leaves every sum and T as they
+                // are), so the two evaluations overlap
+                int e = 0;
+                for (; e + 1 < nl; e += 2) {
+                    const int jA = sList[warp][e], jB = sList[warp][e + 1];
+                    const float pA = eval_poly(fu, fv, sP0[jA], sP1[jA]).poly;
+                    const float pB = eval_poly(fu, fv, sP0[jB], sP1[jB]).poly;
+                    const float4 CA = sC[jA], CB = sC[jB];
+                    const bool cA = pA >= thr, cB = pB >= thr;
+                    const float aA = cA ? fminf(S.alpha_max, ex2_approx(pA)) : 0.f;
+                    const float aB = cB ? fminf(S.alpha_max, ex2_approx(pB)) : 0.f;
+                    ++n_eval;
+                    float Tn = T * (1.f - aA);
+                    if (cA && Tn < S.t_min) {
+                        done = true;
+                        break;
+                    }
+                    float w = aA * T;
+                    cr += CA.x * w;
+                    cg += CA.y * w;
+                    cb += CA.z * w;
+                    D += CA.w * w;
+                    T = Tn;
+                    if (cA) last = b0 + (uint32_t)jA + 1u;
+                    ++n_eval;
+                    n_contrib += cA;
+                    Tn = T * (1.f - aB);
+                    if (cB && Tn < S.t_min) {
+                        done = true;
+                        break;
+                    }
+                    w = aB * T;
+                    cr += CB.x * w;
+                    cg += CB.y * w;
+                    cb += CB.z * w;
+                    D += CB.w * w;
+                    T = Tn;
+                    if (cB) last = b0 + (uint32_t)jB + 1u;
+                    n_contrib += cB;
+                }
+                for (; !done && e < nl; ++e) {
                     const int j = sList[warp][e];
                     const float poly = eval_poly(fu, fv, sP0[j], sP1[j]).poly;
                     ++n_eval;
