@@ -58,6 +58,8 @@ def _args():
                     help="timed windows of the mapping leg (0 skips it)")
     ap.add_argument("--sequence-frames", type=int, default=200,
                     help="frames of the long-sequence leg (0 skips it)")
+    ap.add_argument("--isotropic-steps", type=int, default=400,
+                    help="timed steps of the isotropic-versus-anisotropic leg (0 skips it)")
     ap.add_argument("--autotune-reps", type=int, default=10,
                     help="passes per setting of the launch-schedule autotuner before the tracking and batched "
                          "legs (0: the default schedule)")
@@ -1069,8 +1071,8 @@ def main():
                                                  contrib["fwd_contrib"] // a.steps, contrib["bwd_contrib"] // a.steps,
                                                  mhz),
         }
-        if world == 1:
-            line["isotropic"] = run_isotropic(dev, stream)
+        if world == 1 and a.isotropic_steps > 0:
+            line["isotropic"] = run_isotropic(dev, stream, a.isotropic_steps)
         if world == 1 and a.batched_steps > 0:
             line["batched"] = run_batched(a, dev, stream, mhz)
         if world == 1 and a.mapping_steps > 0:
