@@ -1,0 +1,105 @@
+// fwd_walk.cuh -- one pixel's front-to-back walk of Eqs. 2-4 over a warp's list of staged
+// Gaussians, shared by k_forward and the fused tracking kernel.
+#pragma once
+
+#include "gs_internal.cuh"
+
+namespace gsk {
+
+// The walk's pixel state: transmittance, colour and depth sums, the last contributor's
+// list position + 1, and whether the walk has stopped on t_min.
+struct FwdPixel {
+    float T, cr, cg, cb, D;
+    uint32_t last;
+    bool done;
+};
+
+// Walk `px` over list entries [0, nl) of the batch that starts at list position b0.
+// Two entries per step: both footprints are evaluated before the state takes the front
+// one, then the back one, so the two evaluations overlap.  An entry that misses the pixel
+// has alpha 0, which leaves every sum and T exactly as they are, and T >= t_min holds
+// before every step, so the transmittance after both entries falls below t_min only when
+// one of them stops the walk: one comparison per step, and the rare stop is resolved
+// after it (the front entry if it alone reaches t_min, else the back one).  n_eval counts
+// the entries evaluated before the stop (inclusive), n_contrib the contributions.
+__device__ __forceinline__ void fwd_walk_batch(FwdPixel &px, const uint8_t *list, int nl, uint32_t b0,
+                                               const float4 *sP0, const float2 *sP1, const float4 *sC, float fu,
+                                               float fv, float thr, float amax, float tmin, uint32_t &n_eval,
+                                               uint32_t &n_contrib) {
+    float T = px.T, cr = px.cr, cg = px.cg, cb = px.cb, D = px.D;
+    int lastj = -1;  // batch position of the last contributor in this batch
+    int e = 0;
+    uint32_t contrib = 0;
+    for (; e + 1 < nl; e += 2) {
+        const int jA = list[e], jB = list[e + 1];
+        const float pA = eval_poly(fu, fv, sP0[jA], sP1[jA]).poly;
+        const float pB = eval_poly(fu, fv, sP0[jB], sP1[jB]).poly;
+        const float4 CA = sC[jA], CB = sC[jB];
+        const bool cA = pA >= thr, cB = pB >= thr;
+        const float aA = cA ? fminf(amax, ex2_approx(pA)) : 0.f;
+        const float aB = cB ? fminf(amax, ex2_approx(pB)) : 0.f;
+        const float TA = T * (1.f - aA), TB = TA * (1.f - aB);
+        if (TB < tmin) {
+            px.done = true;
+            if (TA < tmin) {  // the front entry stops the walk
+                e += 1;
+                break;
+            }
+            const float w = aA * T;  // the front entry (if it hits) contributes, the back one stops
+            cr += CA.x * w;
+            cg += CA.y * w;
+            cb += CA.z * w;
+            D += CA.w * w;
+            T = TA;
+            lastj = cA ? jA : lastj;
+            contrib += (uint32_t)cA;
+            e += 2;
+            break;
+        }
+        const float w = aA * T;
+        cr += CA.x * w;
+        cg += CA.y * w;
+        cb += CA.z * w;
+        D += CA.w * w;
+        const float v = aB * TA;
+        cr += CB.x * v;
+        cg += CB.y * v;
+        cb += CB.z * v;
+        D += CB.w * v;
+        T = TB;
+        lastj = cB ? jB : (cA ? jA : lastj);
+        contrib += (uint32_t)cA + (uint32_t)cB;
+    }
+    if (!px.done && e < nl) {  // an odd last entry
+        const int j = list[e];
+        const float poly = eval_poly(fu, fv, sP0[j], sP1[j]).poly;
+        ++e;
+        if (poly >= thr) {
+            const float alpha = fminf(amax, ex2_approx(poly));
+            const float Tn = T * (1.f - alpha);
+            if (Tn < tmin) {
+                px.done = true;
+            } else {
+                const float w = alpha * T;
+                const float4 Cc = sC[j];
+                cr += Cc.x * w;
+                cg += Cc.y * w;
+                cb += Cc.z * w;
+                D += Cc.w * w;
+                T = Tn;
+                lastj = j;
+                ++contrib;
+            }
+        }
+    }
+    n_eval += (uint32_t)e;
+    n_contrib += contrib;
+    if (lastj >= 0) px.last = b0 + (uint32_t)lastj + 1u;
+    px.T = T;
+    px.cr = cr;
+    px.cg = cg;
+    px.cb = cb;
+    px.D = D;
+}
+
+}  // namespace gsk

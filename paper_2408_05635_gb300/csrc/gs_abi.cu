@@ -103,6 +103,12 @@ struct gs_ctx {
     std::vector<const char *> names;
     size_t n_marks = 0;
     std::vector<const char *> graph_names;  // markers baked into the tracking graph
+    // markers inside a captured graph sit on a side branch (mark_stream, forked from the
+    // launch stream at each marker and joined at the end of the capture), so no kernel of
+    // the main chain waits for an event node
+    cudaStream_t mark_stream = nullptr;
+    cudaEvent_t fork_ev = nullptr;
+    bool side_open = false;
 };
 
 namespace {
@@ -139,9 +145,27 @@ cudaError_t record_mark(gs_ctx *ctx, cudaStream_t st, const char *name) {
     ctx->names[k] = name;
     ctx->adjacent = true;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    cudaStreamIsCapturing(st, &cap);
-    return cap != cudaStreamCaptureStatusNone ? cudaEventRecordWithFlags(ctx->events[k], st, cudaEventRecordExternal)
-                                              : cudaEventRecord(ctx->events[k], st);
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return e;
+    if (cap == cudaStreamCaptureStatusNone) return cudaEventRecord(ctx->events[k], st);
+    // captured: an event-record node on the side branch, after everything enqueued so far
+    if (!ctx->mark_stream) {
+        if ((e = cudaStreamCreateWithFlags(&ctx->mark_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    if ((e = cudaEventRecord(ctx->fork_ev, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ctx->mark_stream, ctx->fork_ev, 0)) != cudaSuccess) return e;
+    ctx->side_open = true;
+    return cudaEventRecordWithFlags(ctx->events[k], ctx->mark_stream, cudaEventRecordExternal);
+}
+
+// Join the markers' side branch back into the captured stream `st` (a capture must end
+// with every forked stream joined); a no-op when no marker was captured.
+cudaError_t join_marks(gs_ctx *ctx, cudaStream_t st) {
+    if (!ctx->side_open) return cudaSuccess;
+    ctx->side_open = false;
+    cudaError_t e = cudaEventRecord(ctx->fork_ev, ctx->mark_stream);
+    return e != cudaSuccess ? e : cudaStreamWaitEvent(st, ctx->fork_ev, 0);
 }
 
 // Profiling marker before the launch of kernel `name` (only when it is selected and the
@@ -521,6 +545,8 @@ gs_status gs_destroy(gs_ctx *ctx) {
     if (!ctx) return GS_OK;
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->mark_stream) cudaStreamDestroy(ctx->mark_stream);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     for (cudaEvent_t ev : ctx->events) cudaEventDestroy(ev);
     delete ctx;
     return GS_OK;
@@ -704,7 +730,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
             if ((r = launch_finalize(F, q)) != cudaSuccess) return r;
             if ((r = mark(ctx, q, "k_finalize")) != cudaSuccess) return r;
         }
-        return cudaSuccess;
+        return join_marks(ctx, q);
     };
 
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -747,6 +773,7 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
             cudaGraph_t graph = nullptr;
             e = cudaStreamEndCapture(ctx->cap_stream, &graph);
             if (e_enq != cudaSuccess) {
+                ctx->side_open = false;
                 if (graph) cudaGraphDestroy(graph);
                 return cuda_fail(ctx, e_enq, "tracking capture");
             }

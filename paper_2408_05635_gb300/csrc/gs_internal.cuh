@@ -445,6 +445,55 @@ __device__ __forceinline__ PolyEval eval_poly(float u, float v, float4 p0, float
     return e;
 }
 
+// Can a pixel position of the rectangle [u_lo, u_hi] x [v_lo, v_hi] (tile-local) reach
+// poly >= thr, i.e. alpha >= alpha_min?  poly = lo + kuu dx^2 + kuv dx dy + kvv dy^2 has
+// a concave quadratic part (kuu, kvv < 0: the conic is positive definite), whose maximum
+// over the rectangle is 0 with the mean inside and otherwise lies on the boundary: on each
+// edge, the maximiser of a concave quadratic in one variable, clamped to the edge.  The
+// comparison keeps a margin of 2^-16 of the terms' magnitude over the rectangle (FP32
+// rounding of this maximum, and of eval_poly at any pixel of it, is a few ulp of that), so
+// no entry with a pixel at alpha >= alpha_min is dropped; degenerate footprints pass.
+__device__ __forceinline__ bool footprint_meets_rect(float4 p0, float2 p1, float thr, float u_lo, float u_hi,
+                                                     float v_lo, float v_hi) {
+    const float kuu = p0.w, kuv = p1.x, kvv = p1.y;
+    if (!(kuu < 0.f && kvv < 0.f)) return true;
+    const float x0 = u_lo - p0.y, x1 = u_hi - p0.y, y0 = v_lo - p0.z, y1 = v_hi - p0.z;
+    float q = 0.f;  // max of the quadratic part over the rectangle
+    if (!(x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f)) {
+        const float ru = -0.5f / kuu, rv = -0.5f / kvv;
+        const auto f = [&](float dx, float dy) { return fmaf(dx, fmaf(kuu, dx, kuv * dy), kvv * dy * dy); };
+        const float ya = fminf(fmaxf(kuv * x0 * rv, y0), y1), yb = fminf(fmaxf(kuv * x1 * rv, y0), y1);
+        const float xa = fminf(fmaxf(kuv * y0 * ru, x0), x1), xb = fminf(fmaxf(kuv * y1 * ru, x0), x1);
+        q = fmaxf(fmaxf(f(x0, ya), f(x1, yb)), fmaxf(f(xa, y0), f(xb, y1)));
+    }
+    const float DX = fmaxf(fabsf(x0), fabsf(x1)), DY = fmaxf(fabsf(y0), fabsf(y1));
+    const float mag = fabsf(p0.x) - kuu * DX * DX + fabsf(kuv) * DX * DY - kvv * DY * DY;
+    return p0.x + q >= thr - 0x1p-16f * mag;
+}
+
+// A warp's list of the batch positions [0, cnt) whose footprint reaches its pixel
+// rectangle [pu_lo, pu_hi] x [pv_lo, pv_hi]: the support box first, then the exact
+// footprint test; positions in ascending order.  Returns the count (warp-uniform).
+__device__ __forceinline__ int build_patch_list(const float4 *sBox, const float4 *sP0, const float2 *sP1,
+                                                uint8_t *list, int cnt, int lane, float thr, float pu_lo,
+                                                float pu_hi, float pv_lo, float pv_hi) {
+    int nl = 0;
+    for (int k = 0; k < cnt; k += 32) {
+        const int j = k + lane;
+        bool hit = false;
+        if (j < cnt) {
+            const float4 bx = sBox[j];
+            hit = bx.y >= pu_lo && bx.x <= pu_hi && bx.w >= pv_lo && bx.z <= pv_hi;
+            if (hit) hit = footprint_meets_rect(sP0[j], sP1[j], thr, pu_lo, pu_hi, pv_lo, pv_hi);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, hit);
+        if (hit) list[nl + __popc(m & ((1u << lane) - 1u))] = (uint8_t)j;
+        nl += __popc(m);
+    }
+    __syncwarp();
+    return nl;
+}
+
 // Global tile -> view (binary search over the views' first tiles).
 __device__ __forceinline__ int view_of_tile(const ViewInfo *views, int V, uint32_t tile) {
     int lo = 0, hi = V - 1;

@@ -19,7 +19,8 @@
 // Batches of NB records (64, 128 or 256, the batch depth, picked per context) are staged
 // by the first NB threads, from the tile's last contributor backwards.  Each warp owns an
 // 8 x 4 patch of the tile and walks, back to front, only the staged Gaussians whose
-// support box meets the patch and that precede its last contributor.
+// footprint can reach alpha_min on the patch (build_patch_list) and that precede its last
+// contributor.
 // Reduction: every (pixel, Gaussian) term is summed over the warp with a butterfly
 // reduce-scatter (for the pose-only walk 6 values in 8 shuffles, or two Gaussians' 12 in
 // 13 when it steps two at a time; 16 values in 16 otherwise),
@@ -138,19 +139,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
         __syncthreads();
         // this warp's list, limited to entries below its largest contributor count
         const int wcnt = (int)min((int64_t)cnt, (int64_t)wlast - b0);
-        int nl = 0;
-        for (int k = 0; k < wcnt; k += 32) {
-            const int j = k + lane;
-            bool hit = false;
-            if (j < wcnt) {
-                const float4 bx = sBox[j];
-                hit = bx.y >= pu_lo && bx.x <= pu_hi && bx.w >= pv_lo && bx.z <= pv_hi;
-            }
-            const uint32_t m = __ballot_sync(0xffffffffu, hit);
-            if (hit) sList[warp][nl + __popc(m & ((1u << lane) - 1u))] = (uint8_t)j;
-            nl += __popc(m);
-        }
-        __syncwarp();
+        const int nl = build_patch_list(sBox, sP0, sP1, sList[warp], wcnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
         int e = nl - 1;
         if constexpr (POSE) {
             // two Gaussians per step: the pixel state is updated in depth order (the back

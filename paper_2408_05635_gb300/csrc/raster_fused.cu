@@ -15,6 +15,7 @@
 //     the forward (the longest lists, launched first) overlap the reverse walks of the
 //     others instead of leaving SMs idle before a second kernel.
 #include "bwd_walk.cuh"
+#include "fwd_walk.cuh"
 #include "gs_internal.cuh"
 #include "tile_sort.cuh"
 
@@ -38,25 +39,6 @@ __device__ __forceinline__ void stage_one(const TrackTileLaunch &L, uint32_t r, 
     } else {
         sBox[tid] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);  // empty: never listed
     }
-}
-
-// The warp's list of batch positions [0, cnt) whose support box meets its 8 x 4 patch.
-__device__ __forceinline__ int build_list(const float4 *sBox, uint8_t *list, int cnt, int lane, float pu_lo,
-                                          float pu_hi, float pv_lo, float pv_hi) {
-    int nl = 0;
-    for (int k = 0; k < cnt; k += 32) {
-        const int j = k + lane;
-        bool hit = false;
-        if (j < cnt) {
-            const float4 bx = sBox[j];
-            hit = bx.y >= pu_lo && bx.x <= pu_hi && bx.w >= pv_lo && bx.z <= pv_hi;
-        }
-        const uint32_t m = __ballot_sync(0xffffffffu, hit);
-        if (hit) list[nl + __popc(m & ((1u << lane) - 1u))] = (uint8_t)j;
-        nl += __popc(m);
-    }
-    __syncwarp();
-    return nl;
 }
 
 }  // namespace
@@ -107,86 +89,26 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
     if (!(L.d.flags & GS_SCHED_RADIX)) sort_tile(L.ws, start, (int)n, sKeys);
 
     // ---------------------------------------------------------------- forward (Eqs. 2-4)
-    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, D = 0.f;
-    uint32_t last = 0, n_eval = 0, n_contrib = 0;
-    bool done = !inside;
+    FwdPixel walk{1.f, 0.f, 0.f, 0.f, 0.f, 0u, !inside};
+    uint32_t n_eval = 0, n_contrib = 0;
     int64_t staged = -1;  // first list entry of the batch now in shared memory (block-uniform)
     for (uint32_t b0 = 0; b0 < n; b0 += NB) {
-        if (__syncthreads_count(!done) == 0) break;
+        if (__syncthreads_count(!walk.done) == 0) break;
         const uint32_t idx = b0 + tid;
         if (tid < NB && idx < n) stage_one(L, L.ws.sorted[start + idx], x0, y0, sP0, sP1, sC, sQ, sBox, tid);
         staged = b0;
         __syncthreads();
         const int cnt = (int)min((uint32_t)NB, n - b0);
-        if (__any_sync(0xffffffffu, !done)) {
-            const int nl = build_list(sBox, sList[warp], cnt, lane, pu_lo, pu_hi, pv_lo, pv_hi);
-            if (!done) {
-                // two list entries per step: both footprints are evaluated before the
-                // pixel state is updated with the front one, then the back one (alpha 0
-                // for an entry that misses the pixel, which leaves every sum and T as they
-                // are), so the two evaluations overlap
-                int e = 0;
-                for (; e + 1 < nl; e += 2) {
-                    const int jA = sList[warp][e], jB = sList[warp][e + 1];
-                    const float pA = eval_poly(fu, fv, sP0[jA], sP1[jA]).poly;
-                    const float pB = eval_poly(fu, fv, sP0[jB], sP1[jB]).poly;
-                    const float4 CA = sC[jA], CB = sC[jB];
-                    const bool cA = pA >= thr, cB = pB >= thr;
-                    const float aA = cA ? fminf(S.alpha_max, ex2_approx(pA)) : 0.f;
-                    const float aB = cB ? fminf(S.alpha_max, ex2_approx(pB)) : 0.f;
-                    ++n_eval;
-                    float Tn = T * (1.f - aA);
-                    if (cA && Tn < S.t_min) {
-                        done = true;
-                        break;
-                    }
-                    float w = aA * T;
-                    cr += CA.x * w;
-                    cg += CA.y * w;
-                    cb += CA.z * w;
-                    D += CA.w * w;
-                    T = Tn;
-                    if (cA) last = b0 + (uint32_t)jA + 1u;
-                    ++n_eval;
-                    n_contrib += cA;
-                    Tn = T * (1.f - aB);
-                    if (cB && Tn < S.t_min) {
-                        done = true;
-                        break;
-                    }
-                    w = aB * T;
-                    cr += CB.x * w;
-                    cg += CB.y * w;
-                    cb += CB.z * w;
-                    D += CB.w * w;
-                    T = Tn;
-                    if (cB) last = b0 + (uint32_t)jB + 1u;
-                    n_contrib += cB;
-                }
-                for (; !done && e < nl; ++e) {
-                    const int j = sList[warp][e];
-                    const float poly = eval_poly(fu, fv, sP0[j], sP1[j]).poly;
-                    ++n_eval;
-                    if (poly < thr) continue;
-                    const float alpha = fminf(S.alpha_max, ex2_approx(poly));
-                    const float Tn = T * (1.f - alpha);
-                    if (Tn < S.t_min) {
-                        done = true;
-                        break;
-                    }
-                    const float w = alpha * T;
-                    const float4 Cc = sC[j];
-                    cr += Cc.x * w;
-                    cg += Cc.y * w;
-                    cb += Cc.z * w;
-                    D += Cc.w * w;
-                    T = Tn;
-                    last = b0 + (uint32_t)j + 1u;
-                    ++n_contrib;
-                }
-            }
+        if (__any_sync(0xffffffffu, !walk.done)) {
+            const int nl = build_patch_list(sBox, sP0, sP1, sList[warp], cnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
+            if (!walk.done)
+                fwd_walk_batch(walk, sList[warp], nl, b0, sP0, sP1, sC, fu, fv, thr, S.alpha_max, S.t_min, n_eval,
+                               n_contrib);
         }
     }
+    float T = walk.T;
+    const float cr = walk.cr, cg = walk.cg, cb = walk.cb, D = walk.D;
+    uint32_t last = walk.last;
     const float Sil = 1.f - T;  // Eq. 4 summed: 1 - prod(1 - a_i)
     count_pairs(n_eval, n_contrib, &L.ws.hdr->fwd_evals, &L.ws.hdr->fwd_contrib);
 
@@ -274,7 +196,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
         __syncthreads();
         // this warp's list, limited to entries below its largest contributor count
         const int wcnt = (int)min((int64_t)cnt, (int64_t)wlast - b0);
-        const int nl = build_list(sBox, sList[warp], wcnt, lane, pu_lo, pu_hi, pv_lo, pv_hi);
+        const int nl = build_patch_list(sBox, sP0, sP1, sList[warp], wcnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
         int e = nl - 1;
         // two Gaussians per step: the pixel state is updated in depth order (the back one
         // first), and the two reductions are independent, so they overlap

@@ -11,14 +11,16 @@
 // stops before the Gaussian that would take T below t_min, and the block stops as soon
 // as all its pixels have stopped.  Batches of NB records (64, 128 or 256, the batch
 // depth, picked per context) are gathered into shared memory by the first NB threads;
-// each warp (an 8 x 4 patch of the tile) then lists the batch Gaussians whose
-// conservative support box meets its patch and walks only those.  A smaller batch stages
+// each warp (an 8 x 4 patch of the tile) then lists the batch Gaussians whose footprint
+// can reach alpha_min somewhere on its patch (the support box, then the maximum of the
+// footprint over the patch rectangle: build_patch_list) and walks only those.  A smaller batch stages
 // fewer Gaussians past the point where every pixel of the tile has stopped; a larger one
 // takes fewer barriers.
 //
 // With targets, the combined loss of Sec. III-B (plus the depth-prior term) is
 // evaluated in the epilogue: its per-pixel gradient goes to the workspace for the
 // backward and its value is reduced per tile in double-float (summed per view by k_finalize).
+#include "fwd_walk.cuh"
 #include "gs_internal.cuh"
 #include "tile_sort.cuh"
 
@@ -62,11 +64,10 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     // this tile's list in (depth, Gaussian) order, unless the device-wide radix sort
     // (GS_SCHED_RADIX) has already ordered it
     if (!(L.d.flags & GS_SCHED_RADIX)) sort_tile(L.ws, start, (int)n, sKeys);
-    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, D = 0.f;
-    uint32_t last = 0, n_eval = 0, n_contrib = 0;
-    bool done = !inside;
+    FwdPixel walk{1.f, 0.f, 0.f, 0.f, 0.f, 0u, !inside};
+    uint32_t n_eval = 0, n_contrib = 0;
     for (uint32_t b0 = 0; b0 < n; b0 += NB) {
-        if (__syncthreads_count(!done) == 0) break;
+        if (__syncthreads_count(!walk.done) == 0) break;
         const uint32_t idx = b0 + tid;
         if (tid < NB && idx < n) {  // thread tid stages batch position tid
             const uint32_t r = L.ws.sorted[start + idx];
@@ -83,90 +84,18 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)NB, n - b0);
-        if (__any_sync(0xffffffffu, !done)) {
-            // this warp's list: the batch Gaussians whose support box meets its 8 x 4 patch
-            int nl = 0;
-            for (int k = 0; k < cnt; k += 32) {
-                const int j = k + lane;
-                bool hit = false;
-                if (j < cnt) {
-                    const float4 bx = sBox[j];
-                    hit = bx.y >= pu_lo && bx.x <= pu_hi && bx.w >= pv_lo && bx.z <= pv_hi;
-                }
-                const uint32_t m = __ballot_sync(0xffffffffu, hit);
-                if (hit) sList[warp][nl + __popc(m & ((1u << lane) - 1u))] = (uint8_t)j;
-                nl += __popc(m);
-            }
-            __syncwarp();
-            if (!done) {
-                // two list entries per step: both footprints are evaluated before the
-                // pixel state is updated with the front one, then the back one (alpha 0
-                // for an entry that misses the pixel, which leaves every sum and T as they
-                // are), so the two evaluations overlap
-                int e = 0;
-                for (; e + 1 < nl; e += 2) {
-                    const int jA = sList[warp][e], jB = sList[warp][e + 1];
-                    const float pA = eval_poly(fu, fv, sP0[jA], sP1[jA]).poly;
-                    const float pB = eval_poly(fu, fv, sP0[jB], sP1[jB]).poly;
-                    const float4 CA = sC[jA], CB = sC[jB];
-                    const bool cA = pA >= thr, cB = pB >= thr;
-                    const float aA = cA ? fminf(S.alpha_max, ex2_approx(pA)) : 0.f;
-                    const float aB = cB ? fminf(S.alpha_max, ex2_approx(pB)) : 0.f;
-                    ++n_eval;
-                    float Tn = T * (1.f - aA);
-                    if (cA && Tn < S.t_min) {
-                        done = true;
-                        break;
-                    }
-                    float w = aA * T;
-                    cr += CA.x * w;
-                    cg += CA.y * w;
-                    cb += CA.z * w;
-                    D += CA.w * w;
-                    T = Tn;
-                    if (cA) last = b0 + (uint32_t)jA + 1u;
-                    ++n_eval;
-                    n_contrib += cA;
-                    Tn = T * (1.f - aB);
-                    if (cB && Tn < S.t_min) {
-                        done = true;
-                        break;
-                    }
-                    w = aB * T;
-                    cr += CB.x * w;
-                    cg += CB.y * w;
-                    cb += CB.z * w;
-                    D += CB.w * w;
-                    T = Tn;
-                    if (cB) last = b0 + (uint32_t)jB + 1u;
-                    n_contrib += cB;
-                }
-                for (; !done && e < nl; ++e) {
-                    const int j = sList[warp][e];
-                    const float poly = eval_poly(fu, fv, sP0[j], sP1[j]).poly;
-                    ++n_eval;
-                    if (poly < thr) continue;
-                    const float alpha = fminf(S.alpha_max, ex2_approx(poly));
-                    const float Tn = T * (1.f - alpha);
-                    if (Tn < S.t_min) {
-                        done = true;
-                        break;
-                    }
-                    const float w = alpha * T;
-                    const float4 Cc = sC[j];
-                    cr += Cc.x * w;
-                    cg += Cc.y * w;
-                    cb += Cc.z * w;
-                    D += Cc.w * w;
-                    T = Tn;
-                    last = b0 + (uint32_t)j + 1u;
-                    ++n_contrib;
-                }
-            }
+        if (__any_sync(0xffffffffu, !walk.done)) {
+            // this warp's list: the batch Gaussians whose footprint reaches its 8 x 4 patch
+            const int nl = build_patch_list(sBox, sP0, sP1, sList[warp], cnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
+            if (!walk.done)
+                fwd_walk_batch(walk, sList[warp], nl, b0, sP0, sP1, sC, fu, fv, thr, S.alpha_max, S.t_min, n_eval,
+                               n_contrib);
         }
     }
     // Eq. 4 summed equals 1 - prod(1 - a_i) = 1 - T exactly; the identity is used instead
     // of a fifth accumulator
+    const float T = walk.T, cr = walk.cr, cg = walk.cg, cb = walk.cb, D = walk.D;
+    const uint32_t last = walk.last;
     const float Sil = 1.f - T;
     count_pairs(n_eval, n_contrib, &L.ws.hdr->fwd_evals, &L.ws.hdr->fwd_contrib);
 
