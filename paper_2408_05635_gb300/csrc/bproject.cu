@@ -120,6 +120,8 @@ __device__ __forceinline__ float warp_reduce8(float (&v)[8], int lane, int &idx)
 // as written: one log-radius per Gaussian, no rotation), Sigma_c = s^2 I.
 template <int DT, bool PARAMS, bool ISO>
 __global__ void __launch_bounds__(kBlock, PARAMS ? 4 : 6) k_bproject(BprojLaunch L) {
+    griddep_wait();  // the predecessor's results are visible from here on
+    griddep_launch_dependents();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ float s_red[kWarps][8];
     const uint32_t cell = blockIdx.x;
@@ -309,6 +311,8 @@ constexpr int kFinThreads = 384;
 constexpr int kFinUnroll = 8;
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeLaunch L) {
+    griddep_wait();  // the predecessor's results are visible from here on
+    griddep_launch_dependents();
     const int v = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kPerComp = kFinThreads / 3;  // pose partial columns per component
     __shared__ float2 s_pose_acc[6][kPerComp];
@@ -383,7 +387,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeLaunch L) {
 }
 
 cudaError_t launch_finalize(const FinalizeLaunch &L, cudaStream_t st) {
-    k_finalize<<<L.d.V, kFinThreads, 0, st>>>(L);
+    cudaError_t e = launch_dep(k_finalize, dim3(L.d.V), dim3(kFinThreads), st, L);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -391,15 +396,16 @@ cudaError_t launch_bproject(const BprojLaunch &L, cudaStream_t st) {
     const uint32_t grid = (uint32_t)L.d.V * (uint32_t)L.d.nblk;
     const bool params = L.grads.means || L.grads.quats || L.grads.log_scales || L.grads.opacity_logits || L.grads.rgb;
     const bool iso = L.g.quats == nullptr;
+    cudaError_t e;
 #define GS_BPROJ(DT)                                                   \
     if (params && iso)                                                 \
-        k_bproject<DT, true, true><<<grid, kBlock, 0, st>>>(L);        \
+        e = launch_dep(k_bproject<DT, true, true>, grid, dim3(kBlock), st, L);        \
     else if (params)                                                   \
-        k_bproject<DT, true, false><<<grid, kBlock, 0, st>>>(L);       \
+        e = launch_dep(k_bproject<DT, true, false>, grid, dim3(kBlock), st, L);       \
     else if (iso)                                                      \
-        k_bproject<DT, false, true><<<grid, kBlock, 0, st>>>(L);       \
+        e = launch_dep(k_bproject<DT, false, true>, grid, dim3(kBlock), st, L);       \
     else                                                               \
-        k_bproject<DT, false, false><<<grid, kBlock, 0, st>>>(L);
+        e = launch_dep(k_bproject<DT, false, false>, grid, dim3(kBlock), st, L);
     switch (L.dtype) {
         case GS_F32: GS_BPROJ(GS_F32) break;
         case GS_BF16: GS_BPROJ(GS_BF16) break;
@@ -407,7 +413,7 @@ cudaError_t launch_bproject(const BprojLaunch &L, cudaStream_t st) {
         default: return cudaErrorInvalidValue;
     }
 #undef GS_BPROJ
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace gsk

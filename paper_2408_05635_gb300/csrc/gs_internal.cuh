@@ -334,6 +334,33 @@ struct Footprint {
     float2 p1;  // (kuv, kvv)
 };
 
+// Programmatic dependent launch.  The kernels of a tracking iteration form one chain on a
+// stream; launched with launch_dep, a kernel's blocks may be scheduled while its
+// predecessor's last blocks still run (the predecessor lets them in with
+// griddep_launch_dependents, or by exiting), and each block first waits in griddep_wait
+// until the predecessor grid has completed and its memory is visible.  Every kernel
+// launched this way calls griddep_wait before touching global memory, so completion stays
+// transitive along the chain.  Both are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline cudaError_t launch_dep(void (*kernel)(P...), dim3 grid, dim3 block, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -149,6 +149,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *w
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(WsPtrs ws, Dims d) {
+    griddep_wait();  // the predecessor's results are visible from here on
+    griddep_launch_dependents();
     __shared__ uint32_t warp_sum[kScanThreads / 32];
     __shared__ uint32_t s_bucket[kOrderBuckets];
     __shared__ uint32_t s_max;
@@ -270,12 +272,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(WsPtrs ws, Dims d) 
 }
 
 cudaError_t launch_scan_tiles(const WsPtrs &ws, const Dims &d, cudaStream_t st) {
-    k_scan_tiles<<<1, kScanThreads, 0, st>>>(ws, d);
-    return cudaGetLastError();
+    return launch_dep(k_scan_tiles, dim3(1), dim3(kScanThreads), st, ws, d);
 }
 
 template <int DT, bool ISO>
 __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
+    griddep_wait();  // the predecessor's results are visible from here on
+    griddep_launch_dependents();
     const int v = blockIdx.y, b = blockIdx.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     __shared__ float sRt[12];
@@ -429,22 +432,23 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
 cudaError_t launch_project(const ProjectLaunch &L, cudaStream_t st) {
     dim3 grid(L.d.nblk, L.d.V);
     const bool iso = L.g.quats == nullptr;  // isotropic Gaussians: one log-radius, no rotation
+    cudaError_t e;
     switch (L.dtype) {
         case GS_F32:
-            if (iso) k_project<GS_F32, true><<<grid, kBlock, 0, st>>>(L);
-            else k_project<GS_F32, false><<<grid, kBlock, 0, st>>>(L);
+            if (iso) e = launch_dep(k_project<GS_F32, true>, grid, dim3(kBlock), st, L);
+            else e = launch_dep(k_project<GS_F32, false>, grid, dim3(kBlock), st, L);
             break;
         case GS_BF16:
-            if (iso) k_project<GS_BF16, true><<<grid, kBlock, 0, st>>>(L);
-            else k_project<GS_BF16, false><<<grid, kBlock, 0, st>>>(L);
+            if (iso) e = launch_dep(k_project<GS_BF16, true>, grid, dim3(kBlock), st, L);
+            else e = launch_dep(k_project<GS_BF16, false>, grid, dim3(kBlock), st, L);
             break;
         case GS_F16:
-            if (iso) k_project<GS_F16, true><<<grid, kBlock, 0, st>>>(L);
-            else k_project<GS_F16, false><<<grid, kBlock, 0, st>>>(L);
+            if (iso) e = launch_dep(k_project<GS_F16, true>, grid, dim3(kBlock), st, L);
+            else e = launch_dep(k_project<GS_F16, false>, grid, dim3(kBlock), st, L);
             break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Write one (record, tile) pair at its slot: for the per-tile sort the key depth bits << 32 |
@@ -470,6 +474,12 @@ static_assert(kCell % kEmitThreads == 0 && kEmitThreads % 32 == 0, "emission blo
 // the high word, the record in the low word, stored at the next free slot of the tile's
 // sub-bucket.  One block per cell, one thread per record (record_tiles).
 __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws, Dims d) {
+    // No early griddep_launch_dependents here: the tile compositor's blocks would then be
+    // placed while the emission still runs, on whichever SMs free first, and the longest
+    // tile lists (launched first) would crowd onto a few SMs (k_track_tile measured 110 ->
+    // 131 us on the 640 x 480 / 200k frame); launched as the emission's blocks exit, they
+    // spread over all SMs.
+    griddep_wait();  // the predecessor's results are visible from here on
     // kCell / kEmitThreads blocks per cell, each taking a quarter of the cell's slots: a
     // cell full of visible Gaussians (neighbours in a map built frame by frame) is spread
     // over several SMs instead of running as one long block, and empty quarters leave at once
@@ -542,7 +552,8 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws
 
 cudaError_t launch_emit(const WsPtrs &ws, const Dims &d, cudaStream_t st) {
     const uint32_t cells = (uint32_t)d.V * (uint32_t)d.nblk;
-    k_emit<<<cells * (uint32_t)(kCell / kEmitThreads), kEmitThreads, 0, st>>>(ws, d);
+    const cudaError_t e = launch_dep(k_emit, dim3(cells * (uint32_t)(kCell / kEmitThreads)), dim3(kEmitThreads), st, ws, d);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

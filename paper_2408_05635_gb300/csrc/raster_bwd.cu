@@ -40,6 +40,8 @@ template <bool POSE, int NB, int LW>
 __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     static_assert(NB % 32 == 0 && NB <= kBatch, "batch depth: a multiple of 32, at most kBatch");
     static_assert(LW >= 3 && (1 << LW) * kPatchH <= kTilePix, "tile width: 8 to 32 pixels");
+    griddep_wait();  // the predecessor's results are visible from here on
+    griddep_launch_dependents();
     __shared__ float4 sP0[NB], sC[NB], sQ[NB], sBox[NB];
     __shared__ float2 sP1[NB];
     __shared__ float sAcc[NB * kAccStride];
@@ -218,19 +220,19 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
 }
 
 template <int NB, int LW>
-void launch_backward_nb(const BackwardLaunch &L, cudaStream_t st) {
+cudaError_t launch_backward_nb(const BackwardLaunch &L, cudaStream_t st) {
     if (L.pose_only)
-        k_backward<true, NB, LW><<<L.d.T, tile_threads(L.d), 0, st>>>(L);
+        return launch_dep(k_backward<true, NB, LW>, dim3(L.d.T), dim3(tile_threads(L.d)), st, L);
     else
-        k_backward<false, NB, LW><<<L.d.T, tile_threads(L.d), 0, st>>>(L);
+        return launch_dep(k_backward<false, NB, LW>, dim3(L.d.T), dim3(tile_threads(L.d)), st, L);
 }
 
 template <int NB>
 cudaError_t launch_backward_lw(const BackwardLaunch &L, cudaStream_t st) {
     switch (tile_lw(L.d)) {
-        case 3: launch_backward_nb<NB, 3>(L, st); break;
-        case 4: launch_backward_nb<NB, 4>(L, st); break;
-        case 5: launch_backward_nb<NB, 5>(L, st); break;
+        case 3: return launch_backward_nb<NB, 3>(L, st);
+        case 4: return launch_backward_nb<NB, 4>(L, st);
+        case 5: return launch_backward_nb<NB, 5>(L, st);
         default: return cudaErrorInvalidValue;
     }
     return cudaSuccess;

@@ -32,6 +32,8 @@ template <bool LOSS, int NB, int LW>
 __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     static_assert(NB % 32 == 0 && NB <= kBatch, "batch depth: a multiple of 32, at most kBatch");
     static_assert(LW >= 3 && (1 << LW) * kPatchH <= kTilePix, "tile width: 8 to 32 pixels");
+    griddep_wait();  // the predecessor's results are visible from here on
+    griddep_launch_dependents();
     __shared__ float4 sP0[NB], sC[NB], sBox[NB];
     __shared__ float2 sP1[NB];
     __shared__ uint8_t sList[kTilePix / 32][NB];
@@ -168,19 +170,19 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
 }
 
 template <int NB, int LW>
-void launch_forward_nb(const ForwardLaunch &L, cudaStream_t st) {
+cudaError_t launch_forward_nb(const ForwardLaunch &L, cudaStream_t st) {
     if (L.t_rgb)
-        k_forward<true, NB, LW><<<L.d.T, tile_threads(L.d), 0, st>>>(L);
+        return launch_dep(k_forward<true, NB, LW>, dim3(L.d.T), dim3(tile_threads(L.d)), st, L);
     else
-        k_forward<false, NB, LW><<<L.d.T, tile_threads(L.d), 0, st>>>(L);
+        return launch_dep(k_forward<false, NB, LW>, dim3(L.d.T), dim3(tile_threads(L.d)), st, L);
 }
 
 template <int NB>
 cudaError_t launch_forward_lw(const ForwardLaunch &L, cudaStream_t st) {
     switch (tile_lw(L.d)) {
-        case 3: launch_forward_nb<NB, 3>(L, st); break;
-        case 4: launch_forward_nb<NB, 4>(L, st); break;
-        case 5: launch_forward_nb<NB, 5>(L, st); break;
+        case 3: return launch_forward_nb<NB, 3>(L, st);
+        case 4: return launch_forward_nb<NB, 4>(L, st);
+        case 5: return launch_forward_nb<NB, 5>(L, st);
         default: return cudaErrorInvalidValue;
     }
     return cudaSuccess;
