@@ -757,8 +757,8 @@ def oracle_small_single_thread(budget_s: float = 3.0) -> dict:
 
 
 def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None once the
-    kernel's sources differ from the ones the counters were taken on."""
+    """(DRAM bytes per launch of `kernel` from the committed ncu summary, or None once the
+    kernel's sources differ from the ones the counters were taken on; the summary's path)."""
     import glob
     import hashlib
     root = os.path.dirname(os.path.abspath(__file__))
@@ -769,8 +769,8 @@ def ncu_traffic(kernel):
                 h = hashlib.sha256()
                 for src in f[4:]:
                     h.update(open(os.path.join(root, "paper_2408_05635_gb300", "csrc", src), "rb").read())
-                return int(f[2]) if h.hexdigest()[:16] == f[3] else None
-    return None
+                return (int(f[2]) if h.hexdigest()[:16] == f[3] else None), os.path.relpath(path, root)
+    return None, None
 
 
 def reference_steps(g, cam, start, rgb, depth, prior, steps: int, warmup: int, band: int = 64):
@@ -1038,10 +1038,11 @@ def main():
     if dominant in per_pair:
         f, units, what = per_pair[dominant]
         achieved = f * units / a.steps / (avg[dominant] / 1e3) / 1e12
+        traffic, traffic_src = ncu_traffic(dominant)
         roofline = {"kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": ncu_traffic(dominant),
+                    "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                     "traffic_from": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold cache "
-                                    "(profiles/k_backward_k_forward_tracking_640x480_200k.md)",
+                                    f"({traffic_src})",
                     "work": f"{what}: {f * units // a.steps} FLOP per launch",
                     "peak_from": f"{n_sm} SMs x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz (median SM clock, timed region)"}
     if rank == 0:
