@@ -404,45 +404,62 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 // meets the ellipse iff its pixel-centre columns overlap that interval, so this finds the
 // same tiles as testing each tile of the row, at the cost of one row.  The interval is
 // widened by 1e-3 px + 1e-6 |x| against the rounding of the square roots.  Explicitly
-// rounded operations: k_project and k_emit enumerate identical tiles.
-__device__ __forceinline__ void row_tiles(const ViewInfo &vi, float mx, float my, float a, float b, float c,
-                                          float dmax2, int ty, int tx0, int tx1, int &a0, int &a1) {
+// rounded operations: k_project and k_emit enumerate identical tiles.  The quantities that
+// do not depend on the row (RowSpan) are computed once per record by row_span_setup.
+struct RowSpan {
+    float mx, my, b, R, det, Y, X, t, ia, aR;  // aR = a R
+    bool all;                                  // unbounded support: every column
+};
+
+__device__ __forceinline__ RowSpan row_span_setup(float mx, float my, float a, float b, float c, float dmax2) {
+    RowSpan s;
+    s.mx = mx;
+    s.my = my;
+    s.b = b;
+    s.all = !(dmax2 < INFINITY);
+    s.R = __fadd_rn(__fmul_rn(dmax2, 1.001f), 1e-3f);
+    s.det = diff_of_products(a, c, b, b);
+    s.aR = __fmul_rn(a, s.R);
+    s.Y = __fsqrt_rn(__fdiv_rn(s.aR, s.det));                         // y half-extent of the ellipse
+    s.X = __fsqrt_rn(__fdiv_rn(__fmul_rn(s.R, c), s.det));            // x half-extent of the ellipse
+    s.t = __fmul_rn(b, __fsqrt_rn(__fdiv_rn(s.R, __fmul_rn(c, s.det))));  // |dy| of the x-extremes
+    s.ia = __fdiv_rn(1.f, a);
+    return s;
+}
+
+__device__ __forceinline__ void row_span(const ViewInfo &vi, const RowSpan &s, int ty, int tx0, int tx1, int &a0,
+                                         int &a1) {
     a0 = tx0;
     a1 = tx1;
-    if (!(dmax2 < INFINITY)) return;
-    const float R = __fadd_rn(__fmul_rn(dmax2, 1.001f), 1e-3f);
-    const float det = diff_of_products(a, c, b, b);
+    if (s.all) return;
     const float yb0 = (float)(ty << vi.tile_lh), yb1 = (float)min(((ty + 1) << vi.tile_lh) - 1, vi.height - 1);
-    const float Y = __fsqrt_rn(__fdiv_rn(__fmul_rn(a, R), det));  // y half-extent of the ellipse
-    const float ly = fmaxf(__fsub_rn(yb0, my), -Y), hy = fminf(__fsub_rn(yb1, my), Y);
+    const float ly = fmaxf(__fsub_rn(yb0, s.my), -s.Y), hy = fminf(__fsub_rn(yb1, s.my), s.Y);
     if (!(ly <= hy)) {
         a0 = 1;
         a1 = 0;
         return;
     }
-    const float X = __fsqrt_rn(__fdiv_rn(__fmul_rn(R, c), det));    // x half-extent of the ellipse
-    const float t = __fmul_rn(b, __fsqrt_rn(__fdiv_rn(R, __fmul_rn(c, det))));  // |dy| of the x-extremes
-    const float ia = __fdiv_rn(1.f, a);
     // boundary offsets at the band edges: -b dy / a -+ sqrt(a R - det dy^2) / a
-    const float rl = __fsqrt_rn(fmaxf(__fsub_rn(__fmul_rn(a, R), __fmul_rn(det, __fmul_rn(ly, ly))), 0.f));
-    const float rh = __fsqrt_rn(fmaxf(__fsub_rn(__fmul_rn(a, R), __fmul_rn(det, __fmul_rn(hy, hy))), 0.f));
-    const float cl = __fmul_rn(__fmul_rn(-b, ly), ia), ch = __fmul_rn(__fmul_rn(-b, hy), ia);
+    const float rl = __fsqrt_rn(fmaxf(__fsub_rn(s.aR, __fmul_rn(s.det, __fmul_rn(ly, ly))), 0.f));
+    const float rh = __fsqrt_rn(fmaxf(__fsub_rn(s.aR, __fmul_rn(s.det, __fmul_rn(hy, hy))), 0.f));
+    const float cl = __fmul_rn(__fmul_rn(-s.b, ly), s.ia), ch = __fmul_rn(__fmul_rn(-s.b, hy), s.ia);
     float xr, xl;
-    if (-t >= ly && -t <= hy)
-        xr = X;
+    if (-s.t >= ly && -s.t <= hy)
+        xr = s.X;
     else
-        xr = fmaxf(__fadd_rn(cl, __fmul_rn(rl, ia)), __fadd_rn(ch, __fmul_rn(rh, ia)));
-    if (t >= ly && t <= hy)
-        xl = -X;
+        xr = fmaxf(__fadd_rn(cl, __fmul_rn(rl, s.ia)), __fadd_rn(ch, __fmul_rn(rh, s.ia)));
+    if (s.t >= ly && s.t <= hy)
+        xl = -s.X;
     else
-        xl = fminf(__fsub_rn(cl, __fmul_rn(rl, ia)), __fsub_rn(ch, __fmul_rn(rh, ia)));
-    xl = __fsub_rn(__fadd_rn(mx, xl), __fadd_rn(1e-3f, __fmul_rn(1e-6f, fabsf(__fadd_rn(mx, xl)))));
-    xr = __fadd_rn(__fadd_rn(mx, xr), __fadd_rn(1e-3f, __fmul_rn(1e-6f, fabsf(__fadd_rn(mx, xr)))));
+        xl = fminf(__fsub_rn(cl, __fmul_rn(rl, s.ia)), __fsub_rn(ch, __fmul_rn(rh, s.ia)));
+    xl = __fsub_rn(__fadd_rn(s.mx, xl), __fadd_rn(1e-3f, __fmul_rn(1e-6f, fabsf(__fadd_rn(s.mx, xl)))));
+    xr = __fadd_rn(__fadd_rn(s.mx, xr), __fadd_rn(1e-3f, __fmul_rn(1e-6f, fabsf(__fadd_rn(s.mx, xr)))));
     // tile tx spans pixel centres [TW tx, TW tx + TW - 1]: it meets [xl, xr] iff
-    // TW tx + TW - 1 >= xl and TW tx <= xr (TW a power of two: the divisions are exact)
-    const float TW = (float)(1 << vi.tile_lw);
-    const float lo = fmaxf(ceilf(__fdiv_rn(__fsub_rn(xl, __fsub_rn(TW, 1.f)), TW)), -1.f);
-    const float hi = fminf(floorf(__fdiv_rn(xr, TW)), 1.0e7f);
+    // TW tx + TW - 1 >= xl and TW tx <= xr (TW a power of two: multiplying by 1 / TW is
+    // exact, the same as dividing)
+    const float TW = (float)(1 << vi.tile_lw), iTW = __fdiv_rn(1.f, TW);
+    const float lo = fmaxf(ceilf(__fmul_rn(__fsub_rn(xl, __fsub_rn(TW, 1.f)), iTW)), -1.f);
+    const float hi = fminf(floorf(__fmul_rn(xr, iTW)), 1.0e7f);
     a0 = max(tx0, (int)lo);
     a1 = min(tx1, (int)hi);
 }

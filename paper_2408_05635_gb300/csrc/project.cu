@@ -51,9 +51,10 @@ __device__ __forceinline__ void record_tiles(bool mine, const ViewInfo &vi, floa
     const int rw = tx1 - tx0 + 1;
     const int count = has ? rw * (ty1 - ty0 + 1) : 0;
     if (SOLO && has && count <= kSoloTiles) {
+        const RowSpan span = row_span_setup(A.x, A.y, B.x, B.y, B.z, B.w);
         for (int ty = ty0; ty <= ty1; ++ty) {
             int a0, a1;
-            row_tiles(vi, A.x, A.y, B.x, B.y, B.z, B.w, ty, tx0, tx1, a0, a1);
+            row_span(vi, span, ty, tx0, tx1, a0, a1);
             for (int tx = a0; tx <= a1; ++tx) body(lane, vi.tile_base + (uint32_t)(ty * vi.tiles_x + tx), A, tag);
         }
     }
@@ -511,9 +512,10 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws
     const int count = has ? rw * (ty1 - ty0 + 1) : 0;
     if (has && count <= kSoloTiles) {
         uint32_t hits = 0;  // bit (ty - ty0) rw + (tx - tx0) for every tile met
+        const RowSpan span = row_span_setup(A.x, A.y, B.x, B.y, B.z, B.w);
         for (int ty = ty0; ty <= ty1; ++ty) {
             int a0, a1;
-            row_tiles(vi, A.x, A.y, B.x, B.y, B.z, B.w, ty, tx0, tx1, a0, a1);
+            row_span(vi, span, ty, tx0, tx1, a0, a1);
             if (a0 <= a1) hits |= ((1u << (a1 - a0 + 1)) - 1u) << ((ty - ty0) * rw + (a0 - tx0));
         }
         while (hits) {
