@@ -999,9 +999,13 @@ def main():
     iters_per_s = whole_job_rate(1, a.steps, world, ms_max)
     mpix = iters_per_s * pix / 1e6
 
-    # end to end through the public call with host buffers: pinned frame in, pose and loss out
+    # end to end through the public call with host buffers: pinned frame in (copied by
+    # gs_track_step_upload into the device targets beside the iteration's binning), pose
+    # and loss out
     h_frame = torch.tensor(np.concatenate([rgb.reshape(-1), depth.reshape(-1), prior.reshape(-1)])).pin_memory()
     h_out = torch.empty(8, dtype=torch.float64).pin_memory()
+    src = gs.gs_host_targets(h_frame[:3 * P_px].data_ptr(), h_frame[3 * P_px:4 * P_px].data_ptr(),
+                             h_frame[4 * P_px:].data_ptr())
     e2e_s, e2e_e = [], []
     for k in range(a.warmup + a.steps):
         if k % ITERS_PER_FRAME == 0:
@@ -1010,8 +1014,7 @@ def main():
         flush.fill_(float(k))
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        frame_dev.copy_(h_frame, non_blocking=True)  # this step's frame, host -> device
-        step()
+        gs.gs_track_step_upload(R.ctx, prob, gt.c(), targets, src, poses, adam, loss, 1, ws, nb, stream)
         h_out.copy_(out8, non_blocking=True)  # pose and loss, device -> host
         s1.record(stream)
         if k >= a.warmup:
@@ -1063,8 +1066,9 @@ def main():
             "clocks": clocks,
             "roofline": roofline,
             "kernels_us": {k: round(1e3 * v, 2) for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1])},
-            "kernels_us_note": f"{n_break} steps with event markers around every kernel (they add a few us each); "
-                               f"the timed steps mark only {dominant}",
+            "kernels_us_note": f"{n_break} steps with event markers around every kernel (event nodes on a side "
+                               f"branch of the graph; a kernel's time runs from the previous kernel's end marker "
+                               f"to its own, launch gap included); the timed steps mark only {dominant}",
             "pairs_per_step": {k: v // a.steps for k, v in contrib.items()},
             # (pixel, Gaussian) pairs that contributed to Eqs. 2-4 or were differentiated, per second
             "useful_pair_evals_per_s": (contrib["fwd_contrib"] + contrib["bwd_contrib"]) / (ms / 1e3),

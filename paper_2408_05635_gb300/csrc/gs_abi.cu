@@ -53,7 +53,7 @@ struct Problem {
 struct GraphKey {
     const void *ws = nullptr;
     size_t ws_bytes = 0;
-    const void *ptrs[12] = {};
+    const void *ptrs[15] = {};
     int64_t n = 0;
     int dtype = 0;
     int iters = 0;
@@ -67,7 +67,7 @@ struct GraphKey {
             sched[1] != o.sched[1] || sched[2] != o.sched[2] || sched[3] != o.sched[3] ||
             views.size() != o.views.size())
             return false;
-        for (int k = 0; k < 12; ++k)
+        for (int k = 0; k < 15; ++k)
             if (ptrs[k] != o.ptrs[k]) return false;
         return views.empty() || std::memcmp(views.data(), o.views.data(), views.size() * sizeof(ViewInfo)) == 0;
     }
@@ -109,6 +109,10 @@ struct gs_ctx {
     cudaStream_t mark_stream = nullptr;
     cudaEvent_t fork_ev = nullptr;
     bool side_open = false;
+    // the targets' upload of gs_track_step_upload: a branch forked before the first
+    // projection and joined before the first compositor
+    cudaStream_t up_stream = nullptr;
+    cudaEvent_t up_fork = nullptr, up_join = nullptr;
 };
 
 namespace {
@@ -547,6 +551,9 @@ gs_status gs_destroy(gs_ctx *ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->mark_stream) cudaStreamDestroy(ctx->mark_stream);
     if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
+    if (ctx->up_fork) cudaEventDestroy(ctx->up_fork);
+    if (ctx->up_join) cudaEventDestroy(ctx->up_join);
     for (cudaEvent_t ev : ctx->events) cudaEventDestroy(ev);
     delete ctx;
     return GS_OK;
@@ -681,14 +688,58 @@ gs_status gs_backward(gs_ctx *ctx, const float *d_rgb, const float *d_depth, con
     return GS_OK;
 }
 
-gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const gs_targets *targets,
-                        double *poses, double *adam_state, double *loss_hist, int32_t iters, void *ws,
-                        size_t ws_bytes, void *stream) {
+namespace {
+
+bool pinned_host(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the error an unregistered pointer may leave
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// The upload branch of gs_track_step_upload: src -> targets on ctx->up_stream after
+// everything enqueued on q so far; ctx->up_join marks its end.
+cudaError_t fork_upload(gs_ctx *ctx, const gs_targets *targets, const gs_host_targets *src, uint32_t P,
+                        cudaStream_t q) {
+    cudaError_t e = cudaSuccess;
+    if (!ctx->up_stream) {
+        if ((e = cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ctx->up_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+        if ((e = cudaEventCreateWithFlags(&ctx->up_join, cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    if ((e = cudaEventRecord(ctx->up_fork, q)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ctx->up_stream, ctx->up_fork, 0)) != cudaSuccess) return e;
+    const size_t plane = sizeof(float) * (size_t)P;
+    // the targets' device buffers are the destination of this call's upload
+    if ((e = cudaMemcpyAsync(const_cast<float *>(targets->rgb), src->rgb, 3 * plane, cudaMemcpyHostToDevice,
+                             ctx->up_stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(const_cast<float *>(targets->depth), src->depth, plane, cudaMemcpyHostToDevice,
+                             ctx->up_stream)) != cudaSuccess)
+        return e;
+    if (src->depth_prior &&
+        (e = cudaMemcpyAsync(const_cast<float *>(targets->depth_prior), src->depth_prior, plane,
+                             cudaMemcpyHostToDevice, ctx->up_stream)) != cudaSuccess)
+        return e;
+    return cudaEventRecord(ctx->up_join, ctx->up_stream);
+}
+
+gs_status track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const gs_targets *targets,
+                     const gs_host_targets *src, double *poses, double *adam_state, double *loss_hist, int32_t iters,
+                     void *ws, size_t ws_bytes, void *stream) {
     if (!ctx) return GS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (iters < 1) return fail(ctx, GS_ERR_INVALID_ARG, "iters must be >= 1");
     if (!targets || !targets->rgb || !targets->depth) return fail(ctx, GS_ERR_INVALID_ARG, "targets need rgb and depth");
     if (!poses || !adam_state) return fail(ctx, GS_ERR_INVALID_ARG, "poses and adam_state are required");
+    if (src) {
+        if (!src->rgb || !src->depth || !src->depth_prior != !targets->depth_prior)
+            return fail(ctx, GS_ERR_INVALID_ARG, "src needs rgb and depth, and a depth prior exactly when targets has one");
+        if (!pinned_host(src->rgb) || !pinned_host(src->depth) || (src->depth_prior && !pinned_host(src->depth_prior)))
+            return fail(ctx, GS_ERR_INVALID_ARG, "src arrays must be page-locked host memory");
+    }
     Problem pr;
     gs_status st = build_problem(ctx, prob, pr);
     if (st != GS_OK) return st;
@@ -704,8 +755,11 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
 
     auto enqueue_all = [&](cudaStream_t q) -> cudaError_t {
         for (int it = 0; it < iters; ++it) {
-            cudaError_t r = enqueue_project(ctx, pr, w, gp, g->dtype_attr, poses, q);
-            if (r != cudaSuccess) return r;
+            cudaError_t r = cudaSuccess;
+            // the frame's upload runs beside the first projection, scan and emission
+            if (it == 0 && src && (r = fork_upload(ctx, targets, src, pr.d.P, q)) != cudaSuccess) return r;
+            if ((r = enqueue_project(ctx, pr, w, gp, g->dtype_attr, poses, q)) != cudaSuccess) return r;
+            if (it == 0 && src && (r = cudaStreamWaitEvent(q, ctx->up_join, 0)) != cudaSuccess) return r;
             if ((r = enqueue_compositing(ctx, pr, w, targets, q)) != cudaSuccess) return r;
             BprojLaunch J;
             J.ws = w;
@@ -745,9 +799,11 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
         GraphKey key;
         key.ws = ws;
         key.ws_bytes = ws_bytes;
-        const void *ptrs[12] = {g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb, targets->rgb,
-                                targets->depth, targets->depth_prior, poses, adam_state, loss_hist, nullptr};
-        for (int k = 0; k < 12; ++k) key.ptrs[k] = ptrs[k];
+        const void *ptrs[15] = {g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb, targets->rgb,
+                                targets->depth, targets->depth_prior, poses, adam_state, loss_hist, nullptr,
+                                src ? src->rgb : nullptr, src ? src->depth : nullptr,
+                                src ? src->depth_prior : nullptr};
+        for (int k = 0; k < 15; ++k) key.ptrs[k] = ptrs[k];
         key.n = g->n;
         key.dtype = g->dtype_attr;
         key.iters = iters;
@@ -802,6 +858,21 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
     ctx->have_loss = true;
     ctx->grads_used = true;
     return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const gs_targets *targets,
+                        double *poses, double *adam_state, double *loss_hist, int32_t iters, void *ws,
+                        size_t ws_bytes, void *stream) {
+    return track_step(ctx, prob, g, targets, nullptr, poses, adam_state, loss_hist, iters, ws, ws_bytes, stream);
+}
+
+gs_status gs_track_step_upload(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const gs_targets *targets,
+                               const gs_host_targets *src, double *poses, double *adam_state, double *loss_hist,
+                               int32_t iters, void *ws, size_t ws_bytes, void *stream) {
+    if (!src) return ctx ? fail(ctx, GS_ERR_INVALID_ARG, "src is NULL") : GS_ERR_INVALID_ARG;
+    return track_step(ctx, prob, g, targets, src, poses, adam_state, loss_hist, iters, ws, ws_bytes, stream);
 }
 
 gs_status gs_get_schedule(const gs_ctx *ctx, gs_schedule *out) {

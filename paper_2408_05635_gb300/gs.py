@@ -54,6 +54,10 @@ class gs_targets(ctypes.Structure):
     _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("depth_prior", c_void_p)]
 
 
+class gs_host_targets(ctypes.Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("depth_prior", c_void_p)]
+
+
 class gs_config(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32)] + [
         (n, c_float) for n in ("alpha_min", "alpha_max", "t_min", "dilation", "z_near", "jac_clip", "sil_thresh",
@@ -151,6 +155,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                                       c_void_p]),
             "gs_track_step": (c_int32, [c_void_p, P(gs_problem), P(gs_gaussians), P(gs_targets), c_void_p,
                                         c_void_p, c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
+            "gs_track_step_upload": (c_int32, [c_void_p, P(gs_problem), P(gs_gaussians), P(gs_targets),
+                                               P(gs_host_targets), c_void_p, c_void_p, c_void_p, c_int32, c_void_p,
+                                               c_size_t, c_void_p]),
             "gs_sync_status": (c_int32, [c_void_p, c_void_p, P(gs_counts)]),
             "gs_set_profiling": (c_int32, [c_void_p, c_int32]),
             "gs_set_profiling_mask": (c_int32, [c_void_p, ctypes.c_uint32]),
@@ -263,6 +270,15 @@ def gs_track_step(ctx, prob: gs_problem, g: gs_gaussians, targets: gs_targets, p
     _check(ctx, load().gs_track_step(ctx, ctypes.byref(prob), ctypes.byref(g), ctypes.byref(targets), _ptr(poses),
                                      _ptr(adam_state), _ptr(loss_hist), int(iters), _ptr(ws), ws_bytes,
                                      _stream(stream)), "gs_track_step")
+
+
+def gs_track_step_upload(ctx, prob: gs_problem, g: gs_gaussians, targets: gs_targets, src: gs_host_targets, poses,
+                         adam_state, loss_hist, iters: int, ws, ws_bytes: int, stream=None) -> None:
+    """gs_track_step with the frame copied from page-locked host memory (src) into the
+    device targets beside the first iteration's binning."""
+    _check(ctx, load().gs_track_step_upload(ctx, ctypes.byref(prob), ctypes.byref(g), ctypes.byref(targets),
+                                            ctypes.byref(src), _ptr(poses), _ptr(adam_state), _ptr(loss_hist),
+                                            int(iters), _ptr(ws), ws_bytes, _stream(stream)), "gs_track_step_upload")
 
 
 def gs_sync_status(ctx, stream=None) -> tuple[int, gs_counts]:

@@ -125,6 +125,47 @@ def test_tracking_graph_first_update(tracking, flags):
     assert r2 < 1e-2, (ri, r2)
 
 
+def test_tracking_with_host_upload_equals_device_targets(tracking):
+    """gs_track_step_upload: the frame in page-locked host memory is copied into the
+    device targets beside the first iteration's binning.  Five iterations from the start
+    pose give the poses, losses and Adam state of gs_track_step on the device frame (to
+    the run-to-run spread of the FP32 gradient atomics, whose order is not fixed: 1e-6
+    relative), the device targets hold the host frame afterwards (they start as NaN), and
+    a frame in ordinary (pageable) host memory is refused."""
+    t = tracking
+    R = gs.Rasterizer(gs.Config())
+    R.set_schedule(16, 16, 4, 256, 256, gs.GS_SCHED_FUSED)
+    gt = gs.GaussianTensors.from_numpy(t["g"])
+    start = torch.tensor(np.asarray(t["start"])[None], dtype=torch.float64, device="cuda")
+    prob = R.plan(gt, [t["cam"]], start, margin=1.5)
+    ws, nb = R.workspace(prob)
+    out = []
+    for upload in (False, True):
+        poses = start.clone()
+        adam = torch.zeros(1, 16, dtype=torch.float64, device="cuda")
+        hist = torch.zeros(5, 1, dtype=torch.float64, device="cuda")
+        if upload:
+            dev = tuple(torch.full_like(x, float("nan")) for x in t["targets"])
+            host = tuple(x.cpu().pin_memory() for x in t["targets"])
+            src = gs.gs_host_targets(*(x.data_ptr() for x in host))
+            tg = gs.gs_targets(*(x.data_ptr() for x in dev))
+            gs.gs_track_step_upload(R.ctx, prob, gt.c(), tg, src, poses, adam, hist, 5, ws, nb)
+        else:
+            tg = gs.gs_targets(*(x.data_ptr() for x in t["targets"]))
+            gs.gs_track_step(R.ctx, prob, gt.c(), tg, poses, adam, hist, 5, ws, nb)
+        R.sync()
+        out.append((poses.cpu().numpy(), hist.cpu().numpy(), adam.cpu().numpy()))
+        if upload:
+            for d, h in zip(dev, host):
+                assert torch.equal(d.cpu(), h)
+            pageable = tuple(x.cpu() for x in t["targets"])
+            bad = gs.gs_host_targets(*(x.data_ptr() for x in pageable))
+            with pytest.raises(gs.GsError):
+                gs.gs_track_step_upload(R.ctx, prob, gt.c(), tg, bad, poses, adam, hist, 1, ws, nb)
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-12)
+
+
 # ---------------------------------------------------------------------------- batched hypotheses
 
 @pytest.fixture(scope="module")
