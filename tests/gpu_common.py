@@ -98,3 +98,49 @@ def check_images(rgb, depth, sil, ref, scene, cam, pose, op, tol=IMG_TOL, what="
              "max_err_flagged_nearest_outcome": worst_alt}
     print(f"{what}: {stats}")
     return stats
+
+
+# Relative rounding allowance of the device loss: every pixel's FP32 terms, a 32-lane FP32
+# butterfly per warp (5 additions), double-float across warps and tiles: about 9 unit
+# roundoffs of 2^-24 relative to the total, taken as 1e-6.
+LOSS_ROUNDING = 1e-6
+
+
+def loss_tolerance(loss, ref, scene, cam, pose, op, rgb_t, depth_t, prior=None, max_alt=32) -> float:
+    """Largest |device loss - oracle loss| for an oracle loss `loss`: the FP32 decisions at
+    flagged pixels may give another outcome there, so the sum over the flagged pixels of
+    the largest change of the pixel's loss term among its FP32 outcomes
+    (oracle.render_alternatives; the loss is a sum of per-pixel terms, each evaluated by
+    oracle.loss on a one-pixel image), plus LOSS_ROUNDING of the loss.  A pixel with more
+    than max_alt outcomes counts with the largest value its term can take (every residual
+    at its larger distance to [0, 1] for colour and [0, z_max] for depth, the visibility
+    term at its maximum), since both outcomes' terms lie between 0 and that."""
+    H, W = cam.height, cam.width
+    flagged = ref["amb"].ravel()
+    pix = np.flatnonzero(flagged)
+    rgb_t = np.asarray(rgb_t, np.float64).reshape(3, H * W)
+    depth_t = np.asarray(depth_t, np.float64).reshape(H * W)
+    prior = None if prior is None else np.asarray(prior, np.float64).reshape(H * W)
+    one = oracle.camera(1.0, 1.0, 0.0, 0.0, 1, 1)
+
+    def term(q, c, d, s):
+        return oracle.loss(one, op, np.asarray(c, np.float64).reshape(3, 1, 1), np.full((1, 1), d), np.full((1, 1), s),
+                           rgb_t[:, q].reshape(3, 1, 1), depth_t[q:q + 1].reshape(1, 1),
+                           None if prior is None else prior[q:q + 1].reshape(1, 1))["loss"]
+
+    total = 0.0
+    if pix.size:
+        alts = oracle.render_alternatives(scene, ocam(cam), pose, op, pix, max_alt=max_alt)
+        rgb_r = ref["rgb"].reshape(3, H * W)
+        # no camera-frame depth exceeds |m| + |t| for the scene's means m and the pose's t
+        z_max = float(np.linalg.norm(np.asarray(scene.means), axis=1).max() + np.linalg.norm(np.asarray(pose)[4:7]))
+        for k, n in enumerate(alts["n_alt"]):
+            q = int(pix[k])
+            if n < 1:
+                pr = 0.0 if prior is None or prior[q] <= 0 else max(prior[q], z_max - prior[q])
+                total += (op.w_rgb * np.maximum(rgb_t[:, q], 1.0 - rgb_t[:, q]).sum()
+                          + op.w_depth * max(depth_t[q], z_max - depth_t[q]) + op.w_prior * pr + op.w_vis)
+                continue
+            nom = term(q, rgb_r[:, q], ref["depth"].ravel()[q], ref["sil"].ravel()[q])
+            total += max(abs(term(q, a[:3], a[3], a[4]) - nom) for a in alts["alts"][k, :n])
+    return total + LOSS_ROUNDING * abs(loss)

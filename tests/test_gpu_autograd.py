@@ -88,7 +88,7 @@ def test_autograd_matches_finite_differences():
         if not grad:
             return float(L), None, None
         L.backward()
-        return (float(L), [leaf.grad.cpu().numpy().astype(np.float64) for leaf in leaves],
+        return (float(L.detach()), [leaf.grad.cpu().numpy().astype(np.float64) for leaf in leaves],
                 tangent.grad.cpu().numpy()[0])
 
     def check(what, lm, lp, dm, d0, dp):

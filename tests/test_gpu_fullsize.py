@@ -31,7 +31,7 @@ import torch
 import bench
 import oracle
 import mask_model
-from gpu_common import assert_grads_close, assert_images_close, check_images, ocam, rel_err
+from gpu_common import assert_grads_close, assert_images_close, check_images, loss_tolerance, ocam
 from paper_2408_05635_gb300 import gs, scenes
 
 pytestmark = pytest.mark.gpu
@@ -55,7 +55,8 @@ def tracking():
     ref = oracle.render(sc, oc, start, op)
     L = oracle.loss(oc, op, ref["rgb"], ref["depth"], ref["sil"], rgb, depth, prior)
     targets = tuple(torch.tensor(a.reshape(-1), device="cuda") for a in (rgb, depth, prior))
-    return dict(g=g, cam=cam, start=start, op=op, sc=sc, oc=oc, ref=ref, L=L, targets=targets)
+    return dict(g=g, cam=cam, start=start, op=op, sc=sc, oc=oc, ref=ref, L=L, targets=targets,
+                frame=(rgb, depth, prior))
 
 
 def test_tracking_frame_images_and_loss(tracking):
@@ -73,7 +74,8 @@ def test_tracking_frame_images_and_loss(tracking):
     assert m["alpha_min"] <= m["alpha_min_bound"] and m["t_min"] <= m["t_min_bound"], m
     check_images(out["rgb"].cpu().numpy(), out["depth"].cpu().numpy(), out["sil"].cpu().numpy(), ref, t["sc"],
                  t["cam"], t["start"], t["op"], what="tracking frame")
-    assert out["loss"].item() == pytest.approx(t["L"]["loss"], rel=2e-3)
+    tol = loss_tolerance(t["L"]["loss"], ref, t["sc"], t["cam"], t["start"], t["op"], *t["frame"])
+    assert abs(out["loss"].item() - t["L"]["loss"]) <= tol, (out["loss"].item(), t["L"]["loss"], tol)
 
 
 def test_tracking_frame_gradients(tracking):
@@ -101,7 +103,9 @@ def test_tracking_graph_first_update(tracking, flags):
     Adam step moves each coordinate by lr * g / (|g| + eps), which the fused loss's
     ambiguous pixels do not change unless a gradient component is near zero; the first
     moments it leaves are (1 - beta1) g, the pose gradient itself, which must match the
-    oracle's through the same (unmasked) loss to the fused-loss bound 1e-2."""
+    oracle's through the same (unmasked) loss to the gradient bound 1e-3 (a flagged pixel
+    can flip the sign of its upstream gradient on either side; measured 5e-6 here), and
+    the loss to what the flagged pixels' FP32 outcomes allow (loss_tolerance)."""
     t = tracking
     L = t["L"]
     ob = oracle.backward(t["sc"], t["oc"], t["start"], t["op"], L["d_rgb"], L["d_depth"], L["d_sil"])
@@ -118,11 +122,11 @@ def test_tracking_graph_first_update(tracking, flags):
     gs.gs_track_step(R.ctx, prob, gt.c(), tg, poses, adam, hist, 1, ws, nb)
     R.sync()
     np.testing.assert_allclose(poses.cpu().numpy()[0], o_pose, atol=1e-9)
-    assert hist.item() == pytest.approx(L["loss"], rel=2e-3)
+    tol = loss_tolerance(L["loss"], t["ref"], t["sc"], t["cam"], t["start"], t["op"], *t["frame"])
+    assert abs(hist.item() - L["loss"]) <= tol, (hist.item(), L["loss"], tol)
     st = adam.cpu().numpy()[0]
     g6 = np.concatenate([st[0:3], st[6:9]]) / (1.0 - t["op"].beta1)
-    ri, r2 = rel_err(g6, ob["pose6"])
-    assert r2 < 1e-2, (ri, r2)
+    assert_grads_close(g6, ob["pose6"], what="pose gradient through the fused loss")
 
 
 def test_tracking_with_host_upload_equals_device_targets(tracking):
@@ -187,7 +191,7 @@ def batched():
         rgb, depth, prior = frames[frame_of[v]]
         ref = oracle.render(sc, oc, poses0[v], op)
         L = oracle.loss(oc, op, ref["rgb"], ref["depth"], ref["sil"], rgb, depth, prior)
-        refs[v] = (oc, ref, L)
+        refs[v] = (oc, ref, L, (rgb, depth, prior))
     t_rgb = torch.cat([torch.from_numpy(frames[f][0].reshape(-1)) for f in frame_of]).cuda()
     t_depth = torch.cat([torch.from_numpy(frames[f][1].reshape(-1)) for f in frame_of]).cuda()
     t_prior = torch.cat([torch.from_numpy(frames[f][2].reshape(-1)) for f in frame_of]).cuda()
@@ -205,7 +209,7 @@ def test_batched_sampled_views_images_and_loss(batched):
     R.sync()
     off = b["off"]
     for v in b["sample"]:
-        oc, ref, L = b["refs"][v]
+        oc, ref, L, tg_v = b["refs"][v]
         H, W = oc.height, oc.width
         # the flagged share is what the mask's margins predict (closed forms, mask_model)
         m = mask_model.mask_shares(b["sc"], oc, b["poses0"][v], b["op"], ref)
@@ -214,7 +218,8 @@ def test_batched_sampled_views_images_and_loss(batched):
         check_images(out["rgb"][3 * off[v]:3 * off[v + 1]].cpu().numpy(), out["depth"][off[v]:off[v + 1]].cpu().numpy(),
                      out["sil"][off[v]:off[v + 1]].cpu().numpy(), ref, b["sc"], oc, b["poses0"][v], b["op"],
                      what=f"batched view {v}")
-        assert out["loss"][v].item() == pytest.approx(L["loss"], rel=2e-3)
+        tol = loss_tolerance(L["loss"], ref, b["sc"], oc, b["poses0"][v], b["op"], *tg_v)
+        assert abs(out["loss"][v].item() - L["loss"]) <= tol, (v, out["loss"][v].item(), L["loss"], tol)
 
 
 def test_batched_sampled_views_pose_gradient(batched):
@@ -225,7 +230,7 @@ def test_batched_sampled_views_pose_gradient(batched):
     ups = (up[:3 * P], up[3 * P:4 * P], up[4 * P:])
     expect = {}
     for v in b["sample"]:
-        oc, ref, L = b["refs"][v]
+        oc, ref, L, tg_v = b["refs"][v]
         u_rgb, u_d, u_s, _ = _masked_upstream(ref, L)
         ups[0][3 * off[v]:3 * off[v + 1]] = torch.tensor(u_rgb.reshape(-1).astype(np.float32), device="cuda")
         ups[1][off[v]:off[v + 1]] = torch.tensor(u_d.reshape(-1).astype(np.float32), device="cuda")
@@ -260,11 +265,12 @@ def test_batched_graph_first_update(batched):
     R.sync()
     got = poses.cpu().numpy()
     for v in b["sample"]:
-        oc, ref, L = b["refs"][v]
+        oc, ref, L, tg_v = b["refs"][v]
         ob = oracle.backward(b["sc"], oc, b["poses0"][v], b["op"], L["d_rgb"], L["d_depth"], L["d_sil"])
         o_pose, _ = oracle.adam_step(b["poses0"][v], np.zeros(16), ob["pose6"], b["op"])
         np.testing.assert_allclose(got[v], o_pose, atol=1e-9, err_msg=f"view {v}")
-        assert hist[0, v].item() == pytest.approx(L["loss"], rel=2e-3)
+        tol = loss_tolerance(L["loss"], ref, b["sc"], oc, b["poses0"][v], b["op"], *tg_v)
+        assert abs(hist[0, v].item() - L["loss"]) <= tol, (v, hist[0, v].item(), L["loss"], tol)
 
 
 # ---------------------------------------------------------------------------- mapping window

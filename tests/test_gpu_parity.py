@@ -10,8 +10,8 @@ import torch
 
 import oracle
 import mask_model
-from gpu_common import (assert_grads_close, assert_images_close, check_images, gpu_render, ocam, params_pair, rel_err,
-                        split_views)
+from gpu_common import (assert_grads_close, assert_images_close, check_images, gpu_render, loss_tolerance, ocam,
+                        params_pair, split_views)
 from paper_2408_05635_gb300 import gs, scenes
 
 pytestmark = pytest.mark.gpu
@@ -99,8 +99,9 @@ def test_backward_matches_oracle(cube):
 
 
 def test_pose_gradient_from_fused_loss(cube):
-    """Pose gradient through the fused loss (no shared upstream): only ambiguous pixels
-    differ, so the 6-vector agrees to a stated 1e-2 relative."""
+    """Pose gradient through the fused loss (no shared upstream): only a flagged pixel
+    whose upstream gradient takes the other sign on one side can differ; the 6-vector
+    agrees to the gradient bound 1e-3 (measured 7.5e-7)."""
     g, cam, target_pose, rng = cube
     gcfg, op = params_pair()
     sc, oc = oracle.Scene(*g.arrays()), ocam(cam)
@@ -115,8 +116,7 @@ def test_pose_gradient_from_fused_loss(cube):
     gpu_render(R, gt, [cam], [scenes.identity_pose()], targets=tt)
     b = R.backward(gt, params=False)
     R.sync()
-    ri, r2 = rel_err(b["pose_grad"].cpu().numpy()[0], ob["pose6"])
-    assert r2 < 1e-2, (ri, r2)
+    assert_grads_close(b["pose_grad"].cpu().numpy()[0], ob["pose6"], what="pose gradient through the fused loss")
 
 
 def test_multi_view_uneven_resolution():
@@ -242,7 +242,8 @@ def test_track_step_follows_oracle(cube):
     ob = oracle.backward(sc, oc, start, op, L["d_rgb"], L["d_depth"], L["d_sil"])
     o_pose, o_state = oracle.adam_step(start, np.zeros(16), ob["pose6"], op)
     np.testing.assert_allclose(poses.cpu().numpy()[0], o_pose, atol=1e-9)
-    assert hist.item() == pytest.approx(L["loss"], rel=2e-3)
+    tol = loss_tolerance(L["loss"], ref, sc, cam, start, op, t_rgb, t_depth, None)
+    assert abs(hist.item() - L["loss"]) <= tol, (hist.item(), L["loss"], tol)
     hist = torch.zeros(9, 1, dtype=torch.float64, device="cuda")
     gs.gs_track_step(R.ctx, prob, gt.c(), targets, poses, adam, hist, 9, ws, nb)
     R.sync()
@@ -283,16 +284,18 @@ def test_track_step_converges_on_room():
 def test_mapping_window_grads_sum_over_views():
     """Mapping (Sec. III-C): parameter gradients of the combined loss summed over a
     window of keyframes, processed a chunk of views at a time (lists recomputed per
-    chunk).  Against the oracle's per-view gradients of the same loss, summed (the fused
-    loss differentiates every pixel, so the < 1 % ambiguous pixels enter both sides and
-    the bound is 1e-2 in the 2-norm); and chunk sizes 1 and 4 agree to float-atomic order."""
+    chunk).  Against the oracle's per-view gradients of the same loss, summed, to the
+    gradient bound 1e-3 (the fused loss differentiates every pixel, flagged ones too, whose
+    upstream sign may differ; measured 3e-5), each view's loss to what its flagged pixels'
+    FP32 outcomes allow (loss_tolerance); and chunk sizes 1 and 4 agree to float-atomic
+    order."""
     g = scenes.room_scene(60_000, seed=3)
     cam = scenes.Cam(150.0, 150.0, 79.5, 44.5, 160, 90)
     poses_np = scenes.mapping_keyframes(4)
     gcfg, op = params_pair()
     sc, oc = oracle.Scene(*g.arrays()), ocam(cam)
     rng = np.random.default_rng(5)
-    targets, ref_grads, ref_loss = [], np.zeros((g.n, 14)), []
+    targets, ref_grads, ref_loss, loss_tol = [], np.zeros((g.n, 14)), [], []
     for pose in poses_np:
         t = oracle.render(sc, oc, scenes.perturb_pose(pose, rng, 0.5, 0.01), op)
         prior = scenes.prior_from_depth(t["depth"], rng, 0.03, 0.08)
@@ -301,6 +304,7 @@ def test_mapping_window_grads_sum_over_views():
         L = oracle.loss(oc, op, r["rgb"], r["depth"], r["sil"], t_rgb, t_depth, prior)
         ref_grads += oracle.backward(sc, oc, pose, op, L["d_rgb"], L["d_depth"], L["d_sil"])["grads"]
         ref_loss.append(L["loss"])
+        loss_tol.append(loss_tolerance(L["loss"], r, sc, cam, pose, op, t_rgb, t_depth, prior))
         targets.append(tuple(torch.tensor(a.reshape(-1), device="cuda") for a in (t_rgb, t_depth, prior)))
     gt = gs.GaussianTensors.from_numpy(g)
     poses = torch.tensor(np.stack(poses_np), dtype=torch.float64, device="cuda")
@@ -309,11 +313,10 @@ def test_mapping_window_grads_sum_over_views():
         R = gs.Rasterizer(gcfg)
         outs[chunk] = R.mapping_grads(gt, [cam] * 4, poses, targets, chunk=chunk)
         R.sync()
-    np.testing.assert_allclose(outs[2]["loss"].cpu().numpy(), ref_loss, rtol=2e-3)
+    assert np.all(np.abs(outs[2]["loss"].cpu().numpy() - np.asarray(ref_loss)) <= np.asarray(loss_tol)), loss_tol
     for name, lo, hi in GRAD_KEYS:
         got = outs[2]["grads"][name].cpu().numpy().reshape(g.n, -1)
-        ri, r2 = rel_err(got, ref_grads[:, lo:hi])
-        assert r2 < 1e-2, (name, ri, r2)
+        assert_grads_close(got, ref_grads[:, lo:hi], what=name)
         a = outs[1]["grads"][name].cpu().numpy()
         b = outs[4]["grads"][name].cpu().numpy()
         assert np.abs(a - b).max() <= 1e-5 * max(1e-30, np.abs(a).max()), name
