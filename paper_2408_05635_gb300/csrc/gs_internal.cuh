@@ -66,7 +66,7 @@ struct DevHeader {
     unsigned long long bwd_evals;    // footprints evaluated by k_backward
     unsigned long long bwd_contrib;  // ... of which were differentiated
     uint32_t max_tile;               // longest tile list of the projection
-    uint32_t pad0;
+    uint32_t n_big;                  // records listed in WsPtrs::big (the scan copies the count)
     unsigned long long pad1;
 };
 static_assert(sizeof(DevHeader) == 64, "DevHeader layout");
@@ -122,6 +122,9 @@ struct WsPtrs {
     uint32_t *tile_start;  // T x S + 1, exclusive scan of the counts
     uint32_t *cursor;      // T x S, emission cursors
     uint32_t *tile_order;  // T, tiles by descending list length (launch order of the tile kernels)
+    uint32_t *big;         // V x nblk x 256: records whose tile rectangle has more than kSoloTiles
+                           // tiles, listed by k_project (count at tile_cnt[T x S], moved to
+                           // hdr->n_big by the scan) and emitted by k_emit's extra blocks
     Rec *rec;              // V x nblk x 256 record slots
     RecGrad *rec_grad;     // same slots
     unsigned long long *keys;  // pair_capacity

@@ -43,14 +43,14 @@ __device__ __forceinline__ bool tile_hit(const ViewInfo &vi, float4 A, float4 B,
 // record's A, record's tag) runs once for every tile the support meets.
 constexpr int kSoloTiles = 24;
 
-template <bool SOLO = true, class Body>
+template <class Body>
 __device__ __forceinline__ void record_tiles(bool mine, const ViewInfo &vi, float4 A, float4 B, uint32_t tag, int lane,
                                              Body &&body) {
     int tx0 = 1, tx1 = 0, ty0 = 1, ty1 = 0;
     const bool has = mine && record_rect(vi, A, B, tx0, tx1, ty0, ty1);
     const int rw = tx1 - tx0 + 1;
     const int count = has ? rw * (ty1 - ty0 + 1) : 0;
-    if (SOLO && has && count <= kSoloTiles) {
+    if (has && count <= kSoloTiles) {
         const RowSpan span = row_span_setup(A.x, A.y, B.x, B.y, B.z, B.w);
         for (int ty = ty0; ty <= ty1; ++ty) {
             int a0, a1;
@@ -233,7 +233,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(WsPtrs ws, Dims d) 
         }
         carry += total;
     }
-    if (tid == 0) ws.tile_start[TS] = (uint32_t)min(carry, (unsigned long long)0xffffffffu);
+    if (tid == 0) {
+        ws.tile_start[TS] = (uint32_t)min(carry, (unsigned long long)0xffffffffu);
+        ws.hdr->n_big = ws.tile_cnt[TS];  // the large records k_project listed, zeroed for the next pass
+        ws.tile_cnt[TS] = 0u;
+    }
     __syncthreads();
     {  // exclusive scan of the buckets, one bucket per thread
         uint32_t total;
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
     const int64_t i = (int64_t)b * kBlock + tid;
     const Settings &S = L.s;
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, C = A;
-    bool vis = false;
+    bool vis = false, big = false;
     if (i < L.d.n) {
         const float mx = __ldg(L.g.means + 3 * i), my = __ldg(L.g.means + 3 * i + 1), mz = __ldg(L.g.means + 3 * i + 2);
         const float x = cam_coord(sRt, 0, mx, my, mz);
@@ -395,6 +399,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
                                     __uint_as_float((uint32_t)((int64_t)v * L.d.n + i)));
                     int tx0, tx1, ty0, ty1;
                     vis = record_rect(vi, A, B, tx0, tx1, ty0, ty1);
+                    big = vis && (tx1 - tx0 + 1) * (ty1 - ty0 + 1) > kSoloTiles;
                 }
             }
         }
@@ -421,6 +426,8 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
         RecGrad z;
         z.g0 = z.g1 = z.g2 = make_float4(0.f, 0.f, 0.f, 0.f);
         L.ws.rec_grad[rec] = z;
+        // a large tile rectangle: listed for k_emit's extra blocks (at most one entry per record)
+        if (big) L.ws.big[atomicAdd(L.ws.tile_cnt + L.d.T * L.d.S, 1u)] = rec;
     }
     // per-(tile, sub-bucket) pair counts, the warp sharing each visible Gaussian's tiles
     uint32_t *cnt = L.ws.tile_cnt;
@@ -474,6 +481,40 @@ static_assert(kCell % kEmitThreads == 0 && kEmitThreads % 32 == 0, "emission blo
 // One key per (record, tile met): depth bits (positive floats sort as unsigned ints) in
 // the high word, the record in the low word, stored at the next free slot of the tile's
 // sub-bucket.  One block per cell, one thread per record (record_tiles).
+// Blocks of k_emit after the cells' blocks: each warp emits the pairs of the records that
+// k_project listed as large (ws.big), a record at a time with one tile of its rectangle per
+// lane, so the few records close to the camera are spread over many warps instead of
+// lengthening the warps of the cells that hold them.
+constexpr int kBigBlocks = 256;
+
+__device__ __forceinline__ void emit_big(const WsPtrs &ws, const Dims &d, uint32_t gwarp, int lane) {
+    const uint32_t nbig = ws.hdr->n_big;
+    const uint32_t slots = rec_slots(d);
+    const bool radix = (d.flags & GS_SCHED_RADIX) != 0;
+    for (uint32_t k = gwarp; k < nbig; k += (uint32_t)kBigBlocks * (kEmitThreads / 32)) {
+        const uint32_t r = ws.big[k];
+        if (r >= slots) continue;  // never written past the records (one entry per record)
+        const Rec rec = ws.rec[r];
+        const ViewInfo vi = ws.views[r / ((uint32_t)d.nblk * (uint32_t)kCell)];
+        const uint32_t sub = (uint32_t)((uint64_t)__float_as_uint(rec.c.w) % (uint64_t)d.n) & (d.S - 1);
+        int tx0, tx1, ty0, ty1;
+        if (!record_rect(vi, rec.a, rec.b, tx0, tx1, ty0, ty1)) continue;
+        const int rw = tx1 - tx0 + 1, count = rw * (ty1 - ty0 + 1);
+        const float ia = __fdividef(1.f, rec.b.x), ic = __fdividef(1.f, rec.b.z);
+        for (int t = lane; t < count; t += 32) {
+            const int ty = ty0 + t / rw, tx = tx0 + t % rw;
+            if (!tile_hit(vi, rec.a, rec.b, ia, ic, tx, ty)) continue;
+            const uint32_t tile = vi.tile_base + (uint32_t)(ty * vi.tiles_x + tx);
+            const uint32_t bucket = tile * d.S + sub;
+            const uint32_t slot = atomicAdd(ws.cursor + bucket, 1u);
+            if (slot < ws.tile_start[bucket + 1] && slot < d.pair_cap)
+                put_pair(ws, radix, slot, tile, __float_as_uint(rec.a.z), r);
+            else
+                atomicOr(ws.err, (uint32_t)kErrPairs);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws, Dims d) {
     // No early griddep_launch_dependents here: the tile compositor's blocks would then be
     // placed while the emission still runs, on whichever SMs free first, and the longest
@@ -481,6 +522,11 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws
     // 131 us on the 640 x 480 / 200k frame); launched as the emission's blocks exit, they
     // spread over all SMs.
     griddep_wait();  // the predecessor's results are visible from here on
+    const uint32_t cell_blocks = (uint32_t)d.V * (uint32_t)d.nblk * (uint32_t)(kCell / kEmitThreads);
+    if (blockIdx.x >= cell_blocks) {
+        emit_big(ws, d, (blockIdx.x - cell_blocks) * (kEmitThreads / 32) + (threadIdx.x >> 5), threadIdx.x & 31);
+        return;
+    }
     // kCell / kEmitThreads blocks per cell, each taking a quarter of the cell's slots: a
     // cell full of visible Gaussians (neighbours in a map built frame by frame) is spread
     // over several SMs instead of running as one long block, and empty quarters leave at once
@@ -502,7 +548,6 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws
         B = rec.b;
         sub = (uint32_t)((uint64_t)__float_as_uint(rec.c.w) % (uint64_t)d.n) & (d.S - 1);
     }
-    const uint32_t rbase = cell * kCell + (slot_id & ~31u);
     const bool radix = (d.flags & GS_SCHED_RADIX) != 0;
     // small rectangles: this lane alone, slot atomics issued eight at a time before the
     // dependent stores, so a record waits for about one atomic round trip per eight tiles
@@ -541,20 +586,13 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws
                 }
         }
     }
-    // large rectangles: the warp splits them
-    record_tiles<false>(mine, vi, A, B, sub, lane, [&](int src, uint32_t tile, float4 As, uint32_t sb) {
-        const uint32_t bucket = tile * d.S + sb;
-        const uint32_t slot = atomicAdd(ws.cursor + bucket, 1u);
-        if (slot < ws.tile_start[bucket + 1] && slot < d.pair_cap)
-            put_pair(ws, radix, slot, tile, __float_as_uint(As.z), rbase + (uint32_t)src);
-        else
-            atomicOr(ws.err, (uint32_t)kErrPairs);
-    });
+    // large rectangles (listed by k_project) are emitted by the blocks after the cells' (emit_big)
 }
 
 cudaError_t launch_emit(const WsPtrs &ws, const Dims &d, cudaStream_t st) {
     const uint32_t cells = (uint32_t)d.V * (uint32_t)d.nblk;
-    const cudaError_t e = launch_dep(k_emit, dim3(cells * (uint32_t)(kCell / kEmitThreads)), dim3(kEmitThreads), st, ws, d);
+    const cudaError_t e = launch_dep(k_emit, dim3(cells * (uint32_t)(kCell / kEmitThreads) + kBigBlocks),
+                                     dim3(kEmitThreads), st, ws, d);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
