@@ -280,6 +280,12 @@ cudaError_t launch_scan_tiles(const WsPtrs &ws, const Dims &d, cudaStream_t st) 
     return launch_dep(k_scan_tiles, dim3(1), dim3(kScanThreads), st, ws, d);
 }
 
+// A block's large records (more than kSoloTiles candidate tiles) are counted by all its
+// threads at once, each taking (record, tile) pairs of their concatenated rectangles,
+// instead of one record after the other by the warp that holds it; kBigPerBlock of them,
+// a further one by its warp.
+constexpr int kBigPerBlock = 64;
+
 template <int DT, bool ISO>
 __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
     griddep_wait();  // the predecessor's results are visible from here on
@@ -289,10 +295,14 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
     __shared__ float sRt[12];
     __shared__ ViewInfo sv;
     __shared__ uint32_t warp_off[kWarps];
+    __shared__ float4 sbA[kBigPerBlock], sbB[kBigPerBlock];
+    __shared__ int4 sbR[kBigPerBlock];         // first tile column and row, columns, candidates
+    __shared__ uint32_t sbPre[kBigPerBlock + 1], sbSub[kBigPerBlock], s_nbig;
     const uint32_t cell = (uint32_t)v * (uint32_t)L.d.nblk + (uint32_t)b;
     if (tid == 0) {
         load_pose(L.poses + 7 * v, sRt);
         sv = L.ws.views[v];
+        s_nbig = 0u;
     }
     __syncthreads();
     if (b == 0 && tid < 12) L.ws.view_rt[12 * v + tid] = sRt[tid];
@@ -304,6 +314,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
     const Settings &S = L.s;
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, C = A;
     bool vis = false, big = false;
+    int4 rect = make_int4(0, 0, 0, 0);
     if (i < L.d.n) {
         const float mx = __ldg(L.g.means + 3 * i), my = __ldg(L.g.means + 3 * i + 1), mz = __ldg(L.g.means + 3 * i + 2);
         const float x = cam_coord(sRt, 0, mx, my, mz);
@@ -400,6 +411,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
                     int tx0, tx1, ty0, ty1;
                     vis = record_rect(vi, A, B, tx0, tx1, ty0, ty1);
                     big = vis && (tx1 - tx0 + 1) * (ty1 - ty0 + 1) > kSoloTiles;
+                    rect = make_int4(tx0, ty0, tx1 - tx0 + 1, (tx1 - tx0 + 1) * (ty1 - ty0 + 1));
                 }
             }
         }
@@ -417,6 +429,19 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
         }
         L.ws.cell_cnt[cell] = run;
     }
+    // the block's large records, for the block-wide count below
+    const uint32_t nsub = L.d.S;
+    bool mine_solo = vis;
+    if (big) {
+        const uint32_t k = atomicAdd(&s_nbig, 1u);
+        if (k < (uint32_t)kBigPerBlock) {
+            sbA[k] = A;
+            sbB[k] = B;
+            sbR[k] = rect;
+            sbSub[k] = (uint32_t)i & (nsub - 1);
+            mine_solo = false;
+        }
+    }
     __syncthreads();
     if (vis) {
         const uint32_t rec = cell * kCell + warp_off[warp] + __popc(ballot & ((1u << lane) - 1u));
@@ -429,10 +454,44 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
         // a large tile rectangle: listed for k_emit's extra blocks (at most one entry per record)
         if (big) L.ws.big[atomicAdd(L.ws.tile_cnt + L.d.T * L.d.S, 1u)] = rec;
     }
-    // per-(tile, sub-bucket) pair counts, the warp sharing each visible Gaussian's tiles
+    // per-(tile, sub-bucket) pair counts: the block's listed large records by all threads,
+    // every other visible record by its own lane (or, above kSoloTiles, its warp)
     uint32_t *cnt = L.ws.tile_cnt;
-    const uint32_t nsub = L.d.S;
-    record_tiles(vis, vi, A, B, (uint32_t)i & (nsub - 1), lane, [&](int, uint32_t tile, float4, uint32_t sub) {
+    const uint32_t nbig = min(s_nbig, (uint32_t)kBigPerBlock);  // block-uniform
+    if (nbig) {
+        if (warp == 0) {  // exclusive prefix of the rectangles' candidate counts
+            uint32_t run = 0;
+            for (uint32_t base = 0; base < nbig; base += 32) {
+                const uint32_t e = base + (uint32_t)lane;
+                const uint32_t c = e < nbig ? (uint32_t)sbR[e].w : 0u;
+                uint32_t incl = c;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += y;
+                }
+                if (e < nbig) sbPre[e] = run + incl - c;
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) sbPre[nbig] = run;
+        }
+        __syncthreads();
+        const uint32_t total = sbPre[nbig];
+        for (uint32_t f = (uint32_t)tid; f < total; f += kBlock) {
+            int lo = 0, hi = (int)nbig - 1;  // the last entry whose prefix is at most f
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sbPre[mid] <= f) lo = mid; else hi = mid - 1;
+            }
+            const int4 R = sbR[lo];
+            const int t = (int)(f - sbPre[lo]);
+            const int ty = R.y + t / R.z, tx = R.x + t % R.z;
+            const float4 Ab = sbA[lo], Bb = sbB[lo];
+            if (tile_hit(vi, Ab, Bb, __fdividef(1.f, Bb.x), __fdividef(1.f, Bb.z), tx, ty))
+                red_add(cnt + (vi.tile_base + (uint32_t)(ty * vi.tiles_x + tx)) * nsub + sbSub[lo], 1u);
+        }
+    }
+    record_tiles(mine_solo, vi, A, B, (uint32_t)i & (nsub - 1), lane, [&](int, uint32_t tile, float4, uint32_t sub) {
         red_add(cnt + tile * nsub + sub, 1u);
     });
 }
