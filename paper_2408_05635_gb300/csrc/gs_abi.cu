@@ -40,7 +40,7 @@ uint32_t max_sub(uint64_t T) {
 
 struct Layout {
     size_t err, hdr, tile_cnt, zero_end;
-    size_t views, view_rt, cell_cnt, tile_start, cursor, tile_order, big, rec, rec_grad, keys, sorted, t_final, n_last,
+    size_t views, view_rt, cell_cnt, tile_start, cursor, tile_order, big, big_listed, rec, rec_grad, keys, sorted, t_final, n_last,
         upstream, tile_loss, pose_part, rkeys, rvals, rhist, rtotal, total;
 };
 
@@ -301,7 +301,8 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     L.tile_start = take(sizeof(uint32_t) * ((size_t)lay_cnt + 1));
     L.cursor = take(sizeof(uint32_t) * ((size_t)lay_cnt + 1));
     L.tile_order = take(sizeof(uint32_t) * (size_t)lay_tiles);
-    L.big = take(sizeof(uint32_t) * cells * kCell);
+    L.big = take(sizeof(uint32_t) * kBigListCap);
+    L.big_listed = take(cells * kCell);
     L.rec = take(sizeof(Rec) * cells * kCell);
     L.rec_grad = take(sizeof(RecGrad) * cells * kCell);
     L.keys = take(sizeof(unsigned long long) * (size_t)d.pair_cap);
@@ -333,6 +334,7 @@ WsPtrs ws_ptrs(void *base, const Layout &L) {
     w.cursor = reinterpret_cast<uint32_t *>(b + L.cursor);
     w.tile_order = reinterpret_cast<uint32_t *>(b + L.tile_order);
     w.big = reinterpret_cast<uint32_t *>(b + L.big);
+    w.big_listed = reinterpret_cast<uint8_t *>(b + L.big_listed);
     w.rec = reinterpret_cast<Rec *>(b + L.rec);
     w.rec_grad = reinterpret_cast<RecGrad *>(b + L.rec_grad);
     w.keys = reinterpret_cast<unsigned long long *>(b + L.keys);

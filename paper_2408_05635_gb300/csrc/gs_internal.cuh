@@ -37,6 +37,8 @@ constexpr int kBatch = 256;               // default (and largest) compositing b
 // bytes: NB must not exceed 256 nor the tile's thread count (the host checks the latter).
 static_assert(kBatch <= kTilePix && kBatch <= 256, "a batch stages at most one Gaussian per tile thread");
 constexpr int kSubMax = 4;                // most per-tile sub-buckets a workspace is laid out for
+constexpr int kBigCell = 2;               // large records a cell needs to list them for k_emit's extra blocks
+constexpr int kBigListCap = 2048;         // entries of that list (a listed record per extra warp and pass: 4)
 
 enum ErrFlag : uint32_t { kErrRecords = 1u, kErrPairs = 2u, kErrTimeout = 4u };
 
@@ -122,9 +124,11 @@ struct WsPtrs {
     uint32_t *tile_start;  // T x S + 1, exclusive scan of the counts
     uint32_t *cursor;      // T x S, emission cursors
     uint32_t *tile_order;  // T, tiles by descending list length (launch order of the tile kernels)
-    uint32_t *big;         // V x nblk x 256: records whose tile rectangle has more than kSoloTiles
-                           // tiles, listed by k_project (count at tile_cnt[T x S], moved to
-                           // hdr->n_big by the scan) and emitted by k_emit's extra blocks
+    uint32_t *big;         // kBigListCap: large records of crowded cells (more than kSoloTiles
+                           // candidate tiles, kBigCell of them in one cell), listed by k_project
+                           // (count at tile_cnt[T x S], moved to hdr->n_big by the scan) and
+                           // emitted by k_emit's extra blocks
+    uint8_t *big_listed;   // V x nblk x 256: 1 where the record is in `big` (its cell's warps skip it)
     Rec *rec;              // V x nblk x 256 record slots
     RecGrad *rec_grad;     // same slots
     unsigned long long *keys;  // pair_capacity

@@ -31,7 +31,7 @@ constexpr int64_t kMaxCells = (kMaxGaussians + kBlock - 1) / kBlock;
 constexpr int64_t kMaxTiles = kMaxPixels / (kTile * kTile) + 2 * (kMaxPixels / kTile) + 2;
 constexpr size_t kScratchBytes =
     up(4) + up(sizeof(DevHeader)) + up(4 * (4 * kMaxTiles + 1)) + up(sizeof(ViewInfo)) + up(12 * 4) +
-    up(4 * kMaxCells) + 2 * up(4 * (4 * kMaxTiles + 1)) + up(4 * kMaxTiles) + up(4 * kMaxCells * kCell) +
+    up(4 * kMaxCells) + 2 * up(4 * (4 * kMaxTiles + 1)) + up(4 * kMaxTiles) + up(4 * kBigListCap) + up(kMaxCells * kCell) +
     2 * up(48 * kMaxCells * kCell) +
     up(8 * kMaxPairs) + up(4 * kMaxPairs) + up(4 * kMaxPixels) + up(4 * kMaxPixels) + up(20 * kMaxPixels) +
     up(8 * kMaxTiles) + up(48 * kMaxCells);
@@ -137,7 +137,8 @@ extern "C" gs_status gs_render_static(const gs_config *cfg, const gs_gaussians *
     w.tile_start = reinterpret_cast<uint32_t *>(take(4 * ((size_t)d.T * d.S + 1)));
     w.cursor = reinterpret_cast<uint32_t *>(take(4 * ((size_t)d.T * d.S + 1)));
     w.tile_order = reinterpret_cast<uint32_t *>(take(4 * (size_t)d.T));
-    w.big = reinterpret_cast<uint32_t *>(take(4 * (size_t)d.nblk * kCell));
+    w.big = reinterpret_cast<uint32_t *>(take(4 * (size_t)kBigListCap));
+    w.big_listed = reinterpret_cast<uint8_t *>(take((size_t)d.nblk * kCell));
     w.rec = reinterpret_cast<Rec *>(take(sizeof(Rec) * (size_t)d.nblk * kCell));
     w.rec_grad = reinterpret_cast<RecGrad *>(take(sizeof(RecGrad) * (size_t)d.nblk * kCell));
     w.keys = reinterpret_cast<unsigned long long *>(take(8 * (size_t)d.pair_cap));

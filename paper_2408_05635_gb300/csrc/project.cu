@@ -43,14 +43,14 @@ __device__ __forceinline__ bool tile_hit(const ViewInfo &vi, float4 A, float4 B,
 // record's A, record's tag) runs once for every tile the support meets.
 constexpr int kSoloTiles = 24;
 
-template <class Body>
+template <bool SOLO = true, class Body>
 __device__ __forceinline__ void record_tiles(bool mine, const ViewInfo &vi, float4 A, float4 B, uint32_t tag, int lane,
                                              Body &&body) {
     int tx0 = 1, tx1 = 0, ty0 = 1, ty1 = 0;
     const bool has = mine && record_rect(vi, A, B, tx0, tx1, ty0, ty1);
     const int rw = tx1 - tx0 + 1;
     const int count = has ? rw * (ty1 - ty0 + 1) : 0;
-    if (has && count <= kSoloTiles) {
+    if (SOLO && has && count <= kSoloTiles) {
         const RowSpan span = row_span_setup(A.x, A.y, B.x, B.y, B.z, B.w);
         for (int ty = ty0; ty <= ty1; ++ty) {
             int a0, a1;
@@ -451,8 +451,17 @@ __global__ void __launch_bounds__(kBlock, 6) k_project(ProjectLaunch L) {
         RecGrad z;
         z.g0 = z.g1 = z.g2 = make_float4(0.f, 0.f, 0.f, 0.f);
         L.ws.rec_grad[rec] = z;
-        // a large tile rectangle: listed for k_emit's extra blocks (at most one entry per record)
-        if (big) L.ws.big[atomicAdd(L.ws.tile_cnt + L.d.T * L.d.S, 1u)] = rec;
+        // the large records of a cell that holds kBigCell or more: listed for k_emit's extra
+        // blocks while the list has room (the cell's warps emit the others)
+        uint8_t listed = 0;
+        if (big && s_nbig >= (uint32_t)kBigCell) {
+            const uint32_t k = atomicAdd(L.ws.tile_cnt + L.d.T * L.d.S, 1u);
+            if (k < (uint32_t)kBigListCap) {
+                L.ws.big[k] = rec;
+                listed = 1;
+            }
+        }
+        L.ws.big_listed[rec] = listed;
     }
     // per-(tile, sub-bucket) pair counts: the block's listed large records by all threads,
     // every other visible record by its own lane (or, above kSoloTiles, its warp)
@@ -540,14 +549,14 @@ static_assert(kCell % kEmitThreads == 0 && kEmitThreads % 32 == 0, "emission blo
 // One key per (record, tile met): depth bits (positive floats sort as unsigned ints) in
 // the high word, the record in the low word, stored at the next free slot of the tile's
 // sub-bucket.  One block per cell, one thread per record (record_tiles).
-// Blocks of k_emit after the cells' blocks: each warp emits the pairs of the records that
-// k_project listed as large (ws.big), a record at a time with one tile of its rectangle per
-// lane, so the few records close to the camera are spread over many warps instead of
-// lengthening the warps of the cells that hold them.
+// Blocks of k_emit after the cells' blocks: each warp emits the pairs of the large records
+// k_project listed (those of cells crowded with them, ws.big), a record at a time with one
+// tile of its rectangle per lane, so the records close to the camera are spread over many
+// warps instead of lengthening the few warps of the cells that hold them.
 constexpr int kBigBlocks = 256;
 
 __device__ __forceinline__ void emit_big(const WsPtrs &ws, const Dims &d, uint32_t gwarp, int lane) {
-    const uint32_t nbig = ws.hdr->n_big;
+    const uint32_t nbig = min(ws.hdr->n_big, (uint32_t)kBigListCap);
     const uint32_t slots = rec_slots(d);
     const bool radix = (d.flags & GS_SCHED_RADIX) != 0;
     for (uint32_t k = gwarp; k < nbig; k += (uint32_t)kBigBlocks * (kEmitThreads / 32)) {
@@ -645,7 +654,18 @@ __global__ void __launch_bounds__(kEmitThreads, kEmitMinBlocks) k_emit(WsPtrs ws
                 }
         }
     }
-    // large rectangles (listed by k_project) are emitted by the blocks after the cells' (emit_big)
+    // large rectangles: those k_project listed are emitted by the blocks after the cells'
+    // (emit_big); the warp splits the others
+    const uint32_t rbase = cell * kCell + (slot_id & ~31u);
+    record_tiles<false>(mine && !ws.big_listed[r], vi, A, B, sub, lane,
+                        [&](int src, uint32_t tile, float4 As, uint32_t sb) {
+        const uint32_t bucket = tile * d.S + sb;
+        const uint32_t slot = atomicAdd(ws.cursor + bucket, 1u);
+        if (slot < ws.tile_start[bucket + 1] && slot < d.pair_cap)
+            put_pair(ws, radix, slot, tile, __float_as_uint(As.z), rbase + (uint32_t)src);
+        else
+            atomicOr(ws.err, (uint32_t)kErrPairs);
+    });
 }
 
 cudaError_t launch_emit(const WsPtrs &ws, const Dims &d, cudaStream_t st) {
