@@ -156,6 +156,35 @@ def test_long_tile_list_uses_global_sort():
     assert_images_close(out["depth"].reshape(48, 48), ref["depth"], ref["amb"], what="depth")
 
 
+def test_large_footprints_listed_and_unlisted():
+    """Key emission of large tile rectangles (more than 24 candidate tiles): 3,000 Gaussians
+    a metre in front of a 160 x 120 camera, most covering about 6 x 6 of its 16 x 16 tiles,
+    so every cell is crowded with them and the bounded list for k_emit's extra blocks
+    (2,048 records) overflows: the listed records are emitted by those blocks, the rest by
+    their cells' warps, and k_project counts both kinds block-wide.  Images against the
+    oracle, and no capacity flag."""
+    rng = np.random.default_rng(17)
+    n = 3000
+    means = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.45, 0.45, n), rng.uniform(1.0, 1.6, n)], 1)
+    g = scenes.Gaussians(means.astype(np.float32), rng.normal(size=(n, 4)).astype(np.float32),
+                         rng.normal(-1.9, 0.15, (n, 3)).astype(np.float32),
+                         rng.normal(-1.0, 0.5, n).astype(np.float32), rng.uniform(size=(n, 3)).astype(np.float32))
+    cam = scenes.Cam(140.0, 140.0, 79.5, 59.5, 160, 120)
+    gcfg, op = params_pair()
+    R = gs.Rasterizer(gcfg)
+    gt = gs.GaussianTensors.from_numpy(g)
+    out, prob, _, counts = gpu_render(R, gt, [cam], [scenes.identity_pose()], margin=2.0)
+    assert counts.err_flags == 0
+    pr = oracle.project(oracle.Scene(*g.arrays()), ocam(cam), scenes.identity_pose(), op)
+    b = pr["box"][pr["valid"]]  # pixel boxes, clipped to the image
+    tiles = (b[:, 1] // 16 - b[:, 0] // 16 + 1) * (b[:, 3] // 16 - b[:, 2] // 16 + 1)
+    assert (tiles > 24).sum() > 2048, (tiles > 24).sum()
+    sc = oracle.Scene(*g.arrays())
+    ref = oracle.render(sc, ocam(cam), scenes.identity_pose(), op)
+    check_images(out["rgb"], out["depth"], out["sil"], ref, sc, cam, scenes.identity_pose(), op,
+                 what="large footprints")
+
+
 def test_empty_and_culled_scenes():
     gcfg, op = params_pair()
     R = gs.Rasterizer(gcfg)
