@@ -704,7 +704,9 @@ bool pinned_host(const void *p) {
 }
 
 // The upload branch of gs_track_step_upload: src -> targets on ctx->up_stream after
-// everything enqueued on q so far; ctx->up_join marks its end.
+// everything enqueued on q so far (the colour planes, depth and prior in three copies, one
+// after the other: several copies at once were slower here, 51 against 31 us for the
+// 6.1 MB frame); join_upload makes q wait for it.
 cudaError_t fork_upload(gs_ctx *ctx, const gs_targets *targets, const gs_host_targets *src, uint32_t P,
                         cudaStream_t q) {
     cudaError_t e = cudaSuccess;
@@ -730,6 +732,8 @@ cudaError_t fork_upload(gs_ctx *ctx, const gs_targets *targets, const gs_host_ta
     return cudaEventRecord(ctx->up_join, ctx->up_stream);
 }
 
+cudaError_t join_upload(gs_ctx *ctx, cudaStream_t q) { return cudaStreamWaitEvent(q, ctx->up_join, 0); }
+
 gs_status track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const gs_targets *targets,
                      const gs_host_targets *src, double *poses, double *adam_state, double *loss_hist, int32_t iters,
                      void *ws, size_t ws_bytes, void *stream) {
@@ -752,18 +756,20 @@ gs_status track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
         return fail(ctx, GS_ERR_WORKSPACE, "workspace NULL, smaller than gs_workspace_size or not 256-byte aligned");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const WsPtrs w = ws_ptrs(ws, pr.lay);
-    // flags latch over all iterations of this call
-    cudaError_t e = upload_views(pr, w, ws, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "view upload");
     GaussPtrs gp{g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb};
 
     auto enqueue_all = [&](cudaStream_t q) -> cudaError_t {
+        // the frame's upload runs beside the view upload and the first projection, scan and
+        // emission
+        cudaError_t r0 = src ? fork_upload(ctx, targets, src, pr.d.P, q) : cudaSuccess;
+        if (r0 != cudaSuccess) return r0;
+        // the view table and the per-call reset, as the graph's first node (its arguments
+        // are part of the graph's key); flags latch over all iterations of the call
+        if ((r0 = upload_views(pr, w, ws, q)) != cudaSuccess) return r0;
         for (int it = 0; it < iters; ++it) {
             cudaError_t r = cudaSuccess;
-            // the frame's upload runs beside the first projection, scan and emission
-            if (it == 0 && src && (r = fork_upload(ctx, targets, src, pr.d.P, q)) != cudaSuccess) return r;
             if ((r = enqueue_project(ctx, pr, w, gp, g->dtype_attr, poses, q)) != cudaSuccess) return r;
-            if (it == 0 && src && (r = cudaStreamWaitEvent(q, ctx->up_join, 0)) != cudaSuccess) return r;
+            if (it == 0 && src && (r = join_upload(ctx, q)) != cudaSuccess) return r;
             if ((r = enqueue_compositing(ctx, pr, w, targets, q)) != cudaSuccess) return r;
             BprojLaunch J;
             J.ws = w;
@@ -792,7 +798,7 @@ gs_status track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
     };
 
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    e = cudaStreamIsCapturing(s, &cap);
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream query");
     reset_marks(ctx);
     if (cap != cudaStreamCaptureStatusNone) {

@@ -132,10 +132,12 @@ def test_tracking_graph_first_update(tracking, flags):
 def test_tracking_with_host_upload_equals_device_targets(tracking):
     """gs_track_step_upload: the frame in page-locked host memory is copied into the
     device targets beside the first iteration's binning.  Five iterations from the start
-    pose give the poses, losses and Adam state of gs_track_step on the device frame (to
-    the run-to-run spread of the FP32 gradient atomics, whose order is not fixed: 1e-6
-    relative), the device targets hold the host frame afterwards (they start as NaN), and
-    a frame in ordinary (pageable) host memory is refused."""
+    pose give the poses, losses and Adam state of gs_track_step on the device frame to the
+    run-to-run spread of the FP32 gradient atomics, whose order is not fixed (poses 1e-7
+    absolute: Adam's step lr g / (|g| + eps) moves a coordinate with a near-zero gradient
+    by that noise; losses 1e-6 relative; moments 1e-4 relative), the device targets hold the
+    host frame afterwards (they start as NaN), and a frame in ordinary (pageable) host
+    memory is refused."""
     t = tracking
     R = gs.Rasterizer(gs.Config())
     R.set_schedule(16, 16, 4, 256, 256, gs.GS_SCHED_FUSED)
@@ -166,8 +168,10 @@ def test_tracking_with_host_upload_equals_device_targets(tracking):
             bad = gs.gs_host_targets(*(x.data_ptr() for x in pageable))
             with pytest.raises(gs.GsError):
                 gs.gs_track_step_upload(R.ctx, prob, gt.c(), tg, bad, poses, adam, hist, 1, ws, nb)
-    for a, b in zip(out[0], out[1]):
-        np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-12)
+    (p0, h0, a0), (p1, h1, a1) = out
+    np.testing.assert_allclose(p1, p0, rtol=0, atol=1e-7)
+    np.testing.assert_allclose(h1, h0, rtol=1e-6)
+    np.testing.assert_allclose(a1, a0, rtol=1e-4, atol=1e-9 * np.abs(a0).max())
 
 
 # ---------------------------------------------------------------------------- batched hypotheses
