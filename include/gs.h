@@ -222,22 +222,28 @@ gs_status gs_track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians 
                         double *poses, double *adam_state, double *loss_hist, int32_t iters, void *ws,
                         size_t ws_bytes, void *stream);
 
-/* The host copy of a tracking frame's targets, laid out like gs_targets (rgb 3 x P,
- * depth P, depth_prior P or NULL); page-locked host memory (cudaHostAlloc,
- * cudaHostRegister). */
+/* The host side of gs_track_step_upload, all page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister): the frame's targets laid out like gs_targets (rgb 3 x P, depth P,
+ * depth_prior P or NULL), and result (NULL, or n_views x 8 doubles mapped into the
+ * device's address space) receiving each view's pose after the last iteration (7) and its
+ * loss before the last update (1), stored by the device at the end of the call. */
 typedef struct {
     const float *rgb;
     const float *depth;
     const float *depth_prior;
+    double *result;
 } gs_host_targets;
 
 /* gs_track_step for a frame that is still in host memory: the call first copies src into
  * the device buffers of `targets` (which it overwrites), on a branch of its work that
  * runs beside the first iteration's projection, scan and key emission; the first
  * compositor waits for the copy, everything else is gs_track_step.  The copy is part of
- * the CUDA graph (one per argument set, src included).  Errors: as gs_track_step;
+ * the CUDA graph (one per argument set, src included).  With src->result the poses and
+ * losses reach host memory without a copy after the call (the finalize kernel stores them
+ * there); they are valid once the stream has passed the call.  Errors: as gs_track_step;
  * INVALID_ARG when src is NULL, lacks rgb or depth, has a depth prior exactly when
- * targets has none (or the reverse), or an array is not page-locked host memory. */
+ * targets has none (or the reverse), or an array is not page-locked (result: not mapped)
+ * host memory. */
 gs_status gs_track_step_upload(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const gs_targets *targets,
                                const gs_host_targets *src, double *poses, double *adam_state, double *loss_hist,
                                int32_t iters, void *ws, size_t ws_bytes, void *stream);

@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeLaunch L) {
             s_st[tid - 32] = L.adam[16 * v + tid - 32];
     }
     DF lacc{0.f, 0.f}, pa{0.f, 0.f}, pb{0.f, 0.f};  // loss; components 2 (tid % 3), 2 (tid % 3) + 1
-    if (L.loss_out) {
+    if (L.loss_out || L.host_result) {
         const ViewInfo vi = L.ws.views[v];
         const uint32_t nt = (uint32_t)vi.tiles_x * (uint32_t)vi.tiles_y;
         const float2 *tl = L.ws.tile_loss + vi.tile_base;
@@ -383,6 +383,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeLaunch L) {
     if (tid == 0) {
         for (int k = 0; k < 7; ++k) L.poses[7 * v + k] = s_pose[k];
         for (int k = 0; k < 16; ++k) L.adam[16 * v + k] = s_st[k];
+        if (L.host_result) {  // straight into host memory: no copy after the kernel
+            for (int k = 0; k < 7; ++k) L.host_result[8 * v + k] = s_pose[k];
+            L.host_result[8 * v + 7] = s_g[6];
+        }
     }
 }
 

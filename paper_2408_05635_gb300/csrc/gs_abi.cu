@@ -53,7 +53,7 @@ struct Problem {
 struct GraphKey {
     const void *ws = nullptr;
     size_t ws_bytes = 0;
-    const void *ptrs[15] = {};
+    const void *ptrs[16] = {};
     int64_t n = 0;
     int dtype = 0;
     int iters = 0;
@@ -67,7 +67,7 @@ struct GraphKey {
             sched[1] != o.sched[1] || sched[2] != o.sched[2] || sched[3] != o.sched[3] ||
             views.size() != o.views.size())
             return false;
-        for (int k = 0; k < 15; ++k)
+        for (int k = 0; k < 16; ++k)
             if (ptrs[k] != o.ptrs[k]) return false;
         return views.empty() || std::memcmp(views.data(), o.views.data(), views.size() * sizeof(ViewInfo)) == 0;
     }
@@ -745,8 +745,14 @@ gs_status track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
     if (src) {
         if (!src->rgb || !src->depth || !src->depth_prior != !targets->depth_prior)
             return fail(ctx, GS_ERR_INVALID_ARG, "src needs rgb and depth, and a depth prior exactly when targets has one");
-        if (!pinned_host(src->rgb) || !pinned_host(src->depth) || (src->depth_prior && !pinned_host(src->depth_prior)))
+        if (!pinned_host(src->rgb) || !pinned_host(src->depth) || (src->depth_prior && !pinned_host(src->depth_prior)) ||
+            (src->result && !pinned_host(src->result)))
             return fail(ctx, GS_ERR_INVALID_ARG, "src arrays must be page-locked host memory");
+    }
+    double *result_dev = nullptr;  // the device's address of src->result
+    if (src && src->result && cudaHostGetDevicePointer(reinterpret_cast<void **>(&result_dev), src->result, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GS_ERR_INVALID_ARG, "src->result is not mapped into the device's address space");
     }
     Problem pr;
     gs_status st = build_problem(ctx, prob, pr);
@@ -790,6 +796,7 @@ gs_status track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
             F.pose = true;
             F.poses = poses;
             F.adam = adam_state;
+            F.host_result = it == iters - 1 ? result_dev : nullptr;
             if ((r = mark_begin(ctx, q, "k_finalize")) != cudaSuccess) return r;
             if ((r = launch_finalize(F, q)) != cudaSuccess) return r;
             if ((r = mark(ctx, q, "k_finalize")) != cudaSuccess) return r;
@@ -809,11 +816,11 @@ gs_status track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
         GraphKey key;
         key.ws = ws;
         key.ws_bytes = ws_bytes;
-        const void *ptrs[15] = {g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb, targets->rgb,
+        const void *ptrs[16] = {g->means, g->quats, g->log_scales, g->opacity_logits, g->rgb, targets->rgb,
                                 targets->depth, targets->depth_prior, poses, adam_state, loss_hist, nullptr,
                                 src ? src->rgb : nullptr, src ? src->depth : nullptr,
-                                src ? src->depth_prior : nullptr};
-        for (int k = 0; k < 15; ++k) key.ptrs[k] = ptrs[k];
+                                src ? src->depth_prior : nullptr, src ? src->result : nullptr};
+        for (int k = 0; k < 16; ++k) key.ptrs[k] = ptrs[k];
         key.n = g->n;
         key.dtype = g->dtype_attr;
         key.iters = iters;

@@ -655,6 +655,8 @@ struct FinalizeLaunch {
     double *pose_grad;  // n_views x 6, or nullptr
     double *poses;      // updated in place by the Adam step, or nullptr
     double *adam;       // n_views x 16 (with poses)
+    double *host_result;  // page-locked host memory (device address), n_views x 8: the updated
+                          // pose and the loss, written at the end; or nullptr
     bool pose;          // reduce the pose partials
 };
 cudaError_t launch_finalize(const FinalizeLaunch &L, cudaStream_t st);

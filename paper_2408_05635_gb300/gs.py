@@ -55,7 +55,7 @@ class gs_targets(ctypes.Structure):
 
 
 class gs_host_targets(ctypes.Structure):
-    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("depth_prior", c_void_p)]
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("depth_prior", c_void_p), ("result", c_void_p)]
 
 
 class gs_config(ctypes.Structure):

@@ -136,8 +136,9 @@ def test_tracking_with_host_upload_equals_device_targets(tracking):
     run-to-run spread of the FP32 gradient atomics, whose order is not fixed (poses 1e-7
     absolute: Adam's step lr g / (|g| + eps) moves a coordinate with a near-zero gradient
     by that noise; losses 1e-6 relative; moments 1e-4 relative), the device targets hold the
-    host frame afterwards (they start as NaN), and a frame in ordinary (pageable) host
-    memory is refused."""
+    host frame afterwards (they start as NaN), the host result holds the last pose and loss
+    (stored there by the device), and a frame in ordinary (pageable) host memory is
+    refused."""
     t = tracking
     R = gs.Rasterizer(gs.Config())
     R.set_schedule(16, 16, 4, 256, 256, gs.GS_SCHED_FUSED)
@@ -153,7 +154,8 @@ def test_tracking_with_host_upload_equals_device_targets(tracking):
         if upload:
             dev = tuple(torch.full_like(x, float("nan")) for x in t["targets"])
             host = tuple(x.cpu().pin_memory() for x in t["targets"])
-            src = gs.gs_host_targets(*(x.data_ptr() for x in host))
+            result = torch.full((8,), float("nan"), dtype=torch.float64).pin_memory()
+            src = gs.gs_host_targets(*(x.data_ptr() for x in host), result.data_ptr())
             tg = gs.gs_targets(*(x.data_ptr() for x in dev))
             gs.gs_track_step_upload(R.ctx, prob, gt.c(), tg, src, poses, adam, hist, 5, ws, nb)
         else:
@@ -164,8 +166,11 @@ def test_tracking_with_host_upload_equals_device_targets(tracking):
         if upload:
             for d, h in zip(dev, host):
                 assert torch.equal(d.cpu(), h)
+            # the last iteration's pose and loss, stored into host memory by the device
+            np.testing.assert_array_equal(result.numpy()[:7], out[-1][0][0])
+            assert result.numpy()[7] == out[-1][1][-1, 0]
             pageable = tuple(x.cpu() for x in t["targets"])
-            bad = gs.gs_host_targets(*(x.data_ptr() for x in pageable))
+            bad = gs.gs_host_targets(*(x.data_ptr() for x in pageable), None)
             with pytest.raises(gs.GsError):
                 gs.gs_track_step_upload(R.ctx, prob, gt.c(), tg, bad, poses, adam, hist, 1, ws, nb)
     (p0, h0, a0), (p1, h1, a1) = out
