@@ -41,27 +41,38 @@ __device__ __forceinline__ void cos_sinc_small(double h2, double &c, double &sc)
     sc = 1.0 + h2 * (-1.0 / 6 + h2 * (1.0 / 120 + h2 * (-1.0 / 5040 + h2 * (1.0 / 362880))));
 }
 
-// Decoupled Adam step of one view, FP64, by six threads of the block (one per pose
-// coordinate; tid 0 also applies the step).  state: m_rot 3, v_rot 3, m_t 3, v_t 3, step
-// count, beta1^k, beta2^k (running products, 0 before the first step), 1 unused.
-__device__ void adam_update(double *pose, double *st, const double *g, const Settings &S, double *s_step, int tid) {
-    const double k = st[12] + 1.0;
+// Decoupled Adam step of one view, FP64, writing the new pose and optimiser state to
+// `pose_out` / `st_out` (and `res_out`, n x 8 with the loss last, if not NULL).  state:
+// m_rot 3, v_rot 3, m_t 3, v_t 3, step count, beta1^k, beta2^k (running products, 0 before
+// the first step), 1 unused.  FP64 instructions are slow here (a warp instruction takes
+// the FP64 pipe for many cycles whatever its active lanes), so the work is laid out as few
+// instructions: the six moment updates in one warp's lanes (one per pose coordinate),
+// then the rotation step in warp 0 (lane i: quaternion component i) and the translation
+// step in warp 1 (lane i: component i) at the same time, each warp computing the step's
+// quaternion itself.  Every thread of the block calls it.
+__device__ void adam_update(const double *pose, const double *st, const double *g, double loss, const Settings &S,
+                            double *s_step, int tid, double *pose_out, double *st_out, double *res_out) {
     const double p1 = st[12] > 0.0 ? st[13] * S.beta1 : S.beta1;
     const double p2 = st[12] > 0.0 ? st[14] * S.beta2 : S.beta2;
     if (tid < 6) {
         const int im = tid < 3 ? tid : 6 + (tid - 3), iv = im + 3;
         const double m = S.beta1 * st[im] + (1.0 - S.beta1) * g[tid];
         const double v = S.beta2 * st[iv] + (1.0 - S.beta2) * g[tid] * g[tid];
-        st[im] = m;
-        st[iv] = v;
+        st_out[im] = m;
+        st_out[iv] = v;
         const double lr = tid < 3 ? S.lr_rot : S.lr_trans;
         s_step[tid] = lr * (m / (1.0 - p1)) / (sqrt(v / (1.0 - p2)) + S.eps);
+    } else if (tid == 32) {
+        st_out[12] = st[12] + 1.0;
+        st_out[13] = p1;
+        st_out[14] = p2;
+        st_out[15] = st[15];
+    } else if (tid == 64 && res_out) {
+        res_out[7] = loss;
     }
     __syncthreads();
-    if (tid != 0) return;
-    st[12] = k;
-    st[13] = p1;
-    st[14] = p2;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp > 1) return;
     const double sx = s_step[0], sy = s_step[1], sz = s_step[2];
     const double th2 = sx * sx + sy * sy + sz * sz;
     const double h2 = 0.25 * th2;  // (theta / 2)^2
@@ -75,24 +86,41 @@ __device__ void adam_update(double *pose, double *st, const double *g, const Set
     }
     // quaternion of Exp(-step): (cos(theta/2), -step sin(theta/2) / theta), sin(h)/theta = sinc(h)/2
     const double a0 = c, a1 = -0.5 * sinc * sx, a2 = -0.5 * sinc * sy, a3 = -0.5 * sinc * sz;
-    const double b0 = pose[0], b1 = pose[1], b2 = pose[2], b3 = pose[3];
-    const double q0 = a0 * b0 - a1 * b1 - a2 * b2 - a3 * b3;
-    const double q1 = a0 * b1 + a1 * b0 + a2 * b3 - a3 * b2;
-    const double q2 = a0 * b2 - a1 * b3 + a2 * b0 + a3 * b1;
-    const double q3 = a0 * b3 + a1 * b2 - a2 * b1 + a3 * b0;
-    const double inv = rsqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
-    pose[0] = q0 * inv;
-    pose[1] = q1 * inv;
-    pose[2] = q2 * inv;
-    pose[3] = q3 * inv;
-    // the camera turns about its own centre: t follows the rotation, then moves
-    const double r00 = 1.0 - 2.0 * (a2 * a2 + a3 * a3), r01 = 2.0 * (a1 * a2 - a0 * a3), r02 = 2.0 * (a1 * a3 + a0 * a2);
-    const double r10 = 2.0 * (a1 * a2 + a0 * a3), r11 = 1.0 - 2.0 * (a1 * a1 + a3 * a3), r12 = 2.0 * (a2 * a3 - a0 * a1);
-    const double r20 = 2.0 * (a1 * a3 - a0 * a2), r21 = 2.0 * (a2 * a3 + a0 * a1), r22 = 1.0 - 2.0 * (a1 * a1 + a2 * a2);
-    const double t0 = pose[4], t1 = pose[5], t2 = pose[6];
-    pose[4] = r00 * t0 + r01 * t1 + r02 * t2 - s_step[3];
-    pose[5] = r10 * t0 + r11 * t1 + r12 * t2 - s_step[4];
-    pose[6] = r20 * t0 + r21 * t1 + r22 * t2 - s_step[5];
+    if (warp == 0) {
+        // R <- Exp(-step) R: Hamilton product a (x) pose, component i = lane (0..3) as
+        // a0 b_i + a1 x1 + a2 x2 + a3 x3 with signed, permuted components x of b
+        const int i = lane & 3;
+        const double b0 = pose[0], b1 = pose[1], b2 = pose[2], b3 = pose[3];
+        const double bi = i == 0 ? b0 : (i == 1 ? b1 : (i == 2 ? b2 : b3));
+        const double x1 = i == 0 ? -b1 : (i == 1 ? b0 : (i == 2 ? -b3 : b2));
+        const double x2 = i == 0 ? -b2 : (i == 1 ? b3 : (i == 2 ? b0 : -b1));
+        const double x3 = i == 0 ? -b3 : (i == 1 ? -b2 : (i == 2 ? b1 : b0));
+        const double q = a0 * bi + a1 * x1 + a2 * x2 + a3 * x3;
+        double n2 = q * q;
+        n2 += __shfl_xor_sync(0xffffffffu, n2, 1);
+        n2 += __shfl_xor_sync(0xffffffffu, n2, 2);
+        const double qn = q * rsqrt(n2);
+        if (lane < 4) {
+            pose_out[lane] = qn;
+            if (res_out) res_out[lane] = qn;
+        }
+    } else {
+        // the camera turns about its own centre: t <- Exp(-step) t - step_t, component i =
+        // lane (0..2), with Exp(-step) t = t + 2 a0 (a_v x t) + 2 a_v x (a_v x t) for the unit
+        // quaternion a = (a0, a_v)
+        const int i = lane < 3 ? lane : 0;
+        const double t0 = pose[4], t1 = pose[5], t2 = pose[6];
+        const double u0 = a2 * t2 - a3 * t1, u1 = a3 * t0 - a1 * t2, u2 = a1 * t1 - a2 * t0;
+        const double w0 = a2 * u2 - a3 * u1, w1 = a3 * u0 - a1 * u2, w2 = a1 * u1 - a2 * u0;
+        const double ti = i == 0 ? t0 : (i == 1 ? t1 : t2);
+        const double ui = i == 0 ? u0 : (i == 1 ? u1 : u2);
+        const double wi = i == 0 ? w0 : (i == 1 ? w1 : w2);
+        const double tn = ti + 2.0 * (a0 * ui + wi) - s_step[3 + i];
+        if (lane < 3) {
+            pose_out[4 + lane] = tn;
+            if (res_out) res_out[4 + lane] = tn;
+        }
+    }
 }
 
 // Butterfly reduce-scatter of 8 values over the warp (9 shuffles); afterwards lanes with
@@ -379,15 +407,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeLaunch L) {
     }
     __syncthreads();
     if (!adam) return;
-    adam_update(s_pose, s_st, s_g, L.s, s_step, tid);  // thread 0 alone returns from it with the result
-    if (tid == 0) {
-        for (int k = 0; k < 7; ++k) L.poses[7 * v + k] = s_pose[k];
-        for (int k = 0; k < 16; ++k) L.adam[16 * v + k] = s_st[k];
-        if (L.host_result) {  // straight into host memory: no copy after the kernel
-            for (int k = 0; k < 7; ++k) L.host_result[8 * v + k] = s_pose[k];
-            L.host_result[8 * v + 7] = s_g[6];
-        }
-    }
+    // the new pose and state straight to their arrays (and into host memory: no copy after
+    // the kernel)
+    adam_update(s_pose, s_st, s_g, s_g[6], L.s, s_step, tid, L.poses + 7 * v, L.adam + 16 * v,
+                L.host_result ? L.host_result + 8 * v : nullptr);
 }
 
 cudaError_t launch_finalize(const FinalizeLaunch &L, cudaStream_t st) {

@@ -85,13 +85,14 @@ __device__ __forceinline__ void bwd_step6(bool c, const PolyEval &pe, float4 Cc,
     GB = fmaf(a, diff, GB);
     const float w = a * T;
     const float dp = araw < amax ? dalpha * a : 0.f;
-    const float dpx = dp * pe.dx, dpy = dp * pe.dy;
-    v[0] = dpx;
-    v[1] = dpy;
+    const float2 dpd = __fmul2_rn(make_float2(dp, dp), pe.d);              // (dp dx, dp dy)
+    const float2 mx = __fmul2_rn(make_float2(dpd.x, dpd.x), pe.d);        // (dp dx dx, dp dx dy)
+    v[0] = dpd.x;
+    v[1] = dpd.y;
     v[2] = w * gD;
-    v[3] = dpx * pe.dx;
-    v[4] = dpx * pe.dy;
-    v[5] = dpy * pe.dy;
+    v[3] = mx.x;
+    v[4] = mx.y;
+    v[5] = dpd.y * pe.d.y;
 }
 
 }  // namespace gsk

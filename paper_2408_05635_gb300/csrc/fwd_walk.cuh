@@ -23,17 +23,19 @@ struct FwdPixel {
 // after it (the front entry if it alone reaches t_min, else the back one).  n_eval counts
 // the entries evaluated before the stop (inclusive), n_contrib the contributions.
 __device__ __forceinline__ void fwd_walk_batch(FwdPixel &px, const uint8_t *list, int nl, uint32_t b0,
-                                               const float4 *sP0, const float2 *sP1, const float4 *sC, float fu,
-                                               float fv, float thr, float amax, float tmin, uint32_t &n_eval,
+                                               const float4 *sP0, const float2 *sP1, const float4 *sC, float2 uv,
+                                               float thr, float amax, float tmin, uint32_t &n_eval,
                                                uint32_t &n_contrib) {
-    float T = px.T, cr = px.cr, cg = px.cg, cb = px.cb, D = px.D;
+    float T = px.T;
+    // (colour r, g) and (colour b, depth): each pair takes one two-lane FMA per entry
+    float2 rg = make_float2(px.cr, px.cg), bD = make_float2(px.cb, px.D);
     int lastj = -1;  // batch position of the last contributor in this batch
     int e = 0;
     uint32_t contrib = 0;
     for (; e + 1 < nl; e += 2) {
         const int jA = list[e], jB = list[e + 1];
-        const float pA = eval_poly(fu, fv, sP0[jA], sP1[jA]).poly;
-        const float pB = eval_poly(fu, fv, sP0[jB], sP1[jB]).poly;
+        const float pA = eval_poly(uv, sP0[jA], sP1[jA]).poly;
+        const float pB = eval_poly(uv, sP0[jB], sP1[jB]).poly;
         const float4 CA = sC[jA], CB = sC[jB];
         const bool cA = pA >= thr, cB = pB >= thr;
         const float aA = cA ? fminf(amax, ex2_approx(pA)) : 0.f;
@@ -46,33 +48,26 @@ __device__ __forceinline__ void fwd_walk_batch(FwdPixel &px, const uint8_t *list
                 break;
             }
             const float w = aA * T;  // the front entry (if it hits) contributes, the back one stops
-            cr += CA.x * w;
-            cg += CA.y * w;
-            cb += CA.z * w;
-            D += CA.w * w;
+            rg = __ffma2_rn(make_float2(CA.x, CA.y), make_float2(w, w), rg);
+            bD = __ffma2_rn(make_float2(CA.z, CA.w), make_float2(w, w), bD);
             T = TA;
             lastj = cA ? jA : lastj;
             contrib += (uint32_t)cA;
             e += 2;
             break;
         }
-        const float w = aA * T;
-        cr += CA.x * w;
-        cg += CA.y * w;
-        cb += CA.z * w;
-        D += CA.w * w;
-        const float v = aB * TA;
-        cr += CB.x * v;
-        cg += CB.y * v;
-        cb += CB.z * v;
-        D += CB.w * v;
+        const float w = aA * T, v = aB * TA;
+        rg = __ffma2_rn(make_float2(CA.x, CA.y), make_float2(w, w), rg);
+        bD = __ffma2_rn(make_float2(CA.z, CA.w), make_float2(w, w), bD);
+        rg = __ffma2_rn(make_float2(CB.x, CB.y), make_float2(v, v), rg);
+        bD = __ffma2_rn(make_float2(CB.z, CB.w), make_float2(v, v), bD);
         T = TB;
         lastj = cB ? jB : (cA ? jA : lastj);
         contrib += (uint32_t)cA + (uint32_t)cB;
     }
     if (!px.done && e < nl) {  // an odd last entry
         const int j = list[e];
-        const float poly = eval_poly(fu, fv, sP0[j], sP1[j]).poly;
+        const float poly = eval_poly(uv, sP0[j], sP1[j]).poly;
         ++e;
         if (poly >= thr) {
             const float alpha = fminf(amax, ex2_approx(poly));
@@ -82,10 +77,8 @@ __device__ __forceinline__ void fwd_walk_batch(FwdPixel &px, const uint8_t *list
             } else {
                 const float w = alpha * T;
                 const float4 Cc = sC[j];
-                cr += Cc.x * w;
-                cg += Cc.y * w;
-                cb += Cc.z * w;
-                D += Cc.w * w;
+                rg = __ffma2_rn(make_float2(Cc.x, Cc.y), make_float2(w, w), rg);
+                bD = __ffma2_rn(make_float2(Cc.z, Cc.w), make_float2(w, w), bD);
                 T = Tn;
                 lastj = j;
                 ++contrib;
@@ -96,10 +89,10 @@ __device__ __forceinline__ void fwd_walk_batch(FwdPixel &px, const uint8_t *list
     n_contrib += contrib;
     if (lastj >= 0) px.last = b0 + (uint32_t)lastj + 1u;
     px.T = T;
-    px.cr = cr;
-    px.cg = cg;
-    px.cb = cb;
-    px.D = D;
+    px.cr = rg.x;
+    px.cg = rg.y;
+    px.cb = bD.x;
+    px.D = bD.y;
 }
 
 }  // namespace gsk

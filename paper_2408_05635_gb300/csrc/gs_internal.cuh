@@ -334,11 +334,15 @@ __device__ __forceinline__ void tile_bounds(const ViewInfo &vi, int tx, int ty, 
 // Gaussians centred far from the tile origin.)  A Gaussian is skipped where
 // poly < log2(alpha_min).  Staging and evaluation use explicitly rounded operations and
 // are shared by the forward and the backward, so both take bit-identical decisions.
+// The staged layout pairs the operands of Blackwell's two-lane FP32 instructions: the
+// negated centre (dx and dy in one addition: u + (-cu) is u - cu exactly) and the two
+// coefficients multiplied by dy (one multiplication); each lane of those instructions
+// rounds like the scalar operation, so the values are those of the scalar sequence.
 constexpr float kLog2e = 1.4426950408889634f;
 
 struct Footprint {
-    float4 p0;  // (lo, cu, cv, kuu)
-    float2 p1;  // (kuv, kvv)
+    float4 p0;  // (-cu, -cv, kuv, kvv)
+    float2 p1;  // (kuu, lo)
 };
 
 // Programmatic dependent launch.  The kernels of a tracking iteration form one chain on a
@@ -382,8 +386,8 @@ __device__ __forceinline__ float lg2_approx(float x) {
 
 __device__ __forceinline__ Footprint stage_footprint(const float4 A, const float4 B, float x0, float y0) {
     Footprint f;
-    f.p0 = make_float4(lg2_approx(A.w), __fsub_rn(A.x, x0), __fsub_rn(A.y, y0), __fmul_rn(-0.5f * kLog2e, B.x));
-    f.p1 = make_float2(__fmul_rn(-kLog2e, B.y), __fmul_rn(-0.5f * kLog2e, B.z));
+    f.p0 = make_float4(__fsub_rn(x0, A.x), __fsub_rn(y0, A.y), __fmul_rn(-kLog2e, B.y), __fmul_rn(-0.5f * kLog2e, B.z));
+    f.p1 = make_float2(__fmul_rn(-0.5f * kLog2e, B.x), lg2_approx(A.w));
     return f;
 }
 
@@ -484,15 +488,18 @@ __device__ __forceinline__ float4 stage_box(const float4 B, float cu, float cv) 
 constexpr int kPatchW = 8, kPatchH = 4;
 
 struct PolyEval {
-    float dx, dy, poly;
+    float2 d;  // (dx, dy)
+    float poly;
 };
 
-__device__ __forceinline__ PolyEval eval_poly(float u, float v, float4 p0, float2 p1) {
+// poly at the tile-local pixel centre uv = (u, v): dx = u - cu, dy = v - cv,
+// t = kuu dx + kuv dy (kuv dy rounded first), poly = dx t + (kvv dy dy + lo).
+__device__ __forceinline__ PolyEval eval_poly(float2 uv, float4 p0, float2 p1) {
     PolyEval e;
-    e.dx = __fsub_rn(u, p0.y);
-    e.dy = __fsub_rn(v, p0.z);
-    const float t = __fmaf_rn(p0.w, e.dx, __fmul_rn(p1.x, e.dy));
-    e.poly = __fmaf_rn(e.dx, t, __fmaf_rn(__fmul_rn(p1.y, e.dy), e.dy, p0.x));
+    e.d = __fadd2_rn(uv, make_float2(p0.x, p0.y));
+    const float2 m = __fmul2_rn(make_float2(p0.z, p0.w), make_float2(e.d.y, e.d.y));  // (kuv dy, kvv dy)
+    const float t = __fmaf_rn(p1.x, e.d.x, m.x);
+    e.poly = __fmaf_rn(e.d.x, t, __fmaf_rn(m.y, e.d.y, p1.y));
     return e;
 }
 
@@ -506,9 +513,9 @@ __device__ __forceinline__ PolyEval eval_poly(float u, float v, float4 p0, float
 // no entry with a pixel at alpha >= alpha_min is dropped; degenerate footprints pass.
 __device__ __forceinline__ bool footprint_meets_rect(float4 p0, float2 p1, float thr, float u_lo, float u_hi,
                                                      float v_lo, float v_hi) {
-    const float kuu = p0.w, kuv = p1.x, kvv = p1.y;
+    const float kuu = p1.x, kuv = p0.z, kvv = p0.w, lo = p1.y;
     if (!(kuu < 0.f && kvv < 0.f)) return true;
-    const float x0 = u_lo - p0.y, x1 = u_hi - p0.y, y0 = v_lo - p0.z, y1 = v_hi - p0.z;
+    const float x0 = u_lo + p0.x, x1 = u_hi + p0.x, y0 = v_lo + p0.y, y1 = v_hi + p0.y;
     float q = 0.f;  // max of the quadratic part over the rectangle
     if (!(x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f)) {
         const float ru = -0.5f / kuu, rv = -0.5f / kvv;
@@ -518,8 +525,8 @@ __device__ __forceinline__ bool footprint_meets_rect(float4 p0, float2 p1, float
         q = fmaxf(fmaxf(f(x0, ya), f(x1, yb)), fmaxf(f(xa, y0), f(xb, y1)));
     }
     const float DX = fmaxf(fabsf(x0), fabsf(x1)), DY = fmaxf(fabsf(y0), fabsf(y1));
-    const float mag = fabsf(p0.x) - kuu * DX * DX + fabsf(kuv) * DX * DY - kvv * DY * DY;
-    return p0.x + q >= thr - 0x1p-16f * mag;
+    const float mag = fabsf(lo) - kuu * DX * DX + fabsf(kuv) * DX * DY - kvv * DY * DY;
+    return lo + q >= thr - 0x1p-16f * mag;
 }
 
 // A warp's list of the batch positions [0, cnt) whose footprint reaches its pixel

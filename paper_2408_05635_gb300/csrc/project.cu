@@ -90,6 +90,9 @@ struct ViewChunk {
 // words at `zero` (all blocks, grid-stride): the per-call reset of the flag word, the
 // header and the tile counters, folded into the same launch.
 __global__ void k_copy_views(ViewInfo *dst, int count, ViewChunk chunk, uint32_t *zero, size_t zero_words) {
+    // the projection may be scheduled now: it waits (griddep_wait) for this grid to end
+    // before it touches the workspace
+    griddep_launch_dependents();
     if (blockIdx.x == 0 && threadIdx.x < count) dst[threadIdx.x] = chunk.v[threadIdx.x];
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < zero_words; i += (size_t)gridDim.x * blockDim.x)
         zero[i] = 0u;

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     const int px = (tx << LW) + lu, py = (ty << vi.tile_lh) + lv;
     const bool inside = px < vi.width && py < vi.height;
     const float x0 = (float)(tx << LW), y0 = (float)(ty << vi.tile_lh);
-    const float fu = (float)lu, fv = (float)lv;
+    const float2 uv = make_float2((float)lu, (float)lv);  // tile-local pixel centre
     const float pu_lo = (float)pu0, pu_hi = (float)(pu0 + kPatchW - 1);
     const float pv_lo = (float)pv0, pv_hi = (float)(pv0 + kPatchH - 1);
     const Settings &S = L.s;
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
                 sP1[tid] = f.p1;
                 sC[tid] = make_float4(rr.c.x, rr.c.y, rr.c.z, rr.a.z);
                 sQ[tid] = make_float4(rr.b.x, rr.b.y, rr.b.z, rr.a.w);
-                sBox[tid] = stage_box(rr.b, f.p0.y, f.p0.z);
+                sBox[tid] = stage_box(rr.b, -f.p0.x, -f.p0.y);
             } else {
                 sBox[tid] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);
             }
@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
             for (; e >= 1; e -= 2) {
                 const int jA = sList[warp][e], jB = sList[warp][e - 1];
                 const uint32_t iA = (uint32_t)b0 + (uint32_t)jA, iB = (uint32_t)b0 + (uint32_t)jB;
-                const PolyEval pA = eval_poly(fu, fv, sP0[jA], sP1[jA]);
-                const PolyEval pB = eval_poly(fu, fv, sP0[jB], sP1[jB]);
+                const PolyEval pA = eval_poly(uv, sP0[jA], sP1[jA]);
+                const PolyEval pB = eval_poly(uv, sP0[jB], sP1[jB]);
                 const bool lA = iA < last, lB = iB < last;
                 n_eval += lA + lB;
                 const bool cA = lA && pA.poly >= thr, cB = lB && pB.poly >= thr;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
             const int j = sList[warp][e];
             const uint32_t idx = (uint32_t)b0 + (uint32_t)j;
             const bool live = idx < last;
-            const PolyEval pe = eval_poly(fu, fv, sP0[j], sP1[j]);
+            const PolyEval pe = eval_poly(uv, sP0[j], sP1[j]);
             n_eval += live;
             const bool c = live && pe.poly >= thr;
             if (!__any_sync(0xffffffffu, c)) continue;
@@ -188,9 +188,9 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
                 GB = fmaf(a, diff, GB);
                 const float w = a * T;
                 const float dp = araw < S.alpha_max ? dalpha * a : 0.f;
-                const float dpx = dp * pe.dx, dpy = dp * pe.dy;
+                const float dpx = dp * pe.d.x, dpy = dp * pe.d.y;
                 float vals[16] = {dpx,     dpy,     w * gD, c && araw < S.alpha_max ? dalpha * araw : 0.f,
-                                  dpx * pe.dx, dpx * pe.dy, dpy * pe.dy, 0.f,
+                                  dpx * pe.d.x, dpx * pe.d.y, dpy * pe.d.y, 0.f,
                                   w * g0,  w * g1,  w * g2, 0.f, 0.f, 0.f, 0.f, 0.f};
                 int slot;
                 const float sum = warp_reduce_scatter<16>(vals, lane, slot);

@@ -10,7 +10,8 @@
 //     registers between the walks (they are still written to the workspace, so a later
 //     gs_backward finds the same state as after k_forward);
 //   - the batch the forward staged last is usually the one the reverse walk starts with
-//     (a tile's whole list when it holds at most one batch), and it is not staged again;
+//     (a tile's whole list when it holds at most one batch): it is not staged again, and
+//     each warp cuts the list it built for it in the forward instead of building another;
 //   - a tile's reverse walk starts as soon as its own forward ends, so the tiles that end
 //     the forward (the longest lists, launched first) overlap the reverse walks of the
 //     others instead of leaving SMs idle before a second kernel.
@@ -35,7 +36,7 @@ __device__ __forceinline__ void stage_one(const TrackTileLaunch &L, uint32_t r, 
         sP1[tid] = f.p1;
         sC[tid] = make_float4(rr.c.x, rr.c.y, rr.c.z, rr.a.z);
         sQ[tid] = make_float4(rr.b.x, rr.b.y, rr.b.z, rr.a.w);
-        sBox[tid] = stage_box(rr.b, f.p0.y, f.p0.z);
+        sBox[tid] = stage_box(rr.b, -f.p0.x, -f.p0.y);
     } else {
         sBox[tid] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);  // empty: never listed
     }
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
     const int px = (tx << LW) + lu, py = (ty << vi.tile_lh) + lv;
     const bool inside = px < vi.width && py < vi.height;
     const float x0 = (float)(tx << LW), y0 = (float)(ty << vi.tile_lh);
-    const float fu = (float)lu, fv = (float)lv;
+    const float2 uv = make_float2((float)lu, (float)lv);  // tile-local pixel centre
     const float pu_lo = (float)pu0, pu_hi = (float)(pu0 + kPatchW - 1);
     const float pv_lo = (float)pv0, pv_hi = (float)(pv0 + kPatchH - 1);
     const Settings &S = L.s;
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
     FwdPixel walk{1.f, 0.f, 0.f, 0.f, 0.f, 0u, !inside};
     uint32_t n_eval = 0, n_contrib = 0;
     int64_t staged = -1;  // first list entry of the batch now in shared memory (block-uniform)
+    int nl_staged = 0;    // length of this warp's list of the staged batch (warp-uniform)
     for (uint32_t b0 = 0; b0 < n; b0 += NB) {
         if (__syncthreads_count(!walk.done) == 0) break;
         const uint32_t idx = b0 + tid;
@@ -103,8 +105,9 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
         const int cnt = (int)min((uint32_t)NB, n - b0);
         if (__any_sync(0xffffffffu, !walk.done)) {
             const int nl = build_patch_list(sBox, sP0, sP1, sList[warp], cnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
+            nl_staged = nl;
             if (!walk.done)
-                fwd_walk_batch(walk, sList[warp], nl, b0, sP0, sP1, sC, fu, fv, thr, S.alpha_max, S.t_min, n_eval,
+                fwd_walk_batch(walk, sList[warp], nl, b0, sP0, sP1, sC, uv, thr, S.alpha_max, S.t_min, n_eval,
                                n_contrib);
         }
     }
@@ -198,15 +201,29 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
         __syncthreads();
         // this warp's list, limited to entries below its largest contributor count
         const int wcnt = (int)min((int64_t)cnt, (int64_t)wlast - b0);
-        const int nl = build_patch_list(sBox, sP0, sP1, sList[warp], wcnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
+        int nl = 0;
+        if (b0 == staged) {
+            // the batch the forward ended on: its list (ascending positions) is still in
+            // sList, and the entries below wcnt are the list build_patch_list would give for
+            // wcnt.  A warp whose pixels had all stopped before this batch kept an older
+            // list, but then wlast <= b0 and no entry is below wcnt <= 0.
+            for (int k = 0; k < nl_staged; k += 32) {
+                const bool below = k + lane < nl_staged && (int)sList[warp][k + lane] < wcnt;
+                const int m = __popc(__ballot_sync(0xffffffffu, below));
+                nl += m;
+                if (m < 32) break;
+            }
+        } else {
+            nl = build_patch_list(sBox, sP0, sP1, sList[warp], wcnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
+        }
         int e = nl - 1;
         // two Gaussians per step: the pixel state is updated in depth order (the back one
         // first), and the two reductions are independent, so they overlap
         for (; e >= 1; e -= 2) {
             const int jA = sList[warp][e], jB = sList[warp][e - 1];
             const uint32_t iA = (uint32_t)b0 + (uint32_t)jA, iB = (uint32_t)b0 + (uint32_t)jB;
-            const PolyEval pA = eval_poly(fu, fv, sP0[jA], sP1[jA]);
-            const PolyEval pB = eval_poly(fu, fv, sP0[jB], sP1[jB]);
+            const PolyEval pA = eval_poly(uv, sP0[jA], sP1[jA]);
+            const PolyEval pB = eval_poly(uv, sP0[jB], sP1[jB]);
             const bool lA = iA < last, lB = iB < last;
             n_eval += lA + lB;
             const bool cA = lA && pA.poly >= thr, cB = lB && pB.poly >= thr;
@@ -222,7 +239,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
             const int j = sList[warp][e];
             const uint32_t idx = (uint32_t)b0 + (uint32_t)j;
             const bool live = idx < last;
-            const PolyEval pe = eval_poly(fu, fv, sP0[j], sP1[j]);
+            const PolyEval pe = eval_poly(uv, sP0[j], sP1[j]);
             n_eval += live;
             const bool c = live && pe.poly >= thr;
             if (!__any_sync(0xffffffffu, c)) continue;

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     const int px = (tx << LW) + lu, py = (ty << vi.tile_lh) + lv;
     const bool inside = px < vi.width && py < vi.height;
     const float x0 = (float)(tx << LW), y0 = (float)(ty << vi.tile_lh);
-    const float fu = (float)lu, fv = (float)lv;
+    const float2 uv = make_float2((float)lu, (float)lv);  // tile-local pixel centre
     const float pu_lo = (float)pu0, pu_hi = (float)(pu0 + kPatchW - 1);
     const float pv_lo = (float)pv0, pv_hi = (float)(pv0 + kPatchH - 1);
     const Settings &S = L.s;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
                 sP0[tid] = f.p0;
                 sP1[tid] = f.p1;
                 sC[tid] = make_float4(rr.c.x, rr.c.y, rr.c.z, rr.a.z);
-                sBox[tid] = stage_box(rr.b, f.p0.y, f.p0.z);
+                sBox[tid] = stage_box(rr.b, -f.p0.x, -f.p0.y);
             } else {
                 sBox[tid] = make_float4(INFINITY, -INFINITY, INFINITY, -INFINITY);  // empty: never listed
             }
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
             // this warp's list: the batch Gaussians whose footprint reaches its 8 x 4 patch
             const int nl = build_patch_list(sBox, sP0, sP1, sList[warp], cnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
             if (!walk.done)
-                fwd_walk_batch(walk, sList[warp], nl, b0, sP0, sP1, sC, fu, fv, thr, S.alpha_max, S.t_min, n_eval,
+                fwd_walk_batch(walk, sList[warp], nl, b0, sP0, sP1, sC, uv, thr, S.alpha_max, S.t_min, n_eval,
                                n_contrib);
         }
     }
