@@ -51,17 +51,18 @@ __device__ __forceinline__ float warp_reduce_scatter6(float v0, float v1, float 
     return c;
 }
 
-// Joint reduce-scatter of two Gaussians' six values (a: the first, b: the second) in 13
-// shuffles instead of two times eight: six exchanges over lane bit 4 (the bit-4 half keeps
-// b), three over bit 3, two over bit 2 (the third value of each half is summed by both
-// partners), one over bit 1 and a plain sum over bit 0.  Value 3 * b3 + (b1 ? 2 : b2) of
-// Gaussian b4 ends in the lane; owners are the lanes with bit 0 clear and not both of
-// bits 2, 1 set (twelve of them).
-__device__ __forceinline__ float warp_reduce_scatter12(const float (&a)[6], const float (&b)[6], int lane) {
-    const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0, h2 = (lane & 4) != 0, h1 = (lane & 2) != 0;
+// Joint reduce-scatter of two Gaussians' six values in 13 shuffles instead of two times
+// eight: six exchanges over lane bit 4, three over bit 3, two over bit 2 (the third value of
+// each half is summed by both partners), one over bit 1 and a plain sum over bit 0.  The
+// values come placed per lane: `keep` holds the Gaussian the lane keeps after the exchange
+// over bit 4 (the second one for lanes with bit 4 set), `send` the other, so the first
+// round needs no selection.  Value 3 * b3 + (b1 ? 2 : b2) of Gaussian b4 ends in the lane;
+// owners are the lanes with bit 0 clear and not both of bits 2, 1 set (twelve of them).
+__device__ __forceinline__ float warp_reduce_scatter12(const float (&keep)[6], const float (&send)[6], int lane) {
+    const bool h3 = (lane & 8) != 0, h2 = (lane & 4) != 0, h1 = (lane & 2) != 0;
     float u[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) u[k] = (h4 ? b[k] : a[k]) + __shfl_xor_sync(0xffffffffu, h4 ? a[k] : b[k], 16);
+    for (int k = 0; k < 6; ++k) u[k] = keep[k] + __shfl_xor_sync(0xffffffffu, send[k], 16);
     float w[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) w[m] = (h3 ? u[3 + m] : u[m]) + __shfl_xor_sync(0xffffffffu, h3 ? u[m] : u[3 + m], 8);
@@ -73,9 +74,16 @@ __device__ __forceinline__ float warp_reduce_scatter12(const float (&a)[6], cons
 }
 
 // One back-to-front step of the pose-only walk for this lane's pixel: updates T and g.B
-// and returns the six moment terms (all zero where c is false).
-__device__ __forceinline__ void bwd_step6(bool c, const PolyEval &pe, float4 Cc, float g0, float g1, float g2,
-                                          float gD, float gS, float amax, float &T, float &GB, float (&v)[6]) {
+// and returns what the step's six moment terms are made of (all zero where c is false):
+// dp = dL/dpower, (dx, dy) and a T g_D.
+struct StepMom {
+    float dp;
+    float2 d;
+    float wgD;
+};
+
+__device__ __forceinline__ StepMom bwd_step(bool c, const PolyEval &pe, float4 Cc, float g0, float g1, float g2,
+                                            float gD, float gS, float amax, float &T, float &GB) {
     const float araw = ex2_approx(pe.poly);
     const float a = c ? fminf(amax, araw) : 0.f;
     if (c) T = T * __fdividef(1.f, 1.f - a);  // transmittance in front of this Gaussian
@@ -83,16 +91,44 @@ __device__ __forceinline__ void bwd_step6(bool c, const PolyEval &pe, float4 Cc,
     const float diff = gv - GB;
     const float dalpha = T * diff;
     GB = fmaf(a, diff, GB);
-    const float w = a * T;
-    const float dp = araw < amax ? dalpha * a : 0.f;
-    const float2 dpd = __fmul2_rn(make_float2(dp, dp), pe.d);              // (dp dx, dp dy)
-    const float2 mx = __fmul2_rn(make_float2(dpd.x, dpd.x), pe.d);        // (dp dx dx, dp dx dy)
+    StepMom m;
+    m.dp = araw < amax ? dalpha * a : 0.f;
+    m.d = pe.d;
+    m.wgD = (a * T) * gD;
+    return m;
+}
+
+// The six moment terms dp dx, dp dy, a T g_D, dp dx^2, dp dx dy, dp dy^2 of a step.
+__device__ __forceinline__ void moments6(const StepMom &m, float (&v)[6]) {
+    const float2 dpd = __fmul2_rn(make_float2(m.dp, m.dp), m.d);    // (dp dx, dp dy)
+    const float2 mx = __fmul2_rn(make_float2(dpd.x, dpd.x), m.d);   // (dp dx dx, dp dx dy)
     v[0] = dpd.x;
     v[1] = dpd.y;
-    v[2] = w * gD;
+    v[2] = m.wgD;
     v[3] = mx.x;
     v[4] = mx.y;
-    v[5] = dpd.y * pe.d.y;
+    v[5] = dpd.y * m.d.y;
+}
+
+// Two steps (A, the back one, first) and their moments placed for warp_reduce_scatter12:
+// lanes with bit 4 set keep B's and send A's.
+__device__ __forceinline__ float bwd_pair_reduce(bool cA, const PolyEval &pA, float4 CA, bool cB, const PolyEval &pB,
+                                                 float4 CB, float g0, float g1, float g2, float gD, float gS,
+                                                 float amax, float &T, float &GB, int lane) {
+    const StepMom mA = bwd_step(cA, pA, CA, g0, g1, g2, gD, gS, amax, T, GB);
+    const StepMom mB = bwd_step(cB, pB, CB, g0, g1, g2, gD, gS, amax, T, GB);
+    const bool h4 = (lane & 16) != 0;
+    StepMom mk, ms;
+    mk.dp = h4 ? mB.dp : mA.dp;
+    ms.dp = h4 ? mA.dp : mB.dp;
+    mk.d = make_float2(h4 ? mB.d.x : mA.d.x, h4 ? mB.d.y : mA.d.y);
+    ms.d = make_float2(h4 ? mA.d.x : mB.d.x, h4 ? mA.d.y : mB.d.y);
+    mk.wgD = h4 ? mB.wgD : mA.wgD;
+    ms.wgD = h4 ? mA.wgD : mB.wgD;
+    float vk[6], vs[6];
+    moments6(mk, vk);
+    moments6(ms, vs);
+    return warp_reduce_scatter12(vk, vs, lane);
 }
 
 }  // namespace gsk

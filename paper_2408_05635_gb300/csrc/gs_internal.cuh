@@ -529,11 +529,24 @@ __device__ __forceinline__ bool footprint_meets_rect(float4 p0, float2 p1, float
     return lo + q >= thr - 0x1p-16f * mag;
 }
 
+// Staged Gaussians are addressed by byte offset: a warp's list holds 16 x the batch
+// position, and sP0, sP1 and sC all have a 16-byte stride (sP1 carries (kuu, lo) in the
+// first two words), so one list entry addresses all three without index arithmetic.
+template <class T>
+__device__ __forceinline__ const T &at_off(const T *base, int off) {
+    return *reinterpret_cast<const T *>(reinterpret_cast<const char *>(base) + off);
+}
+__device__ __forceinline__ float2 p1_at(const float4 *sP1, int off) {
+    const float4 &q = at_off(sP1, off);
+    return make_float2(q.x, q.y);
+}
+
 // A warp's list of the batch positions [0, cnt) whose footprint reaches its pixel
 // rectangle [pu_lo, pu_hi] x [pv_lo, pv_hi]: the support box first, then the exact
-// footprint test; positions in ascending order.  Returns the count (warp-uniform).
-__device__ __forceinline__ int build_patch_list(const float4 *sBox, const float4 *sP0, const float2 *sP1,
-                                                uint8_t *list, int cnt, int lane, float thr, float pu_lo,
+// footprint test; entries are byte offsets (16 x position) in ascending order.  Returns
+// the count (warp-uniform).
+__device__ __forceinline__ int build_patch_list(const float4 *sBox, const float4 *sP0, const float4 *sP1,
+                                                uint16_t *list, int cnt, int lane, float thr, float pu_lo,
                                                 float pu_hi, float pv_lo, float pv_hi) {
     int nl = 0;
     for (int k = 0; k < cnt; k += 32) {
@@ -542,10 +555,10 @@ __device__ __forceinline__ int build_patch_list(const float4 *sBox, const float4
         if (j < cnt) {
             const float4 bx = sBox[j];
             hit = bx.y >= pu_lo && bx.x <= pu_hi && bx.w >= pv_lo && bx.z <= pv_hi;
-            if (hit) hit = footprint_meets_rect(sP0[j], sP1[j], thr, pu_lo, pu_hi, pv_lo, pv_hi);
+            if (hit) hit = footprint_meets_rect(sP0[j], make_float2(sP1[j].x, sP1[j].y), thr, pu_lo, pu_hi, pv_lo, pv_hi);
         }
         const uint32_t m = __ballot_sync(0xffffffffu, hit);
-        if (hit) list[nl + __popc(m & ((1u << lane) - 1u))] = (uint8_t)j;
+        if (hit) list[nl + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(j << 4);
         nl += __popc(m);
     }
     __syncwarp();

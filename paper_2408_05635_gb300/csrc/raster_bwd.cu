@@ -43,9 +43,9 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     griddep_wait();  // the predecessor's results are visible from here on
     griddep_launch_dependents();
     __shared__ float4 sP0[NB], sC[NB], sQ[NB], sBox[NB];
-    __shared__ float2 sP1[NB];
+    __shared__ float4 sP1[NB];  // (kuu, lo, -, -): the 16-byte stride of sP0 and sC
     __shared__ float sAcc[NB * kAccStride];
-    __shared__ uint8_t sList[kTilePix / 32][NB];
+    __shared__ uint16_t sList[kTilePix / 32][NB];  // byte offsets: 16 x batch position
     __shared__ int s_view;
     __shared__ uint32_t s_nmax;
     const uint32_t tile = L.ws.tile_order[blockIdx.x];
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
                 const Rec rr = L.ws.rec[r];
                 const Footprint f = stage_footprint(rr.a, rr.b, x0, y0);
                 sP0[tid] = f.p0;
-                sP1[tid] = f.p1;
+                sP1[tid] = make_float4(f.p1.x, f.p1.y, 0.f, 0.f);
                 sC[tid] = make_float4(rr.c.x, rr.c.y, rr.c.z, rr.a.z);
                 sQ[tid] = make_float4(rr.b.x, rr.b.y, rr.b.z, rr.a.w);
                 sBox[tid] = stage_box(rr.b, -f.p0.x, -f.p0.y);
@@ -143,45 +143,44 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
         const int wcnt = (int)min((int64_t)cnt, (int64_t)wlast - b0);
         const int nl = build_patch_list(sBox, sP0, sP1, sList[warp], wcnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
         int e = nl - 1;
+        // entries at byte offsets below lim are in front of this pixel's last contributor
+        const int lim = (int)max(min((int64_t)last - b0, (int64_t)NB), (int64_t)0) * 16;
         if constexpr (POSE) {
             // two Gaussians per step: the pixel state is updated in depth order (the back
             // one first), and the two reductions are independent, so they overlap
             for (; e >= 1; e -= 2) {
                 const int jA = sList[warp][e], jB = sList[warp][e - 1];
-                const uint32_t iA = (uint32_t)b0 + (uint32_t)jA, iB = (uint32_t)b0 + (uint32_t)jB;
-                const PolyEval pA = eval_poly(uv, sP0[jA], sP1[jA]);
-                const PolyEval pB = eval_poly(uv, sP0[jB], sP1[jB]);
-                const bool lA = iA < last, lB = iB < last;
+                const PolyEval pA = eval_poly(uv, at_off(sP0, jA), p1_at(sP1, jA));
+                const PolyEval pB = eval_poly(uv, at_off(sP0, jB), p1_at(sP1, jB));
+                const bool lA = jA < lim, lB = jB < lim;
                 n_eval += lA + lB;
                 const bool cA = lA && pA.poly >= thr, cB = lB && pB.poly >= thr;
                 if (!__any_sync(0xffffffffu, cA || cB)) continue;
                 n_contrib += cA + cB;
-                float vA[6], vB[6];
-                bwd_step6(cA, pA, sC[jA], g0, g1, g2, gD, gS, S.alpha_max, T, GB, vA);
-                bwd_step6(cB, pB, sC[jB], g0, g1, g2, gD, gS, S.alpha_max, T, GB, vB);
-                const float s2 = warp_reduce_scatter12(vA, vB, lane);
-                if (pair_slot >= 0 && s2 != 0.f) atomicAdd(&sAcc[((lane & 16) ? jB : jA) * kAccStride + pair_slot], s2);
+                const float s2 = bwd_pair_reduce(cA, pA, at_off(sC, jA), cB, pB, at_off(sC, jB), g0, g1, g2, gD,
+                                                 gS, S.alpha_max, T, GB, lane);
+                if (pair_slot >= 0 && s2 != 0.f)
+                    atomicAdd(&sAcc[(((lane & 16) ? jB : jA) >> 4) * kAccStride + pair_slot], s2);
             }
         }
         for (; e >= 0; --e) {
             const int j = sList[warp][e];
-            const uint32_t idx = (uint32_t)b0 + (uint32_t)j;
-            const bool live = idx < last;
-            const PolyEval pe = eval_poly(uv, sP0[j], sP1[j]);
+            const bool live = j < lim;
+            const PolyEval pe = eval_poly(uv, at_off(sP0, j), p1_at(sP1, j));
             n_eval += live;
             const bool c = live && pe.poly >= thr;
             if (!__any_sync(0xffffffffu, c)) continue;
             n_contrib += c;
             if constexpr (POSE) {
                 float v[6];
-                bwd_step6(c, pe, sC[j], g0, g1, g2, gD, gS, S.alpha_max, T, GB, v);
+                moments6(bwd_step(c, pe, at_off(sC, j), g0, g1, g2, gD, gS, S.alpha_max, T, GB), v);
                 const float sum = warp_reduce_scatter6(v[0], v[1], v[2], v[3], v[4], v[5], lane);
-                if (my_slot >= 0 && sum != 0.f) atomicAdd(&sAcc[j * kAccStride + my_slot], sum);
+                if (my_slot >= 0 && sum != 0.f) atomicAdd(&sAcc[(j >> 4) * kAccStride + my_slot], sum);
             } else {
                 const float araw = ex2_approx(pe.poly);
                 const float a = c ? fminf(S.alpha_max, araw) : 0.f;
                 if (c) T = T * __fdividef(1.f, 1.f - a);  // transmittance in front of this Gaussian
-                const float4 Cc = sC[j];
+                const float4 Cc = at_off(sC, j);
                 const float gv = fmaf(g0, Cc.x, fmaf(g1, Cc.y, fmaf(g2, Cc.z, fmaf(gD, Cc.w, gS))));
                 const float diff = gv - GB;
                 const float dalpha = T * diff;
@@ -194,7 +193,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
                                   w * g0,  w * g1,  w * g2, 0.f, 0.f, 0.f, 0.f, 0.f};
                 int slot;
                 const float sum = warp_reduce_scatter<16>(vals, lane, slot);
-                if (my_slot >= 0 && sum != 0.f) atomicAdd(&sAcc[j * kAccStride + my_slot], sum);
+                if (my_slot >= 0 && sum != 0.f) atomicAdd(&sAcc[(j >> 4) * kAccStride + my_slot], sum);
             }
         }
         __syncthreads();

@@ -28,12 +28,12 @@ __device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x <
 
 // Stage batch position tid of the tile's sorted list (record r) for both walks.
 __device__ __forceinline__ void stage_one(const TrackTileLaunch &L, uint32_t r, float x0, float y0, float4 *sP0,
-                                          float2 *sP1, float4 *sC, float4 *sQ, float4 *sBox, int tid) {
+                                          float4 *sP1, float4 *sC, float4 *sQ, float4 *sBox, int tid) {
     if (r < rec_slots(L.d)) {
         const Rec rr = L.ws.rec[r];
         const Footprint f = stage_footprint(rr.a, rr.b, x0, y0);
         sP0[tid] = f.p0;
-        sP1[tid] = f.p1;
+        sP1[tid] = make_float4(f.p1.x, f.p1.y, 0.f, 0.f);
         sC[tid] = make_float4(rr.c.x, rr.c.y, rr.c.z, rr.a.z);
         sQ[tid] = make_float4(rr.b.x, rr.b.y, rr.b.z, rr.a.w);
         sBox[tid] = stage_box(rr.b, -f.p0.x, -f.p0.y);
@@ -47,15 +47,17 @@ __device__ __forceinline__ void stage_one(const TrackTileLaunch &L, uint32_t r, 
 constexpr int kFusedScratch = (2 * kSortSmemKeys * 8 > kBatch * kAccStride * 4) ? 2 * kSortSmemKeys * 8
                                                                                : kBatch * kAccStride * 4;
 
+// Four blocks per SM (64 registers a thread): with five (48 registers) the walks spill
+// and issue more instructions, and the kernel is slower.
 template <int NB, int LW>
-__global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
+__global__ void __launch_bounds__(kTilePix, 4) k_track_tile(TrackTileLaunch L) {
     static_assert(NB % 32 == 0 && NB <= kBatch, "batch depth: a multiple of 32, at most kBatch");
     static_assert(LW >= 3 && (1 << LW) * kPatchH <= kTilePix, "tile width: 8 to 32 pixels");
     griddep_wait();  // the predecessor's results are visible from here on
     griddep_launch_dependents();
     __shared__ float4 sP0[NB], sC[NB], sQ[NB], sBox[NB];
-    __shared__ float2 sP1[NB];
-    __shared__ uint8_t sList[kTilePix / 32][NB];
+    __shared__ float4 sP1[NB];                     // (kuu, lo, -, -): the 16-byte stride of sP0 and sC
+    __shared__ uint16_t sList[kTilePix / 32][NB];  // byte offsets: 16 x batch position
     // the sort's two key buffers, then (reverse walk) the per-batch accumulators
     __shared__ __align__(16) unsigned char sScratch[kFusedScratch];
     unsigned long long *sKeys = reinterpret_cast<unsigned long long *>(sScratch);
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
     if (!(L.d.flags & GS_SCHED_RADIX)) sort_tile(L.ws, start, (int)n, sKeys);
 
     // ---------------------------------------------------------------- forward (Eqs. 2-4)
-    FwdPixel walk{1.f, 0.f, 0.f, 0.f, 0.f, 0u, !inside};
+    FwdPixel walk{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !inside};
     uint32_t n_eval = 0, n_contrib = 0;
     int64_t staged = -1;  // first list entry of the batch now in shared memory (block-uniform)
     int nl_staged = 0;    // length of this warp's list of the staged batch (warp-uniform)
@@ -165,6 +167,9 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
 
     // ---------------------------------------------------------------- reverse walk (pose)
     if (!(g0 != 0.f || g1 != 0.f || g2 != 0.f || gD != 0.f || gS != 0.f)) last = 0;
+    // the reverse walk evaluates this pixel's entries in front of its last contributor and
+    // differentiates its contributions: the forward's counts up to that entry
+    const uint32_t rev_eval = last ? walk.eval_last : 0u, rev_contrib = last ? n_contrib : 0u;
     uint32_t wlast = last;  // largest contributor count in the warp
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, off));
@@ -188,8 +193,6 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
         my_slot = k < 3 ? k : k + 1;
     }
     float GB = 0.f;  // g . (colour, depth, 1) of everything behind, back-to-front
-    n_eval = 0;
-    n_contrib = 0;
     for (int64_t b0 = nmax ? (int64_t)((nmax - 1) / NB) * NB : -1; b0 >= 0; b0 -= NB) {
         const int cnt = (int)min((uint32_t)NB, nmax - (uint32_t)b0);
         if (b0 != staged && tid < cnt)
@@ -208,7 +211,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
             // wcnt.  A warp whose pixels had all stopped before this batch kept an older
             // list, but then wlast <= b0 and no entry is below wcnt <= 0.
             for (int k = 0; k < nl_staged; k += 32) {
-                const bool below = k + lane < nl_staged && (int)sList[warp][k + lane] < wcnt;
+                const bool below = k + lane < nl_staged && (int)sList[warp][k + lane] < wcnt * 16;
                 const int m = __popc(__ballot_sync(0xffffffffu, below));
                 nl += m;
                 if (m < 32) break;
@@ -217,37 +220,30 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
             nl = build_patch_list(sBox, sP0, sP1, sList[warp], wcnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
         }
         int e = nl - 1;
+        // entries at byte offsets below lim are in front of this pixel's last contributor
+        const int lim = (int)max(min((int64_t)last - b0, (int64_t)NB), (int64_t)0) * 16;
         // two Gaussians per step: the pixel state is updated in depth order (the back one
         // first), and the two reductions are independent, so they overlap
         for (; e >= 1; e -= 2) {
             const int jA = sList[warp][e], jB = sList[warp][e - 1];
-            const uint32_t iA = (uint32_t)b0 + (uint32_t)jA, iB = (uint32_t)b0 + (uint32_t)jB;
-            const PolyEval pA = eval_poly(uv, sP0[jA], sP1[jA]);
-            const PolyEval pB = eval_poly(uv, sP0[jB], sP1[jB]);
-            const bool lA = iA < last, lB = iB < last;
-            n_eval += lA + lB;
-            const bool cA = lA && pA.poly >= thr, cB = lB && pB.poly >= thr;
+            const PolyEval pA = eval_poly(uv, at_off(sP0, jA), p1_at(sP1, jA));
+            const PolyEval pB = eval_poly(uv, at_off(sP0, jB), p1_at(sP1, jB));
+            const bool cA = jA < lim && pA.poly >= thr, cB = jB < lim && pB.poly >= thr;
             if (!__any_sync(0xffffffffu, cA || cB)) continue;
-            n_contrib += cA + cB;
-            float vA[6], vB[6];
-            bwd_step6(cA, pA, sC[jA], g0, g1, g2, gD, gS, S.alpha_max, T, GB, vA);
-            bwd_step6(cB, pB, sC[jB], g0, g1, g2, gD, gS, S.alpha_max, T, GB, vB);
-            const float s2 = warp_reduce_scatter12(vA, vB, lane);
-            if (pair_slot >= 0 && s2 != 0.f) atomicAdd(&sAcc[((lane & 16) ? jB : jA) * kAccStride + pair_slot], s2);
+            const float s2 = bwd_pair_reduce(cA, pA, at_off(sC, jA), cB, pB, at_off(sC, jB), g0, g1, g2, gD, gS,
+                                             S.alpha_max, T, GB, lane);
+            if (pair_slot >= 0 && s2 != 0.f)
+                atomicAdd(&sAcc[(((lane & 16) ? jB : jA) >> 4) * kAccStride + pair_slot], s2);
         }
         for (; e >= 0; --e) {
             const int j = sList[warp][e];
-            const uint32_t idx = (uint32_t)b0 + (uint32_t)j;
-            const bool live = idx < last;
-            const PolyEval pe = eval_poly(uv, sP0[j], sP1[j]);
-            n_eval += live;
-            const bool c = live && pe.poly >= thr;
+            const PolyEval pe = eval_poly(uv, at_off(sP0, j), p1_at(sP1, j));
+            const bool c = j < lim && pe.poly >= thr;
             if (!__any_sync(0xffffffffu, c)) continue;
-            n_contrib += c;
             float v[6];
-            bwd_step6(c, pe, sC[j], g0, g1, g2, gD, gS, S.alpha_max, T, GB, v);
+            moments6(bwd_step(c, pe, at_off(sC, j), g0, g1, g2, gD, gS, S.alpha_max, T, GB), v);
             const float sum = warp_reduce_scatter6(v[0], v[1], v[2], v[3], v[4], v[5], lane);
-            if (my_slot >= 0 && sum != 0.f) atomicAdd(&sAcc[j * kAccStride + my_slot], sum);
+            if (my_slot >= 0 && sum != 0.f) atomicAdd(&sAcc[(j >> 4) * kAccStride + my_slot], sum);
         }
         __syncthreads();
         if (tid < cnt) {
@@ -264,7 +260,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_track_tile(TrackTileLaunch L) {
         __syncthreads();
         staged = -1;  // every later batch is staged again
     }
-    count_pairs(n_eval, n_contrib, &L.ws.hdr->bwd_evals, &L.ws.hdr->bwd_contrib);
+    count_pairs(rev_eval, rev_contrib, &L.ws.hdr->bwd_evals, &L.ws.hdr->bwd_contrib);
 }
 
 template <int NB, int LW>
