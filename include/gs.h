@@ -234,16 +234,22 @@ typedef struct {
     double *result;
 } gs_host_targets;
 
-/* gs_track_step for a frame that is still in host memory: the call first copies src into
- * the device buffers of `targets` (which it overwrites), on a branch of its work that
- * runs beside the first iteration's projection, scan and key emission; the first
- * compositor waits for the copy, everything else is gs_track_step.  The copy is part of
- * the CUDA graph (one per argument set, src included).  With src->result the poses and
- * losses reach host memory without a copy after the call (the finalize kernel stores them
- * there); they are valid once the stream has passed the call.  Errors: as gs_track_step;
- * INVALID_ARG when src is NULL, lacks rgb or depth, has a depth prior exactly when
- * targets has none (or the reverse), or an array is not page-locked (result: not mapped)
- * host memory. */
+/* gs_track_step for a frame that is still in host memory.  With `targets` (device
+ * buffers, which it overwrites) the call first copies src into them, on a branch of its
+ * work that runs beside the first iteration's projection, scan and key emission; the
+ * first compositor waits for the copy, everything else is gs_track_step.  With targets
+ * NULL there is no copy: the kernels read the frame in place through the device
+ * addresses of src's arrays (page-locked memory mapped into the device's address space,
+ * read over the host link by the compositor where it evaluates the loss) -- the faster
+ * form for one iteration, while a copy is read from device memory by every iteration of a
+ * longer call.  The copy or the
+ * in-place reads are part of the CUDA graph (one per argument set, src included).  With
+ * src->result the poses and losses reach host memory without a copy after the call (the
+ * finalize kernel stores them there); they are valid once the stream has passed the call.
+ * Errors: as gs_track_step; INVALID_ARG when src is NULL, lacks rgb or depth, has a depth
+ * prior exactly when targets has none (or the reverse), or an array is not page-locked
+ * host memory (mapped into the device's address space where it is read in place or is
+ * the result). */
 gs_status gs_track_step_upload(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g, const gs_targets *targets,
                                const gs_host_targets *src, double *poses, double *adam_state, double *loss_hist,
                                int32_t iters, void *ws, size_t ws_bytes, void *stream);

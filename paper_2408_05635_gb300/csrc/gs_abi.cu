@@ -740,6 +740,26 @@ gs_status track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
     if (!ctx) return GS_ERR_INVALID_ARG;
     ctx->err.clear();
     if (iters < 1) return fail(ctx, GS_ERR_INVALID_ARG, "iters must be >= 1");
+    // without device targets (gs_track_step_upload only) the kernels read the frame in
+    // place: src's page-locked arrays through their device addresses
+    const bool in_place = src && !targets;
+    gs_targets src_dev{};
+    if (in_place) {
+        if (!src->rgb || !src->depth) return fail(ctx, GS_ERR_INVALID_ARG, "src needs rgb and depth");
+        const float *const host[3] = {src->rgb, src->depth, src->depth_prior};
+        const float **dev[3] = {&src_dev.rgb, &src_dev.depth, &src_dev.depth_prior};
+        for (int k = 0; k < 3; ++k) {
+            if (!host[k]) continue;
+            void *d = nullptr;
+            if (!pinned_host(host[k]) || cudaHostGetDevicePointer(&d, const_cast<float *>(host[k]), 0) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(ctx, GS_ERR_INVALID_ARG, "src arrays must be page-locked host memory mapped into the device's "
+                                                     "address space");
+            }
+            *dev[k] = static_cast<const float *>(d);
+        }
+        targets = &src_dev;
+    }
     if (!targets || !targets->rgb || !targets->depth) return fail(ctx, GS_ERR_INVALID_ARG, "targets need rgb and depth");
     if (!poses || !adam_state) return fail(ctx, GS_ERR_INVALID_ARG, "poses and adam_state are required");
     if (src) {
@@ -767,7 +787,8 @@ gs_status track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
     auto enqueue_all = [&](cudaStream_t q) -> cudaError_t {
         // the frame's upload runs beside the view upload and the first projection, scan and
         // emission
-        cudaError_t r0 = src ? fork_upload(ctx, targets, src, pr.d.P, q) : cudaSuccess;
+        const bool upload = src && !in_place;
+        cudaError_t r0 = upload ? fork_upload(ctx, targets, src, pr.d.P, q) : cudaSuccess;
         if (r0 != cudaSuccess) return r0;
         // the view table and the per-call reset, as the graph's first node (its arguments
         // are part of the graph's key); flags latch over all iterations of the call
@@ -775,7 +796,7 @@ gs_status track_step(gs_ctx *ctx, const gs_problem *prob, const gs_gaussians *g,
         for (int it = 0; it < iters; ++it) {
             cudaError_t r = cudaSuccess;
             if ((r = enqueue_project(ctx, pr, w, gp, g->dtype_attr, poses, q)) != cudaSuccess) return r;
-            if (it == 0 && src && (r = join_upload(ctx, q)) != cudaSuccess) return r;
+            if (it == 0 && upload && (r = join_upload(ctx, q)) != cudaSuccess) return r;
             if ((r = enqueue_compositing(ctx, pr, w, targets, q)) != cudaSuccess) return r;
             BprojLaunch J;
             J.ws = w;

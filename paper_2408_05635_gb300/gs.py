@@ -272,11 +272,13 @@ def gs_track_step(ctx, prob: gs_problem, g: gs_gaussians, targets: gs_targets, p
                                      _stream(stream)), "gs_track_step")
 
 
-def gs_track_step_upload(ctx, prob: gs_problem, g: gs_gaussians, targets: gs_targets, src: gs_host_targets, poses,
+def gs_track_step_upload(ctx, prob: gs_problem, g: gs_gaussians, targets, src: gs_host_targets, poses,
                          adam_state, loss_hist, iters: int, ws, ws_bytes: int, stream=None) -> None:
-    """gs_track_step with the frame copied from page-locked host memory (src) into the
-    device targets beside the first iteration's binning."""
-    _check(ctx, load().gs_track_step_upload(ctx, ctypes.byref(prob), ctypes.byref(g), ctypes.byref(targets),
+    """gs_track_step with the frame in page-locked host memory (src): copied into the
+    device targets beside the first iteration's binning, or, with targets None, read in
+    place by the kernels."""
+    _check(ctx, load().gs_track_step_upload(ctx, ctypes.byref(prob), ctypes.byref(g),
+                                            ctypes.byref(targets) if targets is not None else None,
                                             ctypes.byref(src), _ptr(poses), _ptr(adam_state), _ptr(loss_hist),
                                             int(iters), _ptr(ws), ws_bytes, _stream(stream)), "gs_track_step_upload")
 

@@ -130,15 +130,15 @@ def test_tracking_graph_first_update(tracking, flags):
 
 
 def test_tracking_with_host_upload_equals_device_targets(tracking):
-    """gs_track_step_upload: the frame in page-locked host memory is copied into the
-    device targets beside the first iteration's binning.  Five iterations from the start
-    pose give the poses, losses and Adam state of gs_track_step on the device frame to the
-    run-to-run spread of the FP32 gradient atomics, whose order is not fixed (poses 1e-7
-    absolute: Adam's step lr g / (|g| + eps) moves a coordinate with a near-zero gradient
-    by that noise; losses 1e-6 relative; moments 1e-4 relative), the device targets hold the
-    host frame afterwards (they start as NaN), the host result holds the last pose and loss
-    (stored there by the device), and a frame in ordinary (pageable) host memory is
-    refused."""
+    """gs_track_step_upload: the frame in page-locked host memory is either copied into the
+    device targets beside the first iteration's binning, or (targets NULL) read in place by
+    the kernels.  Five iterations from the start pose give, in both forms, the poses,
+    losses and Adam state of gs_track_step on the device frame to the run-to-run spread of
+    the FP32 gradient atomics, whose order is not fixed (poses 1e-7 absolute: Adam's step
+    lr g / (|g| + eps) moves a coordinate with a near-zero gradient by that noise; losses
+    1e-6 relative; moments 1e-4 relative); the device targets hold the host frame after the
+    copy (they start as NaN); the host result holds the last pose and loss (stored there by
+    the device); and a frame in ordinary (pageable) host memory is refused in both forms."""
     t = tracking
     R = gs.Rasterizer(gs.Config())
     R.set_schedule(16, 16, 4, 256, 256, gs.GS_SCHED_FUSED)
@@ -147,25 +147,28 @@ def test_tracking_with_host_upload_equals_device_targets(tracking):
     prob = R.plan(gt, [t["cam"]], start, margin=1.5)
     ws, nb = R.workspace(prob)
     out = []
-    for upload in (False, True):
+    for mode in ("device", "copy", "in_place"):
         poses = start.clone()
         adam = torch.zeros(1, 16, dtype=torch.float64, device="cuda")
         hist = torch.zeros(5, 1, dtype=torch.float64, device="cuda")
-        if upload:
+        if mode != "device":
             dev = tuple(torch.full_like(x, float("nan")) for x in t["targets"])
             host = tuple(x.cpu().pin_memory() for x in t["targets"])
             result = torch.full((8,), float("nan"), dtype=torch.float64).pin_memory()
             src = gs.gs_host_targets(*(x.data_ptr() for x in host), result.data_ptr())
-            tg = gs.gs_targets(*(x.data_ptr() for x in dev))
+            tg = gs.gs_targets(*(x.data_ptr() for x in dev)) if mode == "copy" else None
             gs.gs_track_step_upload(R.ctx, prob, gt.c(), tg, src, poses, adam, hist, 5, ws, nb)
         else:
             tg = gs.gs_targets(*(x.data_ptr() for x in t["targets"]))
             gs.gs_track_step(R.ctx, prob, gt.c(), tg, poses, adam, hist, 5, ws, nb)
         R.sync()
         out.append((poses.cpu().numpy(), hist.cpu().numpy(), adam.cpu().numpy()))
-        if upload:
+        if mode != "device":
             for d, h in zip(dev, host):
-                assert torch.equal(d.cpu(), h)
+                if mode == "copy":
+                    assert torch.equal(d.cpu(), h)
+                else:  # read in place: the device buffers are not touched
+                    assert torch.isnan(d).all()
             # the last iteration's pose and loss, stored into host memory by the device
             np.testing.assert_array_equal(result.numpy()[:7], out[-1][0][0])
             assert result.numpy()[7] == out[-1][1][-1, 0]
@@ -173,10 +176,11 @@ def test_tracking_with_host_upload_equals_device_targets(tracking):
             bad = gs.gs_host_targets(*(x.data_ptr() for x in pageable), None)
             with pytest.raises(gs.GsError):
                 gs.gs_track_step_upload(R.ctx, prob, gt.c(), tg, bad, poses, adam, hist, 1, ws, nb)
-    (p0, h0, a0), (p1, h1, a1) = out
-    np.testing.assert_allclose(p1, p0, rtol=0, atol=1e-7)
-    np.testing.assert_allclose(h1, h0, rtol=1e-6)
-    np.testing.assert_allclose(a1, a0, rtol=1e-4, atol=1e-9 * np.abs(a0).max())
+    p0, h0, a0 = out[0]
+    for p1, h1, a1 in out[1:]:
+        np.testing.assert_allclose(p1, p0, rtol=0, atol=1e-7)
+        np.testing.assert_allclose(h1, h0, rtol=1e-6)
+        np.testing.assert_allclose(a1, a0, rtol=1e-4, atol=1e-9 * np.abs(a0).max())
 
 
 # ---------------------------------------------------------------------------- batched hypotheses
