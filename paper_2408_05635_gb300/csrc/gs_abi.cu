@@ -41,7 +41,7 @@ uint32_t max_sub(uint64_t T) {
 struct Layout {
     size_t err, hdr, tile_cnt, zero_end;
     size_t views, view_rt, cell_cnt, tile_start, cursor, tile_order, big, big_listed, rec, rec_grad, keys, sorted, t_final, n_last,
-        upstream, tile_loss, pose_part, rkeys, rvals, rhist, rtotal, total;
+        upstream, tile_loss, pose_part, rkeys, rvals, rhist, rtotal, scan_part, total;
 };
 
 struct Problem {
@@ -317,6 +317,7 @@ gs_status build_problem(gs_ctx *ctx, const gs_problem *p, Problem &out) {
     L.rvals = take(sizeof(uint32_t) * (size_t)d.pair_cap);
     L.rhist = take(sizeof(uint32_t) * 256 * (size_t)radix_blocks(d.pair_cap));
     L.rtotal = take(sizeof(uint32_t) * 256);
+    L.scan_part = take(sizeof(uint32_t) * (3 + kMBuckets) * (size_t)scan_blocks(lay_cnt));
     L.total = o;
     return GS_OK;
 }
@@ -348,6 +349,7 @@ WsPtrs ws_ptrs(void *base, const Layout &L) {
     w.rvals = reinterpret_cast<uint32_t *>(b + L.rvals);
     w.rhist = reinterpret_cast<uint32_t *>(b + L.rhist);
     w.rtotal = reinterpret_cast<uint32_t *>(b + L.rtotal);
+    w.scan_part = reinterpret_cast<uint32_t *>(b + L.scan_part);
     return w;
 }
 

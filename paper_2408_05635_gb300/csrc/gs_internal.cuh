@@ -142,7 +142,21 @@ struct WsPtrs {
     uint32_t *rvals;       // pair_capacity: its second value buffer
     uint32_t *rhist;       // 256 x radix_blocks(pair_capacity) digit counts
     uint32_t *rtotal;      // 256 digit totals
+    uint32_t *scan_part;   // the multi-block scan's per-block sums, longest lists, record
+                           // counts and launch-order bucket counts, or nullptr (one-block scan)
 };
+
+// Multi-block form of the tile scan (problems with more counters than one block takes in
+// one pass): kMBThreads threads a block, kMBPer counters a thread, kMBuckets launch-order
+// buckets.  scan_blocks(c) blocks for c counters; ws.scan_part holds (3 + kMBuckets) words
+// per block.
+constexpr int kMBThreads = 256;
+constexpr int kMBPer = 8;
+constexpr uint32_t kMBChunk = (uint32_t)kMBThreads * kMBPer;
+constexpr int kMBuckets = 64;
+__host__ __device__ inline uint32_t scan_blocks(uint64_t counters) {
+    return (uint32_t)((counters + kMBChunk - 1) / kMBChunk);
+}
 
 struct Dims {
     int64_t n;             // Gaussians

@@ -279,8 +279,228 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(WsPtrs ws, Dims d) 
     }
 }
 
+// ------------------------------------------------------------ multi-block form of the scan
+// For problems with more counters than one block covers in one pass (many views or small
+// tiles), three kernels: (1) each block of kMBThreads sums a chunk of kMBChunk counters,
+// counts its tiles into kMBuckets launch-order buckets (list length / 16, the longest
+// first), and sums a slice of the cells' record counts; (2) one block turns the chunk sums
+// and the bucket counts (bucket-major, so a bucket's blocks are consecutive) into
+// exclusive offsets, and writes the totals to the header; (3) each block scans its chunk
+// again from its offset, writes the list offsets and cursors, zeroes the counters, and
+// places its tiles in the launch order from its buckets' offsets.  The per-block arrays
+// live in ws.scan_part: sums, longest lists, record counts (NB each), then the bucket
+// counts (kMBuckets x NB).
+
+__device__ __forceinline__ uint32_t mb_bucket(uint32_t len) {
+    return kMBuckets - 1 - min(len >> 4, (uint32_t)kMBuckets - 1);
+}
+
+// Exclusive scan of one value per thread over a block of NT threads (NT / 32 <= 32 warps);
+// `total` gets the block sum.  Ends with a barrier.
+template <int NT, class T>
+__device__ __forceinline__ T block_scan_excl(T x, T *warp_sum, T &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    T wi = lane < NT / 32 ? warp_sum[lane] : T(0);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T v = __shfl_up_sync(0xffffffffu, wi, off);
+        if (lane >= off) wi += v;
+    }
+    const T prev = __shfl_sync(0xffffffffu, wi, (warp + 31) & 31);
+    total = __shfl_sync(0xffffffffu, wi, NT / 32 - 1);
+    __syncthreads();
+    return (warp > 0 ? prev : T(0)) + incl - x;
+}
+
+// This thread's kMBPer counters of chunk position i0 (vector loads where the run is whole).
+__device__ __forceinline__ void load_counts(const uint32_t *cnt, uint32_t i0, uint32_t TS, uint32_t (&c)[kMBPer]) {
+    if (i0 + kMBPer <= TS) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(cnt + i0);
+        const uint4 a = q[0], b = q[1];
+        c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+        c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kMBPer; ++k) c[k] = i0 + k < TS ? cnt[i0 + k] : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kMBThreads) k_scan_part(WsPtrs ws, Dims d) {
+    griddep_wait();  // the predecessor's results are visible from here on
+    griddep_launch_dependents();
+    __shared__ uint32_t s_hist[kMBuckets], s_sum, s_max, s_rec;
+    const uint32_t TS = d.T * d.S, smask = d.S - 1, NB = gridDim.x, b = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (tid < kMBuckets) s_hist[tid] = 0u;
+    if (tid == 0) s_sum = s_max = s_rec = 0u;
+    __syncthreads();
+    uint32_t c[kMBPer];
+    const uint32_t i0 = b * kMBChunk + (uint32_t)tid * kMBPer;
+    load_counts(ws.tile_cnt, i0, TS, c);
+    uint32_t mine = 0, mx = 0;
+#pragma unroll
+    for (int j = 0; j < kMBPer; ++j) {
+        mine += c[j];
+        if ((j & smask) == 0 && i0 + j < TS) {  // the S counters of a tile sit in one thread
+            uint32_t l = c[j];
+            if (d.S > 1) l += c[(j + 1) % kMBPer];
+            if (d.S > 2) l += c[(j + 2) % kMBPer] + c[(j + 3) % kMBPer];
+            mx = max(mx, l);
+            atomicAdd(&s_hist[mb_bucket(l)], 1u);
+        }
+    }
+    const uint32_t ncell = (uint32_t)d.V * (uint32_t)d.nblk, cpb = (ncell + NB - 1) / NB;
+    uint32_t rec = 0;
+    for (uint32_t k = b * cpb + (uint32_t)tid; k < min(ncell, (b + 1) * cpb); k += kMBThreads) rec += ws.cell_cnt[k];
+    mine = __reduce_add_sync(0xffffffffu, mine);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    rec = __reduce_add_sync(0xffffffffu, rec);
+    if ((tid & 31) == 0) {
+        atomicAdd(&s_sum, mine);
+        atomicMax(&s_max, mx);
+        atomicAdd(&s_rec, rec);
+    }
+    __syncthreads();
+    uint32_t *part = ws.scan_part;
+    if (tid == 0) {
+        part[b] = s_sum;
+        part[NB + b] = s_max;
+        part[2 * NB + b] = s_rec;
+    }
+    if (tid < kMBuckets) part[3 * NB + (uint32_t)tid * NB + b] = s_hist[tid];
+}
+
+// In-place exclusive scan of a[0, n) by one block of kScanThreads (each thread a
+// contiguous run); returns the total to every thread.  Sums saturate at 2^32 - 1 where
+// they are stored.
+__device__ __forceinline__ unsigned long long block_scan_array(uint32_t *a, uint32_t n,
+                                                               unsigned long long *warp_sum) {
+    const uint32_t per = (n + kScanThreads - 1) / kScanThreads, lo = min(n, (uint32_t)threadIdx.x * per),
+                   hi = min(n, lo + per);
+    unsigned long long sum = 0;
+    for (uint32_t i = lo; i < hi; ++i) sum += a[i];
+    unsigned long long total;
+    unsigned long long run = block_scan_excl<kScanThreads>(sum, warp_sum, total);
+    for (uint32_t i = lo; i < hi; ++i) {
+        const uint32_t v = a[i];
+        a[i] = (uint32_t)min(run, (unsigned long long)0xffffffffu);
+        run += v;
+    }
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(WsPtrs ws, Dims d) {
+    griddep_wait();  // the predecessor's results are visible from here on
+    griddep_launch_dependents();
+    __shared__ unsigned long long warp_sum[kScanThreads / 32];
+    __shared__ uint32_t s_max;
+    __shared__ unsigned long long s_rec;
+    const uint32_t TS = d.T * d.S, NB = (TS + kMBChunk - 1) / kMBChunk;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_max = 0u;
+        s_rec = 0ull;
+    }
+    uint32_t *part = ws.scan_part;
+    const unsigned long long total = block_scan_array(part, NB, warp_sum);  // chunk offsets
+    block_scan_array(part + 3 * NB, kMBuckets * NB, warp_sum);              // launch-order offsets
+    uint32_t mx = 0;
+    unsigned long long rec = 0;
+    for (uint32_t i = (uint32_t)tid; i < NB; i += kScanThreads) {
+        mx = max(mx, part[NB + i]);
+        rec += part[2 * NB + i];
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rec += __shfl_xor_sync(0xffffffffu, rec, off);
+    if ((tid & 31) == 0) {
+        atomicMax(&s_max, mx);
+        atomicAdd(&s_rec, rec);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        ws.tile_start[TS] = (uint32_t)min(total, (unsigned long long)0xffffffffu);
+        ws.hdr->n_big = ws.tile_cnt[TS];  // the large records k_project listed, zeroed for the next pass
+        ws.tile_cnt[TS] = 0u;
+        ws.hdr->max_tile = s_max;
+        ws.hdr->n_rec = s_rec;
+        ws.hdr->n_pairs = total;
+        if (total > d.pair_cap) atomicOr(ws.err, (uint32_t)kErrPairs);
+    }
+}
+
+__global__ void __launch_bounds__(kMBThreads) k_scan_write(WsPtrs ws, Dims d) {
+    griddep_wait();  // the predecessor's results are visible from here on
+    griddep_launch_dependents();
+    __shared__ uint32_t warp_sum[kMBThreads / 32], s_pos[kMBuckets];
+    const uint32_t TS = d.T * d.S, smask = d.S - 1, sshift = __ffs(d.S) - 1, NB = gridDim.x, b = blockIdx.x;
+    const int tid = threadIdx.x;
+    const uint32_t *part = ws.scan_part;
+    if (tid < kMBuckets) s_pos[tid] = part[3 * NB + (uint32_t)tid * NB + b];
+    uint32_t c[kMBPer];
+    const uint32_t i0 = b * kMBChunk + (uint32_t)tid * kMBPer;
+    load_counts(ws.tile_cnt, i0, TS, c);
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < kMBPer; ++k) mine += c[k];
+    uint32_t total;
+    const uint32_t excl = block_scan_excl<kMBThreads>(mine, warp_sum, total);  // (ends with a barrier)
+    unsigned long long run = (unsigned long long)part[b] + excl;
+    uint32_t o[kMBPer];
+#pragma unroll
+    for (int k = 0; k < kMBPer; ++k) {
+        o[k] = (uint32_t)min(run, (unsigned long long)0xffffffffu);
+        run += c[k];
+    }
+    if (i0 + kMBPer <= TS) {  // whole 32-byte rows: two vector stores per array
+        const uint4 a = make_uint4(o[0], o[1], o[2], o[3]), e = make_uint4(o[4], o[5], o[6], o[7]);
+        reinterpret_cast<uint4 *>(ws.tile_start + i0)[0] = a;
+        reinterpret_cast<uint4 *>(ws.tile_start + i0)[1] = e;
+        reinterpret_cast<uint4 *>(ws.cursor + i0)[0] = a;
+        reinterpret_cast<uint4 *>(ws.cursor + i0)[1] = e;
+        reinterpret_cast<uint4 *>(ws.tile_cnt + i0)[0] = make_uint4(0u, 0u, 0u, 0u);
+        reinterpret_cast<uint4 *>(ws.tile_cnt + i0)[1] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kMBPer; ++k)
+            if (i0 + k < TS) {
+                ws.tile_start[i0 + k] = o[k];
+                ws.cursor[i0 + k] = o[k];
+                ws.tile_cnt[i0 + k] = 0u;
+            }
+    }
+#pragma unroll
+    for (int j = 0; j < kMBPer; ++j) {
+        if ((j & smask) == 0 && i0 + j < TS) {
+            uint32_t l = c[j];
+            if (d.S > 1) l += c[(j + 1) % kMBPer];
+            if (d.S > 2) l += c[(j + 2) % kMBPer] + c[(j + 3) % kMBPer];
+            ws.tile_order[atomicAdd(&s_pos[mb_bucket(l)], 1u)] = (i0 + (uint32_t)j) >> sshift;
+        }
+    }
+}
+
+// Up to four passes of the one-block scan take less than the three launches of the
+// multi-block form.
+constexpr uint64_t kMultiBlockScanFrom = 4ull * kScanThreads * kScanPer;
+
 cudaError_t launch_scan_tiles(const WsPtrs &ws, const Dims &d, cudaStream_t st) {
-    return launch_dep(k_scan_tiles, dim3(1), dim3(kScanThreads), st, ws, d);
+    const uint64_t TS = (uint64_t)d.T * d.S;
+    if (TS <= kMultiBlockScanFrom || !ws.scan_part)
+        return launch_dep(k_scan_tiles, dim3(1), dim3(kScanThreads), st, ws, d);
+    const uint32_t NB = scan_blocks(TS);
+    cudaError_t e = launch_dep(k_scan_part, dim3(NB), dim3(kMBThreads), st, ws, d);
+    if (e == cudaSuccess) e = launch_dep(k_scan_top, dim3(1), dim3(kScanThreads), st, ws, d);
+    if (e == cudaSuccess) e = launch_dep(k_scan_write, dim3(NB), dim3(kMBThreads), st, ws, d);
+    return e;
 }
 
 // A block's large records (more than kSoloTiles candidate tiles) are counted by all its

@@ -138,6 +138,38 @@ def test_multi_view_uneven_resolution():
         check_images(rgbs[k], deps[k], sils[k], ref, sc, cam, pose, op, what=f"view {k}")
 
 
+def test_multi_block_scan_matches_single_view_calls():
+    """40 views of 320 x 240 with 8 x 8 tiles and four sub-buckets per tile (192 k tile
+    counters) take the multi-block scan; each view alone (4,800 counters) the one-block
+    scan.  The images of the joint call equal those of the single-view calls bit for bit
+    (the compositors sort each tile's list, so only the offsets and the launch order come
+    from the scan), and the pair and record counts of the joint call are the sums of the
+    single-view counts (the longest list their maximum)."""
+    g, _ = scenes.cube_scene(n=3000, seed=11)
+    cam = scenes.Cam(280.0, 280.0, 159.5, 119.5, 320, 240)
+    rng = np.random.default_rng(12)
+    poses = [scenes.perturb_pose(scenes.identity_pose(), rng, 4.0, 0.06) for _ in range(40)]
+    gcfg, _ = params_pair()
+    R = gs.Rasterizer(gcfg)
+    R.set_schedule(8, 8, 4, 64, 64, 0)
+    gt = gs.GaussianTensors.from_numpy(g)
+    out, _, _, counts = gpu_render(R, gt, [cam] * 40, poses)
+    assert 40 * (320 // 8) * (240 // 8) * 4 > 4 * 8192  # the multi-block form is taken
+    n_pairs = n_records = 0
+    max_tile = 0
+    joint = {key: split_views(out[key], [cam] * 40, ch) for key, ch in (("rgb", 3), ("depth", 1), ("sil", 1))}
+    for v, pose in enumerate(poses):
+        one, _, _, c = gpu_render(R, gt, [cam], [pose])
+        for key, ch in (("rgb", 3), ("depth", 1), ("sil", 1)):
+            np.testing.assert_array_equal(joint[key][v].reshape(-1), one[key].reshape(-1), err_msg=f"view {v} {key}")
+        n_pairs += int(c.n_pairs)
+        n_records += int(c.n_records)
+        max_tile = max(max_tile, int(c.max_tile))
+    assert int(counts.n_pairs) == n_pairs
+    assert int(counts.n_records) == n_records
+    assert int(counts.max_tile) == max_tile
+
+
 def test_long_tile_list_uses_global_sort():
     """More than 4096 Gaussians on one tile: the in-place global-memory sort path."""
     rng = np.random.default_rng(2)
