@@ -356,7 +356,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 
 struct Footprint {
     float4 p0;  // (-cu, -cv, kuv, kvv)
-    float2 p1;  // (kuu, lo)
+    float4 p1;  // (kuu, lo, -1/(2 kuu), -1/(2 kvv)): the last two for footprint_meets_rect
 };
 
 // Programmatic dependent launch.  The kernels of a tracking iteration form one chain on a
@@ -401,7 +401,8 @@ __device__ __forceinline__ float lg2_approx(float x) {
 __device__ __forceinline__ Footprint stage_footprint(const float4 A, const float4 B, float x0, float y0) {
     Footprint f;
     f.p0 = make_float4(__fsub_rn(x0, A.x), __fsub_rn(y0, A.y), __fmul_rn(-kLog2e, B.y), __fmul_rn(-0.5f * kLog2e, B.z));
-    f.p1 = make_float2(__fmul_rn(-0.5f * kLog2e, B.x), lg2_approx(A.w));
+    const float kuu = __fmul_rn(-0.5f * kLog2e, B.x);
+    f.p1 = make_float4(kuu, lg2_approx(A.w), -0.5f / kuu, -0.5f / f.p0.w);
     return f;
 }
 
@@ -525,14 +526,14 @@ __device__ __forceinline__ PolyEval eval_poly(float2 uv, float4 p0, float2 p1) {
 // comparison keeps a margin of 2^-16 of the terms' magnitude over the rectangle (FP32
 // rounding of this maximum, and of eval_poly at any pixel of it, is a few ulp of that), so
 // no entry with a pixel at alpha >= alpha_min is dropped; degenerate footprints pass.
-__device__ __forceinline__ bool footprint_meets_rect(float4 p0, float2 p1, float thr, float u_lo, float u_hi,
+__device__ __forceinline__ bool footprint_meets_rect(float4 p0, float4 p1, float thr, float u_lo, float u_hi,
                                                      float v_lo, float v_hi) {
     const float kuu = p1.x, kuv = p0.z, kvv = p0.w, lo = p1.y;
     if (!(kuu < 0.f && kvv < 0.f)) return true;
     const float x0 = u_lo + p0.x, x1 = u_hi + p0.x, y0 = v_lo + p0.y, y1 = v_hi + p0.y;
     float q = 0.f;  // max of the quadratic part over the rectangle
     if (!(x0 <= 0.f && x1 >= 0.f && y0 <= 0.f && y1 >= 0.f)) {
-        const float ru = -0.5f / kuu, rv = -0.5f / kvv;
+        const float ru = p1.z, rv = p1.w;  // -0.5 / kuu, -0.5 / kvv, divided once at staging
         const auto f = [&](float dx, float dy) { return fmaf(dx, fmaf(kuu, dx, kuv * dy), kvv * dy * dy); };
         const float ya = fminf(fmaxf(kuv * x0 * rv, y0), y1), yb = fminf(fmaxf(kuv * x1 * rv, y0), y1);
         const float xa = fminf(fmaxf(kuv * y0 * ru, x0), x1), xb = fminf(fmaxf(kuv * y1 * ru, x0), x1);
@@ -544,8 +545,8 @@ __device__ __forceinline__ bool footprint_meets_rect(float4 p0, float2 p1, float
 }
 
 // Staged Gaussians are addressed by byte offset: a warp's list holds 16 x the batch
-// position, and sP0, sP1 and sC all have a 16-byte stride (sP1 carries (kuu, lo) in the
-// first two words), so one list entry addresses all three without index arithmetic.
+// position, and sP0, sP1 and sC all have a 16-byte stride, so one list entry addresses
+// all three without index arithmetic.
 template <class T>
 __device__ __forceinline__ const T &at_off(const T *base, int off) {
     return *reinterpret_cast<const T *>(reinterpret_cast<const char *>(base) + off);
@@ -569,7 +570,7 @@ __device__ __forceinline__ int build_patch_list(const float4 *sBox, const float4
         if (j < cnt) {
             const float4 bx = sBox[j];
             hit = bx.y >= pu_lo && bx.x <= pu_hi && bx.w >= pv_lo && bx.z <= pv_hi;
-            if (hit) hit = footprint_meets_rect(sP0[j], make_float2(sP1[j].x, sP1[j].y), thr, pu_lo, pu_hi, pv_lo, pv_hi);
+            if (hit) hit = footprint_meets_rect(sP0[j], sP1[j], thr, pu_lo, pu_hi, pv_lo, pv_hi);
         }
         const uint32_t m = __ballot_sync(0xffffffffu, hit);
         if (hit) list[nl + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(j << 4);

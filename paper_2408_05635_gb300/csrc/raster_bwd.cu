@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
     griddep_wait();  // the predecessor's results are visible from here on
     griddep_launch_dependents();
     __shared__ float4 sP0[NB], sC[NB], sQ[NB], sBox[NB];
-    __shared__ float4 sP1[NB];  // (kuu, lo, -, -): the 16-byte stride of sP0 and sC
+    __shared__ float4 sP1[NB];  // (kuu, lo, -1/(2 kuu), -1/(2 kvv)): the stride of sP0, sC
     __shared__ float sAcc[NB * kAccStride];
     __shared__ uint16_t sList[kTilePix / 32][NB];  // byte offsets: 16 x batch position
     __shared__ int s_view;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_backward(BackwardLaunch L) {
                 const Rec rr = L.ws.rec[r];
                 const Footprint f = stage_footprint(rr.a, rr.b, x0, y0);
                 sP0[tid] = f.p0;
-                sP1[tid] = make_float4(f.p1.x, f.p1.y, 0.f, 0.f);
+                sP1[tid] = f.p1;
                 sC[tid] = make_float4(rr.c.x, rr.c.y, rr.c.z, rr.a.z);
                 sQ[tid] = make_float4(rr.b.x, rr.b.y, rr.b.z, rr.a.w);
                 sBox[tid] = stage_box(rr.b, -f.p0.x, -f.p0.y);
