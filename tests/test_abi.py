@@ -75,6 +75,34 @@ def test_workspace_size_validation(libpath):
     lib.gs_destroy(h)
 
 
+def test_track_step_upload_validates_before_any_cuda_call(libpath):
+    """gs_track_step_upload refuses a missing src, a zero iteration count, and (reading the
+    frame in place, targets NULL) a src without rgb or depth, before any CUDA call."""
+    from paper_2408_05635_gb300 import gs
+    lib = ctypes.CDLL(libpath)
+    lib.gs_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
+    lib.gs_track_step_upload.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.POINTER(gs.gs_host_targets), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                         ctypes.c_void_p]
+    h = ctypes.c_void_p()
+    assert lib.gs_create(ctypes.byref(h), None) == 0
+    frame = (ctypes.c_float * 8)()
+    result = (ctypes.c_double * 8)()
+    addr = ctypes.addressof(frame)
+    ok_src = gs.gs_host_targets(addr, addr, None, ctypes.addressof(result))
+    no_rgb = gs.gs_host_targets(None, addr, None, None)
+    no_depth = gs.gs_host_targets(addr, None, None, None)
+    call = lambda src, iters: lib.gs_track_step_upload(h, None, None, None, src, None, None, None, iters, None, 0,
+                                                       None)
+    assert call(None, 1) == 1
+    assert call(ctypes.byref(ok_src), 0) == 1
+    assert call(ctypes.byref(no_rgb), 1) == 1
+    assert call(ctypes.byref(no_depth), 1) == 1
+    lib.gs_destroy.argtypes = [ctypes.c_void_p]
+    lib.gs_destroy(h)
+
+
 def _ctx(lib, cfg=None):
     lib.gs_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
     h = ctypes.c_void_p()
