@@ -240,9 +240,10 @@ typedef struct {
  * first compositor waits for the copy, everything else is gs_track_step.  With targets
  * NULL there is no copy: the kernels read the frame in place through the device
  * addresses of src's arrays (page-locked memory mapped into the device's address space,
- * read over the host link by the compositor where it evaluates the loss) -- the faster
- * form for one iteration, while a copy is read from device memory by every iteration of a
- * longer call.  The copy or the
+ * read over the host link by the compositor: each block loads its pixels' targets once
+ * its first batch is staged, so the reads overlap its forward walk) -- the faster form for
+ * one iteration, while a copy is read from device memory by every iteration of a longer
+ * call.  The copy or the
  * in-place reads are part of the CUDA graph (one per argument set, src included).  With
  * src->result the poses and losses reach host memory without a copy after the call (the
  * finalize kernel stores them there); they are valid once the stream has passed the call.

@@ -93,6 +93,15 @@ __global__ void __launch_bounds__(kTilePix, 4) k_track_tile(TrackTileLaunch L) {
     // (GS_SCHED_RADIX) has already ordered it
     if (!(L.d.flags & GS_SCHED_RADIX)) sort_tile(L.ws, start, (int)n, sKeys);
 
+    // this pixel's targets: loaded once the first batch is staged (below), so their
+    // latency (host memory when the frame is read in place) passes during the forward walk
+    // (loaded at the start of the block instead, in-place reads made the kernel slower)
+    const uint32_t HW = (uint32_t)vi.width * (uint32_t)vi.height;
+    const uint32_t p = inside ? (uint32_t)py * (uint32_t)vi.width + (uint32_t)px : 0u;
+    const uint32_t gp = vi.pix_base + p;
+    float tr = 0.f, tg = 0.f, tb = 0.f, Dt = 0.f, pr = 0.f;
+    bool targets_loaded = false;
+
     // ---------------------------------------------------------------- forward (Eqs. 2-4)
     FwdPixel walk{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !inside};
     uint32_t n_eval = 0, n_contrib = 0;
@@ -104,6 +113,17 @@ __global__ void __launch_bounds__(kTilePix, 4) k_track_tile(TrackTileLaunch L) {
         if (tid < NB && idx < n) stage_one(L, L.ws.sorted[start + idx], x0, y0, sP0, sP1, sC, sQ, sBox, tid);
         staged = b0;
         __syncthreads();
+        if (!targets_loaded) {
+            targets_loaded = true;
+            if (inside) {
+                const float *trgb = L.t_rgb + 3u * vi.pix_base;
+                tr = trgb[p];
+                tg = trgb[HW + p];
+                tb = trgb[2u * HW + p];
+                Dt = L.t_depth[gp];
+                if (L.t_prior) pr = L.t_prior[gp];
+            }
+        }
         const int cnt = (int)min((uint32_t)NB, n - b0);
         if (__any_sync(0xffffffffu, !walk.done)) {
             const int nl = build_patch_list(sBox, sP0, sP1, sList[warp], cnt, lane, thr, pu_lo, pu_hi, pv_lo, pv_hi);
@@ -120,19 +140,22 @@ __global__ void __launch_bounds__(kTilePix, 4) k_track_tile(TrackTileLaunch L) {
     count_pairs(n_eval, n_contrib, &L.ws.hdr->fwd_evals, &L.ws.hdr->fwd_contrib);
 
     // ---------------------------------------------------------------- fused loss
-    const uint32_t HW = (uint32_t)vi.width * (uint32_t)vi.height;
-    const uint32_t p = (uint32_t)py * (uint32_t)vi.width + (uint32_t)px;
-    const uint32_t gp = vi.pix_base + p;
+    if (!targets_loaded && inside) {  // an empty tile list: no batch was staged
+        const float *trgb = L.t_rgb + 3u * vi.pix_base;
+        tr = trgb[p];
+        tg = trgb[HW + p];
+        tb = trgb[2u * HW + p];
+        Dt = L.t_depth[gp];
+        if (L.t_prior) pr = L.t_prior[gp];
+    }
     float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, gS = 0.f, l = 0.f;
     if (inside) {
         L.ws.t_final[gp] = T;
         L.ws.n_last[gp] = last;
-        const float *trgb = L.t_rgb + 3u * vi.pix_base;
-        const float Dt = L.t_depth[gp];
         const bool valid = Dt > 0.f;
         const bool M = valid && Sil > S.sil_thresh;
         if (M) {
-            const float r0 = cr - trgb[p], r1 = cg - trgb[HW + p], r2 = cb - trgb[2u * HW + p];
+            const float r0 = cr - tr, r1 = cg - tg, r2 = cb - tb;
             l += S.w_rgb * (fabsf(r0) + fabsf(r1) + fabsf(r2));
             g0 = S.w_rgb * sgnf(r0);
             g1 = S.w_rgb * sgnf(r1);
@@ -141,7 +164,6 @@ __global__ void __launch_bounds__(kTilePix, 4) k_track_tile(TrackTileLaunch L) {
             l += S.w_depth * fabsf(rd);
             gD = S.w_depth * sgnf(rd);
             if (L.t_prior) {
-                const float pr = L.t_prior[gp];
                 if (pr > 0.f) {
                     const float rp = D - pr;
                     l += S.w_prior * fabsf(rp);
