@@ -68,6 +68,24 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     if (!(L.d.flags & GS_SCHED_RADIX)) sort_tile(L.ws, start, (int)n, sKeys);
     FwdPixel walk{1.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, !inside};
     uint32_t n_eval = 0, n_contrib = 0;
+    // with the loss: this pixel's targets, loaded once the first batch is staged so their
+    // latency passes during the forward walk
+    const uint32_t HW = (uint32_t)vi.width * (uint32_t)vi.height;
+    const uint32_t p = inside ? (uint32_t)py * (uint32_t)vi.width + (uint32_t)px : 0u;
+    const uint32_t gp = vi.pix_base + p;  // pixel in the concatenated planes
+    float tr = 0.f, tg = 0.f, tb = 0.f, Dt = 0.f, pr = 0.f;
+    bool targets_loaded = !LOSS;
+    const auto load_targets = [&]() {
+        targets_loaded = true;
+        if (inside) {
+            const float *trgb = L.t_rgb + 3u * vi.pix_base;
+            tr = trgb[p];
+            tg = trgb[HW + p];
+            tb = trgb[2u * HW + p];
+            Dt = L.t_depth[gp];
+            if (L.t_prior) pr = L.t_prior[gp];
+        }
+    };
     for (uint32_t b0 = 0; b0 < n; b0 += NB) {
         if (__syncthreads_count(!walk.done) == 0) break;
         const uint32_t idx = b0 + tid;
@@ -85,6 +103,7 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
             }
         }
         __syncthreads();
+        if (!targets_loaded) load_targets();
         const int cnt = (int)min((uint32_t)NB, n - b0);
         if (__any_sync(0xffffffffu, !walk.done)) {
             // this warp's list: the batch Gaussians whose footprint reaches its 8 x 4 patch
@@ -101,9 +120,6 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
     const float Sil = 1.f - T;
     count_pairs(n_eval, n_contrib, &L.ws.hdr->fwd_evals, &L.ws.hdr->fwd_contrib);
 
-    const uint32_t HW = (uint32_t)vi.width * (uint32_t)vi.height;
-    const uint32_t p = (uint32_t)py * (uint32_t)vi.width + (uint32_t)px;
-    const uint32_t gp = vi.pix_base + p;  // pixel in the concatenated planes
     if (inside) {
         if (L.rgb) {
             float *o = L.rgb + 3u * vi.pix_base;
@@ -117,15 +133,14 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
         L.ws.n_last[gp] = last;
     }
     if constexpr (LOSS) {
+        if (!targets_loaded) load_targets();  // an empty tile list: no batch was staged
         float l = 0.f;
         if (inside) {
-            const float *trgb = L.t_rgb + 3u * vi.pix_base;
-            const float Dt = L.t_depth[gp];
             const bool valid = Dt > 0.f;
             const bool M = valid && Sil > S.sil_thresh;
             float g0 = 0.f, g1 = 0.f, g2 = 0.f, gD = 0.f, gS = 0.f;
             if (M) {
-                const float r0 = cr - trgb[p], r1 = cg - trgb[HW + p], r2 = cb - trgb[2u * HW + p];
+                const float r0 = cr - tr, r1 = cg - tg, r2 = cb - tb;
                 l += S.w_rgb * (fabsf(r0) + fabsf(r1) + fabsf(r2));
                 g0 = S.w_rgb * sgnf(r0);
                 g1 = S.w_rgb * sgnf(r1);
@@ -134,7 +149,6 @@ __global__ void __launch_bounds__(kTilePix, 5) k_forward(ForwardLaunch L) {
                 l += S.w_depth * fabsf(rd);
                 gD = S.w_depth * sgnf(rd);
                 if (L.t_prior) {
-                    const float pr = L.t_prior[gp];
                     if (pr > 0.f) {
                         const float rp = D - pr;
                         l += S.w_prior * fabsf(rp);
